@@ -1,0 +1,228 @@
+/*
+ * stitch.h -- C ABI of the B300 video-stitching hot path.
+ *
+ * Implements the per-frame data-parallel path of "GPU Accelerated Color
+ * Correction and Frame Warping for Real-time Video Stitching" (arXiv
+ * 2308.09209): inverse-homography pre-warp (section 3.1), optical-flow local
+ * warping with bilinear sampling (section 3.2, Eq. 17-18), the spatio-temporal
+ * 3D-M colour transfer (section 2.1, Eq. 1-4), the piecewise online colour
+ * balance (section 2.2, Eq. 5-7) and weighted-mean fusion (Eq. 15-16), plus the
+ * integer overlap statistics that estimate M.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status (stitch_status). Argument errors are
+ *    detected on the host before anything is launched. No C++ exception
+ *    crosses this boundary.
+ *  - Device pointers ("_dev") are CUDA device addresses owned by the caller;
+ *    the library never frees them. Host pointers ("_host") are plain host
+ *    memory (page-locked memory makes the copies asynchronous and faster).
+ *  - Launches are asynchronous on the given stream (NULL = legacy default
+ *    stream). Device-side conditions (a singular colour fit) are recorded in
+ *    the context and reported by stitch_sync / stitch_get_color.
+ *  - Camera frames are packed RGB uint8, row-major (HWC), row pitch in bytes
+ *    >= 3 * width. The panorama is planar uint8: three planes (R, G, B), each
+ *    pano_h rows of pano_pitch bytes, plane c starting at c * pano_pitch *
+ *    pano_h. Bytes [pano_w, pano_pitch) of a row are not part of the image and
+ *    may be overwritten with 0.
+ *  - Pixel centres sit at integer coordinates. A camera homography maps a
+ *    camera pixel (u, v, 1) to panorama coordinates.
+ *  - Adjacent cameras k, k+1 form pair k. Each pair has a blend band: an
+ *    integer rectangle [x0, x1) x [y0, y1) of panorama pixels covered by both
+ *    cameras. Flow fields are per pair, float2 (dx, dy) per band pixel,
+ *    row-major band_w x band_h, indexed by (x - x0, y - y0).
+ */
+#ifndef STITCH_H
+#define STITCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *stitch_stream_t;
+
+typedef enum {
+  STITCH_OK = 0,
+  STITCH_EINVAL = -1,     /* bad argument or geometry; nothing was launched */
+  STITCH_ENOMEM = -2,     /* a device or host allocation failed */
+  STITCH_ECUDA = -3,      /* a CUDA runtime call failed (message in stitch_last_error) */
+  STITCH_ESINGULAR = -4,  /* a pair's colour fit was ill-conditioned: its previous M was kept */
+  STITCH_ETIMEOUT = -5,   /* a bounded device-side wait expired */
+  STITCH_EFALLBACK = 1    /* informational: the learned estimator fell back to the plain fit */
+} stitch_status;
+
+/* stitch_config.flags */
+#define STITCH_BALANCE_OFF 1          /* skip the online balance (Eq. 5) */
+#define STITCH_FP16_INTERMEDIATE 2    /* warped band tiles held in FP16; coordinates stay FP32 */
+#define STITCH_FLOW_WEIGHTS_PRINTED 4 /* Eq. 17 exactly as printed (theta_i on flow_ij) */
+#define STITCH_LEARNED 8              /* learned estimator for M (falls back to the plain fit) */
+
+#define STITCH_MAX_CAMS 8
+#define STITCH_MAX_PAIRS (STITCH_MAX_CAMS - 1)
+#define STITCH_MAX_WINDOW 16
+#define STITCH_MAX_FLOW 16.0f
+#define STITCH_CURVE_FLOATS 10        /* per channel, see stitch_get_color */
+
+typedef struct {
+  int n_cams;               /* 2 .. STITCH_MAX_CAMS */
+  const int *cam_w;         /* n_cams widths (>= 2) */
+  const int *cam_h;         /* n_cams heights (>= 2) */
+  const int *cam_pitch;     /* n_cams row pitches in bytes (>= 3 * w); NULL = 3 * w */
+  const double *H;          /* n_cams x 9, camera -> panorama homographies, row-major.
+                               The library inverts them in float64 (section 3.1). */
+  int pano_w, pano_h;       /* panorama size in pixels */
+  int pano_pitch;           /* bytes per panorama row, >= pano_w, multiple of 16 */
+  int projection;           /* 0 = planar homographies (the only projection accepted) */
+  int ref_cam;              /* colour reference camera; -1 = n_cams / 2 */
+  int window;               /* 3D-M temporal window W in frames (Eq. 2-3; 3 in the paper), 1..16 */
+  double lambda;            /* balance quantile (section 2.2; 0.05 in the paper), 0 < lambda < 0.5 */
+  float max_flow;           /* flow components are clamped to +-max_flow pixels, 0..16 */
+  int flags;                /* STITCH_* flags above */
+} stitch_config;
+
+typedef struct stitch_ctx stitch_ctx;
+
+/*
+ * stitch_geometry -- the overlap geometry of a configuration, on the host only
+ * (section 2.1 step 1: the overlap region follows from the homographies;
+ * section 3.1). Needs no GPU and allocates no device memory.
+ *   bands: out, (n_cams - 1) x 4 ints: x0, x1, y0, y1 of each pair's blend band.
+ *   rects: out, (n_cams - 1) x 8 ints: the band's source rectangle in the left
+ *          camera (x0, x1, y0, y1) then in the right camera, both half-open.
+ *   Either output may be NULL. Returns STITCH_EINVAL (message in
+ *   stitch_last_error(NULL)) for an invalid configuration.
+ */
+int stitch_geometry(const stitch_config *cfg, int *bands, int *rects);
+
+/*
+ * stitch_init -- validate cfg, compute the geometry in float64, allocate the
+ * context's device state (statistics ring, colour state, tile lists) on the
+ * current CUDA device. *out receives the new context; free it with
+ * stitch_destroy. cfg and the arrays it points to may be freed afterwards.
+ */
+int stitch_init(const stitch_config *cfg, stitch_ctx **out);
+
+/*
+ * stitch_estimate_color -- colour statistics and estimate of the next frame T
+ * (section 2.1 steps 2-4, Eq. 1-3; section 2.2 Eq. 6-7).
+ *   frames_dev: n_cams device pointers to this frame's camera images.
+ * Launches the statistics reduction (pooled full-frame histograms; per pair
+ * the overlap histograms, value-weighted histograms and Gram sums) and the
+ * single-block estimate (histogram specification, windowed M = A^-1 B in
+ * float64, chaining to the reference camera, balance knots and curve).
+ * Advances the frame index T by one.
+ */
+int stitch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames_dev, stitch_stream_t stream);
+
+/*
+ * stitch_frame -- fused pre-warp, local warping, colour transfer, balance and
+ * blend of one frame into the panorama (section 3.1, Eq. 4-5, Eq. 15-18),
+ * using the colour state of the latest stitch_estimate_color.
+ *   frames_dev:  n_cams device pointers (the same images given to the estimate).
+ *   flow_ij_dev: n_pairs device pointers, flow sampled for the LEFT camera of
+ *                each pair (float2 per band pixel, 8-byte aligned).
+ *   flow_ji_dev: n_pairs device pointers, flow for the RIGHT camera.
+ *   pano_dev:    device pointer (16-byte aligned) to 3 * pano_pitch * pano_h
+ *                bytes, written.
+ */
+int stitch_frame(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
+                 const float *const *flow_ji_dev, uint8_t *pano_dev, stitch_stream_t stream);
+
+/*
+ * stitch_sequence -- n_frames consecutive frames (estimate + frame for each)
+ * in one call. Arrays are frame-major: frames_dev[t * n_cams + k],
+ * flow_*_dev[t * n_pairs + p], pano_dev[t]. The first call with a given set
+ * of pointers records a CUDA graph of the whole sequence; later calls with
+ * the same pointers replay it.
+ */
+int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_dev,
+                    const float *const *flow_ij_dev, const float *const *flow_ji_dev,
+                    uint8_t *const *pano_dev, stitch_stream_t stream);
+
+/*
+ * stitch_sequence_host -- as stitch_sequence, but every array is HOST memory:
+ * the library copies each frame's images and flows to its own device staging
+ * buffers, runs the frame and copies the panorama back, all on `stream`, and
+ * returns after the stream has drained. Host frames are read with the
+ * configured row pitch; host flows are dense band_w x band_h float2.
+ */
+int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_host,
+                         const float *const *flow_ij_host, const float *const *flow_ji_host,
+                         uint8_t *const *pano_host, stitch_stream_t stream);
+
+/*
+ * stitch_sync -- wait for `stream`, then report (and clear) the device-side
+ * condition word: STITCH_ESINGULAR if a colour fit kept its previous M since
+ * the last report, else STITCH_OK.
+ */
+int stitch_sync(stitch_ctx *ctx, stitch_stream_t stream);
+
+/*
+ * stitch_get_color -- current colour state (synchronises the device).
+ *   M_out:     n_cams x 9 doubles, each camera's matrix chained to the
+ *              reference (row-vector convention v' = v . M, Eq. 4). May be NULL.
+ *   curve_out: 3 x STITCH_CURVE_FLOATS floats per channel: m1, m2 (smoothed
+ *              knots, Eq. 6-7), d1, d2, s, g1, g2, 1/m1, 1/(255 - m2),
+ *              identity flag (1.0f when m2 - m1 < 1). May be NULL.
+ *   frame_idx: number of frames estimated so far. May be NULL.
+ * Returns STITCH_ESINGULAR when the latest estimate kept a previous M.
+ */
+int stitch_get_color(stitch_ctx *ctx, double *M_out, float *curve_out, int *frame_idx);
+
+/*
+ * stitch_get_pair_M -- the latest per-pair transfer matrices M = A^-1 B
+ * (n_pairs x 9 doubles, row-major, Eq. 1/Eq. 3), pair p mapping its
+ * colour-source camera onto its neighbour toward the reference. Synchronises.
+ */
+int stitch_get_pair_M(stitch_ctx *ctx, double *M_out);
+
+/*
+ * stitch_get_frame_stats -- the integer statistics of the latest estimated
+ * frame (synchronises the device). Any output may be NULL.
+ *   pooled: 3 x 256 uint32, per-channel histogram of all camera frames.
+ *   Hi, Hj: n_pairs x 3 x 256 uint32, overlap histograms of the colour-source
+ *           camera i and of its reference neighbour j (section 2.1 step 2).
+ *   Wv:     n_pairs x 6 x 256 uint32, value-weighted histograms of side i,
+ *           W_cd[v] = sum of channel c over pixels whose channel d equals v,
+ *           for (c, d) = (0,1), (0,2), (1,0), (1,2), (2,0), (2,1).
+ *   A:      n_pairs x 9 uint64, this frame's I_i^T I_i (Eq. 3 term).
+ *   B:      n_pairs x 9 uint64, this frame's I_i^T I_j with I_j the
+ *           specified ("revised") image i (Eq. 3 term).
+ */
+int stitch_get_frame_stats(stitch_ctx *ctx, uint32_t *pooled, uint32_t *Hi, uint32_t *Hj, uint32_t *Wv,
+                           uint64_t *A, uint64_t *B);
+
+/* stitch_get_bands -- the context's geometry, same layout as stitch_geometry. */
+int stitch_get_bands(stitch_ctx *ctx, int *bands, int *rects);
+
+/*
+ * stitch_save_state / stitch_load_state -- serialise the temporal state (frame
+ * index, windowed statistics ring, knot ring, per-pair M, colour state) so a
+ * stream can resume mid-sequence with identical output. save: if buf is NULL,
+ * *size receives the byte count; else *size must be at least that and the
+ * state is written (synchronises the device). load: buf/size from a context
+ * with the same configuration.
+ */
+int stitch_save_state(stitch_ctx *ctx, void *buf, size_t *size);
+int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size);
+
+/* Number of adjacent pairs (n_cams - 1), or -1 for a NULL context. */
+int stitch_n_pairs(const stitch_ctx *ctx);
+
+/*
+ * stitch_last_error -- message of the last failing call on ctx, or of the
+ * last failing stitch_geometry / stitch_init when ctx is NULL. The string is
+ * owned by the library and valid until the next call on the same context.
+ */
+const char *stitch_last_error(const stitch_ctx *ctx);
+
+/* stitch_destroy -- free the context and its device state (synchronises). */
+void stitch_destroy(stitch_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STITCH_H */

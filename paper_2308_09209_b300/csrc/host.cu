@@ -1,0 +1,825 @@
+// Host side of the stitching library: configuration checks, float64 overlap
+// geometry (paper section 2.1 step 1, section 3.1), device state, launches and
+// the C ABI declared in include/stitch.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "stitch_internal.h"
+
+using namespace stitch;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr double kSnap = 1e-9;
+constexpr uint32_t kStateMagic = 0x53544331u;  // "STC1"
+
+// Bounds round inward; values within 1e-9 of an integer snap to it first so
+// float64 noise cannot move an integer bound.
+int ceil_snap(double v) {
+  const double r = std::nearbyint(v);
+  if (std::fabs(v - r) < kSnap) return (int)r;
+  return (int)std::ceil(v);
+}
+
+int floor_snap(double v) {
+  const double r = std::nearbyint(v);
+  if (std::fabs(v - r) < kSnap) return (int)r;
+  return (int)std::floor(v);
+}
+
+// 3x3 inverse by the adjugate; false if the determinant is not usable.
+bool inv3(const double *m, double *o) {
+  const double c00 = m[4] * m[8] - m[5] * m[7];
+  const double c01 = m[5] * m[6] - m[3] * m[8];
+  const double c02 = m[3] * m[7] - m[4] * m[6];
+  const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+  if (!std::isfinite(det) || std::fabs(det) < 1e-300) return false;
+  const double id = 1.0 / det;
+  o[0] = c00 * id;
+  o[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+  o[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+  o[3] = c01 * id;
+  o[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+  o[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+  o[6] = c02 * id;
+  o[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+  o[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+  return true;
+}
+
+void proj(const double *H, double x, double y, double &X, double &Y, double &W) {
+  const double a = H[0] * x + H[1] * y + H[2];
+  const double b = H[3] * x + H[4] * y + H[5];
+  W = H[6] * x + H[7] * y + H[8];
+  X = a / W;
+  Y = b / W;
+}
+
+struct Geo {
+  int n = 0;
+  int w[kMaxCams], h[kMaxCams], pitch[kMaxCams];
+  double H[kMaxCams][9], Hi[kMaxCams][9];
+  int pano_w = 0, pano_h = 0, pano_pitch = 0;
+  int ref = 0;
+  int band[kMaxPairs][4];            // x0, x1, y0, y1
+  int rect[kMaxPairs][2][4];         // [pair][left/right camera] x0, x1, y0, y1
+  int pair_i[kMaxPairs], pair_j[kMaxPairs];
+  int own_lo[kMaxCams], own_hi[kMaxCams];
+};
+
+bool covered64(const Geo &g, int k, double x, double y) {
+  double sx, sy, sw;
+  proj(g.Hi[k], x, y, sx, sy, sw);
+  return sw > 0 && sx >= 0 && sx <= g.w[k] - 1 && sy >= 0 && sy <= g.h[k] - 1;
+}
+
+// Camera corner pixel centres in the panorama: TL, TR, BR, BL.
+void corners(const Geo &g, int k, double cx[4], double cy[4]) {
+  const double u[4] = {0.0, g.w[k] - 1.0, g.w[k] - 1.0, 0.0};
+  const double v[4] = {0.0, 0.0, g.h[k] - 1.0, g.h[k] - 1.0};
+  for (int i = 0; i < 4; ++i) {
+    double W;
+    proj(g.H[k], u[i], v[i], cx[i], cy[i], W);
+  }
+}
+
+double line_y(double px, double py, double qx, double qy, double x) {
+  return py + (qy - py) * (x - px) / (qx - px);
+}
+
+#define FAIL(msg)               \
+  do {                          \
+    err = (msg);                \
+    return STITCH_EINVAL;       \
+  } while (0)
+
+// The blend band of cameras (a, b = a + 1): columns from the right-most point
+// of b's left edge to the left-most point of a's right edge; rows between the
+// lowest top edge and the highest bottom edge of both cameras over those
+// columns; all bounds rounded inward. The source rectangle of a band in a
+// camera is the inward-rounded box spanned by its corners mapped through
+// H^-1. Colour pairs point toward the reference camera.
+int build_geometry(const stitch_config *cfg, Geo &g, std::string &err) {
+  if (!cfg) FAIL("config is NULL");
+  if (cfg->n_cams < 2 || cfg->n_cams > kMaxCams) FAIL("n_cams must be in [2, 8]");
+  if (!cfg->cam_w || !cfg->cam_h || !cfg->H) FAIL("cam_w, cam_h and H are required");
+  if (cfg->projection != 0) FAIL("only the planar projection (0) is supported");
+  if (cfg->pano_w < 1 || cfg->pano_h < 1) FAIL("panorama size must be positive");
+  if (cfg->pano_w > 32767 * kTileW || cfg->pano_h > 32767 * kTileH) FAIL("panorama too large");
+  if (cfg->pano_pitch < cfg->pano_w || cfg->pano_pitch % 16 != 0)
+    FAIL("pano_pitch must be >= pano_w and a multiple of 16");
+  if (cfg->window < 1 || cfg->window > kMaxWindow) FAIL("window must be in [1, 16]");
+  if (!(cfg->lambda > 0.0 && cfg->lambda < 0.5)) FAIL("lambda must be in (0, 0.5)");
+  if (!(cfg->max_flow >= 0.0f && cfg->max_flow <= STITCH_MAX_FLOW)) FAIL("max_flow must be in [0, 16]");
+  if (cfg->ref_cam < -1 || cfg->ref_cam >= cfg->n_cams) FAIL("ref_cam out of range");
+  if (cfg->flags & ~(STITCH_BALANCE_OFF | STITCH_FP16_INTERMEDIATE | STITCH_FLOW_WEIGHTS_PRINTED | STITCH_LEARNED))
+    FAIL("unknown flag");
+  g.n = cfg->n_cams;
+  g.pano_w = cfg->pano_w;
+  g.pano_h = cfg->pano_h;
+  g.pano_pitch = cfg->pano_pitch;
+  g.ref = cfg->ref_cam < 0 ? cfg->n_cams / 2 : cfg->ref_cam;
+  long long total_px = 0;
+  for (int k = 0; k < g.n; ++k) {
+    g.w[k] = cfg->cam_w[k];
+    g.h[k] = cfg->cam_h[k];
+    if (g.w[k] < 2 || g.h[k] < 2 || g.w[k] > 65535 || g.h[k] > 65535) FAIL("camera size out of range");
+    g.pitch[k] = cfg->cam_pitch ? cfg->cam_pitch[k] : 3 * g.w[k];
+    if (g.pitch[k] < 3 * g.w[k]) FAIL("camera pitch < 3 * width");
+    total_px += (long long)g.w[k] * g.h[k];
+    for (int e = 0; e < 9; ++e) {
+      g.H[k][e] = cfg->H[k * 9 + e];
+      if (!std::isfinite(g.H[k][e])) FAIL("homography has a non-finite entry");
+    }
+    if (!inv3(g.H[k], g.Hi[k])) FAIL("homography is singular");
+  }
+  if (total_px >= (1ll << 32)) FAIL("too many camera pixels for 32-bit histograms");
+  for (int p = 0; p + 1 < g.n; ++p) {
+    const int a = p, b = p + 1;
+    double ax[4], ay[4], bx[4], by[4];
+    corners(g, a, ax, ay);
+    corners(g, b, bx, by);
+    int x0 = ceil_snap(std::fmax(bx[0], bx[3]));
+    int x1 = floor_snap(std::fmin(ax[1], ax[2])) + 1;
+    const double xl = x0, xr = x1 - 1;
+    const double tops[4] = {line_y(ax[0], ay[0], ax[1], ay[1], xl), line_y(ax[0], ay[0], ax[1], ay[1], xr),
+                            line_y(bx[0], by[0], bx[1], by[1], xl), line_y(bx[0], by[0], bx[1], by[1], xr)};
+    const double bots[4] = {line_y(ax[3], ay[3], ax[2], ay[2], xl), line_y(ax[3], ay[3], ax[2], ay[2], xr),
+                            line_y(bx[3], by[3], bx[2], by[2], xl), line_y(bx[3], by[3], bx[2], by[2], xr)};
+    double tmax = tops[0], bmin = bots[0];
+    for (int i = 1; i < 4; ++i) {
+      tmax = std::fmax(tmax, tops[i]);
+      bmin = std::fmin(bmin, bots[i]);
+    }
+    int y0 = ceil_snap(tmax);
+    int y1 = floor_snap(bmin) + 1;
+    x0 = std::max(x0, 0);
+    y0 = std::max(y0, 0);
+    x1 = std::min(x1, g.pano_w);
+    y1 = std::min(y1, g.pano_h);
+    if (x1 - x0 < 2 || y1 - y0 < 2) FAIL("an adjacent camera pair has no overlap band");
+    g.band[p][0] = x0;
+    g.band[p][1] = x1;
+    g.band[p][2] = y0;
+    g.band[p][3] = y1;
+    // The band must lie inside both cameras' coverage. Coverage is convex, so
+    // testing the band's border pixels suffices.
+    for (int cam = a; cam <= b; ++cam) {
+      bool ok = true;
+      for (int x = x0; x < x1 && ok; ++x) ok = covered64(g, cam, x, y0) && covered64(g, cam, x, y1 - 1);
+      for (int y = y0; y < y1 && ok; ++y) ok = covered64(g, cam, x0, y) && covered64(g, cam, x1 - 1, y);
+      if (!ok) FAIL("overlap band is not covered by both cameras (homographies too far from a left-to-right rig)");
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int cam = side == 0 ? a : b;
+      const double px[4] = {(double)x0, (double)(x1 - 1), (double)(x1 - 1), (double)x0};
+      const double py[4] = {(double)y0, (double)y0, (double)(y1 - 1), (double)(y1 - 1)};
+      double sx[4], sy[4];
+      for (int i = 0; i < 4; ++i) {
+        double W;
+        proj(g.Hi[cam], px[i], py[i], sx[i], sy[i], W);
+      }
+      int rx0 = ceil_snap(std::fmax(sx[0], sx[3]));
+      int rx1 = floor_snap(std::fmin(sx[1], sx[2])) + 1;
+      int ry0 = ceil_snap(std::fmax(sy[0], sy[1]));
+      int ry1 = floor_snap(std::fmin(sy[2], sy[3])) + 1;
+      rx0 = std::max(rx0, 0);
+      ry0 = std::max(ry0, 0);
+      rx1 = std::min(rx1, g.w[cam]);
+      ry1 = std::min(ry1, g.h[cam]);
+      if (rx1 <= rx0 || ry1 <= ry0) rx0 = rx1 = ry0 = ry1 = 0;
+      if ((long long)(rx1 - rx0) * (ry1 - ry0) * 255ll >= (1ll << 32)) FAIL("overlap too large for 32-bit sums");
+      g.rect[p][side][0] = rx0;
+      g.rect[p][side][1] = rx1;
+      g.rect[p][side][2] = ry0;
+      g.rect[p][side][3] = ry1;
+    }
+    if (p + 1 <= g.ref) {
+      g.pair_i[p] = p;
+      g.pair_j[p] = p + 1;
+    } else {
+      g.pair_i[p] = p + 1;
+      g.pair_j[p] = p;
+    }
+  }
+  for (int p = 0; p + 2 < g.n; ++p)
+    if (g.band[p][1] > g.band[p + 1][0]) FAIL("overlap bands of successive pairs intersect");
+  for (int k = 0; k < g.n; ++k) {
+    g.own_lo[k] = k == 0 ? 0 : g.band[k - 1][1];
+    g.own_hi[k] = k == g.n - 1 ? g.pano_w : g.band[k][0];
+  }
+  return STITCH_OK;
+}
+
+#undef FAIL
+
+void export_geometry(const Geo &g, int *bands, int *rects) {
+  for (int p = 0; p + 1 < g.n; ++p) {
+    if (bands)
+      for (int e = 0; e < 4; ++e) bands[p * 4 + e] = g.band[p][e];
+    if (rects)
+      for (int s = 0; s < 2; ++s)
+        for (int e = 0; e < 4; ++e) rects[p * 8 + s * 4 + e] = g.rect[p][s][e];
+  }
+}
+
+}  // namespace
+
+struct GraphEntry {
+  std::vector<const void *> key;
+  int n_frames = 0;
+  int parity = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct stitch_ctx {
+  Geo g;
+  int flags = 0;
+  int window = 3;
+  long long lambda_q = 50000;
+  float max_flow = 0.0f;
+  int halo = 1;
+  int device = 0;
+  int host_T = 0;                     // frames estimated (host mirror of the device index)
+  std::string err;
+  RawStats *raw = nullptr;            // 2 slots
+  ColorState *state = nullptr;
+  TileDesc *tiles = nullptr;
+  int n_band_tiles = 0, n_own_tiles = 0;
+  int stats_grid_x = 1;
+  StatsParams sp{};
+  EstimateParams ep{};
+  FuseParams fp{};
+  cudaStream_t cap_stream = nullptr;
+  std::vector<GraphEntry> graphs;
+  uint8_t *stage_frames[kMaxCams] = {};
+  float *stage_fij[kMaxPairs] = {};
+  float *stage_fji[kMaxPairs] = {};
+  uint8_t *stage_pano = nullptr;
+};
+
+namespace {
+
+int set_err(stitch_ctx *ctx, int code, const std::string &msg) {
+  if (ctx)
+    ctx->err = msg;
+  else
+    g_last_error = msg;
+  return code;
+}
+
+int cuda_err(stitch_ctx *ctx, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_err(ctx, e == cudaErrorMemoryAllocation ? STITCH_ENOMEM : STITCH_ECUDA, m);
+}
+
+size_t band_elems(const Geo &g, int p) {
+  return (size_t)(g.band[p][1] - g.band[p][0]) * (size_t)(g.band[p][3] - g.band[p][2]);
+}
+
+int launch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames, cudaStream_t s) {
+  StatsParams sp = ctx->sp;
+  for (int k = 0; k < ctx->g.n; ++k) {
+    sp.src[k] = frames[k];
+    sp.vec_ok[k] = ((reinterpret_cast<uintptr_t>(frames[k]) & 15u) == 0 && ctx->g.pitch[k] % 16 == 0) ? 1 : 0;
+  }
+  cudaError_t e = launch_stats(sp, ctx->stats_grid_x, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "stats launch");
+  e = launch_estimate(ctx->ep, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  ctx->host_T += 1;
+  return STITCH_OK;
+}
+
+int launch_frame(stitch_ctx *ctx, const uint8_t *const *frames, const float *const *fij, const float *const *fji,
+                 uint8_t *pano, cudaStream_t s) {
+  FuseParams fp = ctx->fp;
+  for (int k = 0; k < ctx->g.n; ++k) fp.src[k] = frames[k];
+  for (int p = 0; p + 1 < ctx->g.n; ++p) {
+    fp.flow_ij[p] = reinterpret_cast<const float2 *>(fij[p]);
+    fp.flow_ji[p] = reinterpret_cast<const float2 *>(fji[p]);
+  }
+  fp.out = pano;
+  fp.color = &ctx->state->out[(ctx->host_T + 1) & 1];   // slot written for frame host_T - 1
+  cudaError_t e = launch_fuse(fp, ctx->n_own_tiles, ctx->n_band_tiles, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "fuse launch");
+  return STITCH_OK;
+}
+
+bool check_ptrs(const void *const *p, int n) {
+  if (!p) return false;
+  for (int i = 0; i < n; ++i)
+    if (!p[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stitch_geometry(const stitch_config *cfg, int *bands, int *rects) {
+  Geo g;
+  std::string err;
+  const int rc = build_geometry(cfg, g, err);
+  if (rc != STITCH_OK) return set_err(nullptr, rc, err);
+  export_geometry(g, bands, rects);
+  return STITCH_OK;
+}
+
+int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
+  if (!out) return set_err(nullptr, STITCH_EINVAL, "out is NULL");
+  *out = nullptr;
+  stitch_ctx *ctx = new (std::nothrow) stitch_ctx();
+  if (!ctx) return set_err(nullptr, STITCH_ENOMEM, "host allocation failed");
+  std::string err;
+  int rc = build_geometry(cfg, ctx->g, err);
+  if (rc != STITCH_OK) {
+    delete ctx;
+    return set_err(nullptr, rc, err);
+  }
+  const Geo &g = ctx->g;
+  ctx->flags = cfg->flags;
+  ctx->window = cfg->window;
+  ctx->lambda_q = (long long)std::llround(cfg->lambda * 1e6);
+  if (ctx->lambda_q <= 0 || ctx->lambda_q >= 500000) {
+    delete ctx;
+    return set_err(nullptr, STITCH_EINVAL, "lambda rounds to 0 or 0.5 in millionths");
+  }
+  ctx->max_flow = cfg->max_flow;
+  ctx->halo = (int)std::ceil((double)cfg->max_flow) + 1;
+
+  // Tiles: a tile touching a band's columns is a band tile; others belong to
+  // the one camera whose own columns hold them.
+  std::vector<TileDesc> band_tiles, own_tiles;
+  const int ntx = (g.pano_w + kTileW - 1) / kTileW, nty = (g.pano_h + kTileH - 1) / kTileH;
+  for (int ty = 0; ty < nty; ++ty) {
+    for (int tx = 0; tx < ntx; ++tx) {
+      const int c0 = tx * kTileW, c1 = c0 + kTileW;
+      int hit = -1, nhit = 0;
+      for (int p = 0; p + 1 < g.n; ++p)
+        if (c0 < g.band[p][1] && c1 > g.band[p][0]) {
+          hit = p;
+          ++nhit;
+        }
+      if (nhit > 1) {
+        delete ctx;
+        return set_err(nullptr, STITCH_EINVAL, "a camera's own columns are narrower than a 64-pixel tile");
+      }
+      TileDesc t{};
+      t.tx = (int16_t)tx;
+      t.ty = (int16_t)ty;
+      if (hit >= 0) {
+        t.kind = 1;
+        t.idx = (int8_t)hit;
+        band_tiles.push_back(t);
+      } else {
+        int k = 0;
+        while (k < g.n - 1 && c0 >= g.own_hi[k]) ++k;
+        t.kind = 0;
+        t.idx = (int8_t)k;
+        own_tiles.push_back(t);
+      }
+    }
+  }
+  ctx->n_band_tiles = (int)band_tiles.size();
+  ctx->n_own_tiles = (int)own_tiles.size();
+
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = fuse_setup_attributes((int)std::ceil((double)STITCH_MAX_FLOW) + 1);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->raw, 2 * sizeof(RawStats));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->state, sizeof(ColorState));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, (band_tiles.size() + own_tiles.size()) * sizeof(TileDesc) + 16);
+  if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, 2 * sizeof(RawStats));
+  if (e == cudaSuccess) {
+    std::vector<TileDesc> all(band_tiles);
+    all.insert(all.end(), own_tiles.begin(), own_tiles.end());
+    if (!all.empty())
+      e = cudaMemcpy(ctx->tiles, all.data(), all.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    ColorState *h = new ColorState();
+    std::memset(h, 0, sizeof(ColorState));
+    for (int p = 0; p < kMaxPairs; ++p)
+      for (int k = 0; k < 9; ++k) h->M_pair[p][k] = (k % 4 == 0) ? 1.0 : 0.0;
+    for (int c = 0; c < kMaxCams; ++c)
+      for (int k = 0; k < 9; ++k) {
+        h->M_cam[c][k] = (k % 4 == 0) ? 1.0 : 0.0;
+        h->out[0].M[c][k] = h->out[1].M[c][k] = (k % 4 == 0) ? 1.0f : 0.0f;
+      }
+    for (int s = 0; s < 2; ++s)
+      for (int c = 0; c < 3; ++c) h->out[s].curve[c].ident = 1.0f;
+    e = cudaMemcpy(ctx->state, h, sizeof(ColorState), cudaMemcpyHostToDevice);
+    delete h;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    const int code = cuda_err(nullptr, e, "stitch_init");
+    stitch_destroy(ctx);
+    return code;
+  }
+
+  // Stats launch geometry: about four blocks per SM over all camera rows.
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  long long rows = 0;
+  int max_h = 0;
+  for (int k = 0; k < g.n; ++k) {
+    rows += g.h[k];
+    max_h = std::max(max_h, g.h[k]);
+  }
+  const int rpb = (int)std::max(1ll, (rows + 4ll * sms - 1) / (4ll * sms));
+  StatsParams &sp = ctx->sp;
+  sp = StatsParams{};
+  sp.n_cams = g.n;
+  sp.rows_per_block = rpb;
+  sp.raw = ctx->raw;
+  sp.state = ctx->state;
+  for (int k = 0; k < g.n; ++k) {
+    sp.w[k] = g.w[k];
+    sp.h[k] = g.h[k];
+    sp.pitch[k] = g.pitch[k];
+    sp.n_roles[k] = 0;
+  }
+  for (int p = 0; p + 1 < g.n; ++p) {
+    for (int side = 0; side < 2; ++side) {
+      const int cam = side == 0 ? p : p + 1;
+      RoleDev r{};
+      r.rx0 = g.rect[p][side][0];
+      r.rx1 = g.rect[p][side][1];
+      r.ry0 = g.rect[p][side][2];
+      r.ry1 = g.rect[p][side][3];
+      r.pair = p;
+      r.is_i = (g.pair_i[p] == cam) ? 1 : 0;
+      sp.roles[cam][sp.n_roles[cam]++] = r;
+    }
+  }
+  ctx->stats_grid_x = (max_h + rpb - 1) / rpb;
+
+  EstimateParams &ep = ctx->ep;
+  ep = EstimateParams{};
+  ep.n_cams = g.n;
+  ep.n_pairs = g.n - 1;
+  ep.ref = g.ref;
+  ep.window = ctx->window;
+  ep.lambda_q = ctx->lambda_q;
+  for (int p = 0; p + 1 < g.n; ++p) {
+    ep.pair_i[p] = g.pair_i[p];
+    ep.pair_j[p] = g.pair_j[p];
+  }
+  ep.raw = ctx->raw;
+  ep.state = ctx->state;
+
+  FuseParams &fp = ctx->fp;
+  fp = FuseParams{};
+  fp.n_cams = g.n;
+  fp.flags = ctx->flags;
+  fp.pano_w = g.pano_w;
+  fp.pano_h = g.pano_h;
+  fp.pano_pitch = g.pano_pitch;
+  fp.halo = ctx->halo;
+  fp.max_flow = ctx->max_flow;
+  fp.n_tiles = ctx->n_band_tiles + ctx->n_own_tiles;
+  fp.tiles = ctx->tiles;
+  for (int k = 0; k < g.n; ++k) {
+    CamDev &c = fp.cam[k];
+    double cx, cy, cw;
+    proj(g.H[k], (g.w[k] - 1) * 0.5, (g.h[k] - 1) * 0.5, cx, cy, cw);
+    c.ox = (int)std::lround(cx);
+    c.oy = (int)std::lround(cy);
+    // H^-1 . T(ox, oy): the kernel feeds (x - ox, y - oy, 1).
+    double hs[9];
+    for (int r = 0; r < 3; ++r) {
+      hs[r * 3 + 0] = g.Hi[k][r * 3 + 0];
+      hs[r * 3 + 1] = g.Hi[k][r * 3 + 1];
+      hs[r * 3 + 2] = g.Hi[k][r * 3 + 0] * c.ox + g.Hi[k][r * 3 + 1] * c.oy + g.Hi[k][r * 3 + 2];
+    }
+    const double sc = 1.0 / hs[8];
+    for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(hs[e2] * sc);
+    c.w = g.w[k];
+    c.h_px = g.h[k];
+    c.pitch = g.pitch[k];
+    c.wm1 = (float)(g.w[k] - 1);
+    c.hm1 = (float)(g.h[k] - 1);
+    c.own_lo = g.own_lo[k];
+    c.own_hi = g.own_hi[k];
+  }
+  for (int p = 0; p + 1 < g.n; ++p) {
+    BandDev &b = fp.band[p];
+    b.x0 = g.band[p][0];
+    b.x1 = g.band[p][1];
+    b.y0 = g.band[p][2];
+    b.y1 = g.band[p][3];
+    b.inv_bw = (float)(1.0 / (double)(b.x1 - b.x0));
+  }
+  *out = ctx;
+  return STITCH_OK;
+}
+
+int stitch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames_dev, stitch_stream_t stream) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), ctx->g.n))
+    return set_err(ctx, STITCH_EINVAL, "frames_dev must hold n_cams non-NULL pointers");
+  return launch_estimate_color(ctx, frames_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int stitch_frame(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
+                 const float *const *flow_ji_dev, uint8_t *pano_dev, stitch_stream_t stream) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  const int np = ctx->g.n - 1;
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), ctx->g.n))
+    return set_err(ctx, STITCH_EINVAL, "frames_dev must hold n_cams non-NULL pointers");
+  if (!check_ptrs(reinterpret_cast<const void *const *>(flow_ij_dev), np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_dev), np))
+    return set_err(ctx, STITCH_EINVAL, "flow arrays must hold n_pairs non-NULL pointers");
+  for (int p = 0; p < np; ++p)
+    if ((reinterpret_cast<uintptr_t>(flow_ij_dev[p]) | reinterpret_cast<uintptr_t>(flow_ji_dev[p])) & 7u)
+      return set_err(ctx, STITCH_EINVAL, "flow pointers must be 8-byte aligned (float2)");
+  if (!pano_dev || (reinterpret_cast<uintptr_t>(pano_dev) & 15u))
+    return set_err(ctx, STITCH_EINVAL, "pano_dev must be a non-NULL 16-byte aligned pointer");
+  return launch_frame(ctx, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_dev,
+                    const float *const *flow_ij_dev, const float *const *flow_ji_dev,
+                    uint8_t *const *pano_dev, stitch_stream_t stream) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (n_frames < 1) return set_err(ctx, STITCH_EINVAL, "n_frames must be >= 1");
+  const int n = ctx->g.n, np = n - 1;
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), n_frames * n) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ij_dev), n_frames * np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_dev), n_frames * np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(pano_dev), n_frames))
+    return set_err(ctx, STITCH_EINVAL, "sequence pointer arrays must be complete and non-NULL");
+  for (int t = 0; t < n_frames; ++t)
+    if (reinterpret_cast<uintptr_t>(pano_dev[t]) & 15u)
+      return set_err(ctx, STITCH_EINVAL, "pano_dev pointers must be 16-byte aligned");
+  for (int i = 0; i < n_frames * np; ++i)
+    if ((reinterpret_cast<uintptr_t>(flow_ij_dev[i]) | reinterpret_cast<uintptr_t>(flow_ji_dev[i])) & 7u)
+      return set_err(ctx, STITCH_EINVAL, "flow pointers must be 8-byte aligned (float2)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<const void *> key;
+  key.reserve((size_t)n_frames * (n + 2 * np + 1));
+  for (int i = 0; i < n_frames * n; ++i) key.push_back(frames_dev[i]);
+  for (int i = 0; i < n_frames * np; ++i) key.push_back(flow_ij_dev[i]);
+  for (int i = 0; i < n_frames * np; ++i) key.push_back(flow_ji_dev[i]);
+  for (int i = 0; i < n_frames; ++i) key.push_back(pano_dev[i]);
+  const int parity = ctx->host_T & 1;
+  GraphEntry *hit = nullptr;
+  for (auto &ge : ctx->graphs)
+    if (ge.n_frames == n_frames && ge.parity == parity && ge.key == key) hit = &ge;
+  if (!hit) {
+    // Record the sequence on the library's own stream, then replay on `s`.
+    const int T0 = ctx->host_T;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture begin");
+    int rc = STITCH_OK;
+    for (int t = 0; t < n_frames && rc == STITCH_OK; ++t) {
+      rc = launch_estimate_color(ctx, frames_dev + (size_t)t * n, ctx->cap_stream);
+      if (rc == STITCH_OK)
+        rc = launch_frame(ctx, frames_dev + (size_t)t * n, flow_ij_dev + (size_t)t * np,
+                          flow_ji_dev + (size_t)t * np, pano_dev[t], ctx->cap_stream);
+    }
+    e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->host_T = T0;                 // the capture launched nothing
+    if (rc != STITCH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture end");
+    GraphEntry ge;
+    ge.key = key;
+    ge.n_frames = n_frames;
+    ge.parity = parity;
+    e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "graph instantiate");
+    if (ctx->graphs.size() >= 8) {
+      cudaGraphExecDestroy(ctx->graphs.front().exec);
+      ctx->graphs.erase(ctx->graphs.begin());
+    }
+    ctx->graphs.push_back(std::move(ge));
+    hit = &ctx->graphs.back();
+  }
+  cudaError_t e = cudaGraphLaunch(hit->exec, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
+  ctx->host_T += n_frames;
+  return STITCH_OK;
+}
+
+int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_host,
+                         const float *const *flow_ij_host, const float *const *flow_ji_host,
+                         uint8_t *const *pano_host, stitch_stream_t stream) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (n_frames < 1) return set_err(ctx, STITCH_EINVAL, "n_frames must be >= 1");
+  const Geo &g = ctx->g;
+  const int n = g.n, np = n - 1;
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_host), n_frames * n) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ij_host), n_frames * np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_host), n_frames * np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(pano_host), n_frames))
+    return set_err(ctx, STITCH_EINVAL, "sequence pointer arrays must be complete and non-NULL");
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n && e == cudaSuccess; ++k)
+    if (!ctx->stage_frames[k]) e = cudaMalloc(&ctx->stage_frames[k], (size_t)g.pitch[k] * g.h[k]);
+  for (int p = 0; p < np && e == cudaSuccess; ++p) {
+    if (!ctx->stage_fij[p]) e = cudaMalloc(&ctx->stage_fij[p], band_elems(g, p) * 8);
+    if (e == cudaSuccess && !ctx->stage_fji[p]) e = cudaMalloc(&ctx->stage_fji[p], band_elems(g, p) * 8);
+  }
+  const size_t pano_bytes = (size_t)3 * g.pano_pitch * g.pano_h;
+  if (e == cudaSuccess && !ctx->stage_pano) e = cudaMalloc(&ctx->stage_pano, pano_bytes);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "staging allocation");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const uint8_t *fr[kMaxCams];
+  const float *fi[kMaxPairs], *fj[kMaxPairs];
+  for (int k = 0; k < n; ++k) fr[k] = ctx->stage_frames[k];
+  for (int p = 0; p < np; ++p) {
+    fi[p] = ctx->stage_fij[p];
+    fj[p] = ctx->stage_fji[p];
+  }
+  for (int t = 0; t < n_frames; ++t) {
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync(ctx->stage_frames[k], frames_host[(size_t)t * n + k], (size_t)g.pitch[k] * g.h[k],
+                          cudaMemcpyHostToDevice, s);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+      e = cudaMemcpyAsync(ctx->stage_fij[p], flow_ij_host[(size_t)t * np + p], band_elems(g, p) * 8,
+                          cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->stage_fji[p], flow_ji_host[(size_t)t * np + p], band_elems(g, p) * 8,
+                            cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "host-to-device copy");
+    int rc = launch_estimate_color(ctx, fr, s);
+    if (rc == STITCH_OK) rc = launch_frame(ctx, fr, fi, fj, ctx->stage_pano, s);
+    if (rc != STITCH_OK) return rc;
+    e = cudaMemcpyAsync(pano_host[t], ctx->stage_pano, pano_bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "device-to-host copy");
+  }
+  return stitch_sync(ctx, stream);
+}
+
+int stitch_sync(stitch_ctx *ctx, stitch_stream_t stream) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "stream synchronize");
+  int word = 0;
+  e = cudaMemcpy(&word, &ctx->state->cond_word, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "condition read");
+  if (word) {
+    const int zero = 0;
+    e = cudaMemcpy(&ctx->state->cond_word, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "condition clear");
+    if (word & 2) return set_err(ctx, STITCH_ETIMEOUT, "a bounded device wait expired");
+    return set_err(ctx, STITCH_ESINGULAR, "a colour fit was ill-conditioned; the previous M was kept");
+  }
+  return STITCH_OK;
+}
+
+int stitch_get_color(stitch_ctx *ctx, double *M_out, float *curve_out, int *frame_idx) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
+  ColorState *h = new ColorState();
+  e = cudaMemcpy(h, ctx->state, sizeof(ColorState), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_err(ctx, e, "state read");
+  }
+  if (M_out)
+    for (int k = 0; k < ctx->g.n; ++k)
+      for (int i = 0; i < 9; ++i) M_out[k * 9 + i] = h->M_cam[k][i];
+  if (curve_out) {
+    const Curve *cv = h->out[(h->T + 1) & 1].curve;
+    for (int c = 0; c < 3; ++c) std::memcpy(curve_out + c * STITCH_CURVE_FLOATS, &cv[c], sizeof(Curve));
+  }
+  if (frame_idx) *frame_idx = h->T;
+  const int sing = h->singular_last;
+  delete h;
+  return sing ? set_err(ctx, STITCH_ESINGULAR, "a colour fit kept its previous M at the last estimate") : STITCH_OK;
+}
+
+int stitch_get_pair_M(stitch_ctx *ctx, double *M_out) {
+  if (!ctx || !M_out) return set_err(ctx, STITCH_EINVAL, "ctx and M_out are required");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(M_out, ctx->state->M_pair, sizeof(double) * 9 * (ctx->g.n - 1), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "pair M read");
+  return STITCH_OK;
+}
+
+int stitch_get_frame_stats(stitch_ctx *ctx, uint32_t *pooled, uint32_t *Hi, uint32_t *Hj, uint32_t *Wv,
+                           uint64_t *A, uint64_t *B) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
+  int T = 0;
+  e = cudaMemcpy(&T, &ctx->state->T, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "state read");
+  if (T < 1) return set_err(ctx, STITCH_EINVAL, "no frame has been estimated yet");
+  const int np = ctx->g.n - 1;
+  RawStats *h = new RawStats();
+  e = cudaMemcpy(h, ctx->raw + ((T - 1) & 1), sizeof(RawStats), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_err(ctx, e, "stats read");
+  }
+  if (pooled) std::memcpy(pooled, h->pooled, sizeof(h->pooled));
+  if (Hi) std::memcpy(Hi, h->Hi, sizeof(uint32_t) * 768 * np);
+  if (Hj) std::memcpy(Hj, h->Hj, sizeof(uint32_t) * 768 * np);
+  if (Wv) std::memcpy(Wv, h->Wv, sizeof(uint32_t) * 1536 * np);
+  delete h;
+  if (A || B) {
+    const int slot = (T - 1) % kMaxWindow;
+    unsigned long long a[kMaxPairs][6], b[kMaxPairs][9];
+    e = cudaMemcpy(a, ctx->state->A_ring[slot], sizeof(a), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(b, ctx->state->B_ring[slot], sizeof(b), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "ring read");
+    static const int sym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+    for (int p = 0; p < np; ++p)
+      for (int i = 0; i < 9; ++i) {
+        if (A) A[p * 9 + i] = a[p][sym[i]];
+        if (B) B[p * 9 + i] = b[p][i];
+      }
+  }
+  return STITCH_OK;
+}
+
+int stitch_get_bands(stitch_ctx *ctx, int *bands, int *rects) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  export_geometry(ctx->g, bands, rects);
+  return STITCH_OK;
+}
+
+struct StateHeader {
+  uint32_t magic;
+  int32_t n_cams, window, host_T;
+  uint64_t bytes;
+};
+
+int stitch_save_state(stitch_ctx *ctx, void *buf, size_t *size) {
+  if (!ctx || !size) return set_err(ctx, STITCH_EINVAL, "ctx and size are required");
+  const size_t need = sizeof(StateHeader) + sizeof(ColorState);
+  if (!buf) {
+    *size = need;
+    return STITCH_OK;
+  }
+  if (*size < need) return set_err(ctx, STITCH_EINVAL, "buffer too small");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
+  StateHeader hd{kStateMagic, ctx->g.n, ctx->window, ctx->host_T, sizeof(ColorState)};
+  std::memcpy(buf, &hd, sizeof(hd));
+  e = cudaMemcpy(static_cast<char *>(buf) + sizeof(hd), ctx->state, sizeof(ColorState), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "state read");
+  *size = need;
+  return STITCH_OK;
+}
+
+int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
+  if (!ctx || !buf) return set_err(ctx, STITCH_EINVAL, "ctx and buf are required");
+  if (size < sizeof(StateHeader) + sizeof(ColorState)) return set_err(ctx, STITCH_EINVAL, "state buffer too small");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.bytes != sizeof(ColorState) || hd.n_cams != ctx->g.n || hd.window != ctx->window)
+    return set_err(ctx, STITCH_EINVAL, "state was saved from a different configuration");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->state, static_cast<const char *>(buf) + sizeof(hd), sizeof(ColorState),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, 2 * sizeof(RawStats));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "state write");
+  ctx->host_T = hd.host_T;
+  return STITCH_OK;
+}
+
+int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
+
+const char *stitch_last_error(const stitch_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+void stitch_destroy(stitch_ctx *ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  for (auto &ge : ctx->graphs)
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  cudaFree(ctx->raw);
+  cudaFree(ctx->state);
+  cudaFree(ctx->tiles);
+  for (int k = 0; k < kMaxCams; ++k) cudaFree(ctx->stage_frames[k]);
+  for (int p = 0; p < kMaxPairs; ++p) {
+    cudaFree(ctx->stage_fij[p]);
+    cudaFree(ctx->stage_fji[p]);
+  }
+  cudaFree(ctx->stage_pano);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal device-side structures of the stitching library (not part of the
+// public ABI). Layouts here are shared by the host code and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/stitch.h"
+
+namespace stitch {
+
+constexpr int kMaxCams = STITCH_MAX_CAMS;
+constexpr int kMaxPairs = STITCH_MAX_PAIRS;
+constexpr int kMaxWindow = STITCH_MAX_WINDOW;
+constexpr int kSmoothFrames = 3;      // Eq. 6-7: current frame and its last two
+constexpr int kTileW = 64;            // fuse tile: 64 x 16 panorama pixels
+constexpr int kTileH = 16;
+constexpr int kFuseThreads = 256;     // 4 consecutive pixels per thread
+constexpr int kStatsThreads = 256;
+constexpr int kEstimateThreads = 256;
+constexpr double kCondLimit = 1e12;
+
+// Integer statistics of one frame, written by the stats kernel (K1) and read
+// by the estimate kernel (K2). Two slots alternate by frame parity.
+struct RawStats {
+  uint32_t pooled[3][256];            // full-frame histogram of all cameras
+  uint32_t Hi[kMaxPairs][3][256];     // overlap histogram, colour-source side i
+  uint32_t Hj[kMaxPairs][3][256];     // overlap histogram, reference side j
+  uint32_t Wv[kMaxPairs][6][256];     // value-weighted histograms of side i
+  unsigned long long A[kMaxPairs][6]; // Gram sums (00,01,02,11,12,22) of side i
+};
+
+// Per-channel balance curve used by the fuse kernel (Eq. 5 reading).
+struct Curve {
+  float m1, m2, d1, d2, s, g1, g2, inv_m1, inv_bm, ident;
+};
+
+// What the fuse kernel reads: one slot per frame parity.
+struct ColorOut {
+  float M[kMaxCams][9];               // row-vector convention, v' = v . M
+  Curve curve[3];
+};
+
+// Temporal state of the colour estimate, owned by the estimate kernel.
+struct ColorState {
+  int T;                              // frames estimated so far
+  int cond_word;                      // sticky device conditions (bit 0 singular, bit 1 timeout)
+  int singular_last;                  // bitmask of pairs that kept their M at the last estimate
+  int pad;
+  unsigned long long A_ring[kMaxWindow][kMaxPairs][6];
+  unsigned long long B_ring[kMaxWindow][kMaxPairs][9];
+  int n_ring[kMaxWindow][kMaxPairs][2];
+  int knots[kSmoothFrames][3][2];     // ring of per-frame (m1, m2) per channel
+  double M_pair[kMaxPairs][9];
+  double M_cam[kMaxCams][9];
+  double knot_mean[3][2];
+  ColorOut out[2];
+};
+
+// One camera as the fuse kernel sees it. h maps (x - ox, y - oy, 1) of the
+// panorama to the camera (float32, origin-shifted so that the numbers
+// entering the products stay small).
+struct CamDev {
+  float h[9];
+  int ox, oy;
+  int w, h_px, pitch;
+  float wm1, hm1;
+  int own_lo, own_hi;
+};
+
+struct BandDev {
+  int x0, x1, y0, y1;
+  float inv_bw;
+};
+
+struct TileDesc {
+  int16_t tx, ty;                     // tile origin / (kTileW, kTileH)
+  int8_t kind;                        // 0 = own columns of camera idx, 1 = touches band idx
+  int8_t idx;
+  int16_t pad;
+};
+
+struct FuseParams {
+  int n_cams;
+  int flags;
+  int pano_w, pano_h, pano_pitch;
+  int halo;
+  float max_flow;
+  int n_tiles;
+  const TileDesc *tiles;
+  const ColorOut *color;
+  CamDev cam[kMaxCams];
+  BandDev band[kMaxPairs];
+  const uint8_t *src[kMaxCams];
+  const float2 *flow_ij[kMaxPairs];
+  const float2 *flow_ji[kMaxPairs];
+  uint8_t *out;
+};
+
+struct RoleDev {
+  int rx0, rx1, ry0, ry1;
+  int pair;
+  int is_i;                           // 1: colour-source side (H, W and A), 0: reference side (H)
+};
+
+struct StatsParams {
+  int n_cams;
+  int rows_per_block;
+  int vec_ok[kMaxCams];               // 16-byte aligned rows: vector loads allowed
+  const uint8_t *src[kMaxCams];
+  int w[kMaxCams], h[kMaxCams], pitch[kMaxCams];
+  int n_roles[kMaxCams];
+  RoleDev roles[kMaxCams][2];
+  RawStats *raw;                      // two slots
+  const ColorState *state;            // frame index T selects the slot
+};
+
+struct EstimateParams {
+  int n_cams, n_pairs, ref, window;
+  long long lambda_q;                 // lambda in millionths
+  int pair_i[kMaxPairs], pair_j[kMaxPairs];
+  RawStats *raw;
+  ColorState *state;
+};
+
+// Launchers (defined in the kernel files).
+cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
+cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
+cudaError_t launch_fuse(const FuseParams &p, int n_own_tiles, int n_band_tiles, cudaStream_t s);
+cudaError_t fuse_setup_attributes(int max_halo);
+size_t stats_smem_bytes();
+size_t fuse_band_smem_bytes(int halo, bool fp16);
+
+}  // namespace stitch
