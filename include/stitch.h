@@ -209,6 +209,18 @@ int stitch_get_bands(stitch_ctx *ctx, int *bands, int *rects);
 int stitch_save_state(stitch_ctx *ctx, void *buf, size_t *size);
 int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size);
 
+/*
+ * stitch_profile / stitch_profile_read -- stage timing with CUDA events.
+ * While enabled, every stage launch is bracketed by two events on its stream
+ * (also inside graphs recorded by stitch_sequence, as event nodes). read
+ * synchronises the device and returns, per stage (0 = statistics, 1 =
+ * estimate, 2 = fused warp), the summed GPU milliseconds and the number of
+ * launches since the last read, then forgets them. For a replayed graph, read
+ * after every replay: its events hold the latest replay only.
+ */
+int stitch_profile(stitch_ctx *ctx, int enable);
+int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count);
+
 /* Number of adjacent pairs (n_cams - 1), or -1 for a NULL context. */
 int stitch_n_pairs(const stitch_ctx *ctx);
 

@@ -232,11 +232,19 @@ void export_geometry(const Geo &g, int *bands, int *rects) {
 
 }  // namespace
 
+// A pair of events bracketing one stage launch: 0 = stats, 1 = estimate, 2 = fuse.
+struct ProfPair {
+  cudaEvent_t a, b;
+  int stage;
+};
+
 struct GraphEntry {
   std::vector<const void *> key;
   int n_frames = 0;
   int parity = 0;
+  bool prof = false;
   cudaGraphExec_t exec = nullptr;
+  std::vector<ProfPair> pairs;        // events owned by this graph (profiling only)
 };
 
 struct stitch_ctx {
@@ -259,6 +267,10 @@ struct stitch_ctx {
   FuseParams fp{};
   cudaStream_t cap_stream = nullptr;
   std::vector<GraphEntry> graphs;
+  bool prof = false;                  // record stage events (stitch_profile)
+  std::vector<ProfPair> *prof_sink = nullptr;   // where new pairs go (a graph while capturing)
+  std::vector<ProfPair> pending;      // pairs whose times the next stitch_profile_read sums
+  std::vector<ProfPair> owned;        // per-call pairs, destroyed after they are read
   uint8_t *stage_frames[kMaxCams] = {};
   float *stage_fij[kMaxPairs] = {};
   float *stage_fji[kMaxPairs] = {};
@@ -284,16 +296,44 @@ size_t band_elems(const Geo &g, int p) {
   return (size_t)(g.band[p][1] - g.band[p][0]) * (size_t)(g.band[p][3] - g.band[p][2]);
 }
 
+// Profiling: record an event on `s` and return it (nullptr when off).
+cudaEvent_t prof_mark(stitch_ctx *ctx, cudaStream_t s) {
+  if (!ctx->prof) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  if (cudaEventRecord(e, s) != cudaSuccess) {
+    cudaEventDestroy(e);
+    return nullptr;
+  }
+  return e;
+}
+
+void prof_pair(stitch_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int stage) {
+  if (!a || !b) return;
+  ProfPair pp{a, b, stage};
+  if (ctx->prof_sink) {
+    ctx->prof_sink->push_back(pp);
+  } else {
+    ctx->pending.push_back(pp);
+    ctx->owned.push_back(pp);
+  }
+}
+
 int launch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames, cudaStream_t s) {
   StatsParams sp = ctx->sp;
   for (int k = 0; k < ctx->g.n; ++k) {
     sp.src[k] = frames[k];
     sp.vec_ok[k] = ((reinterpret_cast<uintptr_t>(frames[k]) & 15u) == 0 && ctx->g.pitch[k] % 16 == 0) ? 1 : 0;
   }
+  cudaEvent_t e0 = prof_mark(ctx, s);
   cudaError_t e = launch_stats(sp, ctx->stats_grid_x, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "stats launch");
+  cudaEvent_t e1 = prof_mark(ctx, s);
   e = launch_estimate(ctx->ep, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  cudaEvent_t e2 = prof_mark(ctx, s);
+  prof_pair(ctx, e0, e1, 0);
+  prof_pair(ctx, e1, e2, 1);
   ctx->host_T += 1;
   return STITCH_OK;
 }
@@ -308,8 +348,11 @@ int launch_frame(stitch_ctx *ctx, const uint8_t *const *frames, const float *con
   }
   fp.out = pano;
   fp.color = &ctx->state->out[(ctx->host_T + 1) & 1];   // slot written for frame host_T - 1
+  cudaEvent_t e0 = prof_mark(ctx, s);
   cudaError_t e = launch_fuse(fp, ctx->n_own_tiles, ctx->n_band_tiles, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "fuse launch");
+  cudaEvent_t e1 = prof_mark(ctx, s);
+  prof_pair(ctx, e0, e1, 2);
   return STITCH_OK;
 }
 
@@ -573,13 +616,16 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
   const int parity = ctx->host_T & 1;
   GraphEntry *hit = nullptr;
   for (auto &ge : ctx->graphs)
-    if (ge.n_frames == n_frames && ge.parity == parity && ge.key == key) hit = &ge;
+    if (ge.n_frames == n_frames && ge.parity == parity && ge.prof == ctx->prof && ge.key == key) hit = &ge;
   if (!hit) {
     // Record the sequence on the library's own stream, then replay on `s`.
     const int T0 = ctx->host_T;
     cudaGraph_t graph = nullptr;
+    GraphEntry ge;
+    ge.prof = ctx->prof;
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture begin");
+    ctx->prof_sink = &ge.pairs;
     int rc = STITCH_OK;
     for (int t = 0; t < n_frames && rc == STITCH_OK; ++t) {
       rc = launch_estimate_color(ctx, frames_dev + (size_t)t * n, ctx->cap_stream);
@@ -588,13 +634,16 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
                           flow_ji_dev + (size_t)t * np, pano_dev[t], ctx->cap_stream);
     }
     e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->prof_sink = nullptr;
     ctx->host_T = T0;                 // the capture launched nothing
-    if (rc != STITCH_OK) {
+    if (rc != STITCH_OK || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
-      return rc;
+      for (auto &pp : ge.pairs) {
+        cudaEventDestroy(pp.a);
+        cudaEventDestroy(pp.b);
+      }
+      return rc != STITCH_OK ? rc : cuda_err(ctx, e, "graph capture end");
     }
-    if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture end");
-    GraphEntry ge;
     ge.key = key;
     ge.n_frames = n_frames;
     ge.parity = parity;
@@ -602,7 +651,14 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_err(ctx, e, "graph instantiate");
     if (ctx->graphs.size() >= 8) {
-      cudaGraphExecDestroy(ctx->graphs.front().exec);
+      cudaDeviceSynchronize();
+      GraphEntry &old = ctx->graphs.front();
+      cudaGraphExecDestroy(old.exec);
+      for (auto &pp : old.pairs) {
+        cudaEventDestroy(pp.a);
+        cudaEventDestroy(pp.b);
+      }
+      ctx->pending.clear();
       ctx->graphs.erase(ctx->graphs.begin());
     }
     ctx->graphs.push_back(std::move(ge));
@@ -610,6 +666,7 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
   }
   cudaError_t e = cudaGraphLaunch(hit->exec, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
+  if (hit->prof) ctx->pending.insert(ctx->pending.end(), hit->pairs.begin(), hit->pairs.end());
   ctx->host_T += n_frames;
   return STITCH_OK;
 }
@@ -798,6 +855,38 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
   return STITCH_OK;
 }
 
+int stitch_profile(stitch_ctx *ctx, int enable) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  ctx->prof = enable != 0;
+  return STITCH_OK;
+}
+
+int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
+  double ms[3] = {0.0, 0.0, 0.0};
+  int cnt[3] = {0, 0, 0};
+  for (const ProfPair &pp : ctx->pending) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, pp.a, pp.b);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "event elapsed time");
+    ms[pp.stage] += t;
+    cnt[pp.stage] += 1;
+  }
+  ctx->pending.clear();
+  for (auto &pp : ctx->owned) {
+    cudaEventDestroy(pp.a);
+    cudaEventDestroy(pp.b);
+  }
+  ctx->owned.clear();
+  for (int i = 0; i < 3; ++i) {
+    if (stage_ms) stage_ms[i] = ms[i];
+    if (stage_count) stage_count[i] = cnt[i];
+  }
+  return STITCH_OK;
+}
+
 int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
 
 const char *stitch_last_error(const stitch_ctx *ctx) {
@@ -807,8 +896,17 @@ const char *stitch_last_error(const stitch_ctx *ctx) {
 void stitch_destroy(stitch_ctx *ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
-  for (auto &ge : ctx->graphs)
+  for (auto &ge : ctx->graphs) {
     if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    for (auto &pp : ge.pairs) {
+      cudaEventDestroy(pp.a);
+      cudaEventDestroy(pp.b);
+    }
+  }
+  for (auto &pp : ctx->owned) {
+    cudaEventDestroy(pp.a);
+    cudaEventDestroy(pp.b);
+  }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   cudaFree(ctx->raw);
   cudaFree(ctx->state);

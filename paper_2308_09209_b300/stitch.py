@@ -1,0 +1,345 @@
+"""Python binding of the C-ABI stitching library (include/stitch.h).
+
+Argument marshalling only: every step of the stitching path runs in the CUDA
+kernels of libstitch.so. Functions carry the same names as the C entry
+points. Device buffers are torch CUDA tensors (their data pointers are passed
+through); streams are torch.cuda.Stream objects or None (legacy default).
+There is no CPU fallback: if libstitch.so is missing, using any entry point
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstitch.so")
+
+STITCH_OK = 0
+STITCH_EINVAL = -1
+STITCH_ENOMEM = -2
+STITCH_ECUDA = -3
+STITCH_ESINGULAR = -4
+STITCH_ETIMEOUT = -5
+STITCH_EFALLBACK = 1
+
+STITCH_BALANCE_OFF = 1
+STITCH_FP16_INTERMEDIATE = 2
+STITCH_FLOW_WEIGHTS_PRINTED = 4
+STITCH_LEARNED = 8
+
+STITCH_MAX_CAMS = 8
+STITCH_CURVE_FLOATS = 10
+CURVE_FIELDS = ("m1", "m2", "d1", "d2", "s", "g1", "g2", "inv_m1", "inv_bm", "identity")
+
+
+class StitchError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"stitch error {code}: {msg}")
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("n_cams", ctypes.c_int),
+        ("cam_w", ctypes.POINTER(ctypes.c_int)),
+        ("cam_h", ctypes.POINTER(ctypes.c_int)),
+        ("cam_pitch", ctypes.POINTER(ctypes.c_int)),
+        ("H", ctypes.POINTER(ctypes.c_double)),
+        ("pano_w", ctypes.c_int),
+        ("pano_h", ctypes.c_int),
+        ("pano_pitch", ctypes.c_int),
+        ("projection", ctypes.c_int),
+        ("ref_cam", ctypes.c_int),
+        ("window", ctypes.c_int),
+        ("lambda_", ctypes.c_double),
+        ("max_flow", ctypes.c_float),
+        ("flags", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libstitch.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2308_09209_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, cfgp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(_Config)
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "stitch_geometry": (ip, [cfgp, vp, vp]),
+            "stitch_init": (ip, [cfgp, ctypes.POINTER(vp)]),
+            "stitch_estimate_color": (ip, [vp, pp, vp]),
+            "stitch_frame": (ip, [vp, pp, pp, pp, vp, vp]),
+            "stitch_sequence": (ip, [vp, ip, pp, pp, pp, pp, vp]),
+            "stitch_sequence_host": (ip, [vp, ip, pp, pp, pp, pp, vp]),
+            "stitch_sync": (ip, [vp, vp]),
+            "stitch_get_color": (ip, [vp, vp, vp, vp]),
+            "stitch_get_pair_M": (ip, [vp, vp]),
+            "stitch_get_frame_stats": (ip, [vp, vp, vp, vp, vp, vp, vp]),
+            "stitch_get_bands": (ip, [vp, vp, vp]),
+            "stitch_save_state": (ip, [vp, vp, ctypes.POINTER(ctypes.c_size_t)]),
+            "stitch_load_state": (ip, [vp, vp, ctypes.c_size_t]),
+            "stitch_profile": (ip, [vp, ip]),
+            "stitch_profile_read": (ip, [vp, vp, vp]),
+            "stitch_n_pairs": (ip, [vp]),
+            "stitch_last_error": (ctypes.c_char_p, [vp]),
+            "stitch_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Config:
+    """Python mirror of stitch_config (include/stitch.h)."""
+    cam_w: Sequence[int]
+    cam_h: Sequence[int]
+    H: np.ndarray                       # (n_cams, 3, 3) camera -> panorama
+    pano_w: int
+    pano_h: int
+    pano_pitch: Optional[int] = None    # default: pano_w rounded up to 16
+    cam_pitch: Optional[Sequence[int]] = None
+    ref_cam: int = -1
+    window: int = 3
+    lam: float = 0.05
+    max_flow: float = 8.0
+    flags: int = 0
+    _keep: list = field(default_factory=list, repr=False)
+
+    @property
+    def n_cams(self) -> int:
+        return len(self.cam_w)
+
+    @property
+    def pitch(self) -> int:
+        return self.pano_pitch if self.pano_pitch is not None else (self.pano_w + 15) // 16 * 16
+
+    def c_struct(self) -> _Config:
+        n = self.n_cams
+        w = (ctypes.c_int * n)(*[int(v) for v in self.cam_w])
+        h = (ctypes.c_int * n)(*[int(v) for v in self.cam_h])
+        Hs = np.ascontiguousarray(np.asarray(self.H, dtype=np.float64).reshape(n, 9))
+        Hc = (ctypes.c_double * (9 * n))(*Hs.ravel().tolist())
+        pc = None
+        if self.cam_pitch is not None:
+            pc = (ctypes.c_int * n)(*[int(v) for v in self.cam_pitch])
+        self._keep[:] = [w, h, Hc, pc]
+        c = _Config()
+        c.n_cams = n
+        c.cam_w = w
+        c.cam_h = h
+        c.cam_pitch = pc if pc is not None else ctypes.POINTER(ctypes.c_int)()
+        c.H = Hc
+        c.pano_w = int(self.pano_w)
+        c.pano_h = int(self.pano_h)
+        c.pano_pitch = int(self.pitch)
+        c.projection = 0
+        c.ref_cam = int(self.ref_cam)
+        c.window = int(self.window)
+        c.lambda_ = float(self.lam)
+        c.max_flow = float(self.max_flow)
+        c.flags = int(self.flags)
+        return c
+
+
+def _check(rc: int, ctx=None, allow=(STITCH_OK,)):
+    if rc in allow:
+        return rc
+    msg = lib().stitch_last_error(ctx)
+    raise StitchError(rc, msg.decode() if msg else "")
+
+
+def _ptrs(tensors) -> ctypes.Array:
+    vals = []
+    for t in tensors:
+        vals.append(ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr()))
+    return (ctypes.c_void_p * max(1, len(vals)))(*vals)
+
+
+def _host_ptrs(arrays) -> ctypes.Array:
+    vals = []
+    for a in arrays:
+        if hasattr(a, "data_ptr"):
+            vals.append(ctypes.c_void_p(a.data_ptr()))
+        else:
+            vals.append(ctypes.c_void_p(a.ctypes.data))
+    return (ctypes.c_void_p * max(1, len(vals)))(*vals)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def stitch_geometry(cfg: Config):
+    """Host-only geometry: (bands (n_pairs, 4), rects (n_pairs, 2, 4)) int32."""
+    c = cfg.c_struct()
+    npairs = max(cfg.n_cams - 1, 1)
+    bands = np.zeros((npairs, 4), dtype=np.int32)
+    rects = np.zeros((npairs, 2, 4), dtype=np.int32)
+    rc = lib().stitch_geometry(ctypes.byref(c), bands.ctypes.data, rects.ctypes.data)
+    _check(rc)
+    return bands, rects
+
+
+def stitch_init(cfg: Config):
+    c = cfg.c_struct()
+    out = ctypes.c_void_p()
+    _check(lib().stitch_init(ctypes.byref(c), ctypes.byref(out)))
+    return out
+
+
+def stitch_estimate_color(ctx, frames, stream=None) -> int:
+    return _check(lib().stitch_estimate_color(ctx, _ptrs(frames), _stream(stream)), ctx)
+
+
+def stitch_frame(ctx, frames, flows_ij, flows_ji, pano, stream=None) -> int:
+    return _check(lib().stitch_frame(ctx, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji),
+                                     ctypes.c_void_p(pano.data_ptr()), _stream(stream)), ctx)
+
+
+def stitch_sequence(ctx, n_frames, frames, flows_ij, flows_ji, panos, stream=None) -> int:
+    """frames: flat frame-major list (n_frames * n_cams); flows: n_frames * n_pairs; panos: n_frames."""
+    return _check(lib().stitch_sequence(ctx, int(n_frames), _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji),
+                                        _ptrs(panos), _stream(stream)), ctx)
+
+
+def stitch_sequence_host(ctx, n_frames, frames, flows_ij, flows_ji, panos, stream=None) -> int:
+    """As stitch_sequence with host arrays (numpy or pinned torch CPU tensors)."""
+    return _check(lib().stitch_sequence_host(ctx, int(n_frames), _host_ptrs(frames), _host_ptrs(flows_ij),
+                                             _host_ptrs(flows_ji), _host_ptrs(panos), _stream(stream)),
+                  ctx, allow=(STITCH_OK, STITCH_ESINGULAR))
+
+
+def stitch_sync(ctx, stream=None) -> int:
+    return _check(lib().stitch_sync(ctx, _stream(stream)), ctx, allow=(STITCH_OK, STITCH_ESINGULAR))
+
+
+def stitch_get_color(ctx, n_cams: int):
+    """(status, M (n_cams, 3, 3) float64, curve dict of (3,) arrays, frame index)."""
+    M = np.zeros((n_cams, 9), dtype=np.float64)
+    curve = np.zeros((3, STITCH_CURVE_FLOATS), dtype=np.float32)
+    T = ctypes.c_int(0)
+    rc = _check(lib().stitch_get_color(ctx, M.ctypes.data, curve.ctypes.data, ctypes.byref(T)), ctx,
+                allow=(STITCH_OK, STITCH_ESINGULAR))
+    cd = {name: curve[:, i].copy() for i, name in enumerate(CURVE_FIELDS)}
+    return rc, M.reshape(n_cams, 3, 3), cd, T.value
+
+
+def stitch_get_pair_M(ctx, n_pairs: int) -> np.ndarray:
+    M = np.zeros((n_pairs, 9), dtype=np.float64)
+    _check(lib().stitch_get_pair_M(ctx, M.ctypes.data), ctx)
+    return M.reshape(n_pairs, 3, 3)
+
+
+def stitch_get_frame_stats(ctx, n_pairs: int) -> dict:
+    pooled = np.zeros((3, 256), dtype=np.uint32)
+    Hi = np.zeros((n_pairs, 3, 256), dtype=np.uint32)
+    Hj = np.zeros((n_pairs, 3, 256), dtype=np.uint32)
+    Wv = np.zeros((n_pairs, 6, 256), dtype=np.uint32)
+    A = np.zeros((n_pairs, 9), dtype=np.uint64)
+    B = np.zeros((n_pairs, 9), dtype=np.uint64)
+    _check(lib().stitch_get_frame_stats(ctx, pooled.ctypes.data, Hi.ctypes.data, Hj.ctypes.data, Wv.ctypes.data,
+                                        A.ctypes.data, B.ctypes.data), ctx)
+    return dict(pooled=pooled, Hi=Hi, Hj=Hj, Wv=Wv, A=A.reshape(n_pairs, 3, 3), B=B.reshape(n_pairs, 3, 3))
+
+
+def stitch_get_bands(ctx, n_pairs: int):
+    bands = np.zeros((n_pairs, 4), dtype=np.int32)
+    rects = np.zeros((n_pairs, 2, 4), dtype=np.int32)
+    _check(lib().stitch_get_bands(ctx, bands.ctypes.data, rects.ctypes.data), ctx)
+    return bands, rects
+
+
+def stitch_save_state(ctx) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(lib().stitch_save_state(ctx, None, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().stitch_save_state(ctx, buf, ctypes.byref(n)), ctx)
+    return buf.raw[: n.value]
+
+
+def stitch_load_state(ctx, blob: bytes) -> int:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    return _check(lib().stitch_load_state(ctx, buf, len(blob)), ctx)
+
+
+def stitch_profile(ctx, enable: bool) -> int:
+    return _check(lib().stitch_profile(ctx, 1 if enable else 0), ctx)
+
+
+def stitch_profile_read(ctx) -> dict:
+    """Per-stage GPU milliseconds and launch counts since the last read."""
+    ms = np.zeros(3, dtype=np.float64)
+    cnt = np.zeros(3, dtype=np.int32)
+    _check(lib().stitch_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data), ctx)
+    return dict(stats_ms=float(ms[0]), estimate_ms=float(ms[1]), fuse_ms=float(ms[2]),
+                stats_n=int(cnt[0]), estimate_n=int(cnt[1]), fuse_n=int(cnt[2]))
+
+
+def stitch_n_pairs(ctx) -> int:
+    return lib().stitch_n_pairs(ctx)
+
+
+def stitch_last_error(ctx=None) -> str:
+    m = lib().stitch_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def stitch_destroy(ctx) -> None:
+    if ctx is not None and ctx.value:
+        lib().stitch_destroy(ctx)
+
+
+class Stitcher:
+    """Convenience owner of a context: frames and flows are torch CUDA tensors."""
+
+    def __init__(self, cfg: Config):
+        self.cfg = cfg
+        self.ctx = stitch_init(cfg)
+        self.n_cams = cfg.n_cams
+        self.n_pairs = cfg.n_cams - 1
+        self.bands, self.rects = stitch_get_bands(self.ctx, self.n_pairs)
+
+    def new_pano(self, device="cuda"):
+        import torch
+        return torch.zeros((3, self.cfg.pano_h, self.cfg.pitch), dtype=torch.uint8, device=device)
+
+    def estimate_color(self, frames, stream=None):
+        return stitch_estimate_color(self.ctx, frames, stream)
+
+    def frame(self, frames, flows_ij, flows_ji, pano=None, stream=None):
+        if pano is None:
+            pano = self.new_pano(frames[0].device)
+        stitch_frame(self.ctx, frames, flows_ij, flows_ji, pano, stream)
+        return pano
+
+    def color(self):
+        return stitch_get_color(self.ctx, self.n_cams)
+
+    def close(self):
+        stitch_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None:
+                self.close()
+        except Exception:
+            pass

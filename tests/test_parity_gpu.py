@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64
+oracle on the same seeded inputs.
+
+Bars: integer statistics bit-exact; per-camera M within 1e-4 relative; knots
+exact; panorama pixels within one grey level on >= 99.99 % of the compared
+pixels and never off by more than 2 (pixels within 1e-3 px of a coverage
+edge are left out and counted)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import (Pair, assert_pano_ok, compare_pano, compare_stats, ensure_built, flows_for, rel_err,
+                        M_REL_TOL)
+from oracle.pipeline import OracleStitcher
+from paper_2308_09209_b300 import stitch as S
+from synth import Scene, make_rig, render_camera_frames
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_color(pr):
+    rc, M, curve, T = pr.st.color()
+    assert T == pr.oracle.T
+    for k in range(pr.rig.n_cams):
+        assert rel_err(M[k], pr.oracle.M_cam[k]) <= M_REL_TOL, (k, M[k], pr.oracle.M_cam[k])
+    oc = pr.oracle.curve
+    assert np.array_equal(curve["m1"], oc["m1"].astype(np.float32))
+    assert np.array_equal(curve["m2"], oc["m2"].astype(np.float32))
+    assert np.array_equal(curve["identity"] != 0, oc["identity"])
+    for key in ("s", "g1", "g2"):
+        assert np.allclose(curve[key], oc[key], rtol=1e-6, atol=1e-6), key
+
+
+def test_tiny_sequence_full_parity():
+    pr = Pair("2x640x360", seed=0)
+    for t in range(pr.seq["frames"]):
+        out = pr.step(t)
+        st = S.stitch_get_frame_stats(pr.st.ctx, pr.st.n_pairs)
+        compare_stats(st, pr.oracle.last_stats, pr.st.n_pairs)
+        _check_color(pr)
+        rep = compare_pano(out["pano"], out["planes"], out["near"], pr.rig.pano_w)
+        assert_pano_ok(rep)
+        assert rep["n_near"] < 0.001 * rep["n"]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+@pytest.mark.parametrize("flags", [0, S.STITCH_BALANCE_OFF, S.STITCH_FLOW_WEIGHTS_PRINTED,
+                                   S.STITCH_FP16_INTERMEDIATE])
+def test_tiny_modes(seed, flags):
+    pr = Pair("2x640x360", seed=seed, flags=flags)
+    for t in range(3):
+        out = pr.step(t)
+        assert_pano_ok(compare_pano(out["pano"], out["planes"], out["near"], pr.rig.pano_w))
+
+
+def test_three_cameras_window_one_and_ref_left():
+    pr = Pair("3x1920x1080", seed=3, window=1)
+    out = pr.step(0)
+    compare_stats(S.stitch_get_frame_stats(pr.st.ctx, 2), pr.oracle.last_stats, 2)
+    _check_color(pr)
+    assert_pano_ok(compare_pano(out["pano"], out["planes"], out["near"], pr.rig.pano_w))
+
+
+def test_full_size_4x1080p_stats_and_sampled_pixels():
+    pr = Pair("4x1920x1080", seed=0)
+    rng = np.random.RandomState(0)
+    for t in range(2):
+        out = pr.step(t, compare_pano=False)
+        compare_stats(S.stitch_get_frame_stats(pr.st.ctx, 3), pr.oracle.last_stats, 3)
+        _check_color(pr)
+        W, H = pr.rig.pano_w, pr.rig.pano_h
+        xs = rng.randint(0, W, 40000)
+        ys = rng.randint(0, H, 40000)
+        # plus dense rows through every band, where the remap runs
+        for (x0, x1, y0, y1) in pr.st.bands.tolist():
+            for y in (y0, (y0 + y1) // 2, y1 - 1):
+                xs = np.concatenate([xs, np.arange(x0 - 8, x1 + 8)])
+                ys = np.concatenate([ys, np.full(x1 - x0 + 16, y)])
+        vals, near = pr.oracle.pixels(out["fr_np"], [f.cpu().numpy() for f in out["fij"]],
+                                      [f.cpu().numpy() for f in out["fji"]], xs, ys)
+        g = out["pano"].cpu().numpy()[:, ys, xs].T.astype(np.int16)
+        d = np.abs(g - vals.astype(np.int16)).max(1)[~near]
+        assert d.max() <= 2 and (d <= 1).mean() >= 0.9999, (d.max(), (d <= 1).mean())
+
+
+def _T(tx, ty):
+    return np.array([[1.0, 0, tx], [0, 1.0, ty], [0, 0, 1.0]])
+
+
+def test_identity_and_integer_shift_bit_exact():
+    ensure_built()
+    rng = np.random.RandomState(0)
+    base = rng.randint(0, 256, (96, 360, 3)).astype(np.uint8)
+    frames = [torch.from_numpy(base[:, 0:224].copy()).cuda(), torch.from_numpy(base[:, 136:360].copy()).cuda()]
+    cfg = S.Config([224, 224], [96, 96], np.stack([_T(0, 0), _T(136, 0)]), 360, 96, max_flow=4,
+                   flags=S.STITCH_BALANCE_OFF)
+    st = S.Stitcher(cfg)
+    fij, fji = flows_for(st.bands, 0.0, 0, 0)
+    pano = st.frame(frames, fij, fji)                      # before any estimate: M = I
+    assert np.array_equal(pano.cpu().numpy()[:, :, :360].transpose(1, 2, 0), base)
+    st.estimate_color(frames)                              # identical overlaps: M = I
+    pano = st.frame(frames, fij, fji)
+    assert np.array_equal(pano.cpu().numpy()[:, :, :360].transpose(1, 2, 0), base)
+    # integer shift of the whole rig by (5, 3)
+    cfg2 = S.Config([224, 224], [96, 96], np.stack([_T(5, 3), _T(141, 3)]), 368, 100, max_flow=4,
+                    flags=S.STITCH_BALANCE_OFF)
+    st2 = S.Stitcher(cfg2)
+    f2ij, f2ji = flows_for(st2.bands, 0.0, 0, 0)
+    pano2 = st2.frame(frames, f2ij, f2ji).cpu().numpy()
+    assert np.array_equal(pano2[:, 3:99, 5:365].transpose(1, 2, 0), base)
+    assert (pano2[:, :3] == 0).all() and (pano2[:, 99:] == 0).all() and (pano2[:, :, :5] == 0).all()
+
+
+def test_sequence_graph_matches_per_call():
+    pa = Pair("2x640x360", seed=4)
+    pb = Pair("2x640x360", seed=4)
+    ins = [pa.inputs(t) for t in range(4)]
+    ref = []
+    for fr, fij, fji in ins:
+        pa.st.estimate_color(fr)
+        ref.append(pa.st.frame(fr, fij, fji).clone())
+    panos = [pb.st.new_pano() for _ in range(4)]
+    frames = [f for fr, _, _ in ins for f in fr]
+    S.stitch_sequence(pb.st.ctx, 4, frames, [f for _, fij, _ in ins for f in fij],
+                      [f for _, _, fji in ins for f in fji], panos)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, panos):
+        assert torch.equal(a, b)
+    # replay of the cached graph continues the sequence state
+    S.stitch_sequence(pb.st.ctx, 4, frames, [f for _, fij, _ in ins for f in fij],
+                      [f for _, _, fji in ins for f in fji], panos)
+    for fr, fij, fji in ins:
+        pa.st.estimate_color(fr)
+        pa.st.frame(fr, fij, fji)
+    torch.cuda.synchronize()
+    assert pa.st.color()[3] == pb.st.color()[3] == 8
+
+
+def test_sequence_host_matches_device():
+    pa = Pair("2x640x360", seed=5)
+    pb = Pair("2x640x360", seed=5)
+    ins = [pa.inputs(t) for t in range(3)]
+    ref = []
+    for fr, fij, fji in ins:
+        pa.st.estimate_color(fr)
+        ref.append(pa.st.frame(fr, fij, fji).cpu())
+    frames = [f.cpu().pin_memory() for fr, _, _ in ins for f in fr]
+    fij = [f.cpu().pin_memory() for _, fi, _ in ins for f in fi]
+    fji = [f.cpu().pin_memory() for _, _, fj in ins for f in fj]
+    outs = [torch.zeros_like(r).pin_memory() for r in ref]
+    S.stitch_sequence_host(pb.st.ctx, 3, frames, fij, fji, outs)
+    for a, b in zip(ref, outs):
+        assert torch.equal(a, b)
+
+
+def test_save_and_load_state_resume_identically():
+    pa = Pair("2x640x360", seed=6)
+    ins = [pa.inputs(t) for t in range(6)]
+    for fr, fij, fji in ins[:3]:
+        pa.st.estimate_color(fr)
+        pa.st.frame(fr, fij, fji)
+    blob = S.stitch_save_state(pa.st.ctx)
+    ref = []
+    for fr, fij, fji in ins[3:]:
+        pa.st.estimate_color(fr)
+        ref.append(pa.st.frame(fr, fij, fji).clone())
+    pb = Pair("2x640x360", seed=6)
+    S.stitch_load_state(pb.st.ctx, blob)
+    for (fr, fij, fji), r in zip(ins[3:], ref):
+        pb.st.estimate_color(fr)
+        assert torch.equal(pb.st.frame(fr, fij, fji), r)
+
+
+def test_flat_overlap_keeps_previous_M():
+    pr = Pair("2x640x360", seed=7, window=1)
+    pr.step(0, compare_pano=False)
+    M0 = S.stitch_get_pair_M(pr.st.ctx, 1).copy()
+    assert S.stitch_sync(pr.st.ctx) == S.STITCH_OK
+    flat = [torch.full((360, 640, 3), 90, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    pr.st.estimate_color(flat)
+    rc, M, _, _ = pr.st.color()
+    assert rc == S.STITCH_ESINGULAR
+    assert np.array_equal(S.stitch_get_pair_M(pr.st.ctx, 1), M0)
+    assert S.stitch_sync(pr.st.ctx) == S.STITCH_ESINGULAR
+    assert S.stitch_sync(pr.st.ctx) == S.STITCH_OK       # condition is cleared once reported
+    pr.oracle.estimate_color([f.cpu().numpy() for f in flat])
+    assert pr.oracle.singular and np.allclose(pr.oracle.M_pair[0], M0[0], rtol=1e-12)
+
+
+def test_ragged_widths_unaligned_frames_and_nan_flow():
+    """Camera widths that are not multiples of 16 (tail groups), frame rows
+    that are not 16-byte aligned (scalar loads), a panorama width that is not
+    a multiple of 4, and NaN / huge flow values (clamped as in the oracle)."""
+    ensure_built()
+    rig = make_rig([650, 650], [203, 203], overlap=(0.25, 0.25), rot_deg=2.5, seed=9)
+    pano_w = rig.pano_w - 3
+    sc = Scene(rig.pano_w, rig.pano_h, seed=9)
+    frames_c = render_camera_frames(rig, sc, 0, device="cuda")
+    # copy into buffers offset by 1 byte so rows are not 16-byte aligned
+    frames = []
+    for f in frames_c:
+        buf = torch.zeros(f.numel() + 16, dtype=torch.uint8, device="cuda")
+        buf[1:1 + f.numel()] = f.reshape(-1)
+        frames.append(buf[1:1 + f.numel()])
+    cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, pano_w, rig.pano_h, window=3, max_flow=5.0)
+    st = S.Stitcher(cfg)
+    fij, fji = flows_for(st.bands, 5.0, 9, 0)
+    fij[0][3, 5, 0] = float("nan")
+    fji[0][7, 9, 1] = 1e9
+    st.estimate_color(frames)
+    pano = st.frame(frames, fij, fji)
+    o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, pano_w, rig.pano_h, window=3, max_flow=5.0)
+    fr_np = [f.cpu().numpy() for f in frames_c]
+    o.estimate_color(fr_np)
+    compare_stats(S.stitch_get_frame_stats(st.ctx, 1), o.last_stats, 1)
+    planes, near, _ = o.frame(fr_np, [f.cpu().numpy() for f in fij], [f.cpu().numpy() for f in fji])
+    assert_pano_ok(compare_pano(pano, planes, near, pano_w))
+
+
+def test_zero_max_flow_and_long_window():
+    pr = Pair("2x640x360", seed=8, max_flow=0.0, window=16)
+    for t in range(3):
+        out = pr.step(t)
+        _check_color(pr)
+        assert_pano_ok(compare_pano(out["pano"], out["planes"], out["near"], pr.rig.pano_w))
+
+
+def test_argument_errors_are_reported():
+    pr = Pair("2x640x360", seed=0)
+    frames, fij, fji = pr.inputs(0)
+    with pytest.raises(S.StitchError) as ei:
+        S.stitch_frame(pr.st.ctx, frames, fij, fji, pr.st.new_pano()[:, :, 1:])   # misaligned output
+    assert ei.value.code == S.STITCH_EINVAL
+    with pytest.raises(S.StitchError):
+        S.stitch_estimate_color(pr.st.ctx, [frames[0], 0])
