@@ -301,7 +301,10 @@ cudaEvent_t prof_mark(stitch_ctx *ctx, cudaStream_t s) {
   if (!ctx->prof) return nullptr;
   cudaEvent_t e = nullptr;
   if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  if (cudaEventRecord(e, s) != cudaSuccess) {
+  // Inside stream capture a plain record only forms a dependency; the external
+  // flag makes it an event node that records (with a timestamp) on every replay.
+  const unsigned flags = ctx->prof_sink ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (cudaEventRecordWithFlags(e, s, flags) != cudaSuccess) {
     cudaEventDestroy(e);
     return nullptr;
   }

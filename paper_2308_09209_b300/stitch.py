@@ -334,10 +334,16 @@ class Stitcher:
         return stitch_get_color(self.ctx, self.n_cams)
 
     def close(self):
-        stitch_destroy(self.ctx)
+        if self.ctx is not None:
+            stitch_destroy(self.ctx)
         self.ctx = None
 
     def __del__(self):
+        # Never call into CUDA while the interpreter shuts down: the CUDA
+        # runtime may already be torn down by then.
+        import sys
+        if sys.is_finalizing():
+            return
         try:
             if getattr(self, "ctx", None) is not None:
                 self.close()

@@ -233,3 +233,24 @@ def test_argument_errors_are_reported():
     assert ei.value.code == S.STITCH_EINVAL
     with pytest.raises(S.StitchError):
         S.stitch_estimate_color(pr.st.ctx, [frames[0], 0])
+
+
+def test_stage_profiling_per_call_and_in_graphs():
+    pr = Pair("2x640x360", seed=3)
+    ins = [pr.inputs(t) for t in range(3)]
+    S.stitch_profile(pr.st.ctx, True)
+    for fr, fij, fji in ins:
+        pr.st.estimate_color(fr)
+        pr.st.frame(fr, fij, fji)
+    r = S.stitch_profile_read(pr.st.ctx)
+    assert (r["stats_n"], r["estimate_n"], r["fuse_n"]) == (3, 3, 3)
+    assert r["stats_ms"] > 0 and r["estimate_ms"] > 0 and r["fuse_ms"] > 0
+    panos = [pr.st.new_pano() for _ in range(3)]
+    args = (3, [f for fr, _, _ in ins for f in fr], [f for _, a, _ in ins for f in a],
+            [f for _, _, b in ins for f in b], panos)
+    S.stitch_sequence(pr.st.ctx, *args)
+    r = S.stitch_profile_read(pr.st.ctx)
+    assert (r["stats_n"], r["estimate_n"], r["fuse_n"]) == (3, 3, 3)
+    assert r["fuse_ms"] > 0 and r["stats_ms"] > 0
+    S.stitch_profile(pr.st.ctx, False)
+    assert S.stitch_profile_read(pr.st.ctx)["fuse_n"] == 0
