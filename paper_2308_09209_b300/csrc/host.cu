@@ -312,7 +312,11 @@ cudaEvent_t prof_mark(stitch_ctx *ctx, cudaStream_t s) {
 }
 
 void prof_pair(stitch_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int stage) {
-  if (!a || !b) return;
+  if (!a || !b) {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return;
+  }
   ProfPair pp{a, b, stage};
   if (ctx->prof_sink) {
     ctx->prof_sink->push_back(pp);
@@ -328,15 +332,17 @@ int launch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames, cudaStr
     sp.src[k] = frames[k];
     sp.vec_ok[k] = ((reinterpret_cast<uintptr_t>(frames[k]) & 15u) == 0 && ctx->g.pitch[k] % 16 == 0) ? 1 : 0;
   }
+  // Every timing pair owns its two events (they are destroyed pairwise).
   cudaEvent_t e0 = prof_mark(ctx, s);
   cudaError_t e = launch_stats(sp, ctx->stats_grid_x, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "stats launch");
   cudaEvent_t e1 = prof_mark(ctx, s);
+  cudaEvent_t e2 = prof_mark(ctx, s);
   e = launch_estimate(ctx->ep, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
-  cudaEvent_t e2 = prof_mark(ctx, s);
+  cudaEvent_t e3 = prof_mark(ctx, s);
   prof_pair(ctx, e0, e1, 0);
-  prof_pair(ctx, e1, e2, 1);
+  prof_pair(ctx, e2, e3, 1);
   ctx->host_T += 1;
   return STITCH_OK;
 }

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 from dataclasses import dataclass, field
 from typing import Optional, Sequence
 
@@ -341,8 +342,7 @@ class Stitcher:
     def __del__(self):
         # Never call into CUDA while the interpreter shuts down: the CUDA
         # runtime may already be torn down by then.
-        import sys
-        if sys.is_finalizing():
+        if sys is None or sys.is_finalizing():
             return
         try:
             if getattr(self, "ctx", None) is not None:
