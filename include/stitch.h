@@ -221,6 +221,40 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size);
 int stitch_profile(stitch_ctx *ctx, int enable);
 int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count);
 
+/*
+ * stitch_estimate_color_noalloc -- the colour estimate of ONE frame without
+ * any device allocation. The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc, such as plugins whose host
+ * application owns every device buffer, code that must not allocate while a
+ * stream is being captured, or real-time threads that may not block in the
+ * driver's allocator. It needs no context (stitch_init allocates; this does
+ * not).
+ *   cfg:           as for stitch_init, at most STITCH_NOALLOC_MAX_CAMS cameras
+ *                  (larger rigs are rejected with STITCH_EINVAL). The fit uses
+ *                  this frame only: it equals the first stitch_estimate_color of
+ *                  a fresh context (window and knot mean over one frame).
+ *   frames_dev:    n_cams device pointers to the frame's camera images.
+ *   M_out_dev:     device buffer of n_cams x 9 doubles, written: each camera's
+ *                  matrix chained to the reference (as stitch_get_color).
+ *   curve_out_dev: device buffer of 3 x STITCH_CURVE_FLOATS floats, written (as
+ *                  stitch_get_color).
+ *   flags_out_dev: optional device int, written: bitmask of pairs whose fit was
+ *                  ill-conditioned (those pairs get the identity).
+ * Working memory is a fixed STITCH_NOALLOC_SCRATCH_BYTES array in the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits, and shared by all calls on that GPU: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and corrupt each
+ * other; serialise them. Each call clears the part that must start at zero.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Launches are asynchronous on `stream`; the call performs no cudaMalloc,
+ * cudaFree or other allocation of device memory.
+ */
+#define STITCH_NOALLOC_MAX_CAMS 8
+#define STITCH_NOALLOC_SCRATCH_BYTES 196608
+int stitch_estimate_color_noalloc(const stitch_config *cfg, const uint8_t *const *frames_dev, double *M_out_dev,
+                                  float *curve_out_dev, int *flags_out_dev, stitch_stream_t stream);
+
 /* Number of adjacent pairs (n_cams - 1), or -1 for a NULL context. */
 int stitch_n_pairs(const stitch_ctx *ctx);
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libstitch.so")
-SOURCES = ["host.cu", "k_stats.cu", "k_estimate.cu", "k_fuse.cu"]
+SOURCES = ["host.cu", "k_stats.cu", "k_estimate.cu", "k_fuse.cu", "noalloc.cu"]
 HEADERS = ["stitch_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -238,6 +238,68 @@ struct ProfPair {
   int stage;
 };
 
+namespace stitch {
+
+// Launch parameters of the estimate stage (statistics + estimate) for a
+// configuration, computed on the host only. Allocates no device memory; the
+// caller fills in the frame pointers, the raw-statistics slots and the state.
+int prepare_estimate_params(const stitch_config *cfg, StatsParams &sp, int &grid_x, EstimateParams &ep,
+                            std::string &err) {
+  Geo g;
+  const int rc = build_geometry(cfg, g, err);
+  if (rc != STITCH_OK) return rc;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long rows = 0;
+  int max_h = 0;
+  for (int k = 0; k < g.n; ++k) {
+    rows += g.h[k];
+    max_h = std::max(max_h, g.h[k]);
+  }
+  const int rpb = (int)std::max(1ll, (rows + 4ll * sms - 1) / (4ll * sms));
+  sp = StatsParams{};
+  sp.n_cams = g.n;
+  sp.rows_per_block = rpb;
+  for (int k = 0; k < g.n; ++k) {
+    sp.w[k] = g.w[k];
+    sp.h[k] = g.h[k];
+    sp.pitch[k] = g.pitch[k];
+  }
+  for (int p = 0; p + 1 < g.n; ++p) {
+    for (int side = 0; side < 2; ++side) {
+      const int cam = side == 0 ? p : p + 1;
+      RoleDev r{};
+      r.rx0 = g.rect[p][side][0];
+      r.rx1 = g.rect[p][side][1];
+      r.ry0 = g.rect[p][side][2];
+      r.ry1 = g.rect[p][side][3];
+      r.pair = p;
+      r.is_i = (g.pair_i[p] == cam) ? 1 : 0;
+      sp.roles[cam][sp.n_roles[cam]++] = r;
+    }
+  }
+  grid_x = (max_h + rpb - 1) / rpb;
+  ep = EstimateParams{};
+  ep.n_cams = g.n;
+  ep.n_pairs = g.n - 1;
+  ep.ref = g.ref;
+  ep.window = 1;
+  ep.lambda_q = (long long)std::llround(cfg->lambda * 1e6);
+  if (ep.lambda_q <= 0 || ep.lambda_q >= 500000) {
+    err = "lambda rounds to 0 or 0.5 in millionths";
+    return STITCH_EINVAL;
+  }
+  for (int p = 0; p + 1 < g.n; ++p) {
+    ep.pair_i[p] = g.pair_i[p];
+    ep.pair_j[p] = g.pair_j[p];
+  }
+  return STITCH_OK;
+}
+
+void record_last_error(const std::string &msg) { g_last_error = msg; }
+
+}  // namespace stitch
+
 struct GraphEntry {
   std::vector<const void *> key;
   int n_frames = 0;

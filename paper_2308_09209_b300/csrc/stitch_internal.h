@@ -132,3 +132,10 @@ size_t stats_smem_bytes();
 size_t fuse_band_smem_bytes(int halo, bool fp16);
 
 }  // namespace stitch
+
+#include <string>
+namespace stitch {
+int prepare_estimate_params(const stitch_config *cfg, StatsParams &sp, int &grid_x, EstimateParams &ep,
+                            std::string &err);
+void record_last_error(const std::string &msg);
+}  // namespace stitch

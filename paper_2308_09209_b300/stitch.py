@@ -91,6 +91,7 @@ def lib():
             "stitch_load_state": (ip, [vp, vp, ctypes.c_size_t]),
             "stitch_profile": (ip, [vp, ip]),
             "stitch_profile_read": (ip, [vp, vp, vp]),
+            "stitch_estimate_color_noalloc": (ip, [cfgp, pp, vp, vp, vp, vp]),
             "stitch_n_pairs": (ip, [vp]),
             "stitch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_destroy": (None, [vp]),
@@ -292,6 +293,19 @@ def stitch_profile_read(ctx) -> dict:
     _check(lib().stitch_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data), ctx)
     return dict(stats_ms=float(ms[0]), estimate_ms=float(ms[1]), fuse_ms=float(ms[2]),
                 stats_n=int(cnt[0]), estimate_n=int(cnt[1]), fuse_n=int(cnt[2]))
+
+
+def stitch_estimate_color_noalloc(cfg: Config, frames, M_out, curve_out, flags_out=None, stream=None) -> int:
+    """Single-frame colour estimate into caller-owned device tensors, with no
+    device allocation inside the library (for callers that cannot allocate).
+    M_out: float64 CUDA tensor of n_cams * 9; curve_out: float32 CUDA tensor of
+    3 * STITCH_CURVE_FLOATS; flags_out: optional int32 CUDA tensor of 1."""
+    c = cfg.c_struct()
+    fl = ctypes.c_void_p(flags_out.data_ptr()) if flags_out is not None else None
+    return _check(lib().stitch_estimate_color_noalloc(ctypes.byref(c), _ptrs(frames),
+                                                      ctypes.c_void_p(M_out.data_ptr()),
+                                                      ctypes.c_void_p(curve_out.data_ptr()), fl,
+                                                      _stream(stream)))
 
 
 def stitch_n_pairs(ctx) -> int:
