@@ -214,9 +214,12 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size);
  * While enabled, every stage launch is bracketed by two events on its stream
  * (also inside graphs recorded by stitch_sequence, as event nodes). read
  * synchronises the device and returns, per stage (0 = statistics, 1 =
- * estimate, 2 = fused warp), the summed GPU milliseconds and the number of
- * launches since the last read, then forgets them. For a replayed graph, read
- * after every replay: its events hold the latest replay only.
+ * estimate, 2 = fused warp, 3 = band pre-warp; stage_ms and stage_count hold 4
+ * entries each), the summed GPU milliseconds and the number of launches since
+ * the last read, then forgets them. For a replayed graph, read after every
+ * replay: its events hold the latest replay only. In a recorded sequence the
+ * stages of successive frames overlap on separate streams, so the stage times
+ * add up to more than the elapsed time.
  */
 int stitch_profile(stitch_ctx *ctx, int enable);
 int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count);

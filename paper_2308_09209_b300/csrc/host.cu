@@ -232,7 +232,7 @@ void export_geometry(const Geo &g, int *bands, int *rects) {
 
 }  // namespace
 
-// A pair of events bracketing one stage launch: 0 = stats, 1 = estimate, 2 = fuse.
+// A pair of events bracketing one stage launch: 0 = stats, 1 = estimate, 2 = fuse, 3 = band pre-warp.
 struct ProfPair {
   cudaEvent_t a, b;
   int stage;
@@ -318,16 +318,22 @@ struct stitch_ctx {
   int halo = 1;
   int device = 0;
   int host_T = 0;                     // frames estimated (host mirror of the device index)
+  int host_F = 0;                     // frames fused (selects the band pre-warp slot)
+  size_t pw_slot_bytes = 0;
   std::string err;
-  RawStats *raw = nullptr;            // 2 slots
+  RawStats *raw = nullptr;            // kRawSlots slots
   ColorState *state = nullptr;
   TileDesc *tiles = nullptr;
   int n_band_tiles = 0, n_own_tiles = 0;
+  PwTile *pw_tiles = nullptr;
+  void *pw = nullptr;                 // band pre-warp intermediate
   int stats_grid_x = 1;
   StatsParams sp{};
   EstimateParams ep{};
   FuseParams fp{};
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t pipe[3] = {};          // stats + pre-warp, estimate, fuse streams of a recorded sequence
+  cudaEvent_t pev[4][8] = {};         // per-stage completion events (stats, pre-warp, estimate, fuse) by t % 8
   std::vector<GraphEntry> graphs;
   bool prof = false;                  // record stage events (stitch_profile)
   std::vector<ProfPair> *prof_sink = nullptr;   // where new pairs go (a graph while capturing)
@@ -388,29 +394,34 @@ void prof_pair(stitch_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int stage) {
   }
 }
 
-int launch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames, cudaStream_t s) {
+// Statistics of frame T into slot T % kRawSlots (cleared by the estimate of frame T - 2).
+int launch_stats_for(stitch_ctx *ctx, const uint8_t *const *frames, int T, cudaStream_t s) {
   StatsParams sp = ctx->sp;
   for (int k = 0; k < ctx->g.n; ++k) {
     sp.src[k] = frames[k];
     sp.vec_ok[k] = ((reinterpret_cast<uintptr_t>(frames[k]) & 15u) == 0 && ctx->g.pitch[k] % 16 == 0) ? 1 : 0;
   }
+  sp.raw = ctx->raw + (T % kRawSlots);
   // Every timing pair owns its two events (they are destroyed pairwise).
   cudaEvent_t e0 = prof_mark(ctx, s);
   cudaError_t e = launch_stats(sp, ctx->stats_grid_x, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "stats launch");
   cudaEvent_t e1 = prof_mark(ctx, s);
-  cudaEvent_t e2 = prof_mark(ctx, s);
-  e = launch_estimate(ctx->ep, s);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
-  cudaEvent_t e3 = prof_mark(ctx, s);
   prof_pair(ctx, e0, e1, 0);
-  prof_pair(ctx, e2, e3, 1);
-  ctx->host_T += 1;
   return STITCH_OK;
 }
 
-int launch_frame(stitch_ctx *ctx, const uint8_t *const *frames, const float *const *fij, const float *const *fji,
-                 uint8_t *pano, cudaStream_t s) {
+int launch_estimate_for(stitch_ctx *ctx, cudaStream_t s) {
+  cudaEvent_t e0 = prof_mark(ctx, s);
+  cudaError_t e = launch_estimate(ctx->ep, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  cudaEvent_t e1 = prof_mark(ctx, s);
+  prof_pair(ctx, e0, e1, 1);
+  return STITCH_OK;
+}
+
+FuseParams frame_params(stitch_ctx *ctx, const uint8_t *const *frames, const float *const *fij,
+                        const float *const *fji, uint8_t *pano, int colour_T, int F) {
   FuseParams fp = ctx->fp;
   for (int k = 0; k < ctx->g.n; ++k) fp.src[k] = frames[k];
   for (int p = 0; p + 1 < ctx->g.n; ++p) {
@@ -418,13 +429,45 @@ int launch_frame(stitch_ctx *ctx, const uint8_t *const *frames, const float *con
     fp.flow_ji[p] = reinterpret_cast<const float2 *>(fji[p]);
   }
   fp.out = pano;
-  fp.color = &ctx->state->out[(ctx->host_T + 1) & 1];   // slot written for frame host_T - 1
+  fp.color = &ctx->state->out[((colour_T % kColorSlots) + kColorSlots) % kColorSlots];
+  fp.pw = static_cast<char *>(ctx->pw) + (size_t)(F % kPwSlots) * ctx->pw_slot_bytes;
+  return fp;
+}
+
+// Band pre-warp (stage 3) and fuse (stage 2) of one frame.
+int launch_prewarp_for(stitch_ctx *ctx, const FuseParams &fp, cudaStream_t s) {
   cudaEvent_t e0 = prof_mark(ctx, s);
-  cudaError_t e = launch_fuse(fp, ctx->n_own_tiles, ctx->n_band_tiles, s);
+  cudaError_t e = launch_prewarp(fp, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "band pre-warp launch");
+  cudaEvent_t e1 = prof_mark(ctx, s);
+  prof_pair(ctx, e0, e1, 3);
+  return STITCH_OK;
+}
+
+int launch_fuse_for(stitch_ctx *ctx, const FuseParams &fp, cudaStream_t s) {
+  cudaEvent_t e0 = prof_mark(ctx, s);
+  cudaError_t e = launch_fuse(fp, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "fuse launch");
   cudaEvent_t e1 = prof_mark(ctx, s);
   prof_pair(ctx, e0, e1, 2);
   return STITCH_OK;
+}
+
+int launch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames, cudaStream_t s) {
+  int rc = launch_stats_for(ctx, frames, ctx->host_T, s);
+  if (rc == STITCH_OK) rc = launch_estimate_for(ctx, s);
+  if (rc == STITCH_OK) ctx->host_T += 1;
+  return rc;
+}
+
+int launch_frame(stitch_ctx *ctx, const uint8_t *const *frames, const float *const *fij, const float *const *fji,
+                 uint8_t *pano, cudaStream_t s) {
+  // colour of the latest estimate, frame host_T - 1
+  const FuseParams fp = frame_params(ctx, frames, fij, fji, pano, ctx->host_T - 1, ctx->host_F);
+  int rc = launch_prewarp_for(ctx, fp, s);
+  if (rc == STITCH_OK) rc = launch_fuse_for(ctx, fp, s);
+  if (rc == STITCH_OK) ctx->host_F += 1;
+  return rc;
 }
 
 bool check_ptrs(const void *const *p, int n) {
@@ -496,7 +539,20 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
       } else {
         int k = 0;
         while (k < g.n - 1 && c0 >= g.own_hi[k]) ++k;
-        t.kind = 0;
+        // Kind 0: camera k covers the whole tile with a margin (coverage is
+        // convex, so the four corners decide), so no pixel needs a coverage
+        // test or a fallback camera. Kind 2: partial coverage.
+        const int r0 = ty * kTileH, r1 = std::min(r0 + kTileH, g.pano_h) - 1;
+        const int q1 = std::min(c1, g.pano_w) - 1;
+        bool full = c1 <= g.pano_w && r0 + kTileH <= g.pano_h;
+        const double px[4] = {(double)c0, (double)q1, (double)c0, (double)q1};
+        const double py[4] = {(double)r0, (double)r0, (double)r1, (double)r1};
+        for (int i = 0; i < 4 && full; ++i) {
+          double sx, sy, sw;
+          proj(g.Hi[k], px[i], py[i], sx, sy, sw);
+          full = sw > 0 && sx >= 0.01 && sx <= g.w[k] - 1.01 && sy >= 0.01 && sy <= g.h[k] - 1.01;
+        }
+        t.kind = full ? 0 : 2;
         t.idx = (int8_t)k;
         own_tiles.push_back(t);
       }
@@ -506,11 +562,30 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   ctx->n_own_tiles = (int)own_tiles.size();
 
   cudaError_t e = cudaGetDevice(&ctx->device);
-  if (e == cudaSuccess) e = fuse_setup_attributes((int)std::ceil((double)STITCH_MAX_FLOW) + 1);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->raw, 2 * sizeof(RawStats));
+  if (e == cudaSuccess) e = estimate_setup();
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->raw, kRawSlots * sizeof(RawStats));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->state, sizeof(ColorState));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, (band_tiles.size() + own_tiles.size()) * sizeof(TileDesc) + 16);
-  if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, 2 * sizeof(RawStats));
+  if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, kRawSlots * sizeof(RawStats));
+  // Band pre-warp pieces and the intermediate (both cameras of every band).
+  std::vector<PwTile> pw_tiles;
+  size_t pw_elems = 0;
+  size_t pw_off[kMaxPairs][2] = {};
+  for (int p = 0; p + 1 < g.n; ++p) {
+    const int x0 = g.band[p][0], x1 = g.band[p][1], y0 = g.band[p][2], y1 = g.band[p][3];
+    for (int y = y0; y < y1; y += kTileH)
+      for (int x = x0; x < x1; x += kTileW) pw_tiles.push_back(PwTile{p, x, y});
+    const size_t area = (size_t)(x1 - x0) * (size_t)(y1 - y0);
+    pw_off[p][0] = pw_elems;
+    pw_off[p][1] = pw_elems + area;
+    pw_elems += 2 * area;
+  }
+  const size_t pw_bytes = pw_elems * prewarp_elem_bytes((cfg->flags & STITCH_FP16_INTERMEDIATE) != 0);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->pw_tiles, pw_tiles.size() * sizeof(PwTile) + 16);
+  ctx->pw_slot_bytes = (pw_bytes + 255) / 256 * 256;
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->pw, kPwSlots * ctx->pw_slot_bytes + 16);
+  if (e == cudaSuccess && !pw_tiles.empty())
+    e = cudaMemcpy(ctx->pw_tiles, pw_tiles.data(), pw_tiles.size() * sizeof(PwTile), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     std::vector<TileDesc> all(band_tiles);
     all.insert(all.end(), own_tiles.begin(), own_tiles.end());
@@ -525,14 +600,17 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     for (int c = 0; c < kMaxCams; ++c)
       for (int k = 0; k < 9; ++k) {
         h->M_cam[c][k] = (k % 4 == 0) ? 1.0 : 0.0;
-        h->out[0].M[c][k] = h->out[1].M[c][k] = (k % 4 == 0) ? 1.0f : 0.0f;
+        for (int s = 0; s < kColorSlots; ++s) h->out[s].M[c][k] = (k % 4 == 0) ? 1.0f : 0.0f;
       }
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < kColorSlots; ++s)
       for (int c = 0; c < 3; ++c) h->out[s].curve[c].ident = 1.0f;
     e = cudaMemcpy(ctx->state, h, sizeof(ColorState), cudaMemcpyHostToDevice);
     delete h;
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
+  for (int a = 0; a < 4 && e == cudaSuccess; ++a)
+    for (int b = 0; b < 8 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&ctx->pev[a][b], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     const int code = cuda_err(nullptr, e, "stitch_init");
     stitch_destroy(ctx);
@@ -554,7 +632,6 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   sp.n_cams = g.n;
   sp.rows_per_block = rpb;
   sp.raw = ctx->raw;
-  sp.state = ctx->state;
   for (int k = 0; k < g.n; ++k) {
     sp.w[k] = g.w[k];
     sp.h[k] = g.h[k];
@@ -588,6 +665,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     ep.pair_j[p] = g.pair_j[p];
   }
   ep.raw = ctx->raw;
+  ep.raw_slots = kRawSlots;
   ep.state = ctx->state;
 
   FuseParams &fp = ctx->fp;
@@ -601,6 +679,13 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   fp.max_flow = ctx->max_flow;
   fp.n_tiles = ctx->n_band_tiles + ctx->n_own_tiles;
   fp.tiles = ctx->tiles;
+  fp.n_pw_tiles = (int)pw_tiles.size();
+  fp.pw_tiles = ctx->pw_tiles;
+  fp.pw = ctx->pw;
+  for (int p = 0; p < kMaxPairs; ++p) {
+    fp.pw_off[p][0] = pw_off[p][0];
+    fp.pw_off[p][1] = pw_off[p][1];
+  }
   for (int k = 0; k < g.n; ++k) {
     CamDev &c = fp.cam[k];
     double cx, cy, cw;
@@ -684,29 +769,68 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
   for (int i = 0; i < n_frames * np; ++i) key.push_back(flow_ij_dev[i]);
   for (int i = 0; i < n_frames * np; ++i) key.push_back(flow_ji_dev[i]);
   for (int i = 0; i < n_frames; ++i) key.push_back(pano_dev[i]);
-  const int parity = ctx->host_T & 1;
+  // Slot rings repeat every lcm(kRawSlots, kColorSlots) estimates and every
+  // kPwSlots fused frames: a recorded graph is valid for that phase only.
+  const int parity = (ctx->host_T % 12) * kPwSlots + ctx->host_F % kPwSlots;
   GraphEntry *hit = nullptr;
   for (auto &ge : ctx->graphs)
     if (ge.n_frames == n_frames && ge.parity == parity && ge.prof == ctx->prof && ge.key == key) hit = &ge;
   if (!hit) {
-    // Record the sequence on the library's own stream, then replay on `s`.
-    const int T0 = ctx->host_T;
+    // Record the sequence on the library's own streams, then replay on `s`.
+    // Frame t runs its statistics and band pre-warp on pipe[0], its estimate
+    // on pipe[1] and its fuse on pipe[2]; event edges keep the order the slot
+    // rings need, so frame t+1's statistics overlap frame t's estimate and fuse.
+    const int T0 = ctx->host_T, F0 = ctx->host_F;
     cudaGraph_t graph = nullptr;
     GraphEntry ge;
     ge.prof = ctx->prof;
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture begin");
     ctx->prof_sink = &ge.pairs;
+    cudaStream_t sA = ctx->pipe[0], sB = ctx->pipe[1], sC = ctx->pipe[2];
+    cudaEvent_t (&ev)[4][8] = ctx->pev;
+    enum { kS = 0, kW = 1, kE = 2, kF = 3 };
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(cudaEventRecord(ev[kF][7], ctx->cap_stream));            // fork
+    chk(cudaStreamWaitEvent(sA, ev[kF][7], 0));
+    chk(cudaStreamWaitEvent(sB, ev[kF][7], 0));
+    chk(cudaStreamWaitEvent(sC, ev[kF][7], 0));
     int rc = STITCH_OK;
-    for (int t = 0; t < n_frames && rc == STITCH_OK; ++t) {
-      rc = launch_estimate_color(ctx, frames_dev + (size_t)t * n, ctx->cap_stream);
-      if (rc == STITCH_OK)
-        rc = launch_frame(ctx, frames_dev + (size_t)t * n, flow_ij_dev + (size_t)t * np,
-                          flow_ji_dev + (size_t)t * np, pano_dev[t], ctx->cap_stream);
+    for (int t = 0; t < n_frames && rc == STITCH_OK && e == cudaSuccess; ++t) {
+      const uint8_t *const *fr = frames_dev + (size_t)t * n;
+      const FuseParams fp = frame_params(ctx, fr, flow_ij_dev + (size_t)t * np, flow_ji_dev + (size_t)t * np,
+                                         pano_dev[t], T0 + t, F0 + t);
+      // statistics: slot (T0+t) % 3 was cleared by the estimate of frame t-2
+      if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kE][(t - 2) % 8], 0));
+      rc = launch_stats_for(ctx, fr, T0 + t, sA);
+      chk(cudaEventRecord(ev[kS][t % 8], sA));
+      // band pre-warp: its slot was last read by the fuse of frame t-2
+      if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kF][(t - 2) % 8], 0));
+      if (rc == STITCH_OK) rc = launch_prewarp_for(ctx, fp, sA);
+      chk(cudaEventRecord(ev[kW][t % 8], sA));
+      // estimate: after this frame's statistics; its colour slot was last read by fuse t-4
+      chk(cudaStreamWaitEvent(sB, ev[kS][t % 8], 0));
+      if (t >= 4) chk(cudaStreamWaitEvent(sB, ev[kF][(t - 4) % 8], 0));
+      if (rc == STITCH_OK) rc = launch_estimate_for(ctx, sB);
+      chk(cudaEventRecord(ev[kE][t % 8], sB));
+      // fuse: after this frame's estimate and pre-warp
+      chk(cudaStreamWaitEvent(sC, ev[kE][t % 8], 0));
+      chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
+      if (rc == STITCH_OK) rc = launch_fuse_for(ctx, fp, sC);
+      chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
+    // join
+    chk(cudaEventRecord(ev[kS][0], sA));
+    chk(cudaStreamWaitEvent(ctx->cap_stream, ev[kS][0], 0));
+    chk(cudaEventRecord(ev[kE][0], sB));
+    chk(cudaStreamWaitEvent(ctx->cap_stream, ev[kE][0], 0));
+    chk(cudaEventRecord(ev[kF][0], sC));
+    chk(cudaStreamWaitEvent(ctx->cap_stream, ev[kF][0], 0));
+    if (e != cudaSuccess && rc == STITCH_OK) rc = cuda_err(ctx, e, "graph capture");
     e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     ctx->prof_sink = nullptr;
     ctx->host_T = T0;                 // the capture launched nothing
+    ctx->host_F = F0;
     if (rc != STITCH_OK || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       for (auto &pp : ge.pairs) {
@@ -739,6 +863,7 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
   if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
   if (hit->prof) ctx->pending.insert(ctx->pending.end(), hit->pairs.begin(), hit->pairs.end());
   ctx->host_T += n_frames;
+  ctx->host_F += n_frames;
   return STITCH_OK;
 }
 
@@ -824,7 +949,7 @@ int stitch_get_color(stitch_ctx *ctx, double *M_out, float *curve_out, int *fram
     for (int k = 0; k < ctx->g.n; ++k)
       for (int i = 0; i < 9; ++i) M_out[k * 9 + i] = h->M_cam[k][i];
   if (curve_out) {
-    const Curve *cv = h->out[(h->T + 1) & 1].curve;
+    const Curve *cv = h->out[(h->T + kColorSlots - 1) % kColorSlots].curve;
     for (int c = 0; c < 3; ++c) std::memcpy(curve_out + c * STITCH_CURVE_FLOATS, &cv[c], sizeof(Curve));
   }
   if (frame_idx) *frame_idx = h->T;
@@ -853,7 +978,7 @@ int stitch_get_frame_stats(stitch_ctx *ctx, uint32_t *pooled, uint32_t *Hi, uint
   if (T < 1) return set_err(ctx, STITCH_EINVAL, "no frame has been estimated yet");
   const int np = ctx->g.n - 1;
   RawStats *h = new RawStats();
-  e = cudaMemcpy(h, ctx->raw + ((T - 1) & 1), sizeof(RawStats), cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(h, ctx->raw + ((T - 1) % kRawSlots), sizeof(RawStats), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     delete h;
     return cuda_err(ctx, e, "stats read");
@@ -920,7 +1045,7 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->state, static_cast<const char *>(buf) + sizeof(hd), sizeof(ColorState),
                    cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, 2 * sizeof(RawStats));
+  if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, kRawSlots * sizeof(RawStats));
   if (e != cudaSuccess) return cuda_err(ctx, e, "state write");
   ctx->host_T = hd.host_T;
   return STITCH_OK;
@@ -936,8 +1061,8 @@ int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count) {
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
-  double ms[3] = {0.0, 0.0, 0.0};
-  int cnt[3] = {0, 0, 0};
+  double ms[4] = {0.0, 0.0, 0.0, 0.0};
+  int cnt[4] = {0, 0, 0, 0};
   for (const ProfPair &pp : ctx->pending) {
     float t = 0.0f;
     e = cudaEventElapsedTime(&t, pp.a, pp.b);
@@ -951,7 +1076,7 @@ int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count) {
     cudaEventDestroy(pp.b);
   }
   ctx->owned.clear();
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     if (stage_ms) stage_ms[i] = ms[i];
     if (stage_count) stage_count[i] = cnt[i];
   }
@@ -979,9 +1104,16 @@ void stitch_destroy(stitch_ctx *ctx) {
     cudaEventDestroy(pp.b);
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (int i = 0; i < 3; ++i)
+    if (ctx->pipe[i]) cudaStreamDestroy(ctx->pipe[i]);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 8; ++b)
+      if (ctx->pev[a][b]) cudaEventDestroy(ctx->pev[a][b]);
   cudaFree(ctx->raw);
   cudaFree(ctx->state);
   cudaFree(ctx->tiles);
+  cudaFree(ctx->pw_tiles);
+  cudaFree(ctx->pw);
   for (int k = 0; k < kMaxCams; ++k) cudaFree(ctx->stage_frames[k]);
   for (int p = 0; p < kMaxPairs; ++p) {
     cudaFree(ctx->stage_fij[p]);

@@ -5,7 +5,7 @@
 // reference camera):
 //   * histogram specification of G_i onto G_j (step 3): L_c(v) is the
 //     smallest level u with CDF_j,c(u) * n_i >= CDF_i,c(v) * n_j, exact in
-//     64-bit integers (one thread per level, binary search);
+//     64-bit integers (binary search per level);
 //   * this frame's Eq. 3 terms A_T = I_i^T I_i and B_T = I_i^T L(I_i), B from
 //     the value-weighted histograms of the stats pass, exact in 64-bit
 //     integers, stored in a ring of the last STITCH_MAX_WINDOW frames;
@@ -17,30 +17,49 @@
 // convention of Eq. 4), the lambda-quantile knots of the pooled histogram are
 // found (exact integer test), averaged over the current and the last two
 // frames (Eq. 6-7) and turned into the piecewise curve's parameters (Eq. 5).
-// Finally the other raw-statistics slot is cleared for the next frame and the
-// frame index advances.
+// Finally the statistics slot of the previous frame is cleared for reuse and
+// the frame index advances.
+//
+// Layout of the work: 1024 threads. Every 256-level prefix sum is done by one
+// warp (8 levels per lane plus a shuffle scan), so all of a frame's scans run
+// at once; the B sums are one warp each as well. Only the float64 solves (one
+// thread per pair) and the short chain are serial.
 #include "stitch_internal.h"
 
 namespace stitch {
 
 namespace {
 
-constexpr int kT = kEstimateThreads;  // one thread per histogram level
-constexpr int kW = kT / 32;
+constexpr int kT = 1024;
+constexpr int kWarps = kT / 32;
+constexpr int kScanTasksMax = kMaxPairs * 6 + 3;
 
-__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v, unsigned long long *s_wt) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+struct EstSmem {
+  uint32_t cdf[kScanTasksMax][256];   // task q: pair q/6, side (q%6)/3 (0 = i, 1 = j), channel q%3; last 3: pooled
+  uint8_t L[kMaxPairs][3][256];
+  double M_pair[kMaxPairs][9];
+  double M_cam[kMaxCams][9];
+  int knot[3][2];
+  int sing;
+};
+
+// Inclusive prefix sum of 256 uint32 values by one warp (8 per lane).
+__device__ __forceinline__ void warp_scan256(const uint32_t *__restrict__ in, uint32_t *out) {
+  const int lane = threadIdx.x & 31;
+  const uint4 a = *reinterpret_cast<const uint4 *>(in + 8 * lane);
+  const uint4 b = *reinterpret_cast<const uint4 *>(in + 8 * lane + 4);
+  uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int k = 1; k < 8; ++k) v[k] += v[k - 1];
+  uint32_t run = v[7];
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
+    const uint32_t t = __shfl_up_sync(0xffffffffu, run, o);
+    if (lane >= o) run += t;
   }
-  if (lane == 31) s_wt[wid] = v;
-  __syncthreads();
-  unsigned long long add = 0ull;
-  for (int i = 0; i < wid; ++i) add += s_wt[i];
-  __syncthreads();
-  return v + add;
+  const uint32_t base = run - v[7];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out[8 * lane + k] = v[k] + base;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -94,84 +113,81 @@ __device__ bool solve3(const double A[9], const double B[9], double M[9]) {
   return true;
 }
 
-__device__ __forceinline__ void mat3_mul(const double *X, const double *Y, double *Z) {
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c)
-      Z[r * 3 + c] = X[r * 3 + 0] * Y[0 * 3 + c] + X[r * 3 + 1] * Y[1 * 3 + c] + X[r * 3 + 2] * Y[2 * 3 + c];
-}
-
 // (c, d) with c != d -> index into the value-weighted histograms
 __device__ __forceinline__ int w_index(int c, int d) { return c * 2 + (d > c ? d - 1 : d); }
 
 __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  EstSmem &sm = *reinterpret_cast<EstSmem *>(smem_raw);
   ColorState *S = P.state;
   const int T = S->T;
-  RawStats *raw = P.raw + (T & 1);
-  const int v = threadIdx.x;
-  const int lane = v & 31, wid = v >> 5;
+  RawStats *raw = P.raw + (T % P.raw_slots);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ring = T % kMaxWindow;
+  const int np = P.n_pairs;
+  const int n_scan = np * 6 + 3;
 
-  __shared__ unsigned long long s_ci[3][256];
-  __shared__ unsigned long long s_cj[3][256];
-  __shared__ int s_L[3][256];
-  __shared__ unsigned long long s_wt[kW];
-  __shared__ unsigned long long s_red[9][kW];
-  __shared__ int s_knot[3][2];
-  __shared__ int s_sing;
+  if (tid == 0) sm.sing = 0;
+  if (tid < np * 9) sm.M_pair[tid / 9][tid % 9] = S->M_pair[tid / 9][tid % 9];
 
-  if (v == 0) s_sing = 0;
-
-  for (int p = 0; p < P.n_pairs; ++p) {
-    for (int c = 0; c < 3; ++c) {
-      const unsigned long long ci = block_scan_u64(raw->Hi[p][c][v], s_wt);
-      const unsigned long long cj = block_scan_u64(raw->Hj[p][c][v], s_wt);
-      s_ci[c][v] = ci;
-      s_cj[c][v] = cj;
+  // 1. All prefix sums at once, one warp per histogram.
+  for (int q = warp; q < n_scan; q += kWarps) {
+    const uint32_t *src;
+    if (q < np * 6) {
+      const int p = q / 6, side = (q % 6) / 3, c = q % 3;
+      src = side == 0 ? raw->Hi[p][c] : raw->Hj[p][c];
+    } else {
+      src = raw->pooled[q - np * 6];
     }
-    __syncthreads();
-    const unsigned long long ni = s_ci[0][255], nj = s_cj[0][255];
-    for (int c = 0; c < 3; ++c) {
-      int L = v;
-      if (ni != 0ull && nj != 0ull) {
-        const unsigned long long need = s_ci[c][v] * nj;
-        int lo = 0, hi = 255;                 // smallest u with cdf_j[u] * ni >= need
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (s_cj[c][mid] * ni >= need) hi = mid; else lo = mid + 1;
-        }
-        L = lo;
-      }
-      s_L[c][v] = L;
-    }
-    __syncthreads();
-    unsigned long long part[9];
-    for (int c = 0; c < 3; ++c)
-      for (int d = 0; d < 3; ++d) {
-        const unsigned long long Ld = (unsigned long long)s_L[d][v];
-        part[c * 3 + d] = (c == d) ? Ld * (unsigned long long)v * raw->Hi[p][d][v]
-                                   : Ld * (unsigned long long)raw->Wv[p][w_index(c, d)][v];
-      }
-    for (int k = 0; k < 9; ++k) {
-      const unsigned long long s = warp_sum(part[k]);
-      if (lane == 0) s_red[k][wid] = s;
-    }
-    __syncthreads();
-    if (v < 9) {
-      unsigned long long s = 0ull;
-      for (int k = 0; k < kW; ++k) s += s_red[v][k];
-      S->B_ring[ring][p][v] = s;
-    }
-    if (v >= 16 && v < 22) S->A_ring[ring][p][v - 16] = raw->A[p][v - 16];
-    if (v == 32) {
-      S->n_ring[ring][p][0] = (int)ni;
-      S->n_ring[ring][p][1] = (int)nj;
-    }
-    __syncthreads();
+    warp_scan256(src, sm.cdf[q]);
   }
+  __syncthreads();
 
-  // Windowed solve, one thread per pair.
-  if (v < P.n_pairs) {
-    const int p = v;
+  // 2. Histogram specification of every pair and channel (binary search).
+  for (int i = tid; i < np * 3 * 256; i += kT) {
+    const int p = i / 768, c = (i / 256) % 3, v = i % 256;
+    const uint32_t *ci = sm.cdf[p * 6 + c];
+    const uint32_t *cj = sm.cdf[p * 6 + 3 + c];
+    const unsigned long long ni = ci[255], nj = cj[255];
+    int L = v;
+    if (ni != 0ull && nj != 0ull) {
+      const unsigned long long need = (unsigned long long)ci[v] * nj;
+      int lo = 0, hi = 255;                  // smallest u with cdf_j[u] * ni >= need
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((unsigned long long)cj[mid] * ni >= need) hi = mid; else lo = mid + 1;
+      }
+      L = lo;
+    }
+    sm.L[p][c][v] = (uint8_t)L;
+  }
+  __syncthreads();
+
+  // 3. This frame's B = sum_v L_d(v) W_cd(v) (c != d), sum_v L_d(v) v H_d(v) (c == d); one warp per entry.
+  for (int q = warp; q < np * 9; q += kWarps) {
+    const int p = q / 9, c = (q % 9) / 3, d = q % 3;
+    unsigned long long s = 0ull;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int v = 8 * lane + k;
+      const unsigned long long Ld = sm.L[p][d][v];
+      s += (c == d) ? Ld * (unsigned long long)v * raw->Hi[p][d][v]
+                    : Ld * (unsigned long long)raw->Wv[p][w_index(c, d)][v];
+    }
+    s = warp_sum(s);
+    if (lane == 0) S->B_ring[ring][p][c * 3 + d] = s;
+  }
+  if (tid < np * 6) S->A_ring[ring][tid / 6][tid % 6] = raw->A[tid / 6][tid % 6];
+  if (tid >= 512 && tid < 512 + np) {
+    const int p = tid - 512;
+    S->n_ring[ring][p][0] = (int)sm.cdf[p * 6][255];
+    S->n_ring[ring][p][1] = (int)sm.cdf[p * 6 + 3][255];
+  }
+  __syncthreads();
+
+  // 4. Windowed solve, one thread per pair.
+  if (tid < np) {
+    const int p = tid;
     const int nw = min(T + 1, P.window);
     unsigned long long As[6] = {0, 0, 0, 0, 0, 0}, Bs[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     bool empty = false;
@@ -186,54 +202,71 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
                          (double)As[2], (double)As[4], (double)As[5]};
     double B[9], M[9];
     for (int k = 0; k < 9; ++k) B[k] = (double)Bs[k];
-    const bool ok = !empty && solve3(A, B, M);
-    if (ok) {
-      for (int k = 0; k < 9; ++k) S->M_pair[p][k] = M[k];
+    if (!empty && solve3(A, B, M)) {
+      for (int k = 0; k < 9; ++k) sm.M_pair[p][k] = M[k];
     } else {
-      atomicOr(&s_sing, 1 << p);
+      atomicOr(&sm.sing, 1 << p);
     }
   }
-  __syncthreads();
-
-  // Chain the pair matrices to the reference camera.
-  if (v == 0) {
-    const int n = P.n_cams, r = P.ref;
-    for (int k = 0; k < 9; ++k) S->M_cam[r][k] = (k % 4 == 0) ? 1.0 : 0.0;
-    for (int k = r - 1; k >= 0; --k) mat3_mul(S->M_pair[k], S->M_cam[k + 1], S->M_cam[k]);
-    for (int k = r + 1; k < n; ++k) mat3_mul(S->M_pair[k - 1], S->M_cam[k - 1], S->M_cam[k]);
-    ColorOut &o = S->out[T & 1];
-    for (int k = 0; k < n; ++k)
-      for (int e = 0; e < 9; ++e) o.M[k][e] = (float)S->M_cam[k][e];
-    S->singular_last = s_sing;
-    if (s_sing) S->cond_word |= 1;
-  }
-
-  // Balance knots from the pooled histogram (exact integer quantile test).
-  for (int c = 0; c < 3; ++c) s_ci[c][v] = block_scan_u64(raw->pooled[c][v], s_wt);
-  __syncthreads();
+  // 5. Knots of the pooled histogram (exact integer quantile test).
   {
-    const unsigned long long N = s_ci[0][255];
+    const uint32_t *cp0 = sm.cdf[np * 6];
+    const unsigned long long N = cp0[255];
     const unsigned long long lo = (unsigned long long)P.lambda_q * N;
     const unsigned long long hi = (unsigned long long)(1000000 - P.lambda_q) * N;
-    for (int c = 0; c < 3; ++c) {
-      const unsigned long long cur = 1000000ull * s_ci[c][v];
-      const unsigned long long prev = v ? 1000000ull * s_ci[c][v - 1] : 0ull;
-      if (cur >= lo && (v == 0 || prev < lo)) s_knot[c][0] = v;
-      if (cur >= hi && (v == 0 || prev < hi)) s_knot[c][1] = v;
+    for (int i = tid; i < 3 * 256; i += kT) {
+      const int c = i / 256, v = i % 256;
+      const uint32_t *cp = sm.cdf[np * 6 + c];
+      const unsigned long long cur = 1000000ull * cp[v];
+      const unsigned long long prev = v ? 1000000ull * cp[v - 1] : 0ull;
+      if (cur >= lo && (v == 0 || prev < lo)) sm.knot[c][0] = v;
+      if (cur >= hi && (v == 0 || prev < hi)) sm.knot[c][1] = v;
     }
   }
   __syncthreads();
-  if (v < 3) {
-    const int c = v;
+
+  // 6. Chain to the reference camera (warp 0, one lane per matrix entry) and
+  //    the balance curve (warp 1, one lane per channel).
+  if (warp == 0) {
+    const int e = lane, r = e / 3, c = e % 3;
+    const int n = P.n_cams, ref = P.ref;
+    if (e < 9) sm.M_cam[ref][e] = (r == c) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int k = ref - 1; k >= 0; --k) {
+      if (e < 9)
+        sm.M_cam[k][e] = sm.M_pair[k][r * 3 + 0] * sm.M_cam[k + 1][0 * 3 + c] +
+                         sm.M_pair[k][r * 3 + 1] * sm.M_cam[k + 1][1 * 3 + c] +
+                         sm.M_pair[k][r * 3 + 2] * sm.M_cam[k + 1][2 * 3 + c];
+      __syncwarp();
+    }
+    for (int k = ref + 1; k < n; ++k) {
+      if (e < 9)
+        sm.M_cam[k][e] = sm.M_pair[k - 1][r * 3 + 0] * sm.M_cam[k - 1][0 * 3 + c] +
+                         sm.M_pair[k - 1][r * 3 + 1] * sm.M_cam[k - 1][1 * 3 + c] +
+                         sm.M_pair[k - 1][r * 3 + 2] * sm.M_cam[k - 1][2 * 3 + c];
+      __syncwarp();
+    }
+    ColorOut &o = S->out[T % kColorSlots];
+    for (int i = lane; i < n * 9; i += 32) {
+      S->M_cam[i / 9][i % 9] = sm.M_cam[i / 9][i % 9];
+      o.M[i / 9][i % 9] = (float)sm.M_cam[i / 9][i % 9];
+    }
+    for (int i = lane; i < np * 9; i += 32) S->M_pair[i / 9][i % 9] = sm.M_pair[i / 9][i % 9];
+    if (lane == 0) {
+      S->singular_last = sm.sing;
+      if (sm.sing) S->cond_word |= 1;
+    }
+  } else if (warp == 1 && lane < 3) {
+    const int c = lane;
     const int slot = T % kSmoothFrames;
-    S->knots[slot][c][0] = s_knot[c][0];
-    S->knots[slot][c][1] = s_knot[c][1];
+    S->knots[slot][c][0] = sm.knot[c][0];
+    S->knots[slot][c][1] = sm.knot[c][1];
     const int cnt = min(T + 1, kSmoothFrames);
     long long s1 = 0, s2 = 0;
     for (int i = cnt - 1; i >= 0; --i) {
       const int sl = (T - i) % kSmoothFrames;
-      s1 += S->knots[sl][c][0];
-      s2 += S->knots[sl][c][1];
+      s1 += (sl == slot) ? sm.knot[c][0] : S->knots[sl][c][0];
+      s2 += (sl == slot) ? sm.knot[c][1] : S->knots[sl][c][1];
     }
     const double m1 = (double)s1 / (double)cnt;
     const double m2 = (double)s2 / (double)cnt;
@@ -257,23 +290,30 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
     cv.inv_m1 = m1 > 0.0 ? (float)(1.0 / m1) : 0.0f;
     cv.inv_bm = m2 < 255.0 ? (float)(1.0 / (255.0 - m2)) : 0.0f;
     cv.ident = ident ? 1.0f : 0.0f;
-    S->out[T & 1].curve[c] = cv;
-  }
-
-  // Clear the other raw slot: the stats pass of frame T + 1 accumulates into it.
-  {
-    uint32_t *z = reinterpret_cast<uint32_t *>(P.raw + ((T + 1) & 1));
-    const int words = (int)(sizeof(RawStats) / 4);
-    for (int i = v; i < words; i += kT) z[i] = 0u;
+    S->out[T % kColorSlots].curve[c] = cv;
+  } else if (warp >= 2) {
+    // 7. Clear the slot of frame T - 1 (already consumed): the stats pass of
+    //    frame T + raw_slots - 1 accumulates into it. Warps 2..31 only, so the
+    //    index tid - 64 starts at 0.
+    uint4 *z = reinterpret_cast<uint4 *>(P.raw + ((T + P.raw_slots - 1) % P.raw_slots));
+    const int n16 = (int)(sizeof(RawStats) / 16);
+    for (int i = tid - 64; i < n16; i += kT - 64) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
-  if (v == 0) S->T = T + 1;
+  if (tid == 0) S->T = T + 1;
 }
 
 }  // namespace
 
+// Once per device, outside any stream capture: the block uses ~53 KB of
+// dynamic shared memory.
+cudaError_t estimate_setup() {
+  return cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EstSmem));
+}
+
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s) {
-  k_estimate<<<1, kEstimateThreads, 0, s>>>(p);
+  static_assert(sizeof(RawStats) % 16 == 0, "raw statistics must be a whole number of 16-byte words");
+  k_estimate<<<1, kT, sizeof(EstSmem), s>>>(p);
   return cudaGetLastError();
 }
 

@@ -1,31 +1,38 @@
-// K3 -- fused pre-warp, local warping, colour transfer, blend and balance
+// K3 -- pre-warp, local warping, colour transfer, blend and balance
 // (paper section 3.1 pre-warp; section 3.2 Eq. 15-18; Eq. 4; Eq. 5).
 //
-// The panorama is cut into 64 x 16 tiles; each thread produces 4 consecutive
-// pixels of one row and writes them as one 4-byte store per colour plane.
+// Two kernels per frame:
 //
-// Own tiles (columns that belong to one camera k only): s = H_k^-1 q in
-// float32 relative to the camera's panorama origin, coverage test
-// 0 <= s <= (w-1, h-1), bilinear sample of the packed-RGB source (taps at
-// floor(s), floor(s)+1, far tap clamped), v = P . M_k. A pixel camera k does
-// not cover falls back to camera k-1, then k+1 (Eq. 15's one-image cases),
-// else it is 0.
+// k_prewarp_band: the pre-warped image of section 3.1 over each pair's blend
+//   band, for BOTH cameras of the pair, computed once per band pixel and kept
+//   in a small intermediate (float32 RGB, or float16 with
+//   STITCH_FP16_INTERMEDIATE). It does not depend on the colour estimate.
 //
-// Band tiles (columns of a pair's blend band): the tile's part of the band
-// rectangle, widened by the flow halo and clipped to the band, is pre-warped
-// for BOTH cameras into shared memory with M already applied (the pre-warped
-// image of section 3.1, stored as float32, or float16 with
-// STITCH_FP16_INTERMEDIATE). Each band pixel then computes
-//   theta_j = (x - x0 + 0.5) / (x1 - x0), theta_i = 1 - theta_j (Eq. 16 read
-//   as a ramp), X_i = q + theta_j clamp(flow_ij), X_j = q + theta_i
-//   clamp(flow_ji) (Eq. 17, continuous reading; the printed weights under
-//   STITCH_FLOW_WEIGHTS_PRINTED), clamps X into the band and samples the
-//   staged tile bilinearly (Eq. 18): out = theta_i P_i(X_i) + theta_j P_j(X_j).
-// Pixels of the band columns outside the band rows blend both cameras without
-// flow where both cover them, else take the one that does.
+// k_fuse: one block per 64 x 16 panorama tile.
+//   * Own tiles (columns of one camera k): the source window that the tile
+//     maps to through H_k^-1 is staged in shared memory as one RGBX word per
+//     pixel; every pixel then computes s = H_k^-1 q (float32, relative to the
+//     camera's panorama origin), tests coverage 0 <= s <= (w-1, h-1), reads its
+//     four bilinear taps from shared memory and forms v = P . M_k. Pixels that
+//     camera k does not cover fall back to k-1, then k+1 (Eq. 15's one-image
+//     cases), else 0.
+//   * Band tiles: pixels of the band rectangle compute
+//       theta_j = (x - x0 + 0.5) / (x1 - x0), theta_i = 1 - theta_j (Eq. 16 read
+//       as a ramp), X_i = q + theta_j clamp(flow_ij), X_j = q + theta_i
+//       clamp(flow_ji) (Eq. 17, continuous reading; the printed weights under
+//       STITCH_FLOW_WEIGHTS_PRINTED), clamp X into the band and sample the
+//       pre-warped intermediate bilinearly (Eq. 18):
+//       out = theta_i P_i(X_i) M_i + theta_j P_j(X_j) M_j.
+//     The tile's other pixels (own columns beside the band, band columns
+//     outside the band rows) use the staged windows of both cameras as above,
+//     blending both cameras without flow where both cover a band-column pixel.
+//   * Each channel is clamped to [0, 255], passed through the piecewise balance
+//     curve F (Eq. 5: gamma, linear, gamma) and rounded half to even; pixels
+//     go to a shared-memory tile and leave as 16-byte stores per plane.
 //
-// Finally each channel is clamped to [0, 255], passed through the piecewise
-// balance curve F (Eq. 5: gamma, linear, gamma) and rounded half to even.
+// Thread mapping: warp w, lane l handles the pixels (l + 32 a, 2 w + b),
+// a, b in {0, 1}, so a warp touches 32 consecutive pixels of a row at a time
+// and its shared-memory tap reads fall in distinct banks.
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -34,32 +41,68 @@ namespace stitch {
 
 namespace {
 
-struct Region {
-  int x0, y0, w, h;
-};
+constexpr float kMagicRound = 12582912.0f;   // 1.5 * 2^23: x + kMagicRound rounds x to an integer (RNE)
+constexpr int kMagicRoundBits = 0x4B400000;
+constexpr float kMagicByte = 8388608.0f;     // 2^23: the float with bits 0x4B0000bb is 2^23 + bb
+constexpr int kWinCap = 3072;                // staged source pixels per window (12 KB)
 
-__device__ __forceinline__ bool cam_map(const CamDev &c, int x, int y, float &sx, float &sy) {
-  const float dx = (float)(x - c.ox);
-  const float dy = (float)(y - c.oy);
+// Approximate reciprocal (CUDA's fast division intrinsic: a few ulp).
+__device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
+
+// s = H^-1 q for panorama point (x, y) given as floats relative to the origin.
+__device__ __forceinline__ void cam_map_f(const CamDev &c, float dx, float dy, float &sx, float &sy, float &nw) {
   const float nx = fmaf(c.h[0], dx, fmaf(c.h[1], dy, c.h[2]));
   const float ny = fmaf(c.h[3], dx, fmaf(c.h[4], dy, c.h[5]));
-  const float nw = fmaf(c.h[6], dx, fmaf(c.h[7], dy, c.h[8]));
-  const float r = 1.0f / nw;
+  nw = fmaf(c.h[6], dx, fmaf(c.h[7], dy, c.h[8]));
+  const float r = rcp_approx(nw);
   sx = nx * r;
   sy = ny * r;
+}
+
+__device__ __forceinline__ bool covered(const CamDev &c, float sx, float sy, float nw) {
   return nw > 0.0f && sx >= 0.0f && sx <= c.wm1 && sy >= 0.0f && sy <= c.hm1;
+}
+
+// Integer part and fraction of s with fraction in [0, 1]; for integer s the
+// pair (s - 1, 1) may come back instead of (s, 0): both give the same bilinear
+// sample, and the right-hand tap then never passes the last row / column.
+__device__ __forceinline__ void split(float s, int &i, float &f) {
+  const float r = (s - 0.5f) + kMagicRound;
+  i = __float_as_int(r) - kMagicRoundBits;
+  f = s - (r - kMagicRound);
+}
+
+// Channel c (0..2) of an RGBX word as 2^23 + value (exact).
+__device__ __forceinline__ float mbyte(uint32_t w, int c) {
+  return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + c));
+}
+
+// Bilinear of four RGBX words with fractions (fx, fy): (1-fy)((1-fx) a + fx b) + fy((1-fx) d + fx e).
+__device__ __forceinline__ float3 bilerp_words(uint32_t a, uint32_t b, uint32_t d, uint32_t e, float fx, float fy) {
+  float o[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float A = mbyte(a, c), B = mbyte(b, c), D = mbyte(d, c), E = mbyte(e, c);
+    const float top = fmaf(fx, B - A, A - kMagicByte);
+    const float bot = fmaf(fx, E - D, D - kMagicByte);
+    o[c] = fmaf(fy, bot - top, top);
+  }
+  return make_float3(o[0], o[1], o[2]);
 }
 
 __device__ __forceinline__ float3 load_rgb(const uint8_t *__restrict__ p) {
   return make_float3((float)__ldg(p), (float)__ldg(p + 1), (float)__ldg(p + 2));
 }
 
-// Bilinear sample of a packed-RGB frame at (sx, sy), assumed inside the frame.
-__device__ __forceinline__ float3 src_bilinear(const uint8_t *__restrict__ src, const CamDev &c,
-                                               float sx, float sy) {
-  const float fx0 = floorf(sx), fy0 = floorf(sy);
-  const float fx = sx - fx0, fy = sy - fy0;
-  const int ix = (int)fx0, iy = (int)fy0;
+// Bilinear sample of a packed-RGB frame in global memory at (sx, sy) inside
+// the frame (the general path, used where no staged window applies).
+__device__ __forceinline__ float3 src_bilinear(const uint8_t *__restrict__ src, const CamDev &c, float sx, float sy) {
+  int ix, iy;
+  float fx, fy;
+  split(sx, ix, fx);
+  split(sy, iy, fy);
+  ix = min(max(ix, 0), c.w - 1);
+  iy = min(max(iy, 0), c.h_px - 1);
   const int ix1 = min(ix + 1, c.w - 1), iy1 = min(iy + 1, c.h_px - 1);
   const uint8_t *r0 = src + (size_t)iy * c.pitch;
   const uint8_t *r1 = src + (size_t)iy1 * c.pitch;
@@ -81,83 +124,273 @@ __device__ __forceinline__ float3 mulM(const float *M, float3 v) {
   return o;
 }
 
-__device__ __forceinline__ bool cam_value(const FuseParams &P, const ColorOut &col, int k, int x, int y,
-                                          float3 &v) {
-  float sx, sy;
-  if (!cam_map(P.cam[k], x, y, sx, sy)) return false;
-  v = mulM(col.M[k], src_bilinear(P.src[k], P.cam[k], sx, sy));
+// ---------------------------------------------------------------------------
+// Source windows in shared memory.
+// ---------------------------------------------------------------------------
+
+struct Window {
+  int x0, y0, w, h, stride, ok;
+};
+
+// Source window of the panorama rectangle [rx0, rx1] x [ry0, ry1] (inclusive)
+// in camera c: the bounding box of the mapped corners plus one pixel of margin
+// and the right / bottom tap, clipped to the frame. Computed by one warp (lane
+// & 3 picks a corner); every lane returns the same window. ok = 0 when a corner
+// maps behind the camera, the box is empty or it exceeds the capacity.
+__device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry1) {
+  const int k = threadIdx.x & 3;
+  const int px = (k & 1) ? rx1 : rx0;
+  const int py = (k & 2) ? ry1 : ry0;
+  float sx, sy, nw;
+  cam_map_f(c, (float)(px - c.ox), (float)(py - c.oy), sx, sy, nw);
+  int front = (nw > 0.0f && sx == sx && sy == sy) ? 1 : 0;
+  float lo_x = sx, hi_x = sx, lo_y = sy, hi_y = sy;
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+    hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+    lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+    hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+    front &= __shfl_xor_sync(0xffffffffu, front, o);
+  }
+  lo_x = fmaxf(lo_x, -4.0f);
+  lo_y = fmaxf(lo_y, -4.0f);
+  hi_x = fminf(hi_x, c.wm1 + 4.0f);
+  hi_y = fminf(hi_y, c.hm1 + 4.0f);
+  Window W;
+  W.x0 = max(0, (int)floorf(lo_x) - 1);
+  W.y0 = max(0, (int)floorf(lo_y) - 1);
+  const int x1 = min(c.w - 1, (int)floorf(hi_x) + 2);
+  const int y1 = min(c.h_px - 1, (int)floorf(hi_y) + 2);
+  W.w = x1 - W.x0 + 1;
+  W.h = y1 - W.y0 + 1;
+  W.stride = (W.w + 3) & ~3;
+  W.ok = (front && W.w >= 2 && W.h >= 2 && W.stride * W.h <= kWinCap) ? 1 : 0;
+  return W;
+}
+
+__device__ __forceinline__ Window no_window() {
+  Window W;
+  W.x0 = W.y0 = W.w = W.h = W.stride = W.ok = 0;
+  return W;
+}
+
+// Stage the window as RGBX words: four pixels (12 bytes) per step, read as
+// aligned 32-bit words and realigned with funnel shifts.
+__device__ void stage_window(const uint8_t *__restrict__ src, const CamDev &c, const Window &W, uint32_t *s) {
+  const int G = W.stride >> 2;
+  const uintptr_t end = reinterpret_cast<uintptr_t>(src) + (uintptr_t)c.pitch * (uintptr_t)(c.h_px - 1) +
+                        (uintptr_t)(3 * c.w);
+  const int nt = blockDim.x;
+  const bool rows = G <= nt;
+  const int rpi = rows ? nt / G : 0;
+  if (rows && (int)threadIdx.x >= rpi * G) return;
+  int r = rows ? (int)threadIdx.x / G : 0;
+  int g = rows ? (int)threadIdx.x - r * G : 0;
+  int i = threadIdx.x;
+  while (true) {
+    if (!rows) {
+      if (i >= G * W.h) break;
+      r = i / G;
+      g = i - r * G;
+    } else if (r >= W.h) {
+      break;
+    }
+    const int px = W.x0 + 4 * g;
+    const uint8_t *b = src + (size_t)(W.y0 + r) * c.pitch + 3 * px;
+    const uintptr_t B = reinterpret_cast<uintptr_t>(b);
+    const uintptr_t A = B & ~(uintptr_t)3;
+    uint32_t p0, p1, p2, p3;
+    if (px + 4 <= c.w && A + 16 <= end) {
+      const uint32_t *wp = reinterpret_cast<const uint32_t *>(A);
+      const uint32_t w0 = __ldg(wp), w1 = __ldg(wp + 1), w2 = __ldg(wp + 2), w3 = __ldg(wp + 3);
+      const uint32_t sh = (uint32_t)(B - A) * 8u;
+      const uint32_t q0 = __funnelshift_r(w0, w1, sh);
+      const uint32_t q1 = __funnelshift_r(w1, w2, sh);
+      const uint32_t q2 = __funnelshift_r(w2, w3, sh);
+      p0 = __byte_perm(q0, 0u, 0x4210u);
+      p1 = __byte_perm(q0, q1, 0x4543u);
+      p2 = __byte_perm(q1, q2, 0x4432u);
+      p3 = __byte_perm(q2, 0u, 0x4321u);
+    } else {
+      uint32_t q[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (px + k < c.w)
+          q[k] = (uint32_t)__ldg(b + 3 * k) | ((uint32_t)__ldg(b + 3 * k + 1) << 8) |
+                 ((uint32_t)__ldg(b + 3 * k + 2) << 16);
+      p0 = q[0]; p1 = q[1]; p2 = q[2]; p3 = q[3];
+    }
+    *reinterpret_cast<uint4 *>(s + r * W.stride + 4 * g) = make_uint4(p0, p1, p2, p3);
+    if (rows) r += rpi; else i += nt;
+  }
+}
+
+// Bilinear sample from a staged window (taps clamped into the window).
+__device__ __forceinline__ float3 win_bilinear(const uint32_t *s, const Window &W, float sx, float sy) {
+  int ix, iy;
+  float fx, fy;
+  split(sx, ix, fx);
+  split(sy, iy, fy);
+  int lx = ix - W.x0, ly = iy - W.y0;
+  // A sample exactly on the window's last column / row, (last, 0), is the
+  // same as (last - 1, 1); the clamps below only guard memory.
+  if (lx > W.w - 2) { lx = W.w - 2; fx = 1.0f; }
+  if (ly > W.h - 2) { ly = W.h - 2; fy = 1.0f; }
+  lx = max(lx, 0);
+  ly = max(ly, 0);
+  const uint32_t *p = s + ly * W.stride + lx;
+  return bilerp_words(p[0], p[1], p[W.stride], p[W.stride + 1], fx, fy);
+}
+
+// ---------------------------------------------------------------------------
+// Colour and balance, prepared once per block.
+// ---------------------------------------------------------------------------
+
+struct Tail {       // gamma tails of Eq. 5 on u = v / 255
+  float d1, k1, g1; // dark:   F = d1 (u k1)^g1
+  float e2, k2, g2; // bright: F = 255 - e2 ((1 - u) k2)^g2
+};
+
+struct BlockColor {
+  float M[kMaxCams][9];   // M / 255, so fused values land in [0, 1]
+  float lo[3], hi[3];     // knots m1/255, m2/255 (outside [0, 1] when there is no tail)
+  float A[3], B[3];       // linear part F = A + B u
+  Tail tail[3];
+};
+
+__device__ void load_block_color(const FuseParams &P, BlockColor &bc) {
+  const int t = threadIdx.x;
+  if (t < kMaxCams * 9) bc.M[t / 9][t % 9] = P.color->M[t / 9][t % 9] * (1.0f / 255.0f);
+  if (t >= 96 && t < 99) {
+    const int c = t - 96;
+    const Curve cv = P.color->curve[c];
+    if ((P.flags & STITCH_BALANCE_OFF) || cv.ident != 0.0f) {
+      bc.lo[c] = -1.0f;
+      bc.hi[c] = 2.0f;
+      bc.A[c] = 0.0f;
+      bc.B[c] = 255.0f;
+    } else {
+      bc.lo[c] = cv.m1 * (1.0f / 255.0f);
+      bc.hi[c] = cv.m2 * (1.0f / 255.0f);
+      bc.A[c] = cv.d1 - cv.s * cv.m1;
+      bc.B[c] = 255.0f * cv.s;
+    }
+    Tail tl;
+    tl.d1 = cv.d1;
+    tl.k1 = 255.0f * cv.inv_m1;
+    tl.g1 = cv.g1;
+    tl.e2 = 255.0f - cv.d2;
+    tl.k2 = 255.0f * cv.inv_bm;
+    tl.g2 = cv.g2;
+    bc.tail[c] = tl;
+  }
+}
+
+// Hot per-channel balance parameters, kept in registers.
+struct Hot {
+  float lo[3], hi[3], A[3], B[3];
+};
+
+__device__ __forceinline__ Hot load_hot(const BlockColor &bc) {
+  Hot h;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h.lo[c] = bc.lo[c];
+    h.hi[c] = bc.hi[c];
+    h.A[c] = bc.A[c];
+    h.B[c] = bc.B[c];
+  }
+  return h;
+}
+
+// One channel: clamp (saturate), balance (Eq. 5), round half to even; the low
+// byte of the result is the output byte.
+__device__ __forceinline__ uint32_t finish(const Hot &h, const BlockColor &bc, int c, float v) {
+  const float u = __saturatef(v);
+  float F = fmaf(h.B[c], u, h.A[c]);
+  if (u < h.lo[c]) {
+    const Tail &t = bc.tail[c];
+    F = t.d1 * __powf(u * t.k1, t.g1);
+  } else if (u > h.hi[c]) {
+    const Tail &t = bc.tail[c];
+    F = 255.0f - t.e2 * __powf((1.0f - u) * t.k2, t.g2);
+  }
+  return (uint32_t)__float_as_int(F + kMagicRound);
+}
+
+__device__ __forceinline__ void load_M(const BlockColor &bc, int k, float (&M)[9]) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) M[e] = bc.M[k][e];
+}
+
+// ---------------------------------------------------------------------------
+// Per-pixel general paths (global memory).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool cam_value_g(const FuseParams &P, const BlockColor &bc, int k, int x, int y,
+                                            float3 &v) {
+  const CamDev &c = P.cam[k];
+  float sx, sy, nw;
+  cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
+  if (!covered(c, sx, sy, nw)) return false;
+  v = mulM(bc.M[k], src_bilinear(P.src[k], c, sx, sy));
   return true;
 }
 
-__device__ __forceinline__ bool own_value(const FuseParams &P, const ColorOut &col, int k, int x, int y,
-                                          float3 &v) {
-  if (cam_value(P, col, k, x, y, v)) return true;
-  if (k > 0 && cam_value(P, col, k - 1, x, y, v)) return true;
-  if (k < P.n_cams - 1 && cam_value(P, col, k + 1, x, y, v)) return true;
-  return false;
-}
-
-// Band columns outside the band rows: Eq. 15 without flow.
-__device__ __forceinline__ bool sliver_value(const FuseParams &P, const ColorOut &col, int p, int x, int y,
-                                             float3 &v) {
-  float3 va, vb;
-  const bool ca = cam_value(P, col, p, x, y, va);
-  const bool cb = cam_value(P, col, p + 1, x, y, vb);
-  if (ca && cb) {
-    const float tb = ((float)(x - P.band[p].x0) + 0.5f) * P.band[p].inv_bw;
-    const float ta = 1.0f - tb;
-    v = make_float3(ta * va.x + tb * vb.x, ta * va.y + tb * vb.y, ta * va.z + tb * vb.z);
-    return true;
-  }
-  if (ca) { v = va; return true; }
-  if (cb) { v = vb; return true; }
-  return false;
-}
-
-__device__ __forceinline__ float balance(const Curve &cv, float x) {
-  if (cv.ident != 0.0f) return x;
-  if (x < cv.m1) return cv.d1 * __powf(x * cv.inv_m1, cv.g1);
-  if (x > cv.m2) return 255.0f - (255.0f - cv.d2) * __powf((255.0f - x) * cv.inv_bm, cv.g2);
-  return fmaf(cv.s, x - cv.m1, cv.d1);
-}
-
-__device__ __forceinline__ uint32_t to_u8(const Curve &cv, bool bal, float x) {
-  x = fminf(fmaxf(x, 0.0f), 255.0f);
-  if (bal) x = balance(cv, x);
-  const int r = __float2int_rn(x);
-  return (uint32_t)min(max(r, 0), 255);
+// Camera k's value at q, from its staged window when there is one.
+__device__ __forceinline__ bool cam_value_w(const FuseParams &P, const float (&M)[9], int k, const Window &W,
+                                            const uint32_t *s, int x, int y, float3 &v) {
+  const CamDev &c = P.cam[k];
+  float sx, sy, nw;
+  cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
+  if (!covered(c, sx, sy, nw)) return false;
+  v = mulM(M, W.ok ? win_bilinear(s, W, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
+  return true;
 }
 
 template <bool kHalf>
-struct StageT;
+struct PwT;
 template <>
-struct StageT<false> {
-  using T = float;
-  __device__ static void put(float *s, int i, float3 v) { s[3 * i] = v.x; s[3 * i + 1] = v.y; s[3 * i + 2] = v.z; }
-  __device__ static float3 get(const float *s, int i) { return make_float3(s[3 * i], s[3 * i + 1], s[3 * i + 2]); }
+struct PwT<false> {
+  using T = float4;
+  __device__ static void put(float4 *p, size_t i, float3 v) { p[i] = make_float4(v.x, v.y, v.z, 0.0f); }
+  __device__ static float3 get(const float4 *p, size_t i) {
+    const float4 q = __ldg(p + i);
+    return make_float3(q.x, q.y, q.z);
+  }
 };
 template <>
-struct StageT<true> {
-  using T = __half;
-  __device__ static void put(__half *s, int i, float3 v) {
-    s[3 * i] = __float2half_rn(v.x); s[3 * i + 1] = __float2half_rn(v.y); s[3 * i + 2] = __float2half_rn(v.z);
+struct PwT<true> {
+  using T = uint2;   // four halves
+  __device__ static void put(uint2 *p, size_t i, float3 v) {
+    const __half2 a = __floats2half2_rn(v.x, v.y);
+    const __half2 b = __floats2half2_rn(v.z, 0.0f);
+    p[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&a), *reinterpret_cast<const uint32_t *>(&b));
   }
-  __device__ static float3 get(const __half *s, int i) {
-    return make_float3(__half2float(s[3 * i]), __half2float(s[3 * i + 1]), __half2float(s[3 * i + 2]));
+  __device__ static float3 get(const uint2 *p, size_t i) {
+    const uint2 q = __ldg(p + i);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    return make_float3(a.x, a.y, b.x);
   }
 };
 
+// Bilinear sample of a band's pre-warped intermediate at X (already inside the band).
 template <bool kHalf>
-__device__ __forceinline__ float3 staged_bilinear(const typename StageT<kHalf>::T *s, const Region &R,
-                                                  const BandDev &B, float X, float Y) {
-  const float jx = floorf(X), jy = floorf(Y);
-  const float gx = X - jx, gy = Y - jy;
-  const int ix = (int)jx, iy = (int)jy;
-  const int ix1 = min(ix + 1, B.x1 - 1), iy1 = min(iy + 1, B.y1 - 1);
-  const int lx0 = min(max(ix - R.x0, 0), R.w - 1), lx1 = min(max(ix1 - R.x0, 0), R.w - 1);
-  const int ly0 = min(max(iy - R.y0, 0), R.h - 1), ly1 = min(max(iy1 - R.y0, 0), R.h - 1);
-  const float3 a = StageT<kHalf>::get(s, ly0 * R.w + lx0), b = StageT<kHalf>::get(s, ly0 * R.w + lx1);
-  const float3 d = StageT<kHalf>::get(s, ly1 * R.w + lx0), e = StageT<kHalf>::get(s, ly1 * R.w + lx1);
+__device__ __forceinline__ float3 pw_bilinear(const typename PwT<kHalf>::T *pw, const BandDev &B, float X, float Y) {
+  int ix, iy;
+  float gx, gy;
+  split(X, ix, gx);
+  split(Y, iy, gy);
+  // X == x0 (odd) may come back as (x0 - 1, 1): take the tap at x0 instead.
+  if (ix < B.x0) { ix = B.x0; gx = 0.0f; }
+  if (iy < B.y0) { iy = B.y0; gy = 0.0f; }
+  const int bw = B.x1 - B.x0, bh = B.y1 - B.y0;
+  const int lx = min(ix - B.x0, bw - 1), ly = min(iy - B.y0, bh - 1);
+  const int lx1 = min(lx + 1, bw - 1), ly1 = min(ly + 1, bh - 1);
+  const float3 a = PwT<kHalf>::get(pw, (size_t)ly * bw + lx), b = PwT<kHalf>::get(pw, (size_t)ly * bw + lx1);
+  const float3 d = PwT<kHalf>::get(pw, (size_t)ly1 * bw + lx), e = PwT<kHalf>::get(pw, (size_t)ly1 * bw + lx1);
   float3 t, u, o;
   t.x = fmaf(gx, b.x - a.x, a.x); t.y = fmaf(gx, b.y - a.y, a.y); t.z = fmaf(gx, b.z - a.z, a.z);
   u.x = fmaf(gx, e.x - d.x, d.x); u.y = fmaf(gx, e.y - d.y, d.y); u.z = fmaf(gx, e.z - d.z, d.z);
@@ -165,167 +398,240 @@ __device__ __forceinline__ float3 staged_bilinear(const typename StageT<kHalf>::
   return o;
 }
 
-__device__ __forceinline__ void store4(const FuseParams &P, int x, int y, const uint32_t (&o)[3]) {
-  if (x >= P.pano_pitch || y >= P.pano_h) return;
-  const size_t plane = (size_t)P.pano_pitch * P.pano_h;
-  uint8_t *base = P.out + (size_t)y * P.pano_pitch + x;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) *reinterpret_cast<uint32_t *>(base + c * plane) = o[c];
+__device__ __forceinline__ void put_px(uint8_t (*s_out)[kTileH][kTileW], int lx, int ly, const Hot &h,
+                                       const BlockColor &bc, bool cov, float3 v) {
+  uint32_t o0 = 0u, o1 = 0u, o2 = 0u;
+  if (cov) {
+    o0 = finish(h, bc, 0, v.x);
+    o1 = finish(h, bc, 1, v.y);
+    o2 = finish(h, bc, 2, v.z);
+  }
+  s_out[0][ly][lx] = (uint8_t)o0;
+  s_out[1][ly][lx] = (uint8_t)o1;
+  s_out[2][ly][lx] = (uint8_t)o2;
 }
 
-__device__ __forceinline__ void load_color(const FuseParams &P, ColorOut &s_col) {
-  const int n = (int)(sizeof(ColorOut) / 4);
-  const uint32_t *src = reinterpret_cast<const uint32_t *>(P.color);
-  uint32_t *dst = reinterpret_cast<uint32_t *>(&s_col);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-}
-
-__global__ void __launch_bounds__(kFuseThreads) k_fuse_own(const FuseParams P, int tile0) {
-  __shared__ ColorOut s_col;
-  load_color(P, s_col);
-  __syncthreads();
-  const TileDesc t = P.tiles[tile0 + blockIdx.x];
-  const int k = t.idx;
-  const int x = t.tx * kTileW + (threadIdx.x & 15) * 4;
-  const int y = t.ty * kTileH + (threadIdx.x >> 4);
-  const bool bal = !(P.flags & STITCH_BALANCE_OFF);
-  uint32_t o[3] = {0u, 0u, 0u};
-  if (y < P.pano_h) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int xi = x + i;
-      float3 v;
-      if (xi < P.pano_w && own_value(P, s_col, k, xi, y, v)) {
-        o[0] |= to_u8(s_col.curve[0], bal, v.x) << (8 * i);
-        o[1] |= to_u8(s_col.curve[1], bal, v.y) << (8 * i);
-        o[2] |= to_u8(s_col.curve[2], bal, v.z) << (8 * i);
-      }
-    }
-  }
-  store4(P, x, y, o);
-}
-
-template <bool kHalf>
-__global__ void __launch_bounds__(kFuseThreads) k_fuse_band(const FuseParams P, int tile0) {
-  using ST = typename StageT<kHalf>::T;
-  __shared__ ColorOut s_col;
-  extern __shared__ __align__(16) unsigned char s_raw[];
-  load_color(P, s_col);
-  const TileDesc t = P.tiles[tile0 + blockIdx.x];
-  const int p = t.idx;
-  const BandDev B = P.band[p];
-  const int tx0 = t.tx * kTileW, ty0 = t.ty * kTileH;
-  Region R;
-  R.x0 = max(B.x0, tx0 - P.halo);
-  R.y0 = max(B.y0, ty0 - P.halo);
-  R.w = min(B.x1, tx0 + kTileW + P.halo) - R.x0;
-  R.h = min(B.y1, ty0 + kTileH + P.halo) - R.y0;
-  const bool staged = R.w > 0 && R.h > 0 && tx0 < B.x1 && tx0 + kTileW > B.x0 && ty0 < B.y1 &&
-                      ty0 + kTileH > B.y0;
-  ST *sA = reinterpret_cast<ST *>(s_raw);
-  ST *sB = sA + (staged ? 3 * R.w * R.h : 0);
-  __syncthreads();
-  if (staged) {
-    const CamDev &ca = P.cam[p];
-    const CamDev &cb = P.cam[p + 1];
-    for (int i = threadIdx.x; i < R.w * R.h; i += blockDim.x) {
-      const int ly = i / R.w;
-      const int px = R.x0 + (i - ly * R.w);
-      const int py = R.y0 + ly;
-      float sx, sy;
-      cam_map(ca, px, py, sx, sy);
-      sx = fminf(fmaxf(sx, 0.0f), ca.wm1);
-      sy = fminf(fmaxf(sy, 0.0f), ca.hm1);
-      StageT<kHalf>::put(sA, i, mulM(s_col.M[p], src_bilinear(P.src[p], ca, sx, sy)));
-      cam_map(cb, px, py, sx, sy);
-      sx = fminf(fmaxf(sx, 0.0f), cb.wm1);
-      sy = fminf(fmaxf(sy, 0.0f), cb.hm1);
-      StageT<kHalf>::put(sB, i, mulM(s_col.M[p + 1], src_bilinear(P.src[p + 1], cb, sx, sy)));
-    }
-  }
-  __syncthreads();
-  const int x = tx0 + (threadIdx.x & 15) * 4;
-  const int y = ty0 + (threadIdx.x >> 4);
-  const bool bal = !(P.flags & STITCH_BALANCE_OFF);
-  const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
-  const float mf = P.max_flow;
-  uint32_t o[3] = {0u, 0u, 0u};
-  if (y < P.pano_h) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int xi = x + i;
-      if (xi >= P.pano_w) continue;
-      float3 v;
-      bool cov;
-      if (xi < B.x0) {
-        cov = own_value(P, s_col, p, xi, y, v);
-      } else if (xi >= B.x1) {
-        cov = own_value(P, s_col, p + 1, xi, y, v);
-      } else if (y < B.y0 || y >= B.y1) {
-        cov = sliver_value(P, s_col, p, xi, y, v);
-      } else {
-        const int bw = B.x1 - B.x0;
-        const size_t fi = (size_t)(y - B.y0) * bw + (xi - B.x0);
-        float2 fa = __ldg(P.flow_ij[p] + fi);
-        float2 fb = __ldg(P.flow_ji[p] + fi);
-        fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
-        fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
-        const float tb = ((float)(xi - B.x0) + 0.5f) * B.inv_bw;
-        const float ta = 1.0f - tb;
-        const float wa = printed ? ta : tb;
-        const float wb = printed ? tb : ta;
-        const float lo_x = (float)B.x0, hi_x = (float)(B.x1 - 1);
-        const float lo_y = (float)B.y0, hi_y = (float)(B.y1 - 1);
-        const float Xa = fminf(fmaxf(fmaf(wa, fa.x, (float)xi), lo_x), hi_x);
-        const float Ya = fminf(fmaxf(fmaf(wa, fa.y, (float)y), lo_y), hi_y);
-        const float Xb = fminf(fmaxf(fmaf(wb, fb.x, (float)xi), lo_x), hi_x);
-        const float Yb = fminf(fmaxf(fmaf(wb, fb.y, (float)y), lo_y), hi_y);
-        const float3 Pa = staged_bilinear<kHalf>(sA, R, B, Xa, Ya);
-        const float3 Pb = staged_bilinear<kHalf>(sB, R, B, Xb, Yb);
-        v = make_float3(fmaf(ta, Pa.x, tb * Pb.x), fmaf(ta, Pa.y, tb * Pb.y), fmaf(ta, Pa.z, tb * Pb.z));
-        cov = true;
-      }
-      if (cov) {
-        o[0] |= to_u8(s_col.curve[0], bal, v.x) << (8 * i);
-        o[1] |= to_u8(s_col.curve[1], bal, v.y) << (8 * i);
-        o[2] |= to_u8(s_col.curve[2], bal, v.z) << (8 * i);
-      }
-    }
-  }
-  store4(P, x, y, o);
+__device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0,
+                                           const uint8_t (*s_out)[kTileH][kTileW]) {
+  // 3 planes x 16 rows x 4 sixteen-byte pieces = 192 vector stores.
+  const int t = threadIdx.x;
+  if (t >= 3 * kTileH * (kTileW / 16)) return;
+  const int c = t / (kTileH * 4);
+  const int r = (t / 4) % kTileH;
+  const int q = t % 4;
+  const int y = ty0 + r, x = tx0 + 16 * q;
+  if (y >= P.pano_h || x >= P.pano_pitch) return;
+  const uint4 v = *reinterpret_cast<const uint4 *>(&s_out[c][r][16 * q]);
+  *reinterpret_cast<uint4 *>(P.out + (size_t)c * P.pano_pitch * P.pano_h + (size_t)y * P.pano_pitch + x) = v;
 }
 
 }  // namespace
 
-size_t fuse_band_smem_bytes(int halo, bool fp16) {
-  const size_t pos = (size_t)(kTileW + 2 * halo) * (size_t)(kTileH + 2 * halo);
-  return pos * 2 * 3 * (fp16 ? 2 : 4);
+// ---------------------------------------------------------------------------
+// Kernels.
+// ---------------------------------------------------------------------------
+
+template <bool kHalf>
+__global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams P) {
+  using PT = typename PwT<kHalf>::T;
+  __shared__ __align__(16) uint32_t s_win[2][kWinCap];
+  __shared__ Window sW[2];
+  const PwTile pt = P.pw_tiles[blockIdx.x];
+  const BandDev B = P.band[pt.pair];
+  const int bw = B.x1 - B.x0;
+  const int rx0 = pt.x0, ry0 = pt.y0;
+  const int rx1 = min(rx0 + kTileW, B.x1) - 1, ry1 = min(ry0 + kTileH, B.y1) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < 2) {
+    const Window W = warp_window(P.cam[pt.pair + warp], rx0, ry0, rx1, ry1);
+    if (lane == 0) sW[warp] = W;
+  }
+  __syncthreads();
+  const Window Wa = sW[0], Wb = sW[1];
+  if (Wa.ok) stage_window(P.src[pt.pair], P.cam[pt.pair], Wa, s_win[0]);
+  if (Wb.ok) stage_window(P.src[pt.pair + 1], P.cam[pt.pair + 1], Wb, s_win[1]);
+  __syncthreads();
+  PT *da = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][0];
+  PT *db = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][1];
+  const CamDev &ca = P.cam[pt.pair];
+  const CamDev &cb = P.cam[pt.pair + 1];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int x = rx0 + lane + 32 * (j & 1);
+    const int y = ry0 + 2 * warp + (j >> 1);
+    if (x > rx1 || y > ry1) continue;
+    const size_t o = (size_t)(y - B.y0) * bw + (x - B.x0);
+    float sx, sy, nw;
+    // The band lies inside both cameras' coverage: clamp float32 noise away.
+    cam_map_f(ca, (float)(x - ca.ox), (float)(y - ca.oy), sx, sy, nw);
+    sx = fminf(fmaxf(sx, 0.0f), ca.wm1);
+    sy = fminf(fmaxf(sy, 0.0f), ca.hm1);
+    PwT<kHalf>::put(da, o, Wa.ok ? win_bilinear(s_win[0], Wa, sx, sy) : src_bilinear(P.src[pt.pair], ca, sx, sy));
+    cam_map_f(cb, (float)(x - cb.ox), (float)(y - cb.oy), sx, sy, nw);
+    sx = fminf(fmaxf(sx, 0.0f), cb.wm1);
+    sy = fminf(fmaxf(sy, 0.0f), cb.hm1);
+    PwT<kHalf>::put(db, o, Wb.ok ? win_bilinear(s_win[1], Wb, sx, sy) : src_bilinear(P.src[pt.pair + 1], cb, sx, sy));
+  }
 }
 
-cudaError_t fuse_setup_attributes(int max_halo) {
-  cudaError_t e = cudaFuncSetAttribute(k_fuse_band<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fuse_band_smem_bytes(max_halo, false));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fuse_band<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fuse_band_smem_bytes(max_halo, true));
+template <bool kHalf>
+__global__ void __launch_bounds__(kFuseThreads) k_fuse(const FuseParams P) {
+  using PT = typename PwT<kHalf>::T;
+  __shared__ BlockColor bc;
+  __shared__ Window sW[2];
+  __shared__ __align__(16) uint32_t s_win[2][kWinCap];
+  __shared__ __align__(16) uint8_t s_out[3][kTileH][kTileW];
+  const TileDesc t = P.tiles[blockIdx.x];
+  const int tx0 = t.tx * kTileW, ty0 = t.ty * kTileH;
+  const int tx1 = min(tx0 + kTileW, P.pano_w) - 1, ty1 = min(ty0 + kTileH, P.pano_h) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool empty = tx0 > tx1 || ty0 > ty1;
+  load_block_color(P, bc);
+
+  // Source windows: warp 0 for the tile's camera (or a band's left camera),
+  // warp 1 for a band's right camera, only where tile pixels need them.
+  if (warp < 2) {
+    Window W = no_window();
+    if (!empty) {
+      if (t.kind != 1) {
+        if (warp == 0) W = warp_window(P.cam[t.idx], tx0, ty0, tx1, ty1);
+      } else {
+        const BandDev B = P.band[t.idx];
+        const bool rows_out = ty0 < B.y0 || ty1 >= B.y1;
+        const bool need = warp == 0 ? (tx0 < B.x0 || (rows_out && tx1 >= B.x0))
+                                    : (tx1 >= B.x1 || (rows_out && tx0 < B.x1));
+        if (need) W = warp_window(P.cam[t.idx + warp], tx0, ty0, tx1, ty1);
+      }
+    }
+    if (lane == 0) sW[warp] = W;
+  }
+  __syncthreads();
+  const Window W0 = sW[0], W1 = sW[1];
+  if (W0.ok) stage_window(P.src[t.idx], P.cam[t.idx], W0, s_win[0]);
+  if (W1.ok) stage_window(P.src[t.idx + 1], P.cam[t.idx + 1], W1, s_win[1]);
+  __syncthreads();
+  const Hot hot = load_hot(bc);
+
+  if (t.kind == 0) {
+    // Fully covered own tile: no coverage test, no fallback.
+    const int k = t.idx;
+    const CamDev &c = P.cam[k];
+    float M[9];
+    load_M(bc, k, M);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+      float sx, sy, nw;
+      cam_map_f(c, (float)(tx0 + lx - c.ox), (float)(ty0 + ly - c.oy), sx, sy, nw);
+      const float3 v = mulM(M, W0.ok ? win_bilinear(s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
+      put_px(s_out, lx, ly, hot, bc, true, v);
+    }
+  } else if (t.kind == 2) {
+    const int k = t.idx;
+    float M[9];
+    load_M(bc, k, M);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+      const int x = tx0 + lx, y = ty0 + ly;
+      float3 v = make_float3(0.0f, 0.0f, 0.0f);
+      bool cov = false;
+      if (x < P.pano_w && y < P.pano_h) {
+        cov = cam_value_w(P, M, k, W0, s_win[0], x, y, v);
+        if (!cov && k > 0) cov = cam_value_g(P, bc, k - 1, x, y, v);
+        if (!cov && k < P.n_cams - 1) cov = cam_value_g(P, bc, k + 1, x, y, v);
+      }
+      put_px(s_out, lx, ly, hot, bc, cov, v);
+    }
+  } else {
+    const int p = t.idx;
+    const BandDev B = P.band[p];
+    float Ma[9], Mb[9];
+    load_M(bc, p, Ma);
+    load_M(bc, p + 1, Mb);
+    const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
+    const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
+    const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
+    const float mf = P.max_flow;
+    const int bw = B.x1 - B.x0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+      const int x = tx0 + lx, y = ty0 + ly;
+      float3 v = make_float3(0.0f, 0.0f, 0.0f);
+      bool cov = false;
+      if (x < P.pano_w && y < P.pano_h) {
+        if (x < B.x0) {
+          cov = cam_value_w(P, Ma, p, W0, s_win[0], x, y, v);
+          if (!cov && p > 0) cov = cam_value_g(P, bc, p - 1, x, y, v);
+          if (!cov) cov = cam_value_g(P, bc, p + 1, x, y, v);
+        } else if (x >= B.x1) {
+          cov = cam_value_w(P, Mb, p + 1, W1, s_win[1], x, y, v);
+          if (!cov) cov = cam_value_g(P, bc, p, x, y, v);
+          if (!cov && p + 2 < P.n_cams) cov = cam_value_g(P, bc, p + 2, x, y, v);
+        } else {
+          const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
+          const float ta = 1.0f - tb;
+          if (y < B.y0 || y >= B.y1) {
+            float3 va, vb;
+            const bool ca = cam_value_w(P, Ma, p, W0, s_win[0], x, y, va);
+            const bool cb = cam_value_w(P, Mb, p + 1, W1, s_win[1], x, y, vb);
+            if (ca && cb) {
+              v = make_float3(fmaf(ta, va.x, tb * vb.x), fmaf(ta, va.y, tb * vb.y), fmaf(ta, va.z, tb * vb.z));
+            } else if (ca) {
+              v = va;
+            } else if (cb) {
+              v = vb;
+            }
+            cov = ca || cb;
+          } else {
+            const size_t fi = (size_t)(y - B.y0) * bw + (x - B.x0);
+            float2 fa = __ldg(P.flow_ij[p] + fi);
+            float2 fb = __ldg(P.flow_ji[p] + fi);
+            fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
+            fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
+            const float wa = printed ? ta : tb;
+            const float wb = printed ? tb : ta;
+            const float lo_x = (float)B.x0, hi_x = (float)(B.x1 - 1);
+            const float lo_y = (float)B.y0, hi_y = (float)(B.y1 - 1);
+            const float Xa = fminf(fmaxf(fmaf(wa, fa.x, (float)x), lo_x), hi_x);
+            const float Ya = fminf(fmaxf(fmaf(wa, fa.y, (float)y), lo_y), hi_y);
+            const float Xb = fminf(fmaxf(fmaf(wb, fb.x, (float)x), lo_x), hi_x);
+            const float Yb = fminf(fmaxf(fmaf(wb, fb.y, (float)y), lo_y), hi_y);
+            const float3 Pa = mulM(Ma, pw_bilinear<kHalf>(pwa, B, Xa, Ya));
+            const float3 Pb = mulM(Mb, pw_bilinear<kHalf>(pwb, B, Xb, Yb));
+            v = make_float3(fmaf(ta, Pa.x, tb * Pb.x), fmaf(ta, Pa.y, tb * Pb.y), fmaf(ta, Pa.z, tb * Pb.z));
+            cov = true;
+          }
+        }
+      }
+      put_px(s_out, lx, ly, hot, bc, cov, v);
+    }
+  }
+  __syncthreads();
+  store_tile(P, tx0, ty0, s_out);
 }
 
-cudaError_t launch_fuse(const FuseParams &p, int n_own_tiles, int n_band_tiles, cudaStream_t s) {
-  const bool fp16 = (p.flags & STITCH_FP16_INTERMEDIATE) != 0;
-  if (n_band_tiles > 0) {
-    const size_t smem = fuse_band_smem_bytes(p.halo, fp16);
-    if (fp16)
-      k_fuse_band<true><<<n_band_tiles, kFuseThreads, smem, s>>>(p, 0);
-    else
-      k_fuse_band<false><<<n_band_tiles, kFuseThreads, smem, s>>>(p, 0);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  if (n_own_tiles > 0) {
-    k_fuse_own<<<n_own_tiles, kFuseThreads, 0, s>>>(p, n_band_tiles);
-    return cudaGetLastError();
-  }
-  return cudaSuccess;
+size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
+
+cudaError_t fuse_setup_attributes(int) { return cudaSuccess; }
+
+cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s) {
+  if (p.n_pw_tiles <= 0) return cudaSuccess;
+  if (p.flags & STITCH_FP16_INTERMEDIATE)
+    k_prewarp_band<true><<<p.n_pw_tiles, kFuseThreads, 0, s>>>(p);
+  else
+    k_prewarp_band<false><<<p.n_pw_tiles, kFuseThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fuse(const FuseParams &p, cudaStream_t s) {
+  if (p.n_tiles <= 0) return cudaSuccess;
+  if (p.flags & STITCH_FP16_INTERMEDIATE)
+    k_fuse<true><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
+  else
+    k_fuse<false><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace stitch

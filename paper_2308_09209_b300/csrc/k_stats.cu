@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsParams P) {
     }
   __syncthreads();
 
-  RawStats *raw = P.raw + (P.state->T & 1);
+  RawStats *raw = P.raw;
   for (int i = threadIdx.x; i < kPoolWords; i += blockDim.x) {
     const uint32_t c = s_pool[i];
     if (c) atomicAdd(&raw->pooled[0][0] + i, c);

@@ -6,7 +6,7 @@
 // capture that forbids allocation, or real-time threads that must never
 // block in the driver's allocator. stitch_estimate_color_noalloc serves them:
 // it runs the same statistics and estimate kernels as stitch_estimate_color,
-// but its working memory (two raw-statistics slots and one colour state) is
+// but its working memory (one raw-statistics slot and one colour state) is
 // a file-scope __device__ array of fixed size, which the CUDA module loader
 // places on every GPU that loads this library; it stays there until the
 // process exits. The caller passes the frames and the output buffers.
@@ -18,7 +18,7 @@
 namespace stitch {
 namespace {
 
-constexpr size_t kRawBytes = 2 * sizeof(RawStats);
+constexpr size_t kRawBytes = sizeof(RawStats);
 constexpr size_t kScratchBytes = ((kRawBytes + sizeof(ColorState)) + 255) / 256 * 256;
 static_assert(kScratchBytes <= STITCH_NOALLOC_SCRATCH_BYTES, "scratch larger than the advertised size");
 
@@ -87,6 +87,8 @@ extern "C" int stitch_estimate_color_noalloc(const stitch_config *cfg, const uin
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) return fail(STITCH_ECUDA, "cudaGetSymbolAddress of the scratch failed");
+      e = estimate_setup();
+      if (e != cudaSuccess) return fail(STITCH_ECUDA, "estimate kernel set-up failed");
       g_scratch_addr[dev] = static_cast<unsigned char *>(p);
     }
     scratch = g_scratch_addr[dev];
@@ -105,8 +107,8 @@ extern "C" int stitch_estimate_color_noalloc(const stitch_config *cfg, const uin
     sp.vec_ok[k] = ((reinterpret_cast<uintptr_t>(frames_dev[k]) & 15u) == 0 && sp.pitch[k] % 16 == 0) ? 1 : 0;
   }
   sp.raw = raw;
-  sp.state = state;
   ep.raw = raw;
+  ep.raw_slots = 1;
   ep.state = state;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_stats(sp, grid_x, s);

@@ -19,9 +19,16 @@ constexpr int kFuseThreads = 256;     // 4 consecutive pixels per thread
 constexpr int kStatsThreads = 256;
 constexpr int kEstimateThreads = 256;
 constexpr double kCondLimit = 1e12;
+// Buffer rings that let successive frames overlap in a recorded sequence:
+// statistics slots (stats of frame t+1 run beside the estimate of frame t),
+// colour slots (the estimate of frame t+1 runs beside the fuse of frame t) and
+// band pre-warp slots.
+constexpr int kRawSlots = 3;
+constexpr int kColorSlots = 4;
+constexpr int kPwSlots = 2;
 
 // Integer statistics of one frame, written by the stats kernel (K1) and read
-// by the estimate kernel (K2). Two slots alternate by frame parity.
+// by the estimate kernel (K2). Frame T uses slot T % kRawSlots.
 struct RawStats {
   uint32_t pooled[3][256];            // full-frame histogram of all cameras
   uint32_t Hi[kMaxPairs][3][256];     // overlap histogram, colour-source side i
@@ -35,7 +42,7 @@ struct Curve {
   float m1, m2, d1, d2, s, g1, g2, inv_m1, inv_bm, ident;
 };
 
-// What the fuse kernel reads: one slot per frame parity.
+// What the fuse kernel reads: frame T's estimate is in slot T % kColorSlots.
 struct ColorOut {
   float M[kMaxCams][9];               // row-vector convention, v' = v . M
   Curve curve[3];
@@ -54,7 +61,7 @@ struct ColorState {
   double M_pair[kMaxPairs][9];
   double M_cam[kMaxCams][9];
   double knot_mean[3][2];
-  ColorOut out[2];
+  ColorOut out[kColorSlots];
 };
 
 // One camera as the fuse kernel sees it. h maps (x - ox, y - oy, 1) of the
@@ -75,9 +82,16 @@ struct BandDev {
 
 struct TileDesc {
   int16_t tx, ty;                     // tile origin / (kTileW, kTileH)
-  int8_t kind;                        // 0 = own columns of camera idx, 1 = touches band idx
+  int8_t kind;                        // 0 = own columns of camera idx, fully covered; 1 = touches band
+                                      // idx; 2 = own columns of camera idx, partly covered
   int8_t idx;
   int16_t pad;
+};
+
+// One 64 x 16 piece of a band rectangle for the band pre-warp kernel.
+struct PwTile {
+  int pair;
+  int x0, y0;                         // panorama origin of the piece
 };
 
 struct FuseParams {
@@ -88,6 +102,10 @@ struct FuseParams {
   float max_flow;
   int n_tiles;
   const TileDesc *tiles;
+  int n_pw_tiles;
+  const PwTile *pw_tiles;
+  void *pw;                           // pre-warped band intermediate (both cameras of every band)
+  size_t pw_off[kMaxPairs][2];        // element offsets of band p, left / right camera
   const ColorOut *color;
   CamDev cam[kMaxCams];
   BandDev band[kMaxPairs];
@@ -111,14 +129,14 @@ struct StatsParams {
   int w[kMaxCams], h[kMaxCams], pitch[kMaxCams];
   int n_roles[kMaxCams];
   RoleDev roles[kMaxCams][2];
-  RawStats *raw;                      // two slots
-  const ColorState *state;            // frame index T selects the slot
+  RawStats *raw;                      // the slot this frame accumulates into (cleared beforehand)
 };
 
 struct EstimateParams {
   int n_cams, n_pairs, ref, window;
   long long lambda_q;                 // lambda in millionths
   int pair_i[kMaxPairs], pair_j[kMaxPairs];
+  int raw_slots;                      // frame T reads slot T % raw_slots and clears slot (T - 1) % raw_slots
   RawStats *raw;
   ColorState *state;
 };
@@ -126,10 +144,12 @@ struct EstimateParams {
 // Launchers (defined in the kernel files).
 cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
-cudaError_t launch_fuse(const FuseParams &p, int n_own_tiles, int n_band_tiles, cudaStream_t s);
+cudaError_t estimate_setup();
+cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s);
+cudaError_t launch_fuse(const FuseParams &p, cudaStream_t s);
 cudaError_t fuse_setup_attributes(int max_halo);
 size_t stats_smem_bytes();
-size_t fuse_band_smem_bytes(int halo, bool fp16);
+size_t prewarp_elem_bytes(bool fp16);
 
 }  // namespace stitch
 

@@ -288,11 +288,11 @@ def stitch_profile(ctx, enable: bool) -> int:
 
 def stitch_profile_read(ctx) -> dict:
     """Per-stage GPU milliseconds and launch counts since the last read."""
-    ms = np.zeros(3, dtype=np.float64)
-    cnt = np.zeros(3, dtype=np.int32)
+    ms = np.zeros(4, dtype=np.float64)
+    cnt = np.zeros(4, dtype=np.int32)
     _check(lib().stitch_profile_read(ctx, ms.ctypes.data, cnt.ctypes.data), ctx)
-    return dict(stats_ms=float(ms[0]), estimate_ms=float(ms[1]), fuse_ms=float(ms[2]),
-                stats_n=int(cnt[0]), estimate_n=int(cnt[1]), fuse_n=int(cnt[2]))
+    return dict(stats_ms=float(ms[0]), estimate_ms=float(ms[1]), fuse_ms=float(ms[2]), prewarp_ms=float(ms[3]),
+                stats_n=int(cnt[0]), estimate_n=int(cnt[1]), fuse_n=int(cnt[2]), prewarp_n=int(cnt[3]))
 
 
 def stitch_estimate_color_noalloc(cfg: Config, frames, M_out, curve_out, flags_out=None, stream=None) -> int:

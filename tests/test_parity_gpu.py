@@ -87,12 +87,15 @@ def _T(tx, ty):
     return np.array([[1.0, 0, tx], [0, 1.0, ty], [0, 0, 1.0]])
 
 
-def test_identity_and_integer_shift_bit_exact():
+@pytest.mark.parametrize("w", [224, 225])
+def test_identity_and_integer_shift_bit_exact(w):
+    """w - 1 odd and even: samples exactly on a camera's last column."""
     ensure_built()
     rng = np.random.RandomState(0)
     base = rng.randint(0, 256, (96, 360, 3)).astype(np.uint8)
-    frames = [torch.from_numpy(base[:, 0:224].copy()).cuda(), torch.from_numpy(base[:, 136:360].copy()).cuda()]
-    cfg = S.Config([224, 224], [96, 96], np.stack([_T(0, 0), _T(136, 0)]), 360, 96, max_flow=4,
+    off = 360 - w
+    frames = [torch.from_numpy(base[:, 0:w].copy()).cuda(), torch.from_numpy(base[:, off:360].copy()).cuda()]
+    cfg = S.Config([w, w], [96, 96], np.stack([_T(0, 0), _T(off, 0)]), 360, 96, max_flow=4,
                    flags=S.STITCH_BALANCE_OFF)
     st = S.Stitcher(cfg)
     fij, fji = flows_for(st.bands, 0.0, 0, 0)
@@ -102,7 +105,7 @@ def test_identity_and_integer_shift_bit_exact():
     pano = st.frame(frames, fij, fji)
     assert np.array_equal(pano.cpu().numpy()[:, :, :360].transpose(1, 2, 0), base)
     # integer shift of the whole rig by (5, 3)
-    cfg2 = S.Config([224, 224], [96, 96], np.stack([_T(5, 3), _T(141, 3)]), 368, 100, max_flow=4,
+    cfg2 = S.Config([w, w], [96, 96], np.stack([_T(5, 3), _T(off + 5, 3)]), 368, 100, max_flow=4,
                     flags=S.STITCH_BALANCE_OFF)
     st2 = S.Stitcher(cfg2)
     f2ij, f2ji = flows_for(st2.bands, 0.0, 0, 0)
@@ -243,14 +246,14 @@ def test_stage_profiling_per_call_and_in_graphs():
         pr.st.estimate_color(fr)
         pr.st.frame(fr, fij, fji)
     r = S.stitch_profile_read(pr.st.ctx)
-    assert (r["stats_n"], r["estimate_n"], r["fuse_n"]) == (3, 3, 3)
-    assert r["stats_ms"] > 0 and r["estimate_ms"] > 0 and r["fuse_ms"] > 0
+    assert (r["stats_n"], r["estimate_n"], r["fuse_n"], r["prewarp_n"]) == (3, 3, 3, 3)
+    assert r["stats_ms"] > 0 and r["estimate_ms"] > 0 and r["fuse_ms"] > 0 and r["prewarp_ms"] > 0
     panos = [pr.st.new_pano() for _ in range(3)]
     args = (3, [f for fr, _, _ in ins for f in fr], [f for _, a, _ in ins for f in a],
             [f for _, _, b in ins for f in b], panos)
     S.stitch_sequence(pr.st.ctx, *args)
     r = S.stitch_profile_read(pr.st.ctx)
-    assert (r["stats_n"], r["estimate_n"], r["fuse_n"]) == (3, 3, 3)
+    assert (r["stats_n"], r["estimate_n"], r["fuse_n"], r["prewarp_n"]) == (3, 3, 3, 3)
     assert r["fuse_ms"] > 0 and r["stats_ms"] > 0
     S.stitch_profile(pr.st.ctx, False)
     assert S.stitch_profile_read(pr.st.ctx)["fuse_n"] == 0
