@@ -39,7 +39,7 @@ UNIT = "Mpix/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="4x1920x1080")
@@ -118,7 +118,8 @@ def make_workload(name, n_frames, seed, device):
 # clocks during the timed region
 # --------------------------------------------------------------------------- #
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples every 50 ms; stop() keeps those inside [t0, t1]."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -130,7 +131,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -141,7 +142,7 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -151,16 +152,23 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if ts is not None and t0 is not None and not (t0 - 0.06 <= ts <= t1 + 0.06):
+                continue
+            try:
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         sm.sort()
@@ -284,14 +292,17 @@ def _run_ours(args, dist, ctxs):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    time.sleep(0.2)                      # let the sampler start
+    t_begin = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
+    t_end = time.time()
     dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_begin, t_end)
     ms = e0.elapsed_time(e1) / args.steps
     ms = dist.max(ms)
     rc = S.stitch_sync(st.ctx, stream)
@@ -305,7 +316,7 @@ def _run_ours(args, dist, ctxs):
     S.stitch_profile_read(st.ctx)
     acc = dict(stats_ms=0.0, estimate_ms=0.0, fuse_ms=0.0, prewarp_ms=0.0, stats_n=0, estimate_n=0, fuse_n=0,
                prewarp_n=0)
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 5)):
         step()
         r = S.stitch_profile_read(st.ctx)
         for k in acc:

@@ -701,6 +701,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     }
     const double sc = 1.0 / hs[8];
     for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(hs[e2] * sc);
+    c.affine = (hs[6] == 0.0 && hs[7] == 0.0) ? 1 : 0;
     c.w = g.w[k];
     c.h_px = g.h[k];
     c.pitch = g.pitch[k];

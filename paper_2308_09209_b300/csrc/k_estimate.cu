@@ -68,49 +68,44 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   return v;
 }
 
-// Gaussian elimination with partial pivoting on [A | B | I]. Returns false if
-// a pivot vanishes or cond_1(A) > kCondLimit (NaN counts as ill-conditioned).
-__device__ bool solve3(const double A[9], const double B[9], double M[9]) {
-  double a[3][9];
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c) {
-      a[r][c] = A[r * 3 + c];
-      a[r][3 + c] = B[r * 3 + c];
-      a[r][6 + c] = (r == c) ? 1.0 : 0.0;
-    }
-  }
-  for (int k = 0; k < 3; ++k) {
-    int piv = k;
-    double best = fabs(a[k][k]);
-    for (int r = k + 1; r < 3; ++r)
-      if (fabs(a[r][k]) > best) { best = fabs(a[r][k]); piv = r; }
-    if (!(best > 0.0)) return false;
-    if (piv != k)
-      for (int c = 0; c < 9; ++c) { const double t = a[k][c]; a[k][c] = a[piv][c]; a[piv][c] = t; }
-    for (int r = k + 1; r < 3; ++r) {
-      const double f = a[r][k] / a[k][k];
-      for (int c = k; c < 9; ++c) a[r][c] -= f * a[k][c];
-    }
-  }
-  for (int k = 2; k >= 0; --k) {
-    for (int c = 3; c < 9; ++c) {
-      double s = a[k][c];
-      for (int j = k + 1; j < 3; ++j) s -= a[k][j] * a[j][c];
-      a[k][c] = s / a[k][k];
-    }
-  }
-  double nA = 0.0, nI = 0.0;
-  for (int c = 0; c < 3; ++c) {
-    double sa = 0.0, si = 0.0;
-    for (int r = 0; r < 3; ++r) { sa += fabs(A[r * 3 + c]); si += fabs(a[r][6 + c]); }
-    nA = fmax(nA, sa);
-    nI = fmax(nI, si);
-  }
+// M = A^-1 B for a symmetric 3x3 A by nine lanes of one warp (lane e = 3r + c
+// holds entry (r, c)): cofactors, determinant by the first row, inverse =
+// adjugate / det, then M = A^-1 B. Returns (in every lane) false if det is
+// zero or not finite, or cond_1(A) = |A|_1 |A^-1|_1 exceeds kCondLimit (NaN
+// counts as ill-conditioned). Lanes 9..31 take part in the shuffles only.
+__device__ bool warp_solve3(double a, double b, double &m) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int e = lane < 9 ? lane : 0;
+  const int r = e / 3, c = e % 3;
+  // cofactor of (r, c): rows r1 < r2 != r, columns c1 < c2 != c
+  const int r1 = r == 0 ? 1 : 0, r2 = r == 2 ? 1 : 2;
+  const int c1 = c == 0 ? 1 : 0, c2 = c == 2 ? 1 : 2;
+  const double a11 = __shfl_sync(full, a, r1 * 3 + c1), a12 = __shfl_sync(full, a, r1 * 3 + c2);
+  const double a21 = __shfl_sync(full, a, r2 * 3 + c1), a22 = __shfl_sync(full, a, r2 * 3 + c2);
+  double cof = a11 * a22 - a12 * a21;
+  if ((r + c) & 1) cof = -cof;
+  // det by the first row: sum_c A(0,c) C(0,c)
+  const double p = (lane < 3) ? a * cof : 0.0;
+  double det = p + __shfl_sync(full, p, 1) + __shfl_sync(full, p, 2);
+  det = __shfl_sync(full, det, 0);
+  const bool ok_det = det != 0.0 && isfinite(det);
+  const double inv_det = ok_det ? 1.0 / det : 0.0;
+  // A^-1 = adj(A) / det, adj = cofactor matrix transposed
+  const double ai = __shfl_sync(full, cof, c * 3 + r) * inv_det;
+  // 1-norms: maximum absolute column sum
+  double ca = fabs(a), ci = fabs(ai);
+  ca += __shfl_sync(full, ca, (e + 3) % 9) + __shfl_sync(full, ca, (e + 6) % 9);
+  ci += __shfl_sync(full, ci, (e + 3) % 9) + __shfl_sync(full, ci, (e + 6) % 9);
+  const double nA = fmax(fmax(__shfl_sync(full, ca, 0), __shfl_sync(full, ca, 1)), __shfl_sync(full, ca, 2));
+  const double nI = fmax(fmax(__shfl_sync(full, ci, 0), __shfl_sync(full, ci, 1)), __shfl_sync(full, ci, 2));
+  // M(r, c) = sum_k A^-1(r, k) B(k, c)
+  double mm = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) mm += __shfl_sync(full, ai, r * 3 + k) * __shfl_sync(full, b, k * 3 + c);
+  m = mm;
   const double cond = nA * nI;
-  if (!(cond <= kCondLimit)) return false;
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) M[r * 3 + c] = a[r][3 + c];
-  return true;
+  return ok_det && cond <= kCondLimit;
 }
 
 // (c, d) with c != d -> index into the value-weighted histograms
@@ -185,26 +180,28 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
   }
   __syncthreads();
 
-  // 4. Windowed solve, one thread per pair.
-  if (tid < np) {
-    const int p = tid;
+  // 4. Windowed solve, one warp per pair (nine lanes hold the matrix entries).
+  if (warp < np) {
+    const int p = warp;
+    const int e = lane < 9 ? lane : 0;
+    const int r = e / 3, c = e % 3;
+    static const int sym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
     const int nw = min(T + 1, P.window);
-    unsigned long long As[6] = {0, 0, 0, 0, 0, 0}, Bs[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    bool empty = false;
+    unsigned long long As = 0ull, Bs = 0ull;
+    int empty = 0;
     for (int i = 0; i < nw; ++i) {
       const int sl = (T - i) % kMaxWindow;
-      for (int k = 0; k < 6; ++k) As[k] += S->A_ring[sl][p][k];
-      for (int k = 0; k < 9; ++k) Bs[k] += S->B_ring[sl][p][k];
-      if (S->n_ring[sl][p][0] == 0 || S->n_ring[sl][p][1] == 0) empty = true;
+      As += S->A_ring[sl][p][sym[e]];
+      Bs += S->B_ring[sl][p][e];
+      empty |= (S->n_ring[sl][p][0] == 0 || S->n_ring[sl][p][1] == 0);
     }
-    const double A[9] = {(double)As[0], (double)As[1], (double)As[2],
-                         (double)As[1], (double)As[3], (double)As[4],
-                         (double)As[2], (double)As[4], (double)As[5]};
-    double B[9], M[9];
-    for (int k = 0; k < 9; ++k) B[k] = (double)Bs[k];
-    if (!empty && solve3(A, B, M)) {
-      for (int k = 0; k < 9; ++k) sm.M_pair[p][k] = M[k];
-    } else {
+    (void)r;
+    (void)c;
+    double m = 0.0;
+    const bool ok = warp_solve3((double)As, (double)Bs, m) && !empty;
+    if (ok) {
+      if (lane < 9) sm.M_pair[p][lane] = m;
+    } else if (lane == 0) {
       atomicOr(&sm.sing, 1 << p);
     }
   }
@@ -268,27 +265,29 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
       s1 += (sl == slot) ? sm.knot[c][0] : S->knots[sl][c][0];
       s2 += (sl == slot) ? sm.knot[c][1] : S->knots[sl][c][1];
     }
-    const double m1 = (double)s1 / (double)cnt;
-    const double m2 = (double)s2 / (double)cnt;
+    // Float32 throughout: the fuse kernel reads float32 parameters, and the
+    // knot means of integer sums are correctly rounded either way.
+    const float m1 = (float)s1 / (float)cnt;
+    const float m2 = (float)s2 / (float)cnt;
     S->knot_mean[c][0] = m1;
     S->knot_mean[c][1] = m2;
-    const double lam = (double)P.lambda_q / 1e6;
-    const double d1 = 255.0 * lam, d2 = 255.0 * (1.0 - lam);
-    const bool ident = (m2 - m1) < 1.0;
-    const double span = ident ? 1.0 : (m2 - m1);
-    const double s = (d2 - d1) / span;
-    const double g1 = s * m1 / d1;
-    const double g2 = s * (255.0 - m2) / (255.0 - d2);
+    const float lam = (float)((double)P.lambda_q / 1e6);
+    const float d1 = (float)(255.0 * ((double)P.lambda_q / 1e6));
+    const float d2 = (float)(255.0 * (1.0 - (double)P.lambda_q / 1e6));
+    (void)lam;
+    const bool ident = (m2 - m1) < 1.0f;
+    const float span = ident ? 1.0f : (m2 - m1);
+    const float sl = (d2 - d1) / span;
     Curve cv;
-    cv.m1 = (float)m1;
-    cv.m2 = (float)m2;
-    cv.d1 = (float)d1;
-    cv.d2 = (float)d2;
-    cv.s = (float)s;
-    cv.g1 = (float)g1;
-    cv.g2 = (float)g2;
-    cv.inv_m1 = m1 > 0.0 ? (float)(1.0 / m1) : 0.0f;
-    cv.inv_bm = m2 < 255.0 ? (float)(1.0 / (255.0 - m2)) : 0.0f;
+    cv.m1 = m1;
+    cv.m2 = m2;
+    cv.d1 = d1;
+    cv.d2 = d2;
+    cv.s = sl;
+    cv.g1 = sl * m1 / d1;
+    cv.g2 = sl * (255.0f - m2) / (255.0f - d2);
+    cv.inv_m1 = m1 > 0.0f ? 1.0f / m1 : 0.0f;
+    cv.inv_bm = m2 < 255.0f ? 1.0f / (255.0f - m2) : 0.0f;
     cv.ident = ident ? 1.0f : 0.0f;
     S->out[T % kColorSlots].curve[c] = cv;
   } else if (warp >= 2) {
@@ -311,10 +310,25 @@ cudaError_t estimate_setup() {
   return cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(EstSmem));
 }
 
+// The estimate is one block on the critical path of every frame: launch it at
+// the device's highest priority so that it gets the next free SM ahead of the
+// many blocks of the throughput kernels running beside it.
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s) {
   static_assert(sizeof(RawStats) % 16 == 0, "raw statistics must be a whole number of 16-byte words");
-  k_estimate<<<1, kT, sizeof(EstSmem), s>>>(p);
-  return cudaGetLastError();
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(kT);
+  cfg.dynamicSmemBytes = sizeof(EstSmem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = greatest;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_estimate, p);
 }
 
 }  // namespace stitch

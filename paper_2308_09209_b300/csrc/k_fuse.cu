@@ -30,9 +30,9 @@
 //     curve F (Eq. 5: gamma, linear, gamma) and rounded half to even; pixels
 //     go to a shared-memory tile and leave as 16-byte stores per plane.
 //
-// Thread mapping: warp w, lane l handles the pixels (l + 32 a, 2 w + b),
-// a, b in {0, 1}, so a warp touches 32 consecutive pixels of a row at a time
-// and its shared-memory tap reads fall in distinct banks.
+// Thread mapping: warp w, lane l handles the pixels (l + 32 a, 4 w + b),
+// a in {0, 1}, b in {0..3}, so a warp touches 32 consecutive pixels of a row
+// at a time and its shared-memory tap reads fall in distinct banks.
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -44,7 +44,7 @@ namespace {
 constexpr float kMagicRound = 12582912.0f;   // 1.5 * 2^23: x + kMagicRound rounds x to an integer (RNE)
 constexpr int kMagicRoundBits = 0x4B400000;
 constexpr float kMagicByte = 8388608.0f;     // 2^23: the float with bits 0x4B0000bb is 2^23 + bb
-constexpr int kWinCap = 3072;                // staged source pixels per window (12 KB)
+constexpr int kWinCap = 3584;                // staged source pixels per window (14 KB)
 
 // Approximate reciprocal (CUDA's fast division intrinsic: a few ulp).
 __device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
@@ -57,6 +57,12 @@ __device__ __forceinline__ void cam_map_f(const CamDev &c, float dx, float dy, f
   const float r = rcp_approx(nw);
   sx = nx * r;
   sy = ny * r;
+}
+
+// Affine camera (no perspective row): s = H^-1 q without a divide.
+__device__ __forceinline__ void cam_map_aff(const CamDev &c, float dx, float dy, float &sx, float &sy) {
+  sx = fmaf(c.h[0], dx, fmaf(c.h[1], dy, c.h[2]));
+  sy = fmaf(c.h[3], dx, fmaf(c.h[4], dy, c.h[5]));
 }
 
 __device__ __forceinline__ bool covered(const CamDev &c, float sx, float sy, float nw) {
@@ -255,6 +261,7 @@ struct Tail {       // gamma tails of Eq. 5 on u = v / 255
 struct BlockColor {
   float M[kMaxCams][9];   // M / 255, so fused values land in [0, 1]
   float lo[3], hi[3];     // knots m1/255, m2/255 (outside [0, 1] when there is no tail)
+  float mid[3], half[3];  // (lo + hi) / 2, (hi - lo) / 2: a tail is |u - mid| > half
   float A[3], B[3];       // linear part F = A + B u
   Tail tail[3];
 };
@@ -276,6 +283,8 @@ __device__ void load_block_color(const FuseParams &P, BlockColor &bc) {
       bc.A[c] = cv.d1 - cv.s * cv.m1;
       bc.B[c] = 255.0f * cv.s;
     }
+    bc.mid[c] = 0.5f * (bc.lo[c] + bc.hi[c]);
+    bc.half[c] = 0.5f * (bc.hi[c] - bc.lo[c]);
     Tail tl;
     tl.d1 = cv.d1;
     tl.k1 = 255.0f * cv.inv_m1;
@@ -289,15 +298,15 @@ __device__ void load_block_color(const FuseParams &P, BlockColor &bc) {
 
 // Hot per-channel balance parameters, kept in registers.
 struct Hot {
-  float lo[3], hi[3], A[3], B[3];
+  float mid[3], half[3], A[3], B[3];
 };
 
 __device__ __forceinline__ Hot load_hot(const BlockColor &bc) {
   Hot h;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    h.lo[c] = bc.lo[c];
-    h.hi[c] = bc.hi[c];
+    h.mid[c] = bc.mid[c];
+    h.half[c] = bc.half[c];
     h.A[c] = bc.A[c];
     h.B[c] = bc.B[c];
   }
@@ -309,12 +318,10 @@ __device__ __forceinline__ Hot load_hot(const BlockColor &bc) {
 __device__ __forceinline__ uint32_t finish(const Hot &h, const BlockColor &bc, int c, float v) {
   const float u = __saturatef(v);
   float F = fmaf(h.B[c], u, h.A[c]);
-  if (u < h.lo[c]) {
+  if (fabsf(u - h.mid[c]) > h.half[c]) {
     const Tail &t = bc.tail[c];
-    F = t.d1 * __powf(u * t.k1, t.g1);
-  } else if (u > h.hi[c]) {
-    const Tail &t = bc.tail[c];
-    F = 255.0f - t.e2 * __powf((1.0f - u) * t.k2, t.g2);
+    F = (u < bc.lo[c]) ? t.d1 * __powf(u * t.k1, t.g1)
+                       : 255.0f - t.e2 * __powf((1.0f - u) * t.k2, t.g2);
   }
   return (uint32_t)__float_as_int(F + kMagicRound);
 }
@@ -413,16 +420,16 @@ __device__ __forceinline__ void put_px(uint8_t (*s_out)[kTileH][kTileW], int lx,
 
 __device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0,
                                            const uint8_t (*s_out)[kTileH][kTileW]) {
-  // 3 planes x 16 rows x 4 sixteen-byte pieces = 192 vector stores.
-  const int t = threadIdx.x;
-  if (t >= 3 * kTileH * (kTileW / 16)) return;
-  const int c = t / (kTileH * 4);
-  const int r = (t / 4) % kTileH;
-  const int q = t % 4;
-  const int y = ty0 + r, x = tx0 + 16 * q;
-  if (y >= P.pano_h || x >= P.pano_pitch) return;
-  const uint4 v = *reinterpret_cast<const uint4 *>(&s_out[c][r][16 * q]);
-  *reinterpret_cast<uint4 *>(P.out + (size_t)c * P.pano_pitch * P.pano_h + (size_t)y * P.pano_pitch + x) = v;
+  // 3 planes x kTileH rows x 4 sixteen-byte pieces.
+  for (int t = threadIdx.x; t < 3 * kTileH * (kTileW / 16); t += blockDim.x) {
+    const int c = t / (kTileH * 4);
+    const int r = (t / 4) % kTileH;
+    const int q = t % 4;
+    const int y = ty0 + r, x = tx0 + 16 * q;
+    if (y >= P.pano_h || x >= P.pano_pitch) continue;
+    const uint4 v = *reinterpret_cast<const uint4 *>(&s_out[c][r][16 * q]);
+    *reinterpret_cast<uint4 *>(P.out + (size_t)c * P.pano_pitch * P.pano_h + (size_t)y * P.pano_pitch + x) = v;
+  }
 }
 
 }  // namespace
@@ -455,10 +462,10 @@ __global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams 
   PT *db = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][1];
   const CamDev &ca = P.cam[pt.pair];
   const CamDev &cb = P.cam[pt.pair + 1];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
+#pragma unroll 2
+  for (int j = 0; j < 8; ++j) {
     const int x = rx0 + lane + 32 * (j & 1);
-    const int y = ry0 + 2 * warp + (j >> 1);
+    const int y = ry0 + 4 * warp + (j >> 1);
     if (x > rx1 || y > ry1) continue;
     const size_t o = (size_t)(y - B.y0) * bw + (x - B.x0);
     float sx, sy, nw;
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams 
 }
 
 template <bool kHalf>
-__global__ void __launch_bounds__(kFuseThreads) k_fuse(const FuseParams P) {
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const FuseParams P) {
   using PT = typename PwT<kHalf>::T;
   __shared__ BlockColor bc;
   __shared__ Window sW[2];
@@ -518,21 +525,32 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(const FuseParams P) {
     const CamDev &c = P.cam[k];
     float M[9];
     load_M(bc, k, M);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
-      float sx, sy, nw;
-      cam_map_f(c, (float)(tx0 + lx - c.ox), (float)(ty0 + ly - c.oy), sx, sy, nw);
-      const float3 v = mulM(M, W0.ok ? win_bilinear(s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
-      put_px(s_out, lx, ly, hot, bc, true, v);
+    const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
+    if (c.affine && W0.ok) {
+#pragma unroll 2
+      for (int j = 0; j < 8; ++j) {
+        const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
+        float sx, sy;
+        cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
+        put_px(s_out, lx, ly, hot, bc, true, mulM(M, win_bilinear(s_win[0], W0, sx, sy)));
+      }
+    } else {
+#pragma unroll 2
+      for (int j = 0; j < 8; ++j) {
+        const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
+        float sx, sy, nw;
+        cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
+        const float3 v = mulM(M, W0.ok ? win_bilinear(s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
+        put_px(s_out, lx, ly, hot, bc, true, v);
+      }
     }
   } else if (t.kind == 2) {
     const int k = t.idx;
     float M[9];
     load_M(bc, k, M);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+#pragma unroll 2
+    for (int j = 0; j < 8; ++j) {
+      const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
       const int x = tx0 + lx, y = ty0 + ly;
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       bool cov = false;
@@ -554,9 +572,9 @@ __global__ void __launch_bounds__(kFuseThreads) k_fuse(const FuseParams P) {
     const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
     const float mf = P.max_flow;
     const int bw = B.x1 - B.x0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int lx = lane + 32 * (j & 1), ly = 2 * warp + (j >> 1);
+#pragma unroll 2
+    for (int j = 0; j < 8; ++j) {
+      const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
       const int x = tx0 + lx, y = ty0 + ly;
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       bool cov = false;

@@ -13,9 +13,9 @@ constexpr int kMaxCams = STITCH_MAX_CAMS;
 constexpr int kMaxPairs = STITCH_MAX_PAIRS;
 constexpr int kMaxWindow = STITCH_MAX_WINDOW;
 constexpr int kSmoothFrames = 3;      // Eq. 6-7: current frame and its last two
-constexpr int kTileW = 64;            // fuse tile: 64 x 16 panorama pixels
-constexpr int kTileH = 16;
-constexpr int kFuseThreads = 256;     // 4 consecutive pixels per thread
+constexpr int kTileW = 64;            // fuse tile: 64 x 32 panorama pixels
+constexpr int kTileH = 32;
+constexpr int kFuseThreads = 256;     // 8 pixels per thread
 constexpr int kStatsThreads = 256;
 constexpr int kEstimateThreads = 256;
 constexpr double kCondLimit = 1e12;
@@ -73,6 +73,7 @@ struct CamDev {
   int w, h_px, pitch;
   float wm1, hm1;
   int own_lo, own_hi;
+  int affine;                         // h[6] == h[7] == 0: no perspective divide
 };
 
 struct BandDev {
