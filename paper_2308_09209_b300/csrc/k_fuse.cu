@@ -319,8 +319,11 @@ __device__ __forceinline__ uint32_t finish(const Hot &h, const BlockColor &bc, i
   const float u = __saturatef(v);
   float F = fmaf(h.B[c], u, h.A[c]);
   if (fabsf(u - h.mid[c]) > h.half[c]) {
+    // The side comes from the midpoint: mid -/+ half need not round to the
+    // knots exactly, and a value next to a knot must take that knot's tail
+    // (both pieces meet there).
     const Tail &t = bc.tail[c];
-    F = (u < bc.lo[c]) ? t.d1 * __powf(u * t.k1, t.g1)
+    F = (u < h.mid[c]) ? t.d1 * __powf(u * t.k1, t.g1)
                        : 255.0f - t.e2 * __powf((1.0f - u) * t.k2, t.g2);
   }
   return (uint32_t)__float_as_int(F + kMagicRound);

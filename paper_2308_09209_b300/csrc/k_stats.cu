@@ -12,8 +12,7 @@
 //     x_c x_d. With these, the estimate kernel forms B = I_i^T L(I_i) without
 //     a second pass over the pixels once the specification L is known:
 //     B_cd = sum_v L_d(v) W_cd(v), B_dd = sum_v L_d(v) v H_i,d(v).
-// Runs of equal consecutive values within a thread's 16 pixels are merged
-// into one shared-memory atomic; counts are flushed with one global atomic
+// Counts are accumulated in shared memory and flushed with one global atomic
 // per non-zero bin. All arithmetic is integer, so results are bit-exact.
 #include "stitch_internal.h"
 
@@ -28,24 +27,10 @@ __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int j) {
   return (w[j >> 2] >> ((j & 3) * 8)) & 0xffu;
 }
 
-// Add the 16 values of one channel (bytes 3 i + c of the group) to a
-// histogram, merging runs of equal consecutive values into one atomic each.
-template <int kC>
-__device__ __forceinline__ void hist_runs(const uint32_t (&wd)[12], int i0, int i1, uint32_t *h) {
-  uint32_t run_v = 0xffffffffu, run_n = 0u;
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    if (i >= i0 && i < i1) {
-      const uint32_t v = byte_of(wd, 3 * i + kC);
-      if (v != run_v) {
-        if (run_n) atomicAdd(&h[run_v], run_n);
-        run_v = v;
-        run_n = 0u;
-      }
-      ++run_n;
-    }
-  }
-  if (run_n) atomicAdd(&h[run_v], run_n);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
 }
 
 __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsParams P) {
@@ -84,6 +69,10 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsParams P) {
   const int groups = (w + 15) >> 4;
   const bool vec = P.vec_ok[cam] != 0;
 
+  // A camera is the colour-source side of at most one pair: role iq (or -1).
+  const int iq = (act[0] && R[0].is_i) ? 0 : ((act[1] && R[1].is_i) ? 1 : -1);
+  unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+
   // Rows are walked by a fixed thread -> (row, group) assignment: no division
   // inside the loop when a row has at most blockDim groups.
   const int nt = blockDim.x;
@@ -120,53 +109,61 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsParams P) {
       for (int j = 0; j < 48; ++j)
         if (j < 3 * npx) wd[j >> 2] |= (uint32_t)__ldg(p + j) << ((j & 3) * 8);
     }
-    // Pooled full-frame histogram.
-    hist_runs<0>(wd, 0, npx, s_pool);
-    hist_runs<1>(wd, 0, npx, s_pool + 256);
-    hist_runs<2>(wd, 0, npx, s_pool + 512);
     // Overlap rectangles: the group's pixel range [i0, i1) inside each.
+    int i0q[2], i1q[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      if (!act[q] || y < R[q].ry0 || y >= R[q].ry1) continue;
-      const int i0 = max(0, R[q].rx0 - x0), i1 = min(npx, R[q].rx1 - x0);
-      if (i0 >= i1) continue;
-      uint32_t *Hs = s_role + q * kRoleWords;
-      hist_runs<0>(wd, i0, i1, Hs);
-      hist_runs<1>(wd, i0, i1, Hs + 256);
-      hist_runs<2>(wd, i0, i1, Hs + 512);
-      if (R[q].is_i) {
-        uint32_t *W = Hs + 768;
-        uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u, a4 = 0u, a5 = 0u;
+      const bool in = act[q] && y >= R[q].ry0 && y < R[q].ry1;
+      i0q[q] = in ? max(0, R[q].rx0 - x0) : 16;
+      i1q[q] = in ? min(npx, R[q].rx1 - x0) : 0;
+    }
+    uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u, a4 = 0u, a5 = 0u;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          if (i >= i0 && i < i1) {
-            const uint32_t r = byte_of(wd, 3 * i);
-            const uint32_t gg = byte_of(wd, 3 * i + 1);
-            const uint32_t b = byte_of(wd, 3 * i + 2);
-            atomicAdd(&W[0 * 256 + gg], r);   // (c,d) = (0,1): indexed by x_1, adds x_0
-            atomicAdd(&W[1 * 256 + b], r);    // (0,2)
-            atomicAdd(&W[2 * 256 + r], gg);   // (1,0)
-            atomicAdd(&W[3 * 256 + b], gg);   // (1,2)
-            atomicAdd(&W[4 * 256 + r], b);    // (2,0)
-            atomicAdd(&W[5 * 256 + gg], b);   // (2,1)
-            a0 += r * r;
-            a1 += r * gg;
-            a2 += r * b;
-            a3 += gg * gg;
-            a4 += gg * b;
-            a5 += b * b;
+    for (int i = 0; i < 16; ++i) {
+      if (i < npx) {
+        const uint32_t r = byte_of(wd, 3 * i);
+        const uint32_t gg = byte_of(wd, 3 * i + 1);
+        const uint32_t b = byte_of(wd, 3 * i + 2);
+        atomicAdd(&s_pool[r], 1u);
+        atomicAdd(&s_pool[256 + gg], 1u);
+        atomicAdd(&s_pool[512 + b], 1u);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (i >= i0q[q] && i < i1q[q]) {
+            uint32_t *Hs = s_role + q * kRoleWords;
+            atomicAdd(&Hs[r], 1u);
+            atomicAdd(&Hs[256 + gg], 1u);
+            atomicAdd(&Hs[512 + b], 1u);
+            if (q == iq) {
+              uint32_t *W = Hs + 768;
+              atomicAdd(&W[0 * 256 + gg], r);   // (c,d) = (0,1): indexed by x_1, adds x_0
+              atomicAdd(&W[1 * 256 + b], r);    // (0,2)
+              atomicAdd(&W[2 * 256 + r], gg);   // (1,0)
+              atomicAdd(&W[3 * 256 + b], gg);   // (1,2)
+              atomicAdd(&W[4 * 256 + r], b);    // (2,0)
+              atomicAdd(&W[5 * 256 + gg], b);   // (2,1)
+              a0 += r * r;
+              a1 += r * gg;
+              a2 += r * b;
+              a3 += gg * gg;
+              a4 += gg * b;
+              a5 += b * b;
+            }
           }
         }
-        // 16 pixels x 255^2 fits in 32 bits; the block total needs 64.
-        atomicAdd(&s_A[q * 6 + 0], (unsigned long long)a0);
-        atomicAdd(&s_A[q * 6 + 1], (unsigned long long)a1);
-        atomicAdd(&s_A[q * 6 + 2], (unsigned long long)a2);
-        atomicAdd(&s_A[q * 6 + 3], (unsigned long long)a3);
-        atomicAdd(&s_A[q * 6 + 4], (unsigned long long)a4);
-        atomicAdd(&s_A[q * 6 + 5], (unsigned long long)a5);
       }
     }
+    // 16 pixels x 255^2 fits in 32 bits; the running total needs 64.
+    acc[0] += a0; acc[1] += a1; acc[2] += a2; acc[3] += a3; acc[4] += a4; acc[5] += a5;
     if (rowwise) rr += rpi; else idx += nt;
+  }
+  // Gram sums: warp reduction, then one shared 64-bit add per warp.
+  if (iq >= 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const unsigned long long sum = warp_sum_u64(acc[k]);
+      if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_A[iq * 6 + k], sum);
+    }
   }
   __syncthreads();
 
