@@ -16,6 +16,13 @@ taken before frame T is fused:
 If the window's A is ill-conditioned (1-norm condition > 1e12) or a side of
 the overlap is empty, the pair keeps its previous M (identity before the
 first success) and the frame is flagged singular.
+
+Learned mode (flag LEARNED with a network given): after the plain estimate,
+each pair's features are its window-pooled overlap histograms (side i then
+side j, each scaled by 256 / count, bfloat16), the network predicts M_hat - I
+(``oracle.mlp``), and the pair takes M_hat when its plain fit succeeded and
+r = ||A M_hat - B||_F / ||B||_F <= 1e-3 over the window's A and B; otherwise
+it keeps the plain result. The chosen matrices are chained as usual.
 """
 from __future__ import annotations
 
@@ -23,13 +30,14 @@ import numpy as np
 
 from . import balance as bal
 from . import color as col
+from . import mlp as _mlp
 from .geometry import Geometry
 from .warp import stitch as _stitch, fuse_pixels, finish
 
 
 class OracleStitcher:
     def __init__(self, H, cam_w, cam_h, pano_w, pano_h, ref_cam=None, window=3,
-                 lam=0.05, max_flow=8.0, flags=0):
+                 lam=0.05, max_flow=8.0, flags=0, mlp=None):
         self.geom = Geometry(H, cam_w, cam_h, pano_w, pano_h, ref_cam)
         self.window = int(window)
         self.lam = float(lam)
@@ -44,6 +52,11 @@ class OracleStitcher:
         self.curve = bal.curve_params(np.zeros(3), np.zeros(3), self.lam)
         self.singular = False
         self.last_stats = None
+        self.mlp = mlp                         # dict(params, mu, sd) for learned mode
+        self.hist_hist = []                    # per frame: list of (Hi, Hj) per pair
+        self.learned = None                    # latest (M_hat, r, used) per pair
+        self.n_learned = 0
+        self.n_fallback = 0
 
     # -- statistics of one frame (section 2.1 steps 2-3, Eq. 3 terms) --------
     def frame_stats(self, frames):
@@ -68,8 +81,10 @@ class OracleStitcher:
         st = self.frame_stats(frames)
         self.last_stats = st
         self.ab_hist.append([(pp["A"], pp["B"], pp["n_i"], pp["n_j"]) for pp in st["pairs"]])
+        self.hist_hist.append([(pp["Hi"], pp["Hj"]) for pp in st["pairs"]])
         win = self.ab_hist[-self.window:]
         self.singular = False
+        ok_p, AB = [], []
         for p in range(g.n - 1):
             A = sum(w[p][0] for w in win)
             B = sum(w[p][1] for w in win)
@@ -79,6 +94,10 @@ class OracleStitcher:
                 self.M_pair[p] = M
             else:
                 self.singular = True
+            ok_p.append(ok)
+            AB.append((A, B))
+        if (self.flags & 8) and self.mlp is not None and g.n > 1:
+            self._learned_select(ok_p, AB)
         self.M_cam = col.chain_to_reference(self.M_pair, g.pairs, g.ref, g.n)
         m1, m2 = bal.knots(st["pooled"], self.lam)
         self.knot_hist.append((m1, m2))
@@ -86,6 +105,38 @@ class OracleStitcher:
         self.curve = bal.curve_params(sm1, sm2, self.lam)
         self.T += 1
         return not self.singular
+
+    def learned_features(self):
+        """Window-pooled features of every pair, (n_pairs, 1536) float64 of
+        bfloat16 values."""
+        hw = self.hist_hist[-self.window:]
+        rows = []
+        for p in range(self.geom.n - 1):
+            Hi = sum(np.asarray(h[p][0], dtype=np.int64) for h in hw)
+            Hj = sum(np.asarray(h[p][1], dtype=np.int64) for h in hw)
+            ni, nj = int(Hi[0].sum()), int(Hj[0].sum())
+            fi = (Hi.reshape(-1) * 256.0) / ni if ni else np.zeros(768)
+            fj = (Hj.reshape(-1) * 256.0) / nj if nj else np.zeros(768)
+            rows.append(np.concatenate([fi, fj]))
+        return _mlp.round_bf16(np.stack(rows))
+
+    def _learned_select(self, ok_p, AB):
+        X = self.learned_features()
+        Y, _ = _mlp.forward(self.mlp["params"], X)
+        Y = Y[:, :_mlp.N_OUT] * np.asarray(self.mlp["sd"], dtype=np.float64) + np.asarray(self.mlp["mu"],
+                                                                                           dtype=np.float64)
+        out = []
+        for p, (A, B) in enumerate(AB):
+            M_hat = np.eye(3) + Y[p, :9].reshape(3, 3)
+            r = _mlp.residual(A, B, M_hat)
+            use = bool(ok_p[p] and np.all(np.isfinite(M_hat)) and r <= 1e-3)
+            if use:
+                self.M_pair[p] = M_hat
+                self.n_learned += 1
+            else:
+                self.n_fallback += 1
+            out.append((M_hat, r, use))
+        self.learned = out
 
     def frame(self, frames, flows_ij, flows_ji):
         frames = [np.asarray(f) for f in frames]
