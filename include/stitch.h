@@ -258,6 +258,109 @@ int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count);
 int stitch_estimate_color_noalloc(const stitch_config *cfg, const uint8_t *const *frames_dev, double *M_out_dev,
                                   float *curve_out_dev, int *flags_out_dev, stitch_stream_t stream);
 
+/*
+ * Learned colour estimator. The paper estimates M only by the plain fit of
+ * section 2.1 (Eq. 1-3); this part predicts it with a small network and keeps
+ * the plain fit as its fallback and judge.
+ *
+ * Network: STITCH_MLP_IN -> 512 -> 512 -> 256 -> STITCH_MLP_OUT, bfloat16
+ * weights and activations, float32 accumulation, ReLU after every layer but
+ * the last. Input (features) per overlap pair: bfloat16, the three channel
+ * histograms of side i then of side j, each bin scaled by 256 / pixel count
+ * (so a flat histogram reads 1). Output (targets) per pair, float32:
+ * M - I (9, row-major, row-vector convention of Eq. 4) then, per channel,
+ * the span (m2 - m1) / 255 of the lambda-quantile knots (section 2.2) of the
+ * pair's pooled histograms. The network works on targets normalised
+ * per output, t_n = (t - mu) / sd (stitch_mlp_set_norm).
+ *
+ * Parameters (stitch_mlp_get_params / set_params): float32, layer by layer,
+ * each layer W [out][in] row-major then b [out]; the last layer is stored
+ * padded to 16 outputs (rows 12..15 are zero and stay zero).
+ * stitch_mlp_n_params() gives the total count.
+ */
+#define STITCH_MLP_IN 1536
+#define STITCH_MLP_OUT 12
+typedef struct stitch_mlp stitch_mlp;
+
+int stitch_mlp_n_params(void);
+
+/* Create a network with He-normal weights drawn from `seed` (a host
+ * Mersenne-Twister stream) and buffers for batches up to max_batch (a
+ * multiple of 32, at most 65536). Allocates device memory; synchronises. */
+int stitch_mlp_create(int max_batch, unsigned long long seed, stitch_mlp **out);
+void stitch_mlp_destroy(stitch_mlp *mlp);
+
+/* Target normalisation: mu_host and sd_host hold STITCH_MLP_OUT floats
+ * (sd > 0). Synchronous. Default: mu = 0, sd = 1. */
+int stitch_mlp_set_norm(stitch_mlp *mlp, const float *mu_host, const float *sd_host);
+
+/* Copy all parameters to / from a host buffer of stitch_mlp_n_params()
+ * floats (layout above). Synchronous. */
+int stitch_mlp_get_params(stitch_mlp *mlp, float *params_host);
+int stitch_mlp_set_params(stitch_mlp *mlp, const float *params_host);
+
+/* Inference: x_dev = batch x STITCH_MLP_IN bfloat16 (raw 16-bit patterns,
+ * 16-byte aligned), y_dev = batch x STITCH_MLP_OUT float32 in target units
+ * (de-normalised). 1 <= batch <= max_batch. Asynchronous on `stream`. */
+int stitch_mlp_forward(stitch_mlp *mlp, const uint16_t *x_dev, int batch, float *y_dev, stitch_stream_t stream);
+
+/* One training step: forward, mean squared error over the normalised
+ * targets (t_dev: batch x STITCH_MLP_OUT float32, target units), backward,
+ * Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on the float32 master
+ * parameters, then the bfloat16 copies are refreshed. batch: a multiple of
+ * 32 up to max_batch. loss_dev (optional): one float, the batch loss before
+ * the update. Asynchronous on `stream`. */
+int stitch_mlp_train_step(stitch_mlp *mlp, const uint16_t *x_dev, const float *t_dev, int batch, float lr,
+                          float *loss_dev, stitch_stream_t stream);
+
+/* Gradients of the batch loss with respect to every parameter (same layout
+ * as the parameters), for checking the backward pass; no update. Synchronous
+ * (legacy default stream). */
+int stitch_mlp_gradients(stitch_mlp *mlp, const uint16_t *x_dev, const float *t_dev, int batch, float *grads_host,
+                         float *loss_host);
+
+/*
+ * stitch_pairs_label -- plain estimate of many independent overlap pairs (the
+ * training labeller): per pair the one-frame fit of section 2.1 (spec LUT,
+ * Eq. 3 solved in float64; cond_1(A) > 1e12 or an empty side gives I and a
+ * flag), the features above and the targets above.
+ *   pairs_dev:    n_pairs x 2 x patch_h x patch_w x 3 bytes: per pair the side
+ *                 i patch then the side j patch, packed RGB.
+ *   lambda:       balance quantile, 0 < lambda < 0.5.
+ *   features_dev: n_pairs x STITCH_MLP_IN bfloat16 (written).
+ *   targets_dev:  n_pairs x STITCH_MLP_OUT float32 (written).
+ *   M_dev, flags_dev: optional, n_pairs x 9 doubles and n_pairs ints.
+ * Asynchronous on `stream`.
+ */
+int stitch_pairs_label(const uint8_t *pairs_dev, int n_pairs, int patch_w, int patch_h, double lambda,
+                       uint16_t *features_dev, float *targets_dev, double *M_dev, int *flags_dev,
+                       stitch_stream_t stream);
+
+/*
+ * stitch_attach_mlp -- give a context (created with STITCH_LEARNED) the
+ * network it predicts M with; NULL detaches. The context does not own the
+ * network: keep it alive while the context may use it. With a network
+ * attached, each colour estimate also forms the window-pooled features of
+ * every pair, runs the network and forms the residual
+ * r = ||A M_hat - B||_F / ||B||_F from the window's exact A and B; a pair with
+ * r <= 1e-3 takes M_hat, any other pair keeps the plain fit. The balance
+ * curve always comes from the plain estimate (its knots are exact integer
+ * quantiles). Without a network a STITCH_LEARNED context behaves as a plain
+ * one.
+ */
+int stitch_attach_mlp(stitch_ctx *ctx, stitch_mlp *mlp);
+
+/* Counts since stitch_init: pair estimates that used the network's M, and
+ * pair estimates that fell back to the plain fit. Synchronises the context's
+ * work. */
+int stitch_learned_stats(stitch_ctx *ctx, long long *n_learned, long long *n_fallback);
+
+/* The latest learned estimate of every pair (n_pairs entries each, any may
+ * be NULL): the network's M_hat (9 doubles, row-major), its residual r and
+ * whether the pair took it (1) or kept the plain fit (0). STITCH_LEARNED
+ * contexts only. Synchronises the context's work. */
+int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used);
+
 /* Number of adjacent pairs (n_cams - 1), or -1 for a NULL context. */
 int stitch_n_pairs(const stitch_ctx *ctx);
 

@@ -7,9 +7,8 @@ For one pair (a patch of side i and a patch of side j, packed RGB) the label
 is the one-frame plain fit of section 2.1: histograms (step 2), the
 specification LUT (step 3), A = I_i^T I_i and B = I_i^T L(I_i), M = A^-1 B
 (Eq. 3, float64; an ill-conditioned A or an empty side gives I and a flag),
-plus, per channel, the slope of the linear balance segment (Eq. 5 reading)
-of the two patches' pooled histogram: s = (d2 - d1) / (m2 - m1), or 1 when
-m2 - m1 < 1 (the identity curve).
+plus, per channel, the span (m2 - m1) / 255 of the lambda-quantile knots
+(section 2.2) of the two patches' pooled histogram.
 
 Features: each side's three channel histograms scaled by 256 / pixel count,
 side i first, channel-major, rounded to bfloat16.
@@ -36,10 +35,7 @@ def label(patch_i, patch_j, lam=0.05):
     if not ok:
         M = np.eye(3)
     m1, m2 = balance.knots(Hi + Hj, lam)
-    lq = balance.lambda_q(lam) / 1e6
-    d1, d2 = 255.0 * lq, 255.0 * (1.0 - lq)
-    span = (m2 - m1).astype(np.float64)
-    s = np.where(span < 1.0, 1.0, (d2 - d1) / np.where(span < 1.0, 1.0, span))
+    s = (m2 - m1).astype(np.float64) / 255.0
     ni, nj = pi.shape[0], pj.shape[0]
     fi = (Hi.reshape(-1) * 256.0) / ni if ni else np.zeros(768)
     fj = (Hj.reshape(-1) * 256.0) / nj if nj else np.zeros(768)

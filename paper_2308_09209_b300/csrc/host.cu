@@ -343,6 +343,8 @@ struct stitch_ctx {
   float *stage_fij[kMaxPairs] = {};
   float *stage_fji[kMaxPairs] = {};
   uint8_t *stage_pano = nullptr;
+  LearnedState *ls = nullptr;         // learned estimator state (STITCH_LEARNED contexts)
+  stitch_mlp *mlp = nullptr;          // attached network (not owned)
 };
 
 namespace {
@@ -415,6 +417,25 @@ int launch_estimate_for(stitch_ctx *ctx, cudaStream_t s) {
   cudaEvent_t e0 = prof_mark(ctx, s);
   cudaError_t e = launch_estimate(ctx->ep, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  if (ctx->mlp && ctx->ls && ctx->g.n > 1) {
+    // Learned estimate of frame T (after the plain one): features, network, residual test.
+    LearnedParams lp{};
+    lp.n_cams = ctx->g.n;
+    lp.n_pairs = ctx->g.n - 1;
+    lp.ref = ctx->g.ref;
+    lp.window = ctx->window;
+    lp.raw_slots = kRawSlots;
+    lp.raw = ctx->raw;
+    lp.state = ctx->state;
+    lp.ls = ctx->ls;
+    e = launch_learned_features(lp, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "learned features launch");
+    const int rc = stitch_mlp_forward(ctx->mlp, reinterpret_cast<const uint16_t *>(&ctx->ls->feat[0][0]), lp.n_pairs,
+                                      &ctx->ls->y[0][0], reinterpret_cast<stitch_stream_t>(s));
+    if (rc != STITCH_OK) return set_err(ctx, rc, std::string("network forward: ") + g_last_error);
+    e = launch_learned_select(lp, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "learned select launch");
+  }
   cudaEvent_t e1 = prof_mark(ctx, s);
   prof_pair(ctx, e0, e1, 1);
   return STITCH_OK;
@@ -567,6 +588,10 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->state, sizeof(ColorState));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, (band_tiles.size() + own_tiles.size()) * sizeof(TileDesc) + 16);
   if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, kRawSlots * sizeof(RawStats));
+  if (e == cudaSuccess && (cfg->flags & STITCH_LEARNED)) {
+    e = cudaMalloc(&ctx->ls, sizeof(LearnedState));
+    if (e == cudaSuccess) e = cudaMemset(ctx->ls, 0, sizeof(LearnedState));
+  }
   // Band pre-warp pieces and the intermediate (both cameras of every band).
   std::vector<PwTile> pw_tiles;
   size_t pw_elems = 0;
@@ -1019,7 +1044,7 @@ struct StateHeader {
 
 int stitch_save_state(stitch_ctx *ctx, void *buf, size_t *size) {
   if (!ctx || !size) return set_err(ctx, STITCH_EINVAL, "ctx and size are required");
-  const size_t need = sizeof(StateHeader) + sizeof(ColorState);
+  const size_t need = sizeof(StateHeader) + sizeof(ColorState) + (ctx->ls ? sizeof(LearnedState) : 0);
   if (!buf) {
     *size = need;
     return STITCH_OK;
@@ -1030,6 +1055,9 @@ int stitch_save_state(stitch_ctx *ctx, void *buf, size_t *size) {
   StateHeader hd{kStateMagic, ctx->g.n, ctx->window, ctx->host_T, sizeof(ColorState)};
   std::memcpy(buf, &hd, sizeof(hd));
   e = cudaMemcpy(static_cast<char *>(buf) + sizeof(hd), ctx->state, sizeof(ColorState), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && ctx->ls)
+    e = cudaMemcpy(static_cast<char *>(buf) + sizeof(hd) + sizeof(ColorState), ctx->ls, sizeof(LearnedState),
+                   cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_err(ctx, e, "state read");
   *size = need;
   return STITCH_OK;
@@ -1047,6 +1075,14 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
     e = cudaMemcpy(ctx->state, static_cast<const char *>(buf) + sizeof(hd), sizeof(ColorState),
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, kRawSlots * sizeof(RawStats));
+  if (e == cudaSuccess && ctx->ls) {
+    // A learned context restores its window of histograms when the buffer has it.
+    if (size >= sizeof(StateHeader) + sizeof(ColorState) + sizeof(LearnedState))
+      e = cudaMemcpy(ctx->ls, static_cast<const char *>(buf) + sizeof(hd) + sizeof(ColorState), sizeof(LearnedState),
+                     cudaMemcpyHostToDevice);
+    else
+      e = cudaMemset(ctx->ls, 0, sizeof(LearnedState));
+  }
   if (e != cudaSuccess) return cuda_err(ctx, e, "state write");
   ctx->host_T = hd.host_T;
   return STITCH_OK;
@@ -1084,6 +1120,52 @@ int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count) {
   return STITCH_OK;
 }
 
+int stitch_attach_mlp(stitch_ctx *ctx, stitch_mlp *mlp) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (mlp && !ctx->ls) return set_err(ctx, STITCH_EINVAL, "the context was not created with STITCH_LEARNED");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
+  ctx->mlp = mlp;
+  // Recorded sequences embed the launches of the estimate stage: record again.
+  for (auto &ge : ctx->graphs) {
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    for (auto &pp : ge.pairs) {
+      cudaEventDestroy(pp.a);
+      cudaEventDestroy(pp.b);
+    }
+  }
+  ctx->graphs.clear();
+  return STITCH_OK;
+}
+
+int stitch_learned_stats(stitch_ctx *ctx, long long *n_learned, long long *n_fallback) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  long long a = 0, b = 0;
+  if (ctx->ls) {
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned long long v[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpy(v, &ctx->ls->n_learned, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "learned counters read");
+    a = (long long)v[0];
+    b = (long long)v[1];
+  }
+  if (n_learned) *n_learned = a;
+  if (n_fallback) *n_fallback = b;
+  return STITCH_OK;
+}
+
+int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (!ctx->ls) return set_err(ctx, STITCH_EINVAL, "the context was not created with STITCH_LEARNED");
+  const int np = ctx->g.n - 1;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && M_hat && np > 0) e = cudaMemcpy(M_hat, ctx->ls->M_hat, sizeof(double) * 9 * np, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && resid && np > 0) e = cudaMemcpy(resid, ctx->ls->resid, sizeof(double) * np, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && used && np > 0) e = cudaMemcpy(used, ctx->ls->used, sizeof(int) * np, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "learned state read");
+  return STITCH_OK;
+}
+
 int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
 
 const char *stitch_last_error(const stitch_ctx *ctx) {
@@ -1112,6 +1194,7 @@ void stitch_destroy(stitch_ctx *ctx) {
       if (ctx->pev[a][b]) cudaEventDestroy(ctx->pev[a][b]);
   cudaFree(ctx->raw);
   cudaFree(ctx->state);
+  cudaFree(ctx->ls);
   cudaFree(ctx->tiles);
   cudaFree(ctx->pw_tiles);
   cudaFree(ctx->pw);

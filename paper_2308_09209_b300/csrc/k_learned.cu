@@ -1,0 +1,150 @@
+// Learned estimate of the pair matrices inside the per-frame pipeline. Runs
+// after the plain estimate (K2) of frame T, which has stored the window's
+// exact Eq. 3 terms, the plain M of every pair and advanced the frame index.
+//
+// k_learned_features: per pair, keep frame T's overlap histograms in a ring,
+// pool them over the window {T-W+1..T} and write the network's features
+// (each side's histograms scaled by 256 / count, bfloat16).
+// The network then runs on these features (k_mlp.cu).
+// k_learned_select: per pair, M_hat = I + the network's first nine outputs and
+// the residual r = ||A M_hat - B||_F / ||B||_F over the window's summed A and
+// B (float64). A pair whose plain fit succeeded and whose r <= 1e-3 takes
+// M_hat; any other pair keeps the plain result. The chosen matrices are
+// chained to the reference camera again and replace frame T's colour output.
+#include "estimate_common.cuh"
+#include "stitch_internal.h"
+
+namespace stitch {
+
+namespace {
+
+using namespace est;
+
+constexpr double kResidLimit = 1e-3;
+
+__global__ void __launch_bounds__(256) k_learned_features(const LearnedParams P) {
+  const int p = blockIdx.x;
+  const int frame = P.state->T - 1;
+  const int slot = frame % kMaxWindow;
+  const RawStats *raw = P.raw + (frame % P.raw_slots);
+  LearnedState *L = P.ls;
+  const int nw = min(frame + 1, P.window);
+  __shared__ uint32_t H[2][768];
+  __shared__ unsigned long long n[2];
+  if (threadIdx.x < 2) n[threadIdx.x] = 0ull;
+  for (int i = threadIdx.x; i < 768; i += blockDim.x) {
+    const uint32_t hi = (&raw->Hi[p][0][0])[i], hj = (&raw->Hj[p][0][0])[i];
+    L->H_ring[slot][p][0][i] = hi;
+    L->H_ring[slot][p][1][i] = hj;
+    uint32_t si = hi, sj = hj;
+    for (int k = 1; k < nw; ++k) {
+      const int sl = (frame - k) % kMaxWindow;
+      si += L->H_ring[sl][p][0][i];
+      sj += L->H_ring[sl][p][1][i];
+    }
+    H[0][i] = si;
+    H[1][i] = sj;
+  }
+  __syncthreads();
+  // pixel counts: the sum of channel 0 of each side (one warp per side)
+  const int warp = threadIdx.x >> 5;
+  if (warp < 2) {
+    unsigned long long s = 0ull;
+    for (int v = threadIdx.x & 31; v < 256; v += 32) s += H[warp][v];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) n[warp] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 1536; i += blockDim.x) {
+    const int side = i / 768;
+    const unsigned long long c = n[side];
+    // (H * 256) / n in float64, then float32, then bfloat16 (both round to nearest even)
+    const double f = c ? ((double)H[side][i % 768] * 256.0) / (double)c : 0.0;
+    L->feat[p][i] = __float2bfloat16_rn(__double2float_rn(f));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_learned_select(const LearnedParams P) {
+  ColorState *S = P.state;
+  LearnedState *L = P.ls;
+  const int frame = S->T - 1;
+  const int np = P.n_pairs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double M_pair[kMaxPairs][9];
+  __shared__ double M_cam[kMaxCams][9];
+  __shared__ int n_used;
+  if (threadIdx.x == 0) n_used = 0;
+  __syncthreads();
+  if (warp < np) {
+    const int p = warp;
+    const int e = lane < 9 ? lane : 0;
+    const int r = e / 3, c = e % 3;
+    static const int sym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+    const int nw = min(frame + 1, P.window);
+    unsigned long long As = 0ull, Bs = 0ull;
+    for (int i = 0; i < nw; ++i) {
+      const int sl = (frame - i) % kMaxWindow;
+      As += S->A_ring[sl][p][sym[e]];
+      Bs += S->B_ring[sl][p][e];
+    }
+    const double a = (double)As, b = (double)Bs;
+    const double mh = (double)L->y[p][e] + (r == c ? 1.0 : 0.0);
+    // (A M_hat)(r, c) = sum_k A(r, k) M_hat(k, c)
+    double am = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) am += __shfl_sync(0xffffffffu, a, r * 3 + k) * __shfl_sync(0xffffffffu, mh, k * 3 + c);
+    double num = lane < 9 ? (am - b) * (am - b) : 0.0;
+    double den = lane < 9 ? b * b : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_down_sync(0xffffffffu, num, o);
+      den += __shfl_down_sync(0xffffffffu, den, o);
+    }
+    num = __shfl_sync(0xffffffffu, num, 0);
+    den = __shfl_sync(0xffffffffu, den, 0);
+    const double res = den > 0.0 ? sqrt(num / den) : INFINITY;
+    const bool plain_ok = ((S->singular_last >> p) & 1) == 0;
+    const bool use = plain_ok && isfinite(mh) && res <= kResidLimit;   // NaN fails both tests
+    const bool all_finite = __all_sync(0xffffffffu, lane >= 9 || isfinite(mh));
+    const bool take = use && all_finite;
+    if (lane < 9) {
+      L->M_hat[p][lane] = mh;
+      M_pair[p][lane] = take ? mh : S->M_pair[p][lane];
+    }
+    if (lane == 0) {
+      L->resid[p] = res;
+      L->used[p] = take ? 1 : 0;
+      if (take) atomicAdd(&n_used, 1);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    warp_chain(M_pair, M_cam, P.n_cams, P.ref);
+    ColorOut &o = S->out[frame % kColorSlots];
+    for (int i = lane; i < P.n_cams * 9; i += 32) {
+      S->M_cam[i / 9][i % 9] = M_cam[i / 9][i % 9];
+      o.M[i / 9][i % 9] = (float)M_cam[i / 9][i % 9];
+    }
+    for (int i = lane; i < np * 9; i += 32) S->M_pair[i / 9][i % 9] = M_pair[i / 9][i % 9];
+    if (lane == 0) {
+      L->n_learned += (unsigned long long)n_used;
+      L->n_fallback += (unsigned long long)(np - n_used);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_learned_features(const LearnedParams &p, cudaStream_t s) {
+  if (p.n_pairs <= 0) return cudaSuccess;
+  k_learned_features<<<p.n_pairs, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_learned_select(const LearnedParams &p, cudaStream_t s) {
+  if (p.n_pairs <= 0) return cudaSuccess;
+  k_learned_select<<<1, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace stitch

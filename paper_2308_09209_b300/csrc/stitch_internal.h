@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/stitch.h"
@@ -142,6 +143,40 @@ struct EstimateParams {
   ColorState *state;
 };
 
+// One batch of independent overlap pairs for the labeller of the learned
+// estimator: pair p is two packed-RGB patches of pw x ph pixels, side i then
+// side j, at pairs + p * 2 * pw * ph * 3.
+struct PairParams {
+  const uint8_t *pairs;
+  int n, pw, ph;
+  long long lambda_q;                 // lambda in millionths
+  __nv_bfloat16 *feat;                // [n][1536]
+  float *targ;                        // [n][12]
+  double *M;                          // [n][9] or null
+  int *flags;                         // [n] or null
+};
+
+// State of the learned estimator inside a context: the per-frame overlap
+// histograms of the last kMaxWindow frames (the window-pooled features), the
+// features and network output of the latest frame, and its decisions.
+struct LearnedState {
+  uint32_t H_ring[kMaxWindow][kMaxPairs][2][768];
+  __nv_bfloat16 feat[kMaxPairs][STITCH_MLP_IN];
+  float y[32][STITCH_MLP_OUT];        // network output, target units (rows >= n_pairs unused)
+  double M_hat[kMaxPairs][9];
+  double resid[kMaxPairs];
+  int used[kMaxPairs];
+  int pad;
+  unsigned long long n_learned, n_fallback;
+};
+
+struct LearnedParams {
+  int n_cams, n_pairs, ref, window, raw_slots;
+  const RawStats *raw;
+  ColorState *state;
+  LearnedState *ls;
+};
+
 // Launchers (defined in the kernel files).
 cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
@@ -151,6 +186,8 @@ cudaError_t launch_fuse(const FuseParams &p, cudaStream_t s);
 cudaError_t fuse_setup_attributes(int max_halo);
 size_t stats_smem_bytes();
 size_t prewarp_elem_bytes(bool fp16);
+cudaError_t launch_learned_features(const LearnedParams &p, cudaStream_t s);
+cudaError_t launch_learned_select(const LearnedParams &p, cudaStream_t s);
 
 }  // namespace stitch
 

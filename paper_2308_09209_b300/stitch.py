@@ -92,6 +92,19 @@ def lib():
             "stitch_profile": (ip, [vp, ip]),
             "stitch_profile_read": (ip, [vp, vp, vp]),
             "stitch_estimate_color_noalloc": (ip, [cfgp, pp, vp, vp, vp, vp]),
+            "stitch_mlp_n_params": (ip, []),
+            "stitch_mlp_create": (ip, [ip, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
+            "stitch_mlp_destroy": (None, [vp]),
+            "stitch_mlp_set_norm": (ip, [vp, vp, vp]),
+            "stitch_mlp_get_params": (ip, [vp, vp]),
+            "stitch_mlp_set_params": (ip, [vp, vp]),
+            "stitch_mlp_forward": (ip, [vp, vp, ip, vp, vp]),
+            "stitch_mlp_train_step": (ip, [vp, vp, vp, ip, ctypes.c_float, vp, vp]),
+            "stitch_mlp_gradients": (ip, [vp, vp, vp, ip, vp, vp]),
+            "stitch_pairs_label": (ip, [vp, ip, ip, ip, ctypes.c_double, vp, vp, vp, vp, vp]),
+            "stitch_attach_mlp": (ip, [vp, vp]),
+            "stitch_learned_stats": (ip, [vp, vp, vp]),
+            "stitch_get_learned": (ip, [vp, vp, vp, vp]),
             "stitch_n_pairs": (ip, [vp]),
             "stitch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_destroy": (None, [vp]),
@@ -306,6 +319,117 @@ def stitch_estimate_color_noalloc(cfg: Config, frames, M_out, curve_out, flags_o
                                                       ctypes.c_void_p(M_out.data_ptr()),
                                                       ctypes.c_void_p(curve_out.data_ptr()), fl,
                                                       _stream(stream)))
+
+
+# --------------------------------------------------------------------------- #
+# Learned estimator
+# --------------------------------------------------------------------------- #
+STITCH_MLP_IN = 1536
+STITCH_MLP_OUT = 12
+
+
+def _dp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def stitch_mlp_n_params() -> int:
+    return lib().stitch_mlp_n_params()
+
+
+def stitch_mlp_create(max_batch: int, seed: int):
+    out = ctypes.c_void_p()
+    _check(lib().stitch_mlp_create(max_batch, seed, ctypes.byref(out)))
+    return out
+
+
+def stitch_mlp_destroy(mlp) -> None:
+    if mlp is not None and mlp.value:
+        lib().stitch_mlp_destroy(mlp)
+
+
+def stitch_mlp_set_norm(mlp, mu, sd) -> int:
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    sd = np.ascontiguousarray(sd, dtype=np.float32)
+    assert mu.size == STITCH_MLP_OUT and sd.size == STITCH_MLP_OUT
+    return _check(lib().stitch_mlp_set_norm(mlp, mu.ctypes.data, sd.ctypes.data))
+
+
+def stitch_mlp_get_params(mlp) -> np.ndarray:
+    out = np.zeros(stitch_mlp_n_params(), dtype=np.float32)
+    _check(lib().stitch_mlp_get_params(mlp, out.ctypes.data))
+    return out
+
+
+def stitch_mlp_set_params(mlp, params) -> int:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == stitch_mlp_n_params()
+    return _check(lib().stitch_mlp_set_params(mlp, p.ctypes.data))
+
+
+def stitch_mlp_forward(mlp, x, batch: int, y, stream=None) -> int:
+    """x: bfloat16 (or int16 bit patterns) CUDA tensor [batch, 1536]; y: float32 CUDA tensor [batch, 12]."""
+    return _check(lib().stitch_mlp_forward(mlp, _dp(x), batch, _dp(y), _stream(stream)))
+
+
+def stitch_mlp_train_step(mlp, x, t, batch: int, lr: float, loss=None, stream=None) -> int:
+    return _check(lib().stitch_mlp_train_step(mlp, _dp(x), _dp(t), batch, lr, _dp(loss), _stream(stream)))
+
+
+def stitch_mlp_gradients(mlp, x, t, batch: int):
+    """(gradients float32 [n_params], loss) of one batch, without an update."""
+    g = np.zeros(stitch_mlp_n_params(), dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(lib().stitch_mlp_gradients(mlp, _dp(x), _dp(t), batch, g.ctypes.data, loss.ctypes.data))
+    return g, float(loss[0])
+
+
+def stitch_pairs_label(pairs, n_pairs: int, patch_w: int, patch_h: int, lam: float, features, targets,
+                       M=None, flags=None, stream=None) -> int:
+    """Plain one-frame fit, features and targets of n_pairs independent pairs
+    (uint8 CUDA tensor [n_pairs, 2, patch_h, patch_w, 3])."""
+    return _check(lib().stitch_pairs_label(_dp(pairs), n_pairs, patch_w, patch_h, lam, _dp(features), _dp(targets),
+                                           _dp(M), _dp(flags), _stream(stream)))
+
+
+def stitch_attach_mlp(ctx, mlp) -> int:
+    return _check(lib().stitch_attach_mlp(ctx, mlp), ctx)
+
+
+def stitch_learned_stats(ctx):
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().stitch_learned_stats(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
+
+
+def stitch_get_learned(ctx, n_pairs: int):
+    """(M_hat [n_pairs, 3, 3], residual [n_pairs], used [n_pairs]) of the latest frame."""
+    M = np.zeros((max(n_pairs, 1), 3, 3), dtype=np.float64)
+    r = np.zeros(max(n_pairs, 1), dtype=np.float64)
+    u = np.zeros(max(n_pairs, 1), dtype=np.int32)
+    _check(lib().stitch_get_learned(ctx, M.ctypes.data, r.ctypes.data, u.ctypes.data), ctx)
+    return M[:n_pairs], r[:n_pairs], u[:n_pairs]
+
+
+class Mlp:
+    """Owner of a network handle (stitch_mlp)."""
+
+    def __init__(self, max_batch: int = 256, seed: int = 0):
+        self.max_batch = max_batch
+        self.h = stitch_mlp_create(max_batch, seed)
+
+    def close(self):
+        if self.h is not None:
+            stitch_mlp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        if sys is None or sys.is_finalizing():
+            return
+        try:
+            if getattr(self, "h", None) is not None:
+                self.close()
+        except Exception:
+            pass
 
 
 def stitch_n_pairs(ctx) -> int:

@@ -18,11 +18,14 @@ noise, optional translating textured rectangles as moving objects; cameras
 placed left to right with a given horizontal overlap and a random in-plane
 rotation of up to +-3 degrees; per-camera, per-channel gain U(0.8, 1.2), gamma
 U(0.9, 1.1) and offset U(-8, 8), optionally a 3x3 colour cast; flow fields
-that are sums of low-frequency plane waves limited to the overlap bands.
+that are sums of low-frequency plane waves limited to the overlap bands;
+and, for the learned estimator, pairs of patches of the same content under
+two independent photometric responses.
 """
 from .rig import Rig, make_rig, rig_for_config, CONFIGS
 from .scene import Scene, render_camera_frames
 from .flow import smooth_flow
+from .pairs import make_pairs, apply_response
 
 __all__ = ["Rig", "make_rig", "rig_for_config", "CONFIGS", "Scene",
-           "render_camera_frames", "smooth_flow"]
+           "render_camera_frames", "smooth_flow", "make_pairs", "apply_response"]

@@ -1,0 +1,227 @@
+"""GPU parity of the learned estimator through the C ABI: the pair labeller,
+the network's forward pass, its gradients and Adam step against the float64
+oracle, the learned selection inside a context, and a short training run."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as om
+from oracle import pairs as opairs
+from oracle.pipeline import OracleStitcher
+from paper_2308_09209_b300 import stitch as S
+from synth import make_pairs
+
+from gpu_common import Pair, compare_pano, ensure_built, FRAC_WITHIN_1, MAX_ABS, M_REL_TOL
+
+pytestmark = pytest.mark.gpu
+
+SIZES = om.SIZES
+N_OUT = om.N_OUT
+
+
+def _bf16_bits(x64):
+    """float64 array of bfloat16 values -> int16 tensor of their bit patterns."""
+    return torch.from_numpy(np.ascontiguousarray(x64, dtype=np.float32)).to(torch.bfloat16).view(torch.int16)
+
+
+def _label_gpu(pairs, lam=0.05):
+    n, _, ph, pw, _ = pairs.shape
+    feat = torch.empty((n, S.STITCH_MLP_IN), dtype=torch.int16, device="cuda")
+    targ = torch.empty((n, N_OUT), dtype=torch.float32, device="cuda")
+    M = torch.empty((n, 9), dtype=torch.float64, device="cuda")
+    flags = torch.empty((n,), dtype=torch.int32, device="cuda")
+    S.stitch_pairs_label(pairs, n, pw, ph, lam, feat, targ, M, flags)
+    torch.cuda.synchronize()
+    f = feat.view(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+    return f, targ.cpu().numpy(), M.cpu().numpy().reshape(n, 3, 3), flags.cpu().numpy()
+
+
+def test_pairs_label_matches_oracle():
+    ensure_built()
+    pairs, _ = make_pairs(40, patch_w=40, patch_h=24, seed=11, device="cuda")
+    # degenerate cases: a flat side i (ill-conditioned), a flat side j, a 1x1 patch pair below
+    pairs[3, 0] = 90
+    pairs[4, 1] = 200
+    f, t, M, fl = _label_gpu(pairs)
+    host = pairs.cpu().numpy()
+    for k in range(host.shape[0]):
+        fo, to, Mo, flo = opairs.label(host[k, 0], host[k, 1])
+        assert np.array_equal(f[k], fo), f"features of pair {k}"
+        assert fl[k] == flo, f"flag of pair {k}"
+        assert np.linalg.norm(M[k] - Mo) <= M_REL_TOL * np.linalg.norm(Mo), f"M of pair {k}"
+        assert np.allclose(t[k, 9:], to[9:], rtol=1e-6, atol=0), f"balance span of pair {k}"
+        assert np.allclose(t[k, :9], to[:9], rtol=0, atol=M_REL_TOL * np.linalg.norm(Mo))
+    tiny = torch.tensor([[[[[10, 20, 30]]], [[[40, 50, 60]]]]], dtype=torch.uint8, device="cuda")
+    f, t, M, fl = _label_gpu(tiny)
+    fo, to, Mo, flo = opairs.label(tiny[0, 0].cpu().numpy(), tiny[0, 1].cpu().numpy())
+    assert np.array_equal(f[0], fo) and fl[0] == flo == 1 and np.array_equal(M[0], np.eye(3))
+
+
+def _random_net(seed, max_batch=256):
+    net = S.Mlp(max_batch=max_batch, seed=seed)
+    params = S.stitch_mlp_get_params(net.h).astype(np.float64)
+    return net, params
+
+
+def _features(rng, batch):
+    x = rng.gamma(1.0, 1.0, (batch, S.STITCH_MLP_IN))          # non-negative, mean 1, like scaled histograms
+    return om.round_bf16(x)
+
+
+def test_forward_matches_oracle():
+    ensure_built()
+    rng = np.random.default_rng(21)
+    net, params = _random_net(5)
+    # non-trivial last layer: the library initialises it small
+    mu = rng.normal(0, 0.1, N_OUT).astype(np.float32)
+    sd = rng.uniform(0.05, 0.5, N_OUT).astype(np.float32)
+    S.stitch_mlp_set_norm(net.h, mu, sd)
+    for batch in (1, 37, 256):
+        X = _features(rng, batch)
+        x = _bf16_bits(X).cuda()
+        y = torch.empty((batch, N_OUT), dtype=torch.float32, device="cuda")
+        S.stitch_mlp_forward(net.h, x, batch, y)
+        torch.cuda.synchronize()
+        Yo, _ = om.forward(params, X)
+        Yo = Yo[:, :N_OUT] * sd + mu
+        g = y.cpu().numpy()
+        err = np.linalg.norm(g - Yo) / np.linalg.norm(Yo)
+        assert err < 5e-3, f"batch {batch}: relative error {err}"
+    net.close()
+
+
+def _layer_slices():
+    out, o = [], 0
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        out.append((slice(o, o + a * b), slice(o + a * b, o + a * b + b)))
+        o += a * b + b
+    return out
+
+
+def test_gradients_match_oracle_backward():
+    ensure_built()
+    rng = np.random.default_rng(22)
+    net, params = _random_net(6)
+    # a last layer of useful size so that every layer's gradient is well above rounding noise
+    sl = _layer_slices()
+    params[sl[-1][0]] = (rng.normal(0, 0.05, (16, 256)) * (np.arange(16) < N_OUT)[:, None]).reshape(-1)
+    S.stitch_mlp_set_params(net.h, params.astype(np.float32))
+    params = S.stitch_mlp_get_params(net.h).astype(np.float64)
+    mu = rng.normal(0, 0.1, N_OUT).astype(np.float32)
+    sd = rng.uniform(0.05, 0.5, N_OUT).astype(np.float32)
+    S.stitch_mlp_set_norm(net.h, mu, sd)
+    batch = 64
+    X = _features(rng, batch)
+    T = rng.normal(0, 0.2, (batch, N_OUT)).astype(np.float32)
+    x = _bf16_bits(X).cuda()
+    t = torch.from_numpy(T).cuda()
+    g_gpu, loss_gpu = S.stitch_mlp_gradients(net.h, x, t, batch)
+    loss_o, g_o = om.loss_and_grads(params, X, T.astype(np.float64), mu.astype(np.float64), sd.astype(np.float64))
+    assert abs(loss_gpu - loss_o) <= 1e-3 * loss_o
+    for li, (ws, bs) in enumerate(sl):
+        for name, s_ in (("W", ws), ("b", bs)):
+            a, b = g_gpu[s_].astype(np.float64), g_o[s_]
+            err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            assert err < 2e-2, f"layer {li} d{name}: relative error {err}"
+    # padding outputs of the last layer get no gradient
+    assert np.all(g_gpu[sl[-1][0]].reshape(16, 256)[N_OUT:] == 0.0)
+    assert np.all(g_gpu[sl[-1][1]][N_OUT:] == 0.0)
+
+    # one Adam step from the same state equals the float64 update with the GPU's own gradients
+    lr = 1e-3
+    p0 = S.stitch_mlp_get_params(net.h).astype(np.float64)
+    loss_dev = torch.zeros(1, dtype=torch.float32, device="cuda")
+    S.stitch_mlp_train_step(net.h, x, t, batch, lr, loss_dev)
+    torch.cuda.synchronize()
+    p1 = S.stitch_mlp_get_params(net.h).astype(np.float64)
+    exp, _, _ = om.adam_step(p0, g_gpu.astype(np.float64), np.zeros_like(p0), np.zeros_like(p0), 1, lr)
+    assert np.max(np.abs(p1 - exp)) <= 1e-6 * lr + 1e-7 * np.max(np.abs(p0))
+    assert abs(float(loss_dev.item()) - loss_gpu) <= 1e-6 * loss_gpu
+    net.close()
+
+
+def test_training_reduces_loss():
+    ensure_built()
+    from paper_2308_09209_b300 import learned
+    pairs, _ = make_pairs(4096, seed=31, device="cuda")
+    feat, targ, _, flags = learned.label_pairs(pairs)
+    net, hist = learned.train(feat, targ, epochs=6, batch=256, lr=2e-3, seed=1)
+    assert hist[-1] < 0.5 * hist[0], hist
+    net.close()
+
+
+def _bias_net(M_minus_I):
+    """A network whose output is its last bias: M_hat - I = the given matrix."""
+    net = S.Mlp(max_batch=32, seed=0)
+    params = S.stitch_mlp_get_params(net.h)
+    sl = _layer_slices()
+    params[sl[-1][0]] = 0.0
+    b = np.zeros(16, dtype=np.float32)
+    b[:9] = np.asarray(M_minus_I).reshape(-1)
+    params[sl[-1][1]] = b
+    S.stitch_mlp_set_params(net.h, params)
+    S.stitch_mlp_set_norm(net.h, np.zeros(N_OUT, np.float32), np.ones(N_OUT, np.float32))
+    return net
+
+
+def test_learned_selection_takes_accurate_and_rejects_inaccurate_predictions():
+    ensure_built()
+    plain = Pair("2x640x360", seed=2)
+    frames, fij, fji = plain.inputs(0)
+    plain.st.estimate_color(frames)
+    pano_plain = plain.st.frame(frames, fij, fji)
+    M_plain = S.stitch_get_pair_M(plain.st.ctx, 1)
+    for delta, expect_used in ((0.0, 1), (0.02, 0)):
+        net = _bias_net(M_plain[0] - np.eye(3) + delta * np.eye(3))
+        cfg = plain.cfg
+        cfg_l = S.Config(cfg.cam_w, cfg.cam_h, cfg.H, cfg.pano_w, cfg.pano_h, window=cfg.window,
+                         max_flow=cfg.max_flow, flags=S.STITCH_LEARNED)
+        st = S.Stitcher(cfg_l)
+        S.stitch_attach_mlp(st.ctx, net.h)
+        for _ in range(3):                       # same frame: the plain fit is the same every time
+            st.estimate_color(frames)
+        pano = st.frame(frames, fij, fji)
+        M_hat, r, used = S.stitch_get_learned(st.ctx, 1)
+        torch.cuda.synchronize()
+        assert used[0] == expect_used, (delta, r)
+        n_l, n_f = S.stitch_learned_stats(st.ctx)
+        assert (n_l, n_f) == ((3, 0) if expect_used else (0, 3))
+        if expect_used:
+            assert r[0] < 1e-5
+            d = (pano.cpu().numpy().astype(int) - pano_plain.cpu().numpy().astype(int))
+            assert np.abs(d).max() <= 1
+        else:
+            assert r[0] > 1e-3
+            assert torch.equal(pano, pano_plain)
+        st.close()
+        net.close()
+    plain.st.close()
+
+
+def test_learned_context_matches_oracle_learned_mode():
+    """A random network on a moving sequence: the window-pooled features, the
+    network and the residual of every frame against the oracle's learned mode."""
+    ensure_built()
+    rng = np.random.default_rng(41)
+    net = S.Mlp(max_batch=32, seed=9)
+    mu = np.zeros(N_OUT, np.float32)
+    sd = np.full(N_OUT, 0.05, np.float32)
+    S.stitch_mlp_set_norm(net.h, mu, sd)
+    params = S.stitch_mlp_get_params(net.h).astype(np.float64)
+    pr = Pair("3x1920x1080", seed=4, window=3, flags=S.STITCH_LEARNED)
+    pr.oracle = OracleStitcher(pr.rig.H, pr.rig.cam_w, pr.rig.cam_h, pr.rig.pano_w, pr.rig.pano_h,
+                               window=3, max_flow=pr.seq["max_flow"], flags=S.STITCH_LEARNED,
+                               mlp=dict(params=params, mu=mu, sd=sd))
+    S.stitch_attach_mlp(pr.st.ctx, net.h)
+    for t in range(4):
+        pr.step(t, compare_pano=False)
+        M_hat, r, used = S.stitch_get_learned(pr.st.ctx, 2)
+        for p, (Mo, ro, uo) in enumerate(pr.oracle.learned):
+            assert np.linalg.norm(M_hat[p] - Mo) <= 5e-3 * np.linalg.norm(Mo), (t, p)
+            assert abs(r[p] - ro) <= 5e-3 * ro + 1e-9, (t, p, r[p], ro)
+            if abs(ro - 1e-3) > 0.05e-3:
+                assert used[p] == int(uo)
+    _, Mg, _, _ = S.stitch_get_color(pr.st.ctx, 3)
+    assert np.allclose(Mg, pr.oracle.M_cam, rtol=0, atol=M_REL_TOL * 3)
+    pr.st.close()
+    net.close()

@@ -121,15 +121,15 @@ def test_pair_label_known_gain_and_flat_patch():
     flat = np.full((400, 3), 77, dtype=np.uint8)
     _, targ, M, flag = opairs.label(flat, flat)
     assert flag == 1 and np.array_equal(M, np.eye(3))
-    # flat pooled histogram: m1 == m2, identity curve, slope 1
-    assert np.array_equal(targ[9:], np.ones(3))
+    # flat pooled histogram: m1 == m2, zero span
+    assert np.array_equal(targ[9:], np.zeros(3))
 
 
-def test_pair_label_balance_slope_uniform():
+def test_pair_label_balance_span_uniform():
     # every level 0..255 once per side: pooled CDF(v) = 2 (v + 1), N = 512;
     # m1 = smallest v with CDF >= 0.05 N = 25.6 -> 2 (v + 1) = 26 -> v = 12;
     # m2 = smallest v with CDF >= 0.95 N = 486.4 -> 2 (v + 1) = 488 -> v = 243
     lv = np.arange(256, dtype=np.uint8)
     p = np.stack([lv, lv, lv], 1)
     _, targ, _, _ = opairs.label(p, p, lam=0.05)
-    assert np.allclose(targ[9:], (255 * 0.95 - 255 * 0.05) / (243 - 12), rtol=1e-14)
+    assert np.allclose(targ[9:], (243 - 12) / 255.0, rtol=1e-15)
