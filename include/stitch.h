@@ -71,17 +71,28 @@ typedef struct {
   const int *cam_w;         /* n_cams widths (>= 2) */
   const int *cam_h;         /* n_cams heights (>= 2) */
   const int *cam_pitch;     /* n_cams row pitches in bytes (>= 3 * w); NULL = 3 * w */
-  const double *H;          /* n_cams x 9, camera -> panorama homographies, row-major.
-                               The library inverts them in float64 (section 3.1). */
+  const double *H;          /* n_cams x 9, row-major, inverted by the library in float64
+                               (section 3.1). Planar: camera -> panorama homography.
+                               Cylindrical: camera pixel (u, v, 1) -> viewing ray
+                               (x right, y down, z forward) in the rig's frame,
+                               e.g. R_k^T K_k^-1. */
   int pano_w, pano_h;       /* panorama size in pixels */
   int pano_pitch;           /* bytes per panorama row, >= pano_w, multiple of 16 */
-  int projection;           /* 0 = planar homographies (the only projection accepted) */
+  int projection;           /* STITCH_PROJ_PLANAR or STITCH_PROJ_CYLINDRICAL */
   int ref_cam;              /* colour reference camera; -1 = n_cams / 2 */
   int window;               /* 3D-M temporal window W in frames (Eq. 2-3; 3 in the paper), 1..16 */
   double lambda;            /* balance quantile (section 2.2; 0.05 in the paper), 0 < lambda < 0.5 */
   float max_flow;           /* flow components are clamped to +-max_flow pixels, 0..16 */
   int flags;                /* STITCH_* flags above */
+  /* Cylindrical projection only: panorama pixel (x, y) is the ray at azimuth
+   * theta = (x - cyl_cx) / cyl_focal and height (y - cyl_cy) / cyl_focal on
+   * the unit cylinder, i.e. direction (sin theta, (y - cyl_cy) / cyl_focal,
+   * cos theta). cyl_focal is in panorama pixels per radian. */
+  double cyl_focal, cyl_cx, cyl_cy;
 } stitch_config;
+
+#define STITCH_PROJ_PLANAR 0
+#define STITCH_PROJ_CYLINDRICAL 1
 
 typedef struct stitch_ctx stitch_ctx;
 
@@ -360,6 +371,69 @@ int stitch_learned_stats(stitch_ctx *ctx, long long *n_learned, long long *n_fal
  * whether the pair took it (1) or kept the plain fit (0). STITCH_LEARNED
  * contexts only. Synchronises the context's work. */
 int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used);
+
+/*
+ * Fuse tile shapes and their autotuner. The paper fixes no tiling; the fuse
+ * kernel (pre-warped band remap, colour transfer, blend, balance) runs one
+ * thread block per panorama tile, and the best tile shape depends on the
+ * rig's resolution. Shapes: 0 = 64 x 32 (default), 1 = 64 x 16, 2 = 32 x 32,
+ * 3 = 128 x 16 panorama pixels.
+ *
+ * stitch_autotune times the fuse of one frame (after the band pre-warp of
+ * that frame) with every shape that fits the rig (a tile may touch at most
+ * one blend band), `reps` launches each, keeps the fastest in the context and
+ * records it: for the rest of the process, and in the file named by the
+ * environment variable STITCH_TUNE_CACHE when set, keyed by the GPU model,
+ * the rig geometry and STITCH_FP16_INTERMEDIATE. stitch_init picks up a
+ * recorded shape for the same key. Arguments as stitch_frame (the panorama is
+ * written); the frame uses the latest colour estimate. ms_out (optional):
+ * STITCH_TILE_SHAPES floats, the mean ms per fuse launch of each shape, -1
+ * for a shape that does not fit. Synchronous.
+ */
+#define STITCH_TILE_SHAPES 4
+int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
+                    const float *const *flow_ji_dev, uint8_t *pano_dev, int reps, int *shape_out, float *ms_out);
+
+/* The context's fuse tile shape: returns its index (or -1 for NULL) and
+ * writes the width and height in pixels (either pointer may be NULL). */
+/* Set the fuse tile shape by hand (STITCH_EINVAL if it does not fit the rig).
+ * Synchronises; recorded sequences are recorded again. */
+int stitch_set_tile_shape(stitch_ctx *ctx, int shape);
+int stitch_tile_shape(const stitch_ctx *ctx, int *tile_w, int *tile_h);
+
+/*
+ * Batched launch of several independent rigs (streams of uneven geometry).
+ * A batch drives up to STITCH_BATCH_MAX_RIGS contexts together: every frame
+ * runs each rig's statistics and estimate, then ONE band pre-warp launch and
+ * ONE persistent fuse launch over the tiles of all rigs (blocks take tiles
+ * from a work counter; band tiles first), recorded in a CUDA graph and
+ * replayed like stitch_sequence. The paper stitches one rig; this is the
+ * serving form. The contexts keep their own state and may still be used
+ * alone between batch calls. All contexts must share the device and the
+ * STITCH_FP16_INTERMEDIATE flag. The batch does not own the contexts:
+ * destroy the batch first.
+ */
+#define STITCH_BATCH_MAX_RIGS 16
+typedef struct stitch_batch stitch_batch;
+int stitch_batch_create(stitch_ctx *const *ctxs, int n_ctx, stitch_batch **out);
+
+/* n_frames frames of every rig. Pointer arrays are frame-major, then rig by
+ * rig in the order given to stitch_batch_create: frames_dev[t * C + o_r + k]
+ * with C the total camera count and o_r the cameras of the rigs before r;
+ * flow_*_dev[t * P + q_r + p] likewise over pairs; pano_dev[t * R + r]. The
+ * same checks and alignment rules as stitch_sequence apply. */
+int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *frames_dev,
+                          const float *const *flow_ij_dev, const float *const *flow_ji_dev, uint8_t *const *pano_dev,
+                          stitch_stream_t stream);
+
+/* The batch's own tile shape autotune over one frame of every rig (arrays as
+ * stitch_batch_sequence with n_frames = 1); the panoramas are written.
+ * Synchronous. */
+int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
+                          const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shape_out,
+                          float *ms_out);
+void stitch_batch_destroy(stitch_batch *b);
+const char *stitch_batch_last_error(const stitch_batch *b);
 
 /* Number of adjacent pairs (n_cams - 1), or -1 for a NULL context. */
 int stitch_n_pairs(const stitch_ctx *ctx);

@@ -33,21 +33,37 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
-           "-o", LIB + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES]
+def _compile(src: str, obj: str, verbose: bool):
+    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd))
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    return subprocess.run(cmd, capture_output=True, text=True), cmd
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object in parallel, then link libstitch.so."""
+    if not force and not _stale():
+        return LIB
+    from concurrent.futures import ThreadPoolExecutor
+    objdir = os.path.join(HERE, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, f.replace(".cu", ".o")) for f in SOURCES]
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(lambda a: _compile(*a, verbose),
+                              [(os.path.join(CSRC, f), o) for f, o in zip(SOURCES, objs)]))
+    for res, cmd in results:
+        if verbose:
+            print(" ".join(cmd))
+            sys.stderr.write(res.stderr)
+        if res.returncode != 0:
+            sys.stderr.write(res.stdout + res.stderr)
+            raise RuntimeError("nvcc failed building libstitch.so")
+    link = [_nvcc(), *ARCH, "--shared", "-o", LIB + ".tmp"] + objs
+    res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building libstitch.so")
-    if verbose:
-        sys.stderr.write(res.stderr)
+        raise RuntimeError("nvcc failed linking libstitch.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -4,8 +4,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -72,11 +77,47 @@ struct Geo {
   int rect[kMaxPairs][2][4];         // [pair][left/right camera] x0, x1, y0, y1
   int pair_i[kMaxPairs], pair_j[kMaxPairs];
   int own_lo[kMaxCams], own_hi[kMaxCams];
+  int cyl = 0;                       // cylindrical projection: H = camera pixel -> ray
+  double f = 1.0, cx = 0.0, cy = 0.0;  // cylinder: pixels per radian, centre
 };
+
+// Panorama point -> camera k (homogeneous: source point and its w; w > 0 in
+// front of the camera). Planar: H_k^-1 q. Cylindrical: H_k^-1 applied to the
+// ray (sin theta, h, cos theta), theta = (x - cx) / f, h = (y - cy) / f.
+void pano_to_cam(const Geo &g, int k, double x, double y, double &sx, double &sy, double &sw) {
+  if (!g.cyl) {
+    proj(g.Hi[k], x, y, sx, sy, sw);
+    return;
+  }
+  const double th = (x - g.cx) / g.f, hh = (y - g.cy) / g.f;
+  const double d0 = std::sin(th), d2 = std::cos(th);
+  const double *A = g.Hi[k];
+  const double a = A[0] * d0 + A[1] * hh + A[2] * d2;
+  const double b = A[3] * d0 + A[4] * hh + A[5] * d2;
+  sw = A[6] * d0 + A[7] * hh + A[8] * d2;
+  sx = a / sw;
+  sy = b / sw;
+}
+
+// Camera pixel -> panorama point. Cylindrical: the ray d = H_k (u, v, 1) at
+// azimuth atan2(d_x, d_z) and height d_y / hypot(d_x, d_z).
+void cam_to_pano(const Geo &g, int k, double u, double v, double &X, double &Y) {
+  if (!g.cyl) {
+    double W;
+    proj(g.H[k], u, v, X, Y, W);
+    return;
+  }
+  const double *C = g.H[k];
+  const double d0 = C[0] * u + C[1] * v + C[2];
+  const double d1 = C[3] * u + C[4] * v + C[5];
+  const double d2 = C[6] * u + C[7] * v + C[8];
+  X = g.cx + g.f * std::atan2(d0, d2);
+  Y = g.cy + g.f * (d1 / std::hypot(d0, d2));
+}
 
 bool covered64(const Geo &g, int k, double x, double y) {
   double sx, sy, sw;
-  proj(g.Hi[k], x, y, sx, sy, sw);
+  pano_to_cam(g, k, x, y, sx, sy, sw);
   return sw > 0 && sx >= 0 && sx <= g.w[k] - 1 && sy >= 0 && sy <= g.h[k] - 1;
 }
 
@@ -110,7 +151,12 @@ int build_geometry(const stitch_config *cfg, Geo &g, std::string &err) {
   if (!cfg) FAIL("config is NULL");
   if (cfg->n_cams < 2 || cfg->n_cams > kMaxCams) FAIL("n_cams must be in [2, 8]");
   if (!cfg->cam_w || !cfg->cam_h || !cfg->H) FAIL("cam_w, cam_h and H are required");
-  if (cfg->projection != 0) FAIL("only the planar projection (0) is supported");
+  if (cfg->projection != STITCH_PROJ_PLANAR && cfg->projection != STITCH_PROJ_CYLINDRICAL)
+    FAIL("projection must be STITCH_PROJ_PLANAR or STITCH_PROJ_CYLINDRICAL");
+  if (cfg->projection == STITCH_PROJ_CYLINDRICAL &&
+      !(std::isfinite(cfg->cyl_focal) && cfg->cyl_focal > 0.0 && std::isfinite(cfg->cyl_cx) &&
+        std::isfinite(cfg->cyl_cy)))
+    FAIL("the cylindrical projection needs a positive finite cyl_focal and a finite centre");
   if (cfg->pano_w < 1 || cfg->pano_h < 1) FAIL("panorama size must be positive");
   if (cfg->pano_w > 32767 * kTileW || cfg->pano_h > 32767 * kTileH) FAIL("panorama too large");
   if (cfg->pano_pitch < cfg->pano_w || cfg->pano_pitch % 16 != 0)
@@ -126,6 +172,12 @@ int build_geometry(const stitch_config *cfg, Geo &g, std::string &err) {
   g.pano_h = cfg->pano_h;
   g.pano_pitch = cfg->pano_pitch;
   g.ref = cfg->ref_cam < 0 ? cfg->n_cams / 2 : cfg->ref_cam;
+  g.cyl = cfg->projection == STITCH_PROJ_CYLINDRICAL ? 1 : 0;
+  if (g.cyl) {
+    g.f = cfg->cyl_focal;
+    g.cx = cfg->cyl_cx;
+    g.cy = cfg->cyl_cy;
+  }
   long long total_px = 0;
   for (int k = 0; k < g.n; ++k) {
     g.w[k] = cfg->cam_w[k];
@@ -143,27 +195,59 @@ int build_geometry(const stitch_config *cfg, Geo &g, std::string &err) {
   if (total_px >= (1ll << 32)) FAIL("too many camera pixels for 32-bit histograms");
   for (int p = 0; p + 1 < g.n; ++p) {
     const int a = p, b = p + 1;
-    double ax[4], ay[4], bx[4], by[4];
-    corners(g, a, ax, ay);
-    corners(g, b, bx, by);
-    int x0 = ceil_snap(std::fmax(bx[0], bx[3]));
-    int x1 = floor_snap(std::fmin(ax[1], ax[2])) + 1;
-    const double xl = x0, xr = x1 - 1;
-    const double tops[4] = {line_y(ax[0], ay[0], ax[1], ay[1], xl), line_y(ax[0], ay[0], ax[1], ay[1], xr),
-                            line_y(bx[0], by[0], bx[1], by[1], xl), line_y(bx[0], by[0], bx[1], by[1], xr)};
-    const double bots[4] = {line_y(ax[3], ay[3], ax[2], ay[2], xl), line_y(ax[3], ay[3], ax[2], ay[2], xr),
-                            line_y(bx[3], by[3], bx[2], by[2], xl), line_y(bx[3], by[3], bx[2], by[2], xr)};
-    double tmax = tops[0], bmin = bots[0];
-    for (int i = 1; i < 4; ++i) {
-      tmax = std::fmax(tmax, tops[i]);
-      bmin = std::fmin(bmin, bots[i]);
+    int x0, x1, y0, y1;
+    if (!g.cyl) {
+      double ax[4], ay[4], bx[4], by[4];
+      corners(g, a, ax, ay);
+      corners(g, b, bx, by);
+      x0 = ceil_snap(std::fmax(bx[0], bx[3]));
+      x1 = floor_snap(std::fmin(ax[1], ax[2])) + 1;
+      const double xl = x0, xr = x1 - 1;
+      const double tops[4] = {line_y(ax[0], ay[0], ax[1], ay[1], xl), line_y(ax[0], ay[0], ax[1], ay[1], xr),
+                              line_y(bx[0], by[0], bx[1], by[1], xl), line_y(bx[0], by[0], bx[1], by[1], xr)};
+      const double bots[4] = {line_y(ax[3], ay[3], ax[2], ay[2], xl), line_y(ax[3], ay[3], ax[2], ay[2], xr),
+                              line_y(bx[3], by[3], bx[2], by[2], xl), line_y(bx[3], by[3], bx[2], by[2], xr)};
+      double tmax = tops[0], bmin = bots[0];
+      for (int i = 1; i < 4; ++i) {
+        tmax = std::fmax(tmax, tops[i]);
+        bmin = std::fmin(bmin, bots[i]);
+      }
+      y0 = ceil_snap(tmax);
+      y1 = floor_snap(bmin) + 1;
+      x0 = std::max(x0, 0);
+      y0 = std::max(y0, 0);
+      x1 = std::min(x1, g.pano_w);
+      y1 = std::min(y1, g.pano_h);
+    } else {
+      // Cylinder: camera edges map to curves, so the extreme columns come
+      // from every pixel of b's left and a's right edge; rows from the
+      // coverage of every band column by both cameras.
+      double xl_max = -1e300, xr_min = 1e300;
+      for (int v = 0; v < g.h[b]; ++v) {
+        double X, Y;
+        cam_to_pano(g, b, 0.0, (double)v, X, Y);
+        xl_max = std::fmax(xl_max, X);
+      }
+      for (int v = 0; v < g.h[a]; ++v) {
+        double X, Y;
+        cam_to_pano(g, a, g.w[a] - 1.0, (double)v, X, Y);
+        xr_min = std::fmin(xr_min, X);
+      }
+      x0 = std::max(ceil_snap(xl_max), 0);
+      x1 = std::min(floor_snap(xr_min) + 1, g.pano_w);
+      if (x1 - x0 < 2) FAIL("an adjacent camera pair has no overlap band");
+      y0 = 0;
+      y1 = g.pano_h;
+      for (int x = x0; x < x1; ++x)
+        for (int cam = a; cam <= b; ++cam) {
+          int top = 0, bot = g.pano_h - 1;
+          while (top < g.pano_h && !covered64(g, cam, x, top)) ++top;
+          while (bot >= 0 && !covered64(g, cam, x, bot)) --bot;
+          if (top > bot) FAIL("an adjacent camera pair has no overlap band");
+          y0 = std::max(y0, top);
+          y1 = std::min(y1, bot + 1);
+        }
     }
-    int y0 = ceil_snap(tmax);
-    int y1 = floor_snap(bmin) + 1;
-    x0 = std::max(x0, 0);
-    y0 = std::max(y0, 0);
-    x1 = std::min(x1, g.pano_w);
-    y1 = std::min(y1, g.pano_h);
     if (x1 - x0 < 2 || y1 - y0 < 2) FAIL("an adjacent camera pair has no overlap band");
     g.band[p][0] = x0;
     g.band[p][1] = x1;
@@ -179,17 +263,39 @@ int build_geometry(const stitch_config *cfg, Geo &g, std::string &err) {
     }
     for (int side = 0; side < 2; ++side) {
       const int cam = side == 0 ? a : b;
-      const double px[4] = {(double)x0, (double)(x1 - 1), (double)(x1 - 1), (double)x0};
-      const double py[4] = {(double)y0, (double)y0, (double)(y1 - 1), (double)(y1 - 1)};
-      double sx[4], sy[4];
-      for (int i = 0; i < 4; ++i) {
-        double W;
-        proj(g.Hi[cam], px[i], py[i], sx[i], sy[i], W);
+      int rx0, rx1, ry0, ry1;
+      if (!g.cyl) {
+        const double px[4] = {(double)x0, (double)(x1 - 1), (double)(x1 - 1), (double)x0};
+        const double py[4] = {(double)y0, (double)y0, (double)(y1 - 1), (double)(y1 - 1)};
+        double sx[4], sy[4];
+        for (int i = 0; i < 4; ++i) {
+          double W;
+          proj(g.Hi[cam], px[i], py[i], sx[i], sy[i], W);
+        }
+        rx0 = ceil_snap(std::fmax(sx[0], sx[3]));
+        rx1 = floor_snap(std::fmin(sx[1], sx[2])) + 1;
+        ry0 = ceil_snap(std::fmax(sy[0], sy[1]));
+        ry1 = floor_snap(std::fmin(sy[2], sy[3])) + 1;
+      } else {
+        // every pixel of the band's border: left / right columns, top / bottom rows
+        double l = -1e300, r = 1e300, t = -1e300, bo = 1e300, sx, sy, sw;
+        for (int y = y0; y < y1; ++y) {
+          pano_to_cam(g, cam, x0, y, sx, sy, sw);
+          l = std::fmax(l, sx);
+          pano_to_cam(g, cam, x1 - 1, y, sx, sy, sw);
+          r = std::fmin(r, sx);
+        }
+        for (int x = x0; x < x1; ++x) {
+          pano_to_cam(g, cam, x, y0, sx, sy, sw);
+          t = std::fmax(t, sy);
+          pano_to_cam(g, cam, x, y1 - 1, sx, sy, sw);
+          bo = std::fmin(bo, sy);
+        }
+        rx0 = ceil_snap(l);
+        rx1 = floor_snap(r) + 1;
+        ry0 = ceil_snap(t);
+        ry1 = floor_snap(bo) + 1;
       }
-      int rx0 = ceil_snap(std::fmax(sx[0], sx[3]));
-      int rx1 = floor_snap(std::fmin(sx[1], sx[2])) + 1;
-      int ry0 = ceil_snap(std::fmax(sy[0], sy[1]));
-      int ry1 = floor_snap(std::fmin(sy[2], sy[3])) + 1;
       rx0 = std::max(rx0, 0);
       ry0 = std::max(ry0, 0);
       rx1 = std::min(rx1, g.w[cam]);
@@ -343,6 +449,7 @@ struct stitch_ctx {
   float *stage_fij[kMaxPairs] = {};
   float *stage_fji[kMaxPairs] = {};
   uint8_t *stage_pano = nullptr;
+  int shape = 0;                      // fuse tile shape (index into kTileShapes)
   LearnedState *ls = nullptr;         // learned estimator state (STITCH_LEARNED contexts)
   stitch_mlp *mlp = nullptr;          // attached network (not owned)
 };
@@ -467,7 +574,7 @@ int launch_prewarp_for(stitch_ctx *ctx, const FuseParams &fp, cudaStream_t s) {
 
 int launch_fuse_for(stitch_ctx *ctx, const FuseParams &fp, cudaStream_t s) {
   cudaEvent_t e0 = prof_mark(ctx, s);
-  cudaError_t e = launch_fuse(fp, s);
+  cudaError_t e = launch_fuse(fp, ctx->shape, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "fuse launch");
   cudaEvent_t e1 = prof_mark(ctx, s);
   prof_pair(ctx, e0, e1, 2);
@@ -496,6 +603,137 @@ bool check_ptrs(const void *const *p, int n) {
   for (int i = 0; i < n; ++i)
     if (!p[i]) return false;
   return true;
+}
+
+// Fuse tiles of one shape. A tile touching a band's columns is a band tile
+// (kind 1); others belong to the one camera whose own columns hold them: kind
+// 0 when that camera covers the whole tile with a margin (coverage is convex,
+// so the four corners decide) and no pixel needs a coverage test or a fallback
+// camera, kind 2 for partial coverage. Band tiles come first. Returns false
+// (with a message) when a tile would touch two bands.
+bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &band_tiles, std::vector<TileDesc> &own_tiles,
+                 std::string &err) {
+  const int TW = kTileShapes[shape].w, TH = kTileShapes[shape].h;
+  const int ntx = (g.pano_w + TW - 1) / TW, nty = (g.pano_h + TH - 1) / TH;
+  if (ntx > 32767 || nty > 32767) {
+    err = "panorama too large for the tile index";
+    return false;
+  }
+  for (int ty = 0; ty < nty; ++ty) {
+    for (int tx = 0; tx < ntx; ++tx) {
+      const int c0 = tx * TW, c1 = c0 + TW;
+      int hit = -1, nhit = 0;
+      for (int p = 0; p + 1 < g.n; ++p)
+        if (c0 < g.band[p][1] && c1 > g.band[p][0]) {
+          hit = p;
+          ++nhit;
+        }
+      if (nhit > 1) {
+        err = "a camera's own columns are narrower than a fuse tile (" + std::to_string(TW) + " pixels)";
+        return false;
+      }
+      TileDesc t{};
+      t.tx = (int16_t)tx;
+      t.ty = (int16_t)ty;
+      if (hit >= 0) {
+        t.kind = 1;
+        t.idx = (int8_t)hit;
+        band_tiles.push_back(t);
+      } else {
+        int k = 0;
+        while (k < g.n - 1 && c0 >= g.own_hi[k]) ++k;
+        const int r0 = ty * TH, r1 = std::min(r0 + TH, g.pano_h) - 1;
+        const int q1 = std::min(c1, g.pano_w) - 1;
+        bool full = c1 <= g.pano_w && r0 + TH <= g.pano_h;
+        auto inside = [&](int x, int y) {
+          double sx, sy, sw;
+          pano_to_cam(g, k, x, y, sx, sy, sw);
+          return sw > 0 && sx >= 0.01 && sx <= g.w[k] - 1.01 && sy >= 0.01 && sy <= g.h[k] - 1.01;
+        };
+        if (!g.cyl) {
+          // planar coverage is convex: the four corners decide
+          full = full && inside(c0, r0) && inside(q1, r0) && inside(c0, r1) && inside(q1, r1);
+        } else {
+          // the cylinder bends the coverage border: test every border pixel
+          for (int x = c0; x <= q1 && full; ++x) full = inside(x, r0) && inside(x, r1);
+          for (int y = r0; y <= r1 && full; ++y) full = inside(c0, y) && inside(q1, y);
+        }
+        t.kind = full ? 0 : 2;
+        t.idx = (int8_t)k;
+        own_tiles.push_back(t);
+      }
+    }
+  }
+  return true;
+}
+
+// Tiles of the smallest shape (at least 32 x 16): room for any shape's list.
+size_t max_tiles(const Geo &g) { return (size_t)((g.pano_w + 31) / 32) * (size_t)((g.pano_h + 15) / 16); }
+
+// ---------------------------------------------------------------------------
+// Autotuner results: the fastest fuse tile shape per (GPU, rig geometry,
+// intermediate precision), kept for the process and, when STITCH_TUNE_CACHE
+// names a file, in that file (one "key<TAB>shape" line per result; the last
+// line of a key wins).
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_file_read = false;
+
+std::string tune_key(const Geo &g, int flags) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  std::string name = "unknown";
+  int sms = 0;
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+    name = prop.name;
+    sms = prop.multiProcessorCount;
+  }
+  for (char &c : name)
+    if (c == '\t' || c == '\n') c = ' ';
+  std::ostringstream k;
+  k << name << "/" << sms << "sm|" << g.n;
+  for (int i = 0; i < g.n; ++i) k << ":" << g.w[i] << "x" << g.h[i];
+  k << "|" << g.pano_w << "x" << g.pano_h << "|";
+  for (int p = 0; p + 1 < g.n; ++p) k << (g.band[p][1] - g.band[p][0]) << "x" << (g.band[p][3] - g.band[p][2]) << ",";
+  k << "|fp16=" << ((flags & STITCH_FP16_INTERMEDIATE) ? 1 : 0);
+  return k.str();
+}
+
+void tune_file_read_locked() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char *path = std::getenv("STITCH_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t tab = line.rfind('\t');
+    if (tab == std::string::npos) continue;
+    const int shape = std::atoi(line.c_str() + tab + 1);
+    if (shape >= 0 && shape < kNumTileShapes) g_tune[line.substr(0, tab)] = shape;
+  }
+}
+
+int tuned_shape(const Geo &g, int flags) {
+  const std::string key = tune_key(g, flags);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_file_read_locked();
+  const auto it = g_tune.find(key);
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+void tune_record(const Geo &g, int flags, int shape) {
+  const std::string key = tune_key(g, flags);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_file_read_locked();
+  g_tune[key] = shape;
+  const char *path = std::getenv("STITCH_TUNE_CACHE");
+  if (path && *path) {
+    std::ofstream f(path, std::ios::app);
+    if (f) f << key << '\t' << shape << '\n';
+  }
 }
 
 }  // namespace
@@ -533,50 +771,17 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   ctx->max_flow = cfg->max_flow;
   ctx->halo = (int)std::ceil((double)cfg->max_flow) + 1;
 
-  // Tiles: a tile touching a band's columns is a band tile; others belong to
-  // the one camera whose own columns hold them.
+  ctx->shape = tuned_shape(g, cfg->flags);
   std::vector<TileDesc> band_tiles, own_tiles;
-  const int ntx = (g.pano_w + kTileW - 1) / kTileW, nty = (g.pano_h + kTileH - 1) / kTileH;
-  for (int ty = 0; ty < nty; ++ty) {
-    for (int tx = 0; tx < ntx; ++tx) {
-      const int c0 = tx * kTileW, c1 = c0 + kTileW;
-      int hit = -1, nhit = 0;
-      for (int p = 0; p + 1 < g.n; ++p)
-        if (c0 < g.band[p][1] && c1 > g.band[p][0]) {
-          hit = p;
-          ++nhit;
-        }
-      if (nhit > 1) {
-        delete ctx;
-        return set_err(nullptr, STITCH_EINVAL, "a camera's own columns are narrower than a 64-pixel tile");
-      }
-      TileDesc t{};
-      t.tx = (int16_t)tx;
-      t.ty = (int16_t)ty;
-      if (hit >= 0) {
-        t.kind = 1;
-        t.idx = (int8_t)hit;
-        band_tiles.push_back(t);
-      } else {
-        int k = 0;
-        while (k < g.n - 1 && c0 >= g.own_hi[k]) ++k;
-        // Kind 0: camera k covers the whole tile with a margin (coverage is
-        // convex, so the four corners decide), so no pixel needs a coverage
-        // test or a fallback camera. Kind 2: partial coverage.
-        const int r0 = ty * kTileH, r1 = std::min(r0 + kTileH, g.pano_h) - 1;
-        const int q1 = std::min(c1, g.pano_w) - 1;
-        bool full = c1 <= g.pano_w && r0 + kTileH <= g.pano_h;
-        const double px[4] = {(double)c0, (double)q1, (double)c0, (double)q1};
-        const double py[4] = {(double)r0, (double)r0, (double)r1, (double)r1};
-        for (int i = 0; i < 4 && full; ++i) {
-          double sx, sy, sw;
-          proj(g.Hi[k], px[i], py[i], sx, sy, sw);
-          full = sw > 0 && sx >= 0.01 && sx <= g.w[k] - 1.01 && sy >= 0.01 && sy <= g.h[k] - 1.01;
-        }
-        t.kind = full ? 0 : 2;
-        t.idx = (int8_t)k;
-        own_tiles.push_back(t);
-      }
+  if (!build_tiles(g, ctx->shape, band_tiles, own_tiles, err)) {
+    if (ctx->shape != 0) {
+      ctx->shape = 0;
+      band_tiles.clear();
+      own_tiles.clear();
+    }
+    if (ctx->shape != 0 || !build_tiles(g, 0, band_tiles, own_tiles, err)) {
+      delete ctx;
+      return set_err(nullptr, STITCH_EINVAL, err);
     }
   }
   ctx->n_band_tiles = (int)band_tiles.size();
@@ -586,7 +791,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   if (e == cudaSuccess) e = estimate_setup();
   if (e == cudaSuccess) e = cudaMalloc(&ctx->raw, kRawSlots * sizeof(RawStats));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->state, sizeof(ColorState));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, (band_tiles.size() + own_tiles.size()) * sizeof(TileDesc) + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, max_tiles(g) * sizeof(TileDesc) + 16);
   if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, kRawSlots * sizeof(RawStats));
   if (e == cudaSuccess && (cfg->flags & STITCH_LEARNED)) {
     e = cudaMalloc(&ctx->ls, sizeof(LearnedState));
@@ -713,20 +918,36 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   }
   for (int k = 0; k < g.n; ++k) {
     CamDev &c = fp.cam[k];
-    double cx, cy, cw;
-    proj(g.H[k], (g.w[k] - 1) * 0.5, (g.h[k] - 1) * 0.5, cx, cy, cw);
-    c.ox = (int)std::lround(cx);
-    c.oy = (int)std::lround(cy);
-    // H^-1 . T(ox, oy): the kernel feeds (x - ox, y - oy, 1).
-    double hs[9];
-    for (int r = 0; r < 3; ++r) {
-      hs[r * 3 + 0] = g.Hi[k][r * 3 + 0];
-      hs[r * 3 + 1] = g.Hi[k][r * 3 + 1];
-      hs[r * 3 + 2] = g.Hi[k][r * 3 + 0] * c.ox + g.Hi[k][r * 3 + 1] * c.oy + g.Hi[k][r * 3 + 2];
+    if (!g.cyl) {
+      double cx, cy, cw;
+      proj(g.H[k], (g.w[k] - 1) * 0.5, (g.h[k] - 1) * 0.5, cx, cy, cw);
+      c.ox = (int)std::lround(cx);
+      c.oy = (int)std::lround(cy);
+      // H^-1 . T(ox, oy): the kernel feeds (x - ox, y - oy, 1).
+      double hs[9];
+      for (int r = 0; r < 3; ++r) {
+        hs[r * 3 + 0] = g.Hi[k][r * 3 + 0];
+        hs[r * 3 + 1] = g.Hi[k][r * 3 + 1];
+        hs[r * 3 + 2] = g.Hi[k][r * 3 + 0] * c.ox + g.Hi[k][r * 3 + 1] * c.oy + g.Hi[k][r * 3 + 2];
+      }
+      const double sc = 1.0 / hs[8];
+      for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(hs[e2] * sc);
+      c.affine = (hs[6] == 0.0 && hs[7] == 0.0) ? 1 : 0;
+      c.cyl = 0;
+    } else {
+      // The kernel feeds the ray (sin theta, h, cos theta) of panorama (x, y);
+      // H^-1 is scaled by the norm of its last row (a positive factor keeps
+      // the sign of w, which tells front from back).
+      c.ox = c.oy = 0;
+      const double *A = g.Hi[k];
+      const double sc = 1.0 / std::sqrt(A[6] * A[6] + A[7] * A[7] + A[8] * A[8]);
+      for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(A[e2] * sc);
+      c.affine = 0;
+      c.cyl = 1;
+      c.cyl_finv = (float)(1.0 / g.f);
+      c.cyl_cx = (float)g.cx;
+      c.cyl_cy = (float)g.cy;
     }
-    const double sc = 1.0 / hs[8];
-    for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(hs[e2] * sc);
-    c.affine = (hs[6] == 0.0 && hs[7] == 0.0) ? 1 : 0;
     c.w = g.w[k];
     c.h_px = g.h[k];
     c.pitch = g.pitch[k];
@@ -1167,6 +1388,463 @@ int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used)
 }
 
 int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
+
+int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
+                    const float *const *flow_ji_dev, uint8_t *pano_dev, int reps, int *shape_out, float *ms_out) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  const int np = ctx->g.n - 1;
+  if (reps < 1 || reps > 1000) return set_err(ctx, STITCH_EINVAL, "reps must be in 1..1000");
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), ctx->g.n) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ij_dev), np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_dev), np))
+    return set_err(ctx, STITCH_EINVAL, "frame and flow arrays must be complete and non-NULL");
+  for (int p = 0; p < np; ++p)
+    if ((reinterpret_cast<uintptr_t>(flow_ij_dev[p]) | reinterpret_cast<uintptr_t>(flow_ji_dev[p])) & 7u)
+      return set_err(ctx, STITCH_EINVAL, "flow pointers must be 8-byte aligned (float2)");
+  if (!pano_dev || (reinterpret_cast<uintptr_t>(pano_dev) & 15u))
+    return set_err(ctx, STITCH_EINVAL, "pano_dev must be a non-NULL 16-byte aligned pointer");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
+  cudaStream_t s = ctx->cap_stream;
+  FuseParams fp = frame_params(ctx, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev, ctx->host_T - 1, ctx->host_F);
+  e = launch_prewarp(fp, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms[kNumTileShapes];
+  int best = -1;
+  std::vector<TileDesc> bt, ot;
+  std::string err;
+  for (int sh = 0; sh < kNumTileShapes && e == cudaSuccess; ++sh) {
+    ms[sh] = -1.0f;
+    bt.clear();
+    ot.clear();
+    if (!build_tiles(ctx->g, sh, bt, ot, err)) continue;
+    bt.insert(bt.end(), ot.begin(), ot.end());
+    e = cudaMemcpyAsync(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s);
+    fp.tiles = ctx->tiles;
+    fp.n_tiles = (int)bt.size();
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_fuse(fp, sh, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fuse(fp, sh, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) {
+      ms[sh] = t / (float)reps;
+      if (best < 0 || ms[sh] < ms[best]) best = sh;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e == cudaSuccess && best < 0) e = cudaErrorInvalidValue;
+  // Keep the winner: its tile list goes back into the context.
+  if (e == cudaSuccess) {
+    bt.clear();
+    ot.clear();
+    build_tiles(ctx->g, best, bt, ot, err);
+    ctx->n_band_tiles = (int)bt.size();
+    ctx->n_own_tiles = (int)ot.size();
+    bt.insert(bt.end(), ot.begin(), ot.end());
+    e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+    ctx->fp.n_tiles = (int)bt.size();
+    ctx->shape = best;
+  }
+  if (e != cudaSuccess) return cuda_err(ctx, e, "autotune");
+  for (auto &ge : ctx->graphs) {
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    for (auto &pp : ge.pairs) {
+      cudaEventDestroy(pp.a);
+      cudaEventDestroy(pp.b);
+    }
+  }
+  ctx->graphs.clear();
+  tune_record(ctx->g, ctx->flags, best);
+  if (shape_out) *shape_out = best;
+  if (ms_out)
+    for (int sh = 0; sh < kNumTileShapes; ++sh) ms_out[sh] = ms[sh];
+  return STITCH_OK;
+}
+
+int stitch_set_tile_shape(stitch_ctx *ctx, int shape) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (shape < 0 || shape >= kNumTileShapes) return set_err(ctx, STITCH_EINVAL, "no such tile shape");
+  std::vector<TileDesc> bt, ot;
+  std::string err;
+  if (!build_tiles(ctx->g, shape, bt, ot, err)) return set_err(ctx, STITCH_EINVAL, err);
+  cudaError_t e = cudaDeviceSynchronize();
+  ctx->n_band_tiles = (int)bt.size();
+  ctx->n_own_tiles = (int)ot.size();
+  bt.insert(bt.end(), ot.begin(), ot.end());
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "tile list upload");
+  ctx->fp.n_tiles = (int)bt.size();
+  ctx->shape = shape;
+  for (auto &ge : ctx->graphs) {
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    for (auto &pp : ge.pairs) {
+      cudaEventDestroy(pp.a);
+      cudaEventDestroy(pp.b);
+    }
+  }
+  ctx->graphs.clear();
+  return STITCH_OK;
+}
+
+int stitch_tile_shape(const stitch_ctx *ctx, int *tile_w, int *tile_h) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (tile_w) *tile_w = kTileShapes[ctx->shape].w;
+  if (tile_h) *tile_h = kTileShapes[ctx->shape].h;
+  return ctx->shape;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched launch of several independent rigs.
+// ---------------------------------------------------------------------------
+
+struct BatchGraph {
+  std::vector<const void *> key;
+  int n_frames = 0;
+  cudaGraphExec_t exec = nullptr;
+  FuseParams *params = nullptr;       // n_frames x n_rigs parameter blocks
+  int *counters = nullptr;            // one work counter per frame
+};
+
+struct stitch_batch {
+  std::vector<stitch_ctx *> ctx;
+  int shape = 0;
+  bool half = false;
+  int cams = 0, pairs = 0;            // totals over the rigs
+  std::vector<int> cam_off, pair_off;
+  MultiItem *fuse_items = nullptr;
+  int n_fuse_items = 0;
+  MultiItem *pw_items = nullptr;
+  int n_pw_items = 0;
+  int grid = 0;                       // persistent fuse blocks
+  cudaStream_t cap = nullptr;
+  cudaStream_t pipe[3] = {};
+  cudaEvent_t ev[4][8] = {};
+  std::vector<BatchGraph> graphs;
+  std::string err;
+};
+
+namespace {
+
+int batch_err(stitch_batch *b, int code, const std::string &m) {
+  if (b) b->err = m;
+  g_last_error = m;
+  return code;
+}
+
+void free_batch_graph(BatchGraph &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  cudaFree(g.params);
+  cudaFree(g.counters);
+  g.exec = nullptr;
+  g.params = nullptr;
+  g.counters = nullptr;
+}
+
+// Work lists of the batch for a tile shape: every rig's fuse tiles (band
+// tiles first, the costliest, so that the dynamic schedule ends evenly) and
+// band pre-warp pieces.
+int batch_items(stitch_batch *b, int shape) {
+  std::vector<MultiItem> band, part, full, pw;
+  std::string err;
+  for (int r = 0; r < (int)b->ctx.size(); ++r) {
+    std::vector<TileDesc> bt, ot;
+    if (!build_tiles(b->ctx[r]->g, shape, bt, ot, err)) return batch_err(b, STITCH_EINVAL, err);
+    for (const TileDesc &t : bt) band.push_back(MultiItem{r, t, PwTile{}});
+    for (const TileDesc &t : ot) (t.kind == 0 ? full : part).push_back(MultiItem{r, t, PwTile{}});
+    const Geo &g = b->ctx[r]->g;
+    for (int p = 0; p + 1 < g.n; ++p)
+      for (int y = g.band[p][2]; y < g.band[p][3]; y += kTileH)
+        for (int x = g.band[p][0]; x < g.band[p][1]; x += kTileW) pw.push_back(MultiItem{r, TileDesc{}, PwTile{p, x, y}});
+  }
+  band.insert(band.end(), part.begin(), part.end());
+  band.insert(band.end(), full.begin(), full.end());
+  cudaFree(b->fuse_items);
+  cudaFree(b->pw_items);
+  b->fuse_items = nullptr;
+  b->pw_items = nullptr;
+  cudaError_t e = cudaMalloc(&b->fuse_items, band.size() * sizeof(MultiItem) + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&b->pw_items, pw.size() * sizeof(MultiItem) + 16);
+  if (e == cudaSuccess && !band.empty())
+    e = cudaMemcpy(b->fuse_items, band.data(), band.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pw.empty())
+    e = cudaMemcpy(b->pw_items, pw.data(), pw.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return batch_err(b, STITCH_ECUDA, std::string("batch work lists: ") + cudaGetErrorString(e));
+  b->n_fuse_items = (int)band.size();
+  b->n_pw_items = (int)pw.size();
+  int sms = 148, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, shape));
+  b->grid = std::max(1, std::min(b->n_fuse_items, per_sm * sms));
+  b->shape = shape;
+  for (auto &g : b->graphs) free_batch_graph(g);
+  b->graphs.clear();
+  return STITCH_OK;
+}
+
+bool batch_ptrs_ok(stitch_batch *b, int n_frames, const uint8_t *const *frames_dev, const float *const *fij,
+                   const float *const *fji, uint8_t *const *pano_dev) {
+  const int R = (int)b->ctx.size();
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), n_frames * b->cams) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(pano_dev), n_frames * R))
+    return false;
+  if (b->pairs > 0 && (!check_ptrs(reinterpret_cast<const void *const *>(fij), n_frames * b->pairs) ||
+                       !check_ptrs(reinterpret_cast<const void *const *>(fji), n_frames * b->pairs)))
+    return false;
+  for (int i = 0; i < n_frames * R; ++i)
+    if (reinterpret_cast<uintptr_t>(pano_dev[i]) & 15u) return false;
+  for (int i = 0; i < n_frames * b->pairs; ++i)
+    if ((reinterpret_cast<uintptr_t>(fij[i]) | reinterpret_cast<uintptr_t>(fji[i])) & 7u) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stitch_batch_create(stitch_ctx *const *ctxs, int n_ctx, stitch_batch **out) {
+  if (!out) return batch_err(nullptr, STITCH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || n_ctx < 1 || n_ctx > STITCH_BATCH_MAX_RIGS)
+    return batch_err(nullptr, STITCH_EINVAL, "need 1..STITCH_BATCH_MAX_RIGS contexts");
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]) return batch_err(nullptr, STITCH_EINVAL, "a context is NULL");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return batch_err(nullptr, STITCH_EINVAL, "a context appears twice");
+    if ((ctxs[i]->flags & STITCH_FP16_INTERMEDIATE) != (ctxs[0]->flags & STITCH_FP16_INTERMEDIATE))
+      return batch_err(nullptr, STITCH_EINVAL, "all contexts must agree on STITCH_FP16_INTERMEDIATE");
+    if (ctxs[i]->device != ctxs[0]->device) return batch_err(nullptr, STITCH_EINVAL, "contexts are on different GPUs");
+  }
+  stitch_batch *b = new (std::nothrow) stitch_batch();
+  if (!b) return batch_err(nullptr, STITCH_ENOMEM, "host allocation failed");
+  b->ctx.assign(ctxs, ctxs + n_ctx);
+  b->half = (ctxs[0]->flags & STITCH_FP16_INTERMEDIATE) != 0;
+  for (stitch_ctx *c : b->ctx) {
+    b->cam_off.push_back(b->cams);
+    b->pair_off.push_back(b->pairs);
+    b->cams += c->g.n;
+    b->pairs += c->g.n - 1;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&b->pipe[i], cudaStreamNonBlocking);
+  for (int a = 0; a < 4 && e == cudaSuccess; ++a)
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev[a][k], cudaEventDisableTiming);
+  int rc = e == cudaSuccess ? batch_items(b, ctxs[0]->shape) : batch_err(b, STITCH_ECUDA, cudaGetErrorString(e));
+  if (rc != STITCH_OK && ctxs[0]->shape != 0) rc = batch_items(b, 0);
+  if (rc != STITCH_OK) {
+    const std::string m = b->err;
+    stitch_batch_destroy(b);
+    return batch_err(nullptr, rc, m);
+  }
+  *out = b;
+  return STITCH_OK;
+}
+
+int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *frames_dev,
+                          const float *const *flow_ij_dev, const float *const *flow_ji_dev, uint8_t *const *pano_dev,
+                          stitch_stream_t stream) {
+  if (!b) return batch_err(nullptr, STITCH_EINVAL, "batch is NULL");
+  if (n_frames < 1) return batch_err(b, STITCH_EINVAL, "n_frames must be >= 1");
+  if (!batch_ptrs_ok(b, n_frames, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev))
+    return batch_err(b, STITCH_EINVAL,
+                     "pointer arrays must be complete and non-NULL, panoramas 16-byte and flows 8-byte aligned");
+  const int R = (int)b->ctx.size();
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<const void *> key;
+  for (int i = 0; i < n_frames * b->cams; ++i) key.push_back(frames_dev[i]);
+  for (int i = 0; i < n_frames * b->pairs; ++i) key.push_back(flow_ij_dev[i]);
+  for (int i = 0; i < n_frames * b->pairs; ++i) key.push_back(flow_ji_dev[i]);
+  for (int i = 0; i < n_frames * R; ++i) key.push_back(pano_dev[i]);
+  for (stitch_ctx *c : b->ctx) {   // each rig's slot phases and its network
+    key.push_back(reinterpret_cast<const void *>((uintptr_t)((c->host_T % 12) * kPwSlots + c->host_F % kPwSlots)));
+    key.push_back(c->mlp);
+  }
+  BatchGraph *hit = nullptr;
+  for (auto &bg : b->graphs)
+    if (bg.n_frames == n_frames && bg.key == key) hit = &bg;
+  if (!hit) {
+    BatchGraph bg;
+    bg.key = key;
+    bg.n_frames = n_frames;
+    cudaError_t e = cudaMalloc(&bg.params, (size_t)n_frames * R * sizeof(FuseParams));
+    if (e == cudaSuccess) e = cudaMalloc(&bg.counters, (size_t)n_frames * sizeof(int));
+    std::vector<FuseParams> hp((size_t)n_frames * R);
+    for (int t = 0; t < n_frames; ++t)
+      for (int r = 0; r < R; ++r) {
+        stitch_ctx *c = b->ctx[r];
+        const int np = c->g.n - 1;
+        const size_t fo = (size_t)t * b->cams + b->cam_off[r], po = (size_t)t * b->pairs + b->pair_off[r];
+        hp[(size_t)t * R + r] = frame_params(c, frames_dev + fo, np ? flow_ij_dev + po : nullptr,
+                                             np ? flow_ji_dev + po : nullptr, pano_dev[(size_t)t * R + r],
+                                             c->host_T + t, c->host_F + t);
+      }
+    if (e == cudaSuccess)
+      e = cudaMemcpy(bg.params, hp.data(), hp.size() * sizeof(FuseParams), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      free_batch_graph(bg);
+      return batch_err(b, STITCH_ECUDA, std::string("batch parameters: ") + cudaGetErrorString(e));
+    }
+    // Same three-stream structure and slot-ring edges as stitch_sequence, with
+    // every rig's statistics and estimate launched per rig and the band
+    // pre-warp and fuse of all rigs in one launch each.
+    std::vector<char> prof(R);
+    for (int r = 0; r < R; ++r) {
+      prof[r] = b->ctx[r]->prof;
+      b->ctx[r]->prof = false;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    cudaStream_t sA = b->pipe[0], sB = b->pipe[1], sC = b->pipe[2];
+    auto &ev = b->ev;
+    enum { kS = 0, kW = 1, kE = 2, kF = 3 };
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(cudaEventRecord(ev[kF][7], b->cap));
+    chk(cudaStreamWaitEvent(sA, ev[kF][7], 0));
+    chk(cudaStreamWaitEvent(sB, ev[kF][7], 0));
+    chk(cudaStreamWaitEvent(sC, ev[kF][7], 0));
+    int rc = STITCH_OK;
+    for (int t = 0; t < n_frames && rc == STITCH_OK && e == cudaSuccess; ++t) {
+      if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kE][(t - 2) % 8], 0));
+      for (int r = 0; r < R && rc == STITCH_OK; ++r)
+        rc = launch_stats_for(b->ctx[r], frames_dev + (size_t)t * b->cams + b->cam_off[r], b->ctx[r]->host_T + t, sA);
+      chk(cudaEventRecord(ev[kS][t % 8], sA));
+      if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kF][(t - 2) % 8], 0));
+      MultiParams mp{bg.params, t * R, b->n_pw_items, b->pw_items, nullptr};
+      chk(launch_prewarp_multi(mp, b->half, sA));
+      chk(cudaEventRecord(ev[kW][t % 8], sA));
+      chk(cudaStreamWaitEvent(sB, ev[kS][t % 8], 0));
+      if (t >= 4) chk(cudaStreamWaitEvent(sB, ev[kF][(t - 4) % 8], 0));
+      for (int r = 0; r < R && rc == STITCH_OK; ++r) rc = launch_estimate_for(b->ctx[r], sB);
+      chk(cudaEventRecord(ev[kE][t % 8], sB));
+      chk(cudaStreamWaitEvent(sC, ev[kE][t % 8], 0));
+      chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
+      chk(cudaMemsetAsync(bg.counters + t, 0, sizeof(int), sC));
+      MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + t};
+      chk(launch_fuse_multi(mf, b->half, b->shape, b->grid, sC));
+      chk(cudaEventRecord(ev[kF][t % 8], sC));
+    }
+    chk(cudaEventRecord(ev[kS][0], sA));
+    chk(cudaStreamWaitEvent(b->cap, ev[kS][0], 0));
+    chk(cudaEventRecord(ev[kE][0], sB));
+    chk(cudaStreamWaitEvent(b->cap, ev[kE][0], 0));
+    chk(cudaEventRecord(ev[kF][0], sC));
+    chk(cudaStreamWaitEvent(b->cap, ev[kF][0], 0));
+    const cudaError_t e_end = cudaStreamEndCapture(b->cap, &graph);
+    for (int r = 0; r < R; ++r) b->ctx[r]->prof = prof[r] != 0;
+    if (e == cudaSuccess) e = e_end;
+    if (rc == STITCH_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bg.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != STITCH_OK || e != cudaSuccess) {
+      free_batch_graph(bg);
+      if (rc != STITCH_OK) return batch_err(b, rc, "batch capture: " + b->ctx[0]->err);
+      return batch_err(b, STITCH_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    }
+    if (b->graphs.size() >= 4) {
+      cudaDeviceSynchronize();
+      free_batch_graph(b->graphs.front());
+      b->graphs.erase(b->graphs.begin());
+    }
+    b->graphs.push_back(std::move(bg));
+    hit = &b->graphs.back();
+  }
+  const cudaError_t e = cudaGraphLaunch(hit->exec, s);
+  if (e != cudaSuccess) return batch_err(b, STITCH_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  for (stitch_ctx *c : b->ctx) {
+    c->host_T += n_frames;
+    c->host_F += n_frames;
+  }
+  return STITCH_OK;
+}
+
+int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
+                          const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shape_out,
+                          float *ms_out) {
+  if (!b) return batch_err(nullptr, STITCH_EINVAL, "batch is NULL");
+  if (reps < 1 || reps > 1000) return batch_err(b, STITCH_EINVAL, "reps must be in 1..1000");
+  if (!batch_ptrs_ok(b, 1, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev))
+    return batch_err(b, STITCH_EINVAL, "pointer arrays must be complete, non-NULL and aligned");
+  const int R = (int)b->ctx.size();
+  cudaError_t e = cudaDeviceSynchronize();
+  FuseParams *params = nullptr;
+  int *counter = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&params, R * sizeof(FuseParams));
+  if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(int));
+  std::vector<FuseParams> hp(R);
+  for (int r = 0; r < R; ++r) {
+    stitch_ctx *c = b->ctx[r];
+    const int np = c->g.n - 1;
+    hp[r] = frame_params(c, frames_dev + b->cam_off[r], np ? flow_ij_dev + b->pair_off[r] : nullptr,
+                         np ? flow_ji_dev + b->pair_off[r] : nullptr, pano_dev[r], c->host_T - 1, c->host_F);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(params, hp.data(), R * sizeof(FuseParams), cudaMemcpyHostToDevice);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms[kNumTileShapes];
+  int best = -1;
+  const int keep = b->shape;
+  for (int sh = 0; sh < kNumTileShapes && e == cudaSuccess; ++sh) {
+    ms[sh] = -1.0f;
+    if (batch_items(b, sh) != STITCH_OK) continue;
+    MultiParams pw{params, 0, b->n_pw_items, b->pw_items, nullptr};
+    e = launch_prewarp_multi(pw, b->half, b->cap);
+    MultiParams mf{params, 0, b->n_fuse_items, b->fuse_items, counter};
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+      e = cudaMemsetAsync(counter, 0, sizeof(int), b->cap);
+      if (e == cudaSuccess) e = launch_fuse_multi(mf, b->half, sh, b->grid, b->cap);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->cap);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) {
+      e = cudaMemsetAsync(counter, 0, sizeof(int), b->cap);
+      if (e == cudaSuccess) e = launch_fuse_multi(mf, b->half, sh, b->grid, b->cap);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->cap);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) {
+      ms[sh] = t / (float)reps;
+      if (best < 0 || ms[sh] < ms[best]) best = sh;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(params);
+  cudaFree(counter);
+  const int chosen = best >= 0 ? best : keep;
+  const int rc = batch_items(b, chosen);
+  if (e != cudaSuccess) return batch_err(b, STITCH_ECUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
+  if (rc != STITCH_OK) return rc;
+  if (shape_out) *shape_out = chosen;
+  if (ms_out)
+    for (int sh = 0; sh < kNumTileShapes; ++sh) ms_out[sh] = ms[sh];
+  return STITCH_OK;
+}
+
+void stitch_batch_destroy(stitch_batch *b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  for (auto &g : b->graphs) free_batch_graph(g);
+  cudaFree(b->fuse_items);
+  cudaFree(b->pw_items);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (int i = 0; i < 3; ++i)
+    if (b->pipe[i]) cudaStreamDestroy(b->pipe[i]);
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 8; ++k)
+      if (b->ev[a][k]) cudaEventDestroy(b->ev[a][k]);
+  delete b;
+}
+
+const char *stitch_batch_last_error(const stitch_batch *b) { return b ? b->err.c_str() : g_last_error.c_str(); }
 
 const char *stitch_last_error(const stitch_ctx *ctx) {
   return ctx ? ctx->err.c_str() : g_last_error.c_str();

@@ -8,9 +8,11 @@
 //   in a small intermediate (float32 RGB, or float16 with
 //   STITCH_FP16_INTERMEDIATE). It does not depend on the colour estimate.
 //
-// k_fuse: one block per 64 x 16 panorama tile.
+// k_fuse: one block per panorama tile (64 x 32 by default; the shape is a
+//   template parameter the autotuner picks per rig).
 //   * Own tiles (columns of one camera k): the source window that the tile
-//     maps to through H_k^-1 is staged in shared memory as one RGBX word per
+//     maps to through H_k^-1 (planar) or through the cylinder's ray and H_k^-1
+//     (cylindrical panorama) is staged in shared memory as one RGBX word per
 //     pixel; every pixel then computes s = H_k^-1 q (float32, relative to the
 //     camera's panorama origin), tests coverage 0 <= s <= (w-1, h-1), reads its
 //     four bilinear taps from shared memory and forms v = P . M_k. Pixels that
@@ -30,9 +32,13 @@
 //     curve F (Eq. 5: gamma, linear, gamma) and rounded half to even; pixels
 //     go to a shared-memory tile and leave as 16-byte stores per plane.
 //
-// Thread mapping: warp w, lane l handles the pixels (l + 32 a, 4 w + b),
-// a in {0, 1}, b in {0..3}, so a warp touches 32 consecutive pixels of a row
-// at a time and its shared-memory tap reads fall in distinct banks.
+// Thread mapping: lane l of a warp handles columns l + 32 a of the warp's
+// rows, so a warp touches 32 consecutive pixels of a row at a time and its
+// shared-memory tap reads fall in distinct banks.
+//
+// k_prewarp_multi / k_fuse_multi: the same work over the tiles of several
+// independent rigs in one launch; the fuse is persistent (one block per
+// resident slot, tiles taken from a work counter).
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -44,16 +50,29 @@ namespace {
 constexpr float kMagicRound = 12582912.0f;   // 1.5 * 2^23: x + kMagicRound rounds x to an integer (RNE)
 constexpr int kMagicRoundBits = 0x4B400000;
 constexpr float kMagicByte = 8388608.0f;     // 2^23: the float with bits 0x4B0000bb is 2^23 + bb
-constexpr int kWinCap = 3584;                // staged source pixels per window (14 KB)
+constexpr int kWinCap = 3840;                // staged source pixels per window (15 KB)
 
 // Approximate reciprocal (CUDA's fast division intrinsic: a few ulp).
 __device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
 
 // s = H^-1 q for panorama point (x, y) given as floats relative to the origin.
+// Cylindrical panorama: q stands for the ray (sin theta, h, cos theta) with
+// theta = (x - cx) / f and h = (y - cy) / f (the origin is 0 there).
 __device__ __forceinline__ void cam_map_f(const CamDev &c, float dx, float dy, float &sx, float &sy, float &nw) {
-  const float nx = fmaf(c.h[0], dx, fmaf(c.h[1], dy, c.h[2]));
-  const float ny = fmaf(c.h[3], dx, fmaf(c.h[4], dy, c.h[5]));
-  nw = fmaf(c.h[6], dx, fmaf(c.h[7], dy, c.h[8]));
+  float nx, ny;
+  if (c.cyl) {
+    const float th = (dx - c.cyl_cx) * c.cyl_finv;
+    const float hh = (dy - c.cyl_cy) * c.cyl_finv;
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    nx = fmaf(c.h[0], sn, fmaf(c.h[1], hh, c.h[2] * cs));
+    ny = fmaf(c.h[3], sn, fmaf(c.h[4], hh, c.h[5] * cs));
+    nw = fmaf(c.h[6], sn, fmaf(c.h[7], hh, c.h[8] * cs));
+  } else {
+    nx = fmaf(c.h[0], dx, fmaf(c.h[1], dy, c.h[2]));
+    ny = fmaf(c.h[3], dx, fmaf(c.h[4], dy, c.h[5]));
+    nw = fmaf(c.h[6], dx, fmaf(c.h[7], dy, c.h[8]));
+  }
   const float r = rcp_approx(nw);
   sx = nx * r;
   sy = ny * r;
@@ -408,8 +427,9 @@ __device__ __forceinline__ float3 pw_bilinear(const typename PwT<kHalf>::T *pw, 
   return o;
 }
 
-__device__ __forceinline__ void put_px(uint8_t (*s_out)[kTileH][kTileW], int lx, int ly, const Hot &h,
-                                       const BlockColor &bc, bool cov, float3 v) {
+template <int TW, int TH>
+__device__ __forceinline__ void put_px(uint8_t (*s_out)[TH][TW], int lx, int ly, const Hot &h, const BlockColor &bc,
+                                       bool cov, float3 v) {
   uint32_t o0 = 0u, o1 = 0u, o2 = 0u;
   if (cov) {
     o0 = finish(h, bc, 0, v.x);
@@ -421,13 +441,14 @@ __device__ __forceinline__ void put_px(uint8_t (*s_out)[kTileH][kTileW], int lx,
   s_out[2][ly][lx] = (uint8_t)o2;
 }
 
-__device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0,
-                                           const uint8_t (*s_out)[kTileH][kTileW]) {
-  // 3 planes x kTileH rows x 4 sixteen-byte pieces.
-  for (int t = threadIdx.x; t < 3 * kTileH * (kTileW / 16); t += blockDim.x) {
-    const int c = t / (kTileH * 4);
-    const int r = (t / 4) % kTileH;
-    const int q = t % 4;
+template <int TW, int TH>
+__device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0, const uint8_t (*s_out)[TH][TW]) {
+  // 3 planes x TH rows x TW / 16 sixteen-byte pieces.
+  constexpr int kPieces = TW / 16;
+  for (int t = threadIdx.x; t < 3 * TH * kPieces; t += blockDim.x) {
+    const int c = t / (TH * kPieces);
+    const int r = (t / kPieces) % TH;
+    const int q = t % kPieces;
     const int y = ty0 + r, x = tx0 + 16 * q;
     if (y >= P.pano_h || x >= P.pano_pitch) continue;
     const uint4 v = *reinterpret_cast<const uint4 *>(&s_out[c][r][16 * q]);
@@ -435,18 +456,182 @@ __device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0
   }
 }
 
-}  // namespace
+// Shared memory of one fuse tile.
+template <int TW, int TH>
+struct FuseSmem {
+  BlockColor bc;
+  Window sW[2];
+  __align__(16) uint32_t s_win[2][kWinCap];
+  __align__(16) uint8_t s_out[3][TH][TW];
+};
 
-// ---------------------------------------------------------------------------
-// Kernels.
-// ---------------------------------------------------------------------------
+// Thread -> pixel mapping of a TW x TH tile: warp w owns rows
+// [w TH / 8, (w + 1) TH / 8), lane l the columns l + 32 a; pixel j of a thread
+// is column group j % (TW / 32) of row j / (TW / 32) of its warp's rows.
+template <int TW, int TH>
+struct Map {
+  static constexpr int kGroups = TW / 32;
+  static constexpr int kRowsPerWarp = TH / 8;
+  static constexpr int kPix = kGroups * kRowsPerWarp;
+  static_assert(TW % 32 == 0 && TH % 8 == 0, "tile shape");
+  __device__ static int lx(int lane, int j) { return lane + 32 * (j % kGroups); }
+  __device__ static int ly(int warp, int j) { return kRowsPerWarp * warp + j / kGroups; }
+};
 
-template <bool kHalf>
-__global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams P) {
+// One panorama tile (see the file header): source windows, per-pixel work,
+// then the tile's three planes leave as 16-byte stores.
+template <bool kHalf, int TW, int TH>
+__device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t, FuseSmem<TW, TH> &sm) {
   using PT = typename PwT<kHalf>::T;
-  __shared__ __align__(16) uint32_t s_win[2][kWinCap];
-  __shared__ Window sW[2];
-  const PwTile pt = P.pw_tiles[blockIdx.x];
+  using MP = Map<TW, TH>;
+  BlockColor &bc = sm.bc;
+  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
+  const int tx1 = min(tx0 + TW, P.pano_w) - 1, ty1 = min(ty0 + TH, P.pano_h) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool empty = tx0 > tx1 || ty0 > ty1;
+  load_block_color(P, bc);
+
+  // Source windows: warp 0 for the tile's camera (or a band's left camera),
+  // warp 1 for a band's right camera, only where tile pixels need them.
+  if (warp < 2) {
+    Window W = no_window();
+    if (!empty) {
+      if (t.kind != 1) {
+        if (warp == 0) W = warp_window(P.cam[t.idx], tx0, ty0, tx1, ty1);
+      } else {
+        const BandDev B = P.band[t.idx];
+        const bool rows_out = ty0 < B.y0 || ty1 >= B.y1;
+        const bool need = warp == 0 ? (tx0 < B.x0 || (rows_out && tx1 >= B.x0))
+                                    : (tx1 >= B.x1 || (rows_out && tx0 < B.x1));
+        if (need) W = warp_window(P.cam[t.idx + warp], tx0, ty0, tx1, ty1);
+      }
+    }
+    if (lane == 0) sm.sW[warp] = W;
+  }
+  __syncthreads();
+  const Window W0 = sm.sW[0], W1 = sm.sW[1];
+  if (W0.ok) stage_window(P.src[t.idx], P.cam[t.idx], W0, sm.s_win[0]);
+  if (W1.ok) stage_window(P.src[t.idx + 1], P.cam[t.idx + 1], W1, sm.s_win[1]);
+  __syncthreads();
+  const Hot hot = load_hot(bc);
+
+  if (t.kind == 0) {
+    // Fully covered own tile: no coverage test, no fallback.
+    const int k = t.idx;
+    const CamDev &c = P.cam[k];
+    float M[9];
+    load_M(bc, k, M);
+    const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
+    if (c.affine && W0.ok) {
+#pragma unroll 2
+      for (int j = 0; j < MP::kPix; ++j) {
+        const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+        float sx, sy;
+        cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
+        put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, true, mulM(M, win_bilinear(sm.s_win[0], W0, sx, sy)));
+      }
+    } else {
+#pragma unroll 2
+      for (int j = 0; j < MP::kPix; ++j) {
+        const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+        float sx, sy, nw;
+        cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
+        const float3 v =
+            mulM(M, W0.ok ? win_bilinear(sm.s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
+        put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, true, v);
+      }
+    }
+  } else if (t.kind == 2) {
+    const int k = t.idx;
+    float M[9];
+    load_M(bc, k, M);
+#pragma unroll 2
+    for (int j = 0; j < MP::kPix; ++j) {
+      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+      const int x = tx0 + lx, y = ty0 + ly;
+      float3 v = make_float3(0.0f, 0.0f, 0.0f);
+      bool cov = false;
+      if (x < P.pano_w && y < P.pano_h) {
+        cov = cam_value_w(P, M, k, W0, sm.s_win[0], x, y, v);
+        if (!cov && k > 0) cov = cam_value_g(P, bc, k - 1, x, y, v);
+        if (!cov && k < P.n_cams - 1) cov = cam_value_g(P, bc, k + 1, x, y, v);
+      }
+      put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, cov, v);
+    }
+  } else {
+    const int p = t.idx;
+    const BandDev B = P.band[p];
+    float Ma[9], Mb[9];
+    load_M(bc, p, Ma);
+    load_M(bc, p + 1, Mb);
+    const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
+    const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
+    const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
+    const float mf = P.max_flow;
+    const int bw = B.x1 - B.x0;
+#pragma unroll 2
+    for (int j = 0; j < MP::kPix; ++j) {
+      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+      const int x = tx0 + lx, y = ty0 + ly;
+      float3 v = make_float3(0.0f, 0.0f, 0.0f);
+      bool cov = false;
+      if (x < P.pano_w && y < P.pano_h) {
+        if (x < B.x0) {
+          cov = cam_value_w(P, Ma, p, W0, sm.s_win[0], x, y, v);
+          if (!cov && p > 0) cov = cam_value_g(P, bc, p - 1, x, y, v);
+          if (!cov) cov = cam_value_g(P, bc, p + 1, x, y, v);
+        } else if (x >= B.x1) {
+          cov = cam_value_w(P, Mb, p + 1, W1, sm.s_win[1], x, y, v);
+          if (!cov) cov = cam_value_g(P, bc, p, x, y, v);
+          if (!cov && p + 2 < P.n_cams) cov = cam_value_g(P, bc, p + 2, x, y, v);
+        } else {
+          const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
+          const float ta = 1.0f - tb;
+          if (y < B.y0 || y >= B.y1) {
+            float3 va, vb;
+            const bool ca = cam_value_w(P, Ma, p, W0, sm.s_win[0], x, y, va);
+            const bool cb = cam_value_w(P, Mb, p + 1, W1, sm.s_win[1], x, y, vb);
+            if (ca && cb) {
+              v = make_float3(fmaf(ta, va.x, tb * vb.x), fmaf(ta, va.y, tb * vb.y), fmaf(ta, va.z, tb * vb.z));
+            } else if (ca) {
+              v = va;
+            } else if (cb) {
+              v = vb;
+            }
+            cov = ca || cb;
+          } else {
+            const size_t fi = (size_t)(y - B.y0) * bw + (x - B.x0);
+            float2 fa = __ldg(P.flow_ij[p] + fi);
+            float2 fb = __ldg(P.flow_ji[p] + fi);
+            fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
+            fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
+            const float wa = printed ? ta : tb;
+            const float wb = printed ? tb : ta;
+            const float lo_x = (float)B.x0, hi_x = (float)(B.x1 - 1);
+            const float lo_y = (float)B.y0, hi_y = (float)(B.y1 - 1);
+            const float Xa = fminf(fmaxf(fmaf(wa, fa.x, (float)x), lo_x), hi_x);
+            const float Ya = fminf(fmaxf(fmaf(wa, fa.y, (float)y), lo_y), hi_y);
+            const float Xb = fminf(fmaxf(fmaf(wb, fb.x, (float)x), lo_x), hi_x);
+            const float Yb = fminf(fmaxf(fmaf(wb, fb.y, (float)y), lo_y), hi_y);
+            const float3 Pa = mulM(Ma, pw_bilinear<kHalf>(pwa, B, Xa, Ya));
+            const float3 Pb = mulM(Mb, pw_bilinear<kHalf>(pwb, B, Xb, Yb));
+            v = make_float3(fmaf(ta, Pa.x, tb * Pb.x), fmaf(ta, Pa.y, tb * Pb.y), fmaf(ta, Pa.z, tb * Pb.z));
+            cov = true;
+          }
+        }
+      }
+      put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, cov, v);
+    }
+  }
+  __syncthreads();
+  store_tile<TW, TH>(P, tx0, ty0, sm.s_out);
+}
+
+// One band pre-warp piece (kTileW x kTileH) of pair pt.pair, both cameras.
+template <bool kHalf>
+__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, uint32_t (*s_win)[kWinCap],
+                                              Window *sW) {
+  using PT = typename PwT<kHalf>::T;
   const BandDev B = P.band[pt.pair];
   const int bw = B.x1 - B.x0;
   const int rx0 = pt.x0, ry0 = pt.y0;
@@ -484,153 +669,68 @@ __global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams 
   }
 }
 
+// Copy one rig's parameters into shared memory (16-byte words).
+__device__ __forceinline__ void copy_params(FuseParams &dst, const FuseParams *src) {
+  static_assert(sizeof(FuseParams) % 16 == 0, "parameter block must be a whole number of 16-byte words");
+  const int4 *s = reinterpret_cast<const int4 *>(src);
+  int4 *d = reinterpret_cast<int4 *>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(FuseParams) / 16); i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Kernels.
+// ---------------------------------------------------------------------------
+
 template <bool kHalf>
-__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const FuseParams P) {
-  using PT = typename PwT<kHalf>::T;
-  __shared__ BlockColor bc;
-  __shared__ Window sW[2];
+__global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams P) {
   __shared__ __align__(16) uint32_t s_win[2][kWinCap];
-  __shared__ __align__(16) uint8_t s_out[3][kTileH][kTileW];
-  const TileDesc t = P.tiles[blockIdx.x];
-  const int tx0 = t.tx * kTileW, ty0 = t.ty * kTileH;
-  const int tx1 = min(tx0 + kTileW, P.pano_w) - 1, ty1 = min(ty0 + kTileH, P.pano_h) - 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool empty = tx0 > tx1 || ty0 > ty1;
-  load_block_color(P, bc);
+  __shared__ Window sW[2];
+  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], s_win, sW);
+}
 
-  // Source windows: warp 0 for the tile's camera (or a band's left camera),
-  // warp 1 for a band's right camera, only where tile pixels need them.
-  if (warp < 2) {
-    Window W = no_window();
-    if (!empty) {
-      if (t.kind != 1) {
-        if (warp == 0) W = warp_window(P.cam[t.idx], tx0, ty0, tx1, ty1);
-      } else {
-        const BandDev B = P.band[t.idx];
-        const bool rows_out = ty0 < B.y0 || ty1 >= B.y1;
-        const bool need = warp == 0 ? (tx0 < B.x0 || (rows_out && tx1 >= B.x0))
-                                    : (tx1 >= B.x1 || (rows_out && tx0 < B.x1));
-        if (need) W = warp_window(P.cam[t.idx + warp], tx0, ty0, tx1, ty1);
-      }
-    }
-    if (lane == 0) sW[warp] = W;
-  }
-  __syncthreads();
-  const Window W0 = sW[0], W1 = sW[1];
-  if (W0.ok) stage_window(P.src[t.idx], P.cam[t.idx], W0, s_win[0]);
-  if (W1.ok) stage_window(P.src[t.idx + 1], P.cam[t.idx + 1], W1, s_win[1]);
-  __syncthreads();
-  const Hot hot = load_hot(bc);
+template <bool kHalf, int TW, int TH>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const FuseParams P) {
+  __shared__ FuseSmem<TW, TH> sm;
+  fuse_tile<kHalf, TW, TH>(P, P.tiles[blockIdx.x], sm);
+}
 
-  if (t.kind == 0) {
-    // Fully covered own tile: no coverage test, no fallback.
-    const int k = t.idx;
-    const CamDev &c = P.cam[k];
-    float M[9];
-    load_M(bc, k, M);
-    const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
-    if (c.affine && W0.ok) {
-#pragma unroll 2
-      for (int j = 0; j < 8; ++j) {
-        const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
-        float sx, sy;
-        cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
-        put_px(s_out, lx, ly, hot, bc, true, mulM(M, win_bilinear(s_win[0], W0, sx, sy)));
-      }
-    } else {
-#pragma unroll 2
-      for (int j = 0; j < 8; ++j) {
-        const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
-        float sx, sy, nw;
-        cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
-        const float3 v = mulM(M, W0.ok ? win_bilinear(s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
-        put_px(s_out, lx, ly, hot, bc, true, v);
-      }
-    }
-  } else if (t.kind == 2) {
-    const int k = t.idx;
-    float M[9];
-    load_M(bc, k, M);
-#pragma unroll 2
-    for (int j = 0; j < 8; ++j) {
-      const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
-      const int x = tx0 + lx, y = ty0 + ly;
-      float3 v = make_float3(0.0f, 0.0f, 0.0f);
-      bool cov = false;
-      if (x < P.pano_w && y < P.pano_h) {
-        cov = cam_value_w(P, M, k, W0, s_win[0], x, y, v);
-        if (!cov && k > 0) cov = cam_value_g(P, bc, k - 1, x, y, v);
-        if (!cov && k < P.n_cams - 1) cov = cam_value_g(P, bc, k + 1, x, y, v);
-      }
-      put_px(s_out, lx, ly, hot, bc, cov, v);
-    }
-  } else {
-    const int p = t.idx;
-    const BandDev B = P.band[p];
-    float Ma[9], Mb[9];
-    load_M(bc, p, Ma);
-    load_M(bc, p + 1, Mb);
-    const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
-    const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
-    const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
-    const float mf = P.max_flow;
-    const int bw = B.x1 - B.x0;
-#pragma unroll 2
-    for (int j = 0; j < 8; ++j) {
-      const int lx = lane + 32 * (j & 1), ly = 4 * warp + (j >> 1);
-      const int x = tx0 + lx, y = ty0 + ly;
-      float3 v = make_float3(0.0f, 0.0f, 0.0f);
-      bool cov = false;
-      if (x < P.pano_w && y < P.pano_h) {
-        if (x < B.x0) {
-          cov = cam_value_w(P, Ma, p, W0, s_win[0], x, y, v);
-          if (!cov && p > 0) cov = cam_value_g(P, bc, p - 1, x, y, v);
-          if (!cov) cov = cam_value_g(P, bc, p + 1, x, y, v);
-        } else if (x >= B.x1) {
-          cov = cam_value_w(P, Mb, p + 1, W1, s_win[1], x, y, v);
-          if (!cov) cov = cam_value_g(P, bc, p, x, y, v);
-          if (!cov && p + 2 < P.n_cams) cov = cam_value_g(P, bc, p + 2, x, y, v);
-        } else {
-          const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
-          const float ta = 1.0f - tb;
-          if (y < B.y0 || y >= B.y1) {
-            float3 va, vb;
-            const bool ca = cam_value_w(P, Ma, p, W0, s_win[0], x, y, va);
-            const bool cb = cam_value_w(P, Mb, p + 1, W1, s_win[1], x, y, vb);
-            if (ca && cb) {
-              v = make_float3(fmaf(ta, va.x, tb * vb.x), fmaf(ta, va.y, tb * vb.y), fmaf(ta, va.z, tb * vb.z));
-            } else if (ca) {
-              v = va;
-            } else if (cb) {
-              v = vb;
-            }
-            cov = ca || cb;
-          } else {
-            const size_t fi = (size_t)(y - B.y0) * bw + (x - B.x0);
-            float2 fa = __ldg(P.flow_ij[p] + fi);
-            float2 fb = __ldg(P.flow_ji[p] + fi);
-            fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
-            fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
-            const float wa = printed ? ta : tb;
-            const float wb = printed ? tb : ta;
-            const float lo_x = (float)B.x0, hi_x = (float)(B.x1 - 1);
-            const float lo_y = (float)B.y0, hi_y = (float)(B.y1 - 1);
-            const float Xa = fminf(fmaxf(fmaf(wa, fa.x, (float)x), lo_x), hi_x);
-            const float Ya = fminf(fmaxf(fmaf(wa, fa.y, (float)y), lo_y), hi_y);
-            const float Xb = fminf(fmaxf(fmaf(wb, fb.x, (float)x), lo_x), hi_x);
-            const float Yb = fminf(fmaxf(fmaf(wb, fb.y, (float)y), lo_y), hi_y);
-            const float3 Pa = mulM(Ma, pw_bilinear<kHalf>(pwa, B, Xa, Ya));
-            const float3 Pb = mulM(Mb, pw_bilinear<kHalf>(pwb, B, Xb, Yb));
-            v = make_float3(fmaf(ta, Pa.x, tb * Pb.x), fmaf(ta, Pa.y, tb * Pb.y), fmaf(ta, Pa.z, tb * Pb.z));
-            cov = true;
-          }
-        }
-      }
-      put_px(s_out, lx, ly, hot, bc, cov, v);
-    }
-  }
+// Band pre-warp of several rigs in one launch: block b takes item b.
+template <bool kHalf>
+__global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParams M) {
+  __shared__ __align__(16) uint32_t s_win[2][kWinCap];
+  __shared__ Window sW[2];
+  __shared__ FuseParams sp;
+  const MultiItem it = M.items[blockIdx.x];
+  copy_params(sp, M.params + M.base + it.rig);
   __syncthreads();
-  store_tile(P, tx0, ty0, s_out);
+  prewarp_piece<kHalf>(sp, it.pw, s_win, sW);
+}
+
+// Persistent fuse over the tiles of several rigs: each block takes the next
+// item from a work counter until none is left (dynamic balance of uneven tile
+// costs), loading a rig's parameters into shared memory when the rig changes.
+template <bool kHalf, int TW, int TH>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi(const MultiParams M) {
+  __shared__ FuseSmem<TW, TH> sm;
+  __shared__ FuseParams sp;
+  __shared__ int s_item;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= M.n_items) break;
+    const MultiItem it = M.items[item];
+    if (it.rig != cur) {
+      copy_params(sp, M.params + M.base + it.rig);
+      cur = it.rig;
+    }
+    __syncthreads();
+    fuse_tile<kHalf, TW, TH>(sp, it.tile, sm);
+    __syncthreads();
+  }
 }
 
 size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
@@ -646,13 +746,82 @@ cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fuse(const FuseParams &p, cudaStream_t s) {
-  if (p.n_tiles <= 0) return cudaSuccess;
+namespace {
+
+template <int TW, int TH>
+void fuse_by_half(const FuseParams &p, cudaStream_t s) {
   if (p.flags & STITCH_FP16_INTERMEDIATE)
-    k_fuse<true><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
+    k_fuse<true, TW, TH><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
   else
-    k_fuse<false><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
+    k_fuse<false, TW, TH><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
+}
+
+template <int TW, int TH>
+void fuse_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t s) {
+  if (half)
+    k_fuse_multi<true, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
+  else
+    k_fuse_multi<false, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
+}
+
+template <int TW, int TH>
+int occupancy(bool half) {
+  int n = 0;
+  if (half)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi<true, TW, TH>, kFuseThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi<false, TW, TH>, kFuseThreads, 0);
+  return n;
+}
+
+}  // namespace
+
+static_assert(kTileShapes[0].w == 64 && kTileShapes[0].h == 32 && kTileShapes[1].w == 64 && kTileShapes[1].h == 16 &&
+                  kTileShapes[2].w == 32 && kTileShapes[2].h == 32 && kTileShapes[3].w == 128 &&
+                  kTileShapes[3].h == 16,
+              "the shape table and the kernel instantiations below must agree");
+
+cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s) {
+  if (p.n_tiles <= 0) return cudaSuccess;
+  switch (shape) {
+    case 0: fuse_by_half<64, 32>(p, s); break;
+    case 1: fuse_by_half<64, 16>(p, s); break;
+    case 2: fuse_by_half<32, 32>(p, s); break;
+    case 3: fuse_by_half<128, 16>(p, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
+}
+
+cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s) {
+  if (m.n_items <= 0) return cudaSuccess;
+  if (half)
+    k_prewarp_multi<true><<<m.n_items, kFuseThreads, 0, s>>>(m);
+  else
+    k_prewarp_multi<false><<<m.n_items, kFuseThreads, 0, s>>>(m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s) {
+  if (m.n_items <= 0) return cudaSuccess;
+  switch (shape) {
+    case 0: fuse_multi_by_half<64, 32>(m, half, grid, s); break;
+    case 1: fuse_multi_by_half<64, 16>(m, half, grid, s); break;
+    case 2: fuse_multi_by_half<32, 32>(m, half, grid, s); break;
+    case 3: fuse_multi_by_half<128, 16>(m, half, grid, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int fuse_multi_blocks_per_sm(bool half, int shape) {
+  switch (shape) {
+    case 0: return occupancy<64, 32>(half);
+    case 1: return occupancy<64, 16>(half);
+    case 2: return occupancy<32, 32>(half);
+    case 3: return occupancy<128, 16>(half);
+    default: return 0;
+  }
 }
 
 }  // namespace stitch

@@ -14,9 +14,17 @@ constexpr int kMaxCams = STITCH_MAX_CAMS;
 constexpr int kMaxPairs = STITCH_MAX_PAIRS;
 constexpr int kMaxWindow = STITCH_MAX_WINDOW;
 constexpr int kSmoothFrames = 3;      // Eq. 6-7: current frame and its last two
-constexpr int kTileW = 64;            // fuse tile: 64 x 32 panorama pixels
+constexpr int kTileW = 64;            // band pre-warp piece: 64 x 32 panorama pixels
 constexpr int kTileH = 32;
-constexpr int kFuseThreads = 256;     // 8 pixels per thread
+constexpr int kFuseThreads = 256;
+// Fuse tile shapes (panorama pixels) the autotuner chooses from; shape 0 is
+// the default. Width is a multiple of 32 (a warp spans 32 columns), and
+// width x height is a multiple of the 256 threads of a block.
+struct TileShape {
+  int w, h;
+};
+constexpr int kNumTileShapes = 4;
+constexpr TileShape kTileShapes[kNumTileShapes] = {{64, 32}, {64, 16}, {32, 32}, {128, 16}};
 constexpr int kStatsThreads = 256;
 constexpr int kEstimateThreads = 256;
 constexpr double kCondLimit = 1e12;
@@ -75,6 +83,8 @@ struct CamDev {
   float wm1, hm1;
   int own_lo, own_hi;
   int affine;                         // h[6] == h[7] == 0: no perspective divide
+  int cyl;                            // cylindrical panorama: h maps the ray of (x, y), see below
+  float cyl_finv, cyl_cx, cyl_cy;     // theta = (x - cyl_cx) * cyl_finv, height = (y - cyl_cy) * cyl_finv
 };
 
 struct BandDev {
@@ -83,7 +93,7 @@ struct BandDev {
 };
 
 struct TileDesc {
-  int16_t tx, ty;                     // tile origin / (kTileW, kTileH)
+  int16_t tx, ty;                     // tile origin / (tile width, tile height)
   int8_t kind;                        // 0 = own columns of camera idx, fully covered; 1 = touches band
                                       // idx; 2 = own columns of camera idx, partly covered
   int8_t idx;
@@ -96,7 +106,7 @@ struct PwTile {
   int x0, y0;                         // panorama origin of the piece
 };
 
-struct FuseParams {
+struct alignas(16) FuseParams {
   int n_cams;
   int flags;
   int pano_w, pano_h, pano_pitch;
@@ -115,6 +125,22 @@ struct FuseParams {
   const float2 *flow_ij[kMaxPairs];
   const float2 *flow_ji[kMaxPairs];
   uint8_t *out;
+};
+
+// One unit of a launch that covers several rigs (and frames): rig r's tile
+// (or band pre-warp piece) with the parameters params[base + r].
+struct MultiItem {
+  int rig;
+  TileDesc tile;                      // fuse items
+  PwTile pw;                          // pre-warp items
+};
+
+struct MultiParams {
+  const FuseParams *params;           // device array, indexed by base + rig
+  int base;
+  int n_items;
+  const MultiItem *items;
+  int *counter;                       // work counter of the persistent fuse (zero before the launch)
 };
 
 struct RoleDev {
@@ -182,7 +208,10 @@ cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
 cudaError_t estimate_setup();
 cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s);
-cudaError_t launch_fuse(const FuseParams &p, cudaStream_t s);
+cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s);
+cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s);
+cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s);
+int fuse_multi_blocks_per_sm(bool half, int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
 size_t stats_smem_bytes();
 size_t prewarp_elem_bytes(bool fp16);

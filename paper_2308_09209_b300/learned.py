@@ -5,7 +5,7 @@ that labels the pairs (stitch_pairs_label), the network's forward pass, loss,
 backward pass and Adam (stitch_mlp_train_step). This module only moves tensors
 and picks batches.
 
-    python -m paper_2308_09209_b300.learned --pairs 200000 --epochs 8 --out weights.npz
+    python -m paper_2308_09209_b300.learned --pairs 200000 --epochs 40 --out weights.npz --evaluate
 
 draws the seeded training pairs (synthetic scenes under random gain, gamma,
 offset and colour cast), labels them on the GPU, trains, and writes the
@@ -107,16 +107,97 @@ def load(path, max_batch=256):
     return net, d["mu"], d["sd"]
 
 
+def evaluate_gain(net, config="2x640x360", seeds=(101, 102, 103, 104), n_frames=8):
+    """Learned against plain colour estimate on held-out synthetic rigs with a
+    known photometric response per camera.
+
+    For every frame and pair (i -> j) the true transfer is the least-squares
+    3x3 map from camera i's pixels to what camera j's response gives for the
+    same scene colours over camera i's whole frame; a matrix's error is the RMS
+    colour error (grey levels) of that map applied with the matrix instead.
+    Reported per estimator: the mean error, the frame-to-frame standard
+    deviation of M (mean over entries, frames after the window fills), and the
+    estimate's GPU time per frame; plus the learned path's fallback rate."""
+    from synth import Scene, render_camera_frames, rig_for_config
+    from synth.scene import _photometric
+    res = {k: dict(err=[], M=[]) for k in ("plain", "learned_raw", "learned_used", "truth")}
+    t_plain, t_learned, n_l, n_f = 0.0, 0.0, 0, 0
+    n_est = 0
+    for seed in seeds:
+        rig, seq = rig_for_config(config, seed=seed)
+        scene = Scene(rig.pano_w, rig.pano_h, n_objects=seq.get("objects", 0), seed=seed)
+        base = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
+                        max_flow=seq["max_flow"], flags=0)
+        lcfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
+                        max_flow=seq["max_flow"], flags=S.STITCH_LEARNED)
+        sp, sl = S.Stitcher(base), S.Stitcher(lcfg)
+        S.stitch_attach_mlp(sl.ctx, net.h)
+        S.stitch_profile(sp.ctx, True)
+        S.stitch_profile(sl.ctx, True)
+        npair = rig.n_cams - 1
+        per = {k: [] for k in res}
+        for t in range(n_frames):
+            frames = render_camera_frames(rig, scene, t, device="cuda")
+            sp.estimate_color(frames)
+            sl.estimate_color(frames)
+            Mp = S.stitch_get_pair_M(sp.ctx, npair)
+            Mh, r, used = S.stitch_get_learned(sl.ctx, npair)
+            Mu = S.stitch_get_pair_M(sl.ctx, npair)
+            mats = dict(plain=Mp, learned_raw=Mh, learned_used=Mu)
+            truth = []
+            for p in range(npair):
+                i = p if p < rig.n_cams // 2 else p + 1          # colour source of pair p
+                j = p + 1 if p < rig.n_cams // 2 else p          # its neighbour toward the reference
+                w, h = rig.cam_w[i], rig.cam_h[i]
+                G = torch.tensor(rig.G[i], dtype=torch.float64, device="cuda")
+                v, u = torch.meshgrid(torch.arange(0, h, 4, dtype=torch.float64, device="cuda"),
+                                      torch.arange(0, w, 4, dtype=torch.float64, device="cuda"), indexing="ij")
+                den = G[2, 0] * u + G[2, 1] * v + G[2, 2]
+                X = ((G[0, 0] * u + G[0, 1] * v + G[0, 2]) / den).float()
+                Y = ((G[1, 0] * u + G[1, 1] * v + G[1, 2]) / den).float()
+                sc = scene.render(X, Y, t)
+                xi = _photometric(sc, rig.gain[i], rig.gamma[i], rig.offset[i], rig.cast[i]).reshape(-1, 3).double()
+                yj = _photometric(sc, rig.gain[j], rig.gamma[j], rig.offset[j], rig.cast[j]).reshape(-1, 3).double()
+                Mt = torch.linalg.lstsq(xi, yj).solution
+                truth.append(Mt.cpu().numpy())
+                for k, Ms in list(mats.items()) + [("truth", None)]:
+                    Mk = Mt if Ms is None else torch.tensor(Ms[p], dtype=torch.float64, device="cuda")
+                    e = float((xi @ Mk - yj).pow(2).sum(1).mean().sqrt())
+                    per[k].append((t, p, e, (Mk.cpu().numpy() if Ms is None else Ms[p]).copy()))
+        pr_p = S.stitch_profile_read(sp.ctx)
+        pr_l = S.stitch_profile_read(sl.ctx)
+        t_plain += pr_p["estimate_ms"]
+        t_learned += pr_l["estimate_ms"]
+        n_est += pr_p["estimate_n"]
+        a, b = S.stitch_learned_stats(sl.ctx)
+        n_l += a
+        n_f += b
+        for k in res:
+            res[k]["err"] += [e for (_, _, e, _) in per[k]]
+            for p in range(npair):
+                Ms = np.stack([M for (t, pp, _, M) in per[k] if pp == p and t >= seq["window"]])
+                res[k]["M"].append(float(Ms.std(axis=0).mean()) if len(Ms) > 1 else 0.0)
+        sp.close()
+        sl.close()
+    out = {k: dict(rms_colour_error=float(np.mean(v["err"])), sigma_M=float(np.mean(v["M"]))) for k, v in res.items()}
+    out["plain"]["estimate_ms_per_frame"] = t_plain / max(n_est, 1)
+    out["learned_used"]["estimate_ms_per_frame"] = t_learned / max(n_est, 1)
+    out["fallback_rate"] = n_f / max(n_l + n_f, 1)
+    out["rigs"] = f"{len(seeds)} x {config}, {n_frames} frames each"
+    return out
+
+
 def main():
     from synth import make_pairs
     ap = argparse.ArgumentParser()
     ap.add_argument("--pairs", type=int, default=200000)
     ap.add_argument("--held-out", type=int, default=8192)
-    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--evaluate", action="store_true", help="also run the learned-vs-plain evaluation")
     a = ap.parse_args()
     S.stitch_mlp_n_params()
     t0 = time.perf_counter()
@@ -138,6 +219,8 @@ def main():
     if a.out:
         mu, sd = target_norm(targ[:n][ok])
         save(net, a.out, mu, sd)
+    if a.evaluate:
+        rep["gain"] = evaluate_gain(net)
     print(json.dumps(rep))
     net.close()
 

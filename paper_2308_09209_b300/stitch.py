@@ -32,6 +32,8 @@ STITCH_BALANCE_OFF = 1
 STITCH_FP16_INTERMEDIATE = 2
 STITCH_FLOW_WEIGHTS_PRINTED = 4
 STITCH_LEARNED = 8
+STITCH_PROJ_PLANAR = 0
+STITCH_PROJ_CYLINDRICAL = 1
 
 STITCH_MAX_CAMS = 8
 STITCH_CURVE_FLOATS = 10
@@ -60,6 +62,9 @@ class _Config(ctypes.Structure):
         ("lambda_", ctypes.c_double),
         ("max_flow", ctypes.c_float),
         ("flags", ctypes.c_int),
+        ("cyl_focal", ctypes.c_double),
+        ("cyl_cx", ctypes.c_double),
+        ("cyl_cy", ctypes.c_double),
     ]
 
 
@@ -105,6 +110,14 @@ def lib():
             "stitch_attach_mlp": (ip, [vp, vp]),
             "stitch_learned_stats": (ip, [vp, vp, vp]),
             "stitch_get_learned": (ip, [vp, vp, vp, vp]),
+            "stitch_autotune": (ip, [vp, pp, pp, pp, vp, ip, vp, vp]),
+            "stitch_tile_shape": (ip, [vp, vp, vp]),
+            "stitch_set_tile_shape": (ip, [vp, ip]),
+            "stitch_batch_create": (ip, [pp, ip, ctypes.POINTER(vp)]),
+            "stitch_batch_sequence": (ip, [vp, ip, pp, pp, pp, pp, vp]),
+            "stitch_batch_autotune": (ip, [vp, pp, pp, pp, pp, ip, vp, vp]),
+            "stitch_batch_destroy": (None, [vp]),
+            "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
             "stitch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_destroy": (None, [vp]),
@@ -132,6 +145,8 @@ class Config:
     lam: float = 0.05
     max_flow: float = 8.0
     flags: int = 0
+    projection: int = 0                 # 0 planar, 1 cylindrical (H = camera pixel -> ray)
+    cyl: Optional[Sequence[float]] = None   # (focal px/rad, cx, cy) for the cylindrical projection
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -161,7 +176,9 @@ class Config:
         c.pano_w = int(self.pano_w)
         c.pano_h = int(self.pano_h)
         c.pano_pitch = int(self.pitch)
-        c.projection = 0
+        c.projection = int(self.projection)
+        if self.cyl is not None:
+            c.cyl_focal, c.cyl_cx, c.cyl_cy = (float(v) for v in self.cyl)
         c.ref_cam = int(self.ref_cam)
         c.window = int(self.window)
         c.lambda_ = float(self.lam)
@@ -430,6 +447,66 @@ class Mlp:
                 self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- #
+# Tile shapes, autotuner, batched rigs
+# --------------------------------------------------------------------------- #
+STITCH_TILE_SHAPES = 4
+STITCH_BATCH_MAX_RIGS = 16
+TILE_SHAPES = ((64, 32), (64, 16), (32, 32), (128, 16))
+
+
+def stitch_autotune(ctx, frames, flows_ij, flows_ji, pano, reps: int = 5):
+    """(chosen shape index, mean ms per fuse launch for every shape, -1 = does not fit)."""
+    ms = np.zeros(STITCH_TILE_SHAPES, dtype=np.float32)
+    shape = ctypes.c_int(0)
+    _check(lib().stitch_autotune(ctx, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji), ctypes.c_void_p(pano.data_ptr()),
+                                 reps, ctypes.byref(shape), ms.ctypes.data), ctx)
+    return shape.value, ms
+
+
+def stitch_tile_shape(ctx):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    idx = lib().stitch_tile_shape(ctx, ctypes.byref(w), ctypes.byref(h))
+    return idx, (w.value, h.value)
+
+
+def stitch_set_tile_shape(ctx, shape: int) -> int:
+    return _check(lib().stitch_set_tile_shape(ctx, shape), ctx)
+
+
+def _batch_check(rc, b):
+    if rc != STITCH_OK:
+        m = lib().stitch_batch_last_error(b)
+        raise StitchError(rc, m.decode() if m else "")
+    return rc
+
+
+def stitch_batch_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    out = ctypes.c_void_p()
+    _batch_check(lib().stitch_batch_create(arr, len(ctxs), ctypes.byref(out)), None)
+    return out
+
+
+def stitch_batch_sequence(b, n_frames, frames, flows_ij, flows_ji, panos, stream=None) -> int:
+    """Flat, frame-major pointer lists (see include/stitch.h)."""
+    return _batch_check(lib().stitch_batch_sequence(b, n_frames, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji),
+                                                    _ptrs(panos), _stream(stream)), b)
+
+
+def stitch_batch_autotune(b, frames, flows_ij, flows_ji, panos, reps: int = 5):
+    ms = np.zeros(STITCH_TILE_SHAPES, dtype=np.float32)
+    shape = ctypes.c_int(0)
+    _batch_check(lib().stitch_batch_autotune(b, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji), _ptrs(panos), reps,
+                                             ctypes.byref(shape), ms.ctypes.data), b)
+    return shape.value, ms
+
+
+def stitch_batch_destroy(b) -> None:
+    if b is not None and b.value:
+        lib().stitch_batch_destroy(b)
 
 
 def stitch_n_pairs(ctx) -> int:

@@ -22,10 +22,10 @@ that are sums of low-frequency plane waves limited to the overlap bands;
 and, for the learned estimator, pairs of patches of the same content under
 two independent photometric responses.
 """
-from .rig import Rig, make_rig, rig_for_config, CONFIGS
+from .rig import Rig, make_rig, rig_for_config, CONFIGS, BATCH_RIGS
 from .scene import Scene, render_camera_frames
 from .flow import smooth_flow
 from .pairs import make_pairs, apply_response
 
-__all__ = ["Rig", "make_rig", "rig_for_config", "CONFIGS", "Scene",
+__all__ = ["Rig", "make_rig", "rig_for_config", "CONFIGS", "BATCH_RIGS", "Scene",
            "render_camera_frames", "smooth_flow", "make_pairs", "apply_response"]

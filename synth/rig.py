@@ -122,7 +122,14 @@ CONFIGS = {
                         perturb=0.01, frames=8, window=3, max_flow=3.0, objects=0),
     "4x3840x2160": dict(cams=[(3840, 2160)] * 4, pano_w=None, pano_h=2160, overlap=(0.15, 0.25),
                         perturb=0.01, frames=8, window=3, max_flow=3.0, objects=0),
+    # one rig mixing resolutions: six 1080p cameras followed by two 720p cameras
+    "6x1920x1080+2x1280x720": dict(cams=[(1920, 1080)] * 6 + [(1280, 720)] * 2, pano_w=None, pano_h=1080,
+                                   overlap=(0.15, 0.25), perturb=0.01, frames=8, window=3, max_flow=3.0,
+                                   objects=0),
 }
+
+# The batched workload: four independent rigs of uneven geometry stitched together.
+BATCH_RIGS = ("6x1920x1080+2x1280x720", "3x1920x1080", "4x3840x2160", "2x1280x720")
 
 
 def rig_for_config(name: str, seed: int = 0, **over) -> tuple[Rig, dict]:
