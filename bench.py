@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / learned / cylindrical comparisons (rank 0 of a 1-GPU run only)")
     return ap.parse_args()
 
 
@@ -91,8 +93,9 @@ def make_workload(name, n_frames, seed, device):
     from synth import Scene, render_camera_frames, rig_for_config, smooth_flow
     from paper_2308_09209_b300 import stitch as S
     rig, seq = rig_for_config(name, seed=seed)
+    ex = rig.extra or {}
     cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
-                   max_flow=seq["max_flow"])
+                   max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"))
     bands, _ = S.stitch_geometry(cfg)
     scene = Scene(rig.pano_w, rig.pano_h, n_objects=seq["objects"], seed=seed)
     frames, fij, fji = [], [], []
@@ -207,21 +210,41 @@ def traffic_from_profile(workload):
 # --------------------------------------------------------------------------- #
 # CPU baseline / reference arm: the FP64 oracle, as it stands
 # --------------------------------------------------------------------------- #
-def oracle_frames(wl, frame_ids):
-    """Run the oracle on the given frames; returns (seconds, output pixels)."""
-    import numpy as np
+def oracle_frames(wl, frame_ids, keep=False):
+    """Run the oracle on the given frames; returns (seconds, output pixels,
+    [(planes, near-edge mask)] when keep)."""
     from oracle.pipeline import OracleStitcher
     rig, seq = wl["rig"], wl["seq"]
+    ex = rig.extra or {}
     o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
-                       max_flow=seq["max_flow"])
+                       max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"))
     host = [([f.cpu().numpy() for f in wl["frames"][t]], [f.cpu().numpy() for f in wl["fij"][t]],
              [f.cpu().numpy() for f in wl["fji"][t]]) for t in frame_ids]
+    outs = []
     t0 = time.perf_counter()
     for fr, a, b in host:
         o.estimate_color(fr)
-        o.frame(fr, a, b)
+        planes, near, _ = o.frame(fr, a, b)
+        if keep:
+            outs.append((planes, near))
     dt = time.perf_counter() - t0
-    return dt, len(frame_ids) * wl["pano_px"]
+    return dt, len(frame_ids) * wl["pano_px"], outs
+
+
+def oracle_error(gpu_panos, oracle_outs, pano_w):
+    """Per-output error of the GPU panoramas against the FP64 oracle's (grey
+    levels, pixels within 1e-3 px of a coverage edge left out and counted)."""
+    import numpy as np
+    mx, n, n1, n0, nn = 0, 0, 0, 0, 0
+    for g, (planes, near) in zip(gpu_panos, oracle_outs):
+        d = np.abs(g.cpu().numpy()[:, :, :pano_w].astype(np.int16) - planes.astype(np.int16)).max(0)[~near]
+        mx = max(mx, int(d.max()) if d.size else 0)
+        n += d.size
+        n1 += int((d <= 1).sum())
+        n0 += int((d == 0).sum())
+        nn += int(near.sum())
+    return {"max_abs": mx, "frac_within_1": n1 / max(n, 1), "frac_exact": n0 / max(n, 1), "n_near_edge": nn,
+            "frames": len(gpu_panos)}
 
 
 def run_reference(args, dist):
@@ -231,7 +254,7 @@ def run_reference(args, dist):
     n = len(wl["frames"])
     times = []
     for s in range(args.warmup + args.steps):
-        dt, px = oracle_frames(wl, [s % n])
+        dt, px, _ = oracle_frames(wl, [s % n])
         if s >= args.warmup:
             times.append(dt)
     ms = 1e3 * sum(times) / len(times)
@@ -247,6 +270,131 @@ def run_reference(args, dist):
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# batched / learned / cylindrical comparisons (outside the timed main step)
+# --------------------------------------------------------------------------- #
+def _time(fn, stream, steps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _flat_seq(wls, F):
+    fr, fij, fji = [], [], []
+    for t in range(F):
+        for w in wls:
+            fr += w["frames"][t]
+            fij += w["fij"][t]
+            fji += w["fji"][t]
+    return fr, fij, fji
+
+
+def run_extras(args, dev, stream, ctxs):
+    """The batched form (four rigs of uneven geometry, FP16 intermediates,
+    one persistent fuse launch per frame) against the same rigs stitched one
+    after the other; the learned estimator against the plain one; and the
+    cylindrical 8 x 3840x2160 rig in its full form (learned estimate, FP16
+    intermediates, batched launch) against its plain form."""
+    import torch
+    from paper_2308_09209_b300 import learned
+    from paper_2308_09209_b300 import stitch as S
+    from synth import BATCH_RIGS, make_pairs
+    out = {}
+
+    # batched vs plain
+    F = 8
+    wls = [make_workload(n, F, 20 + i, dev) for i, n in enumerate(BATCH_RIGS)]
+    for w in wls:
+        w["cfg"].flags = S.STITCH_FP16_INTERMEDIATE
+    sts = [S.Stitcher(w["cfg"]) for w in wls]
+    ctxs.extend(sts)
+    b = S.stitch_batch_create([st.ctx for st in sts])
+    panos = [torch.empty((3, w["cfg"].pano_h, w["cfg"].pitch), dtype=torch.uint8, device=dev)
+             for _ in range(F) for w in wls]
+    fr, fij, fji = _flat_seq(wls, F)
+    shape, ms_shapes = S.stitch_batch_autotune(b, fr[:sum(len(w["frames"][0]) for w in wls)],
+                                               fij[:sum(len(w["fij"][0]) for w in wls)],
+                                               fji[:sum(len(w["fji"][0]) for w in wls)], panos[:len(wls)], reps=3)
+    ms_b = _time(lambda: S.stitch_batch_sequence(b, F, fr, fij, fji, panos, stream), stream, 5)
+    alone = [S.Stitcher(w["cfg"]) for w in wls]
+    ctxs.extend(alone)
+    for st in alone:
+        S.stitch_set_tile_shape(st.ctx, shape)
+    per = []
+    for w, st in zip(wls, alone):
+        pp = [torch.empty((3, w["cfg"].pano_h, w["cfg"].pitch), dtype=torch.uint8, device=dev) for _ in range(F)]
+        per.append(([f for t in range(F) for f in w["frames"][t]], [f for t in range(F) for f in w["fij"][t]],
+                    [f for t in range(F) for f in w["fji"][t]], pp))
+
+    def seq_all():
+        for st, (a, c, d, pp) in zip(alone, per):
+            S.stitch_sequence(st.ctx, F, a, c, d, pp, stream)
+
+    ms_p = _time(seq_all, stream, 5)
+    px = F * sum(w["pano_px"] for w in wls)
+    out["batched"] = {"rigs": list(BATCH_RIGS), "frames_per_step": F, "intermediate": "fp16",
+                      "tile_shape": S.TILE_SHAPES[shape], "autotune_ms": [round(float(m), 4) for m in ms_shapes],
+                      "batched_mpix_s": px / (ms_b / 1e3) / 1e6, "one_rig_at_a_time_mpix_s": px / (ms_p / 1e3) / 1e6,
+                      "speedup": ms_p / ms_b}
+    S.stitch_batch_destroy(b)
+    for st in sts + alone:
+        st.close()
+    del wls, panos, per, fr, fij, fji
+    torch.cuda.empty_cache()
+
+    # learned vs plain
+    t0 = time.perf_counter()
+    pairs, _ = make_pairs(65536, seed=1, device=dev)
+    feat, targ, _, flags = learned.label_pairs(pairs)
+    net, hist = learned.train(feat, targ, epochs=20, batch=512, lr=1e-3, seed=1, mask=flags == 0)
+    train_s = time.perf_counter() - t0
+    del pairs
+    gain = learned.evaluate_gain(net, seeds=(201, 202), n_frames=8, objects=6)
+    out["learned"] = {"train_pairs": 65536, "epochs": 20, "final_loss": hist[-1], "train_s": train_s, **gain}
+
+    # cylindrical large rig: full form vs plain form on the same frames
+    F = 4
+    wl = make_workload("8x3840x2160cyl", F, 0, dev)
+    fr = [f for t in range(F) for f in wl["frames"][t]]
+    a = [f for t in range(F) for f in wl["fij"][t]]
+    c = [f for t in range(F) for f in wl["fji"][t]]
+    pp = [torch.empty((3, wl["cfg"].pano_h, wl["cfg"].pitch), dtype=torch.uint8, device=dev) for _ in range(F)]
+    plain = S.Stitcher(wl["cfg"])
+    ctxs.append(plain)
+    ms_plain = _time(lambda: S.stitch_sequence(plain.ctx, F, fr, a, c, pp, stream), stream, 3)
+    wl["cfg"].flags = S.STITCH_FP16_INTERMEDIATE | S.STITCH_LEARNED
+    full = S.Stitcher(wl["cfg"])
+    ctxs.append(full)
+    S.stitch_attach_mlp(full.ctx, net.h)
+    bf = S.stitch_batch_create([full.ctx])
+    shape, _ = S.stitch_batch_autotune(bf, fr[:8], a[:7], c[:7], pp[:1], reps=2)
+    ms_full = _time(lambda: S.stitch_batch_sequence(bf, F, fr, a, c, pp, stream), stream, 3)
+    n_l, n_f = S.stitch_learned_stats(full.ctx)
+    px = F * wl["pano_px"]
+    rig = wl["rig"]
+    out["cylindrical"] = {"workload": f"8x3840x2160 cylindrical rig -> {rig.pano_w}x{rig.pano_h}, window "
+                                      f"{wl['seq']['window']}, max flow {wl['seq']['max_flow']} px, "
+                                      f"{wl['seq']['objects']} moving objects, {F} frames per step",
+                          "plain_mpix_s": px / (ms_plain / 1e3) / 1e6,
+                          "full_form_mpix_s": px / (ms_full / 1e3) / 1e6,
+                          "full_form": "learned estimate with fallback, fp16 intermediates, batched launch, "
+                                       f"tile {S.TILE_SHAPES[shape]}",
+                          "learned_fallback_rate": n_f / max(n_l + n_f, 1),
+                          "path_bytes_per_frame": wl["in_bytes"] + wl["flow_bytes"] + wl["out_bytes"]}
+    S.stitch_batch_destroy(bf)
+    net.close()
+    return out
 
 
 # --------------------------------------------------------------------------- #
@@ -356,11 +504,26 @@ def _run_ours(args, dist, ctxs):
     d2h = n_e2e * 3 * cfg.pitch * cfg.pano_h
 
     cpu_baseline = None
+    err = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        dt, px = oracle_frames(wl, [0, 1])
+        dt, px, outs = oracle_frames(wl, [0, 1], keep=True)
         cpu_baseline = {"value": px / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                         "sample": f"frames 0-1 of the workload: estimate + full {wl['rig'].pano_w}x"
                                   f"{wl['rig'].pano_h} panorama each, numpy float64, one thread"}
+        # the same two frames from a fresh context, compared with the oracle's panoramas
+        st3 = S.Stitcher(cfg)
+        ctxs.append(st3)
+        g = []
+        for t in (0, 1):
+            st3.estimate_color(wl["frames"][t])
+            g.append(st3.frame(wl["frames"][t], wl["fij"][t], wl["fji"][t]))
+        torch.cuda.synchronize()
+        err = oracle_error(g, outs, cfg.pano_w)
+
+    extras = {}
+    if dist.rank == 0 and dist.world == 1 and not args.no_extras:
+        del panos, h_frames, h_fij, h_fji, h_out
+        extras = run_extras(args, dev, stream, ctxs)
 
     launches = args.steps * F * 4     # stats, estimate, band pre-warp, fuse per frame
     if dist.rank == 0:
@@ -379,7 +542,8 @@ def _run_ours(args, dist, ctxs):
                        "stage_ms_per_frame": {"stats": stats_ms, "estimate": est_ms, "band_prewarp": prewarp_ms,
                                               "fuse": fuse_ms},
                        "stage_timing": stage_timing,
-                       "status": rc, "parallelism": f"replicas x{dist.world}"},
+                       "status": rc, "parallelism": f"replicas x{dist.world}",
+                       "oracle_error": err, **extras},
             "roofline": {"bound": "hbm", "kernel": "fused warp stage of a frame (k_prewarp_band + k_fuse)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_kind": peak_kind,

@@ -37,8 +37,8 @@ from .warp import stitch as _stitch, fuse_pixels, finish
 
 class OracleStitcher:
     def __init__(self, H, cam_w, cam_h, pano_w, pano_h, ref_cam=None, window=3,
-                 lam=0.05, max_flow=8.0, flags=0, mlp=None):
-        self.geom = Geometry(H, cam_w, cam_h, pano_w, pano_h, ref_cam)
+                 lam=0.05, max_flow=8.0, flags=0, mlp=None, projection=0, cyl=None):
+        self.geom = Geometry(H, cam_w, cam_h, pano_w, pano_h, ref_cam, projection=projection, cyl=cyl)
         self.window = int(window)
         self.lam = float(lam)
         self.max_flow = float(max_flow)

@@ -100,7 +100,7 @@ void pano_to_cam(const Geo &g, int k, double x, double y, double &sx, double &sy
 }
 
 // Camera pixel -> panorama point. Cylindrical: the ray d = H_k (u, v, 1) at
-// azimuth atan2(d_x, d_z) and height d_y / hypot(d_x, d_z).
+// azimuth atan2(d_x, d_z) and height d_y / sqrt(d_x^2 + d_z^2).
 void cam_to_pano(const Geo &g, int k, double u, double v, double &X, double &Y) {
   if (!g.cyl) {
     double W;
@@ -112,7 +112,7 @@ void cam_to_pano(const Geo &g, int k, double u, double v, double &X, double &Y) 
   const double d1 = C[3] * u + C[4] * v + C[5];
   const double d2 = C[6] * u + C[7] * v + C[8];
   X = g.cx + g.f * std::atan2(d0, d2);
-  Y = g.cy + g.f * (d1 / std::hypot(d0, d2));
+  Y = g.cy + g.f * (d1 / std::sqrt(d0 * d0 + d2 * d2));
 }
 
 bool covered64(const Geo &g, int k, double x, double y) {

@@ -107,7 +107,7 @@ def load(path, max_batch=256):
     return net, d["mu"], d["sd"]
 
 
-def evaluate_gain(net, config="2x640x360", seeds=(101, 102, 103, 104), n_frames=8):
+def evaluate_gain(net, config="2x640x360", seeds=(101, 102, 103, 104), n_frames=8, objects=6):
     """Learned against plain colour estimate on held-out synthetic rigs with a
     known photometric response per camera.
 
@@ -117,14 +117,15 @@ def evaluate_gain(net, config="2x640x360", seeds=(101, 102, 103, 104), n_frames=
     colour error (grey levels) of that map applied with the matrix instead.
     Reported per estimator: the mean error, the frame-to-frame standard
     deviation of M (mean over entries, frames after the window fills), and the
-    estimate's GPU time per frame; plus the learned path's fallback rate."""
+    estimate's GPU time per frame; plus the learned path's fallback rate.
+    ``objects`` moving objects make the frames (and so M) change over time."""
     from synth import Scene, render_camera_frames, rig_for_config
     from synth.scene import _photometric
     res = {k: dict(err=[], M=[]) for k in ("plain", "learned_raw", "learned_used", "truth")}
     t_plain, t_learned, n_l, n_f = 0.0, 0.0, 0, 0
     n_est = 0
     for seed in seeds:
-        rig, seq = rig_for_config(config, seed=seed)
+        rig, seq = rig_for_config(config, seed=seed, **({} if objects is None else {"objects": objects}))
         scene = Scene(rig.pano_w, rig.pano_h, n_objects=seq.get("objects", 0), seed=seed)
         base = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
                         max_flow=seq["max_flow"], flags=0)

@@ -107,6 +107,75 @@ def make_rig(cam_w, cam_h, overlap=(0.2, 0.2), rot_deg=3.0, perturb=0.0,
     return Rig(n, cam_w, cam_h, G, H, pw, ph, gain, gamma, offset, cast, seed)
 
 
+def _rx(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+
+
+def _ry(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def _rz(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def make_cyl_rig(cam_w, cam_h, f_cam, overlap=0.2, f_pano=None, pano_h=None, pitch_deg=1.0, roll_deg=1.0,
+                 yaw_jitter_deg=0.3, perturb_deg=0.0, cast_offdiag=0.0, photometric=True, seed=0) -> Rig:
+    """A rotating rig on a cylindrical panorama. Camera k (focal f_cam, pixel
+    centre in the image middle) looks at azimuth psi_k; successive azimuths
+    are (1 - overlap) of a camera's horizontal field of view apart, plus a
+    small jitter, with small random pitch and roll. G_k / H_k are the true /
+    coarse maps from camera pixel (u, v, 1) to a viewing ray, R_k^T K^-1; the
+    coarse one adds a random rotation of up to perturb_deg degrees. The
+    panorama (f_pano pixels per radian, default f_cam) spans the rig's
+    azimuth range; rig.extra holds projection = 1 and cyl = (f, cx, cy)."""
+    rng = np.random.RandomState(seed)
+    n = len(cam_w)
+    cam_w = [int(w) for w in cam_w]
+    cam_h = [int(h) for h in cam_h]
+    fov = 2.0 * math.atan((max(cam_w) / 2.0) / f_cam)
+    step = (1.0 - overlap) * fov
+    psi = np.array([(k - (n - 1) / 2.0) * step for k in range(n)])
+    psi += np.deg2rad(rng.uniform(-yaw_jitter_deg, yaw_jitter_deg, n))
+    pitch = np.deg2rad(rng.uniform(-pitch_deg, pitch_deg, n))
+    roll = np.deg2rad(rng.uniform(-roll_deg, roll_deg, n))
+    f = float(f_pano if f_pano is not None else f_cam)
+    lo = psi[0] - fov / 2.0
+    hi = psi[-1] + fov / 2.0
+    pw = int(math.ceil(f * (hi - lo)))
+    ph = int(pano_h) if pano_h is not None else max(cam_h)
+    cx = -f * lo
+    cy = (ph - 1) / 2.0
+    G = np.zeros((n, 3, 3))
+    H = np.zeros((n, 3, 3))
+    for k in range(n):
+        K = np.array([[f_cam, 0.0, (cam_w[k] - 1) / 2.0], [0.0, f_cam, (cam_h[k] - 1) / 2.0], [0.0, 0.0, 1.0]])
+        R = _rz(roll[k]) @ _rx(pitch[k]) @ _ry(psi[k]).T          # world -> camera
+        G[k] = R.T @ np.linalg.inv(K)
+        if perturb_deg > 0:
+            a, b, c = np.deg2rad(rng.uniform(-perturb_deg, perturb_deg, 3))
+            H[k] = (_rz(c) @ _rx(b) @ _ry(a) @ R).T @ np.linalg.inv(K)
+        else:
+            H[k] = G[k].copy()
+    if photometric:
+        gain = rng.uniform(0.8, 1.2, size=(n, 3))
+        gamma = rng.uniform(0.9, 1.1, size=(n, 3))
+        offset = rng.uniform(-8.0, 8.0, size=(n, 3))
+    else:
+        gain, gamma, offset = np.ones((n, 3)), np.ones((n, 3)), np.zeros((n, 3))
+    cast = np.tile(np.eye(3), (n, 1, 1))
+    if cast_offdiag > 0:
+        for k in range(n):
+            off = rng.uniform(-cast_offdiag, cast_offdiag, size=(3, 3))
+            np.fill_diagonal(off, 0.0)
+            cast[k] = np.eye(3) + off
+    return Rig(n, cam_w, cam_h, G, H, pw, ph, gain, gamma, offset, cast, seed,
+               extra=dict(projection=1, cyl=(f, cx, cy)))
+
+
 # The workloads, by what they are. Each entry gives the rig recipe plus the
 # per-sequence parameters (frames, temporal window, maximum flow, objects).
 CONFIGS = {
@@ -128,6 +197,12 @@ CONFIGS = {
                                    objects=0),
 }
 
+# Cylindrical rigs (rotating cameras on a cylindrical panorama).
+CONFIGS["8x3840x2160cyl"] = dict(cams=[(3840, 2160)] * 8, projection=1, f_cam=4117.0, overlap=0.2, perturb_deg=0.2,
+                                 frames=120, window=7, max_flow=16.0, objects=12)
+CONFIGS["4x640x360cyl"] = dict(cams=[(640, 360)] * 4, projection=1, f_cam=686.0, overlap=0.2, perturb_deg=0.0,
+                               frames=8, window=3, max_flow=3.0, objects=0)
+
 # The batched workload: four independent rigs of uneven geometry stitched together.
 BATCH_RIGS = ("6x1920x1080+2x1280x720", "3x1920x1080", "4x3840x2160", "2x1280x720")
 
@@ -138,6 +213,11 @@ def rig_for_config(name: str, seed: int = 0, **over) -> tuple[Rig, dict]:
     cfg.update(over)
     ws = [c[0] for c in cfg["cams"]]
     hs = [c[1] for c in cfg["cams"]]
+    if cfg.get("projection", 0) == 1:
+        rig = make_cyl_rig(ws, hs, cfg["f_cam"], overlap=cfg.get("overlap", 0.2), f_pano=cfg.get("f_pano"),
+                           pano_h=cfg.get("pano_h"), perturb_deg=cfg.get("perturb_deg", 0.0),
+                           cast_offdiag=cfg.get("cast_offdiag", 0.0), seed=seed)
+        return rig, cfg
     rig = make_rig(ws, hs, overlap=cfg["overlap"], rot_deg=cfg.get("rot_deg", 3.0),
                    perturb=cfg["perturb"], pano_w=cfg["pano_w"], pano_h=cfg["pano_h"],
                    cast_offdiag=cfg.get("cast_offdiag", 0.0), seed=seed)

@@ -116,9 +116,18 @@ def render_camera_frames(rig, scene: Scene, t: int = 0, device="cpu",
             r1 = min(h, r0 + rows_per_chunk)
             v = torch.arange(r0, r1, dtype=torch.float64, device=device)
             V, U = torch.meshgrid(v, u, indexing="ij")
-            den = G[2, 0] * U + G[2, 1] * V + G[2, 2]
-            X = ((G[0, 0] * U + G[0, 1] * V + G[0, 2]) / den).float()
-            Y = ((G[1, 0] * U + G[1, 1] * V + G[1, 2]) / den).float()
+            if rig.extra.get("projection", 0) == 1:
+                # cylindrical rig: the ray of each pixel, unrolled on the cylinder
+                f, cx, cy = rig.extra["cyl"]
+                d0 = G[0, 0] * U + G[0, 1] * V + G[0, 2]
+                d1 = G[1, 0] * U + G[1, 1] * V + G[1, 2]
+                d2 = G[2, 0] * U + G[2, 1] * V + G[2, 2]
+                X = (cx + f * torch.atan2(d0, d2)).float()
+                Y = (cy + f * d1 / torch.sqrt(d0 * d0 + d2 * d2)).float()
+            else:
+                den = G[2, 0] * U + G[2, 1] * V + G[2, 2]
+                X = ((G[0, 0] * U + G[0, 1] * V + G[0, 2]) / den).float()
+                Y = ((G[1, 0] * U + G[1, 1] * V + G[1, 2]) / den).float()
             rgb = scene.render(X, Y, t)
             if photometric:
                 img[r0:r1] = _photometric(rgb, rig.gain[k], rig.gamma[k], rig.offset[k], rig.cast[k])

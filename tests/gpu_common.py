@@ -41,11 +41,13 @@ class Pair:
         rig, seq = self.rig, self.seq
         self.seed = seed
         self.scene = Scene(rig.pano_w, rig.pano_h, n_objects=seq.get("objects", 0), seed=seed)
+        ex = rig.extra or {}
+        self.proj = dict(projection=ex.get("projection", 0), cyl=ex.get("cyl"))
         self.cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
-                            max_flow=seq["max_flow"], flags=flags)
+                            max_flow=seq["max_flow"], flags=flags, **self.proj)
         self.st = S.Stitcher(self.cfg)
         self.oracle = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
-                                     max_flow=seq["max_flow"], flags=flags)
+                                     max_flow=seq["max_flow"], flags=flags, **self.proj)
 
     def inputs(self, t):
         frames = render_camera_frames(self.rig, self.scene, t, device="cuda")

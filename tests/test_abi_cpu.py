@@ -48,6 +48,42 @@ def test_geometry_matches_oracle(name, seed):
     assert [tuple(map(tuple, r)) for r in rects.tolist()] == g.rects
 
 
+def _cfg_of(rig, **kw):
+    ex = rig.extra or {}
+    return S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, projection=ex.get("projection", 0),
+                    cyl=ex.get("cyl"), **kw)
+
+
+@pytest.mark.parametrize("name,seed", [("4x640x360cyl", 0), ("4x640x360cyl", 1), ("4x640x360cyl", 7),
+                                       ("8x3840x2160cyl", 0)])
+def test_cylindrical_geometry_matches_oracle(name, seed):
+    rig, _ = rig_for_config(name, seed=seed)
+    bands, rects = S.stitch_geometry(_cfg_of(rig))
+    g = Geometry(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, projection=1, cyl=rig.extra["cyl"])
+    assert [tuple(b) for b in bands.tolist()] == g.bands
+    assert [tuple(map(tuple, r)) for r in rects.tolist()] == g.rects
+    # bands lie inside both cameras' coverage and are not trivially small
+    for p, (x0, x1, y0, y1) in enumerate(g.bands):
+        assert x1 - x0 >= 16 and y1 - y0 >= rig.pano_h // 2
+        for cam in (p, p + 1):
+            xs = np.array([x0, x1 - 1, x0, x1 - 1], dtype=np.float64)
+            ys = np.array([y0, y0, y1 - 1, y1 - 1], dtype=np.float64)
+            sx, sy, sw = g.Hinv[cam].map(xs, ys)
+            assert np.all(sw > 0) and np.all((sx >= 0) & (sx <= rig.cam_w[cam] - 1))
+
+
+def test_cylindrical_config_checked():
+    rig, _ = rig_for_config("4x640x360cyl", seed=0)
+    with pytest.raises(S.StitchError) as ei:
+        S.stitch_geometry(_cfg_of(rig) if False else S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h,
+                                                               projection=1, cyl=(0.0, 0.0, 0.0)))
+    assert "cyl_focal" in str(ei.value)
+    with pytest.raises(S.StitchError) as ei:
+        S.stitch_geometry(S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, projection=2,
+                                   cyl=rig.extra["cyl"]))
+    assert "projection" in str(ei.value)
+
+
 def test_geometry_integer_translation():
     T = lambda tx, ty: np.array([[1.0, 0, tx], [0, 1.0, ty], [0, 0, 1.0]])
     cfg = S.Config([200, 200], [100, 100], np.stack([T(0, 0), T(120, 0)]), 320, 100)
