@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
     if (lane == 0) S->B_ring[ring][p][c * 3 + d] = s;
   }
   if (tid < np * 6) S->A_ring[ring][tid / 6][tid % 6] = raw->A[tid / 6][tid % 6];
-  if (tid >= 512 && tid < 512 + np) {
-    const int p = tid - 512;
+  if (tid >= kT / 2 && tid < kT / 2 + np) {
+    const int p = tid - kT / 2;
     S->n_ring[ring][p][0] = (int)sm.cdf[p * 6][255];
     S->n_ring[ring][p][1] = (int)sm.cdf[p * 6 + 3][255];
   }

@@ -130,6 +130,61 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_nt(const bf16 *__restrict
       }
 }
 
+// One layer for a small batch (at most 16 rows, e.g. the pairs of one rig at
+// inference): Y = act(X W^T + b). Block b owns output columns [8 b, 8 b + 8);
+// its four warps split K into four ranges and each runs one m16n8k16 tile
+// (rows >= batch read as zero) with fragments loaded straight from global
+// memory (X is a few KB and stays in L1; each k-step reads one 32-byte
+// sector of eight W rows). The four partial tiles are summed in a fixed order
+// in shared memory, so results do not depend on scheduling.
+constexpr int kSmallThreads = 128;
+
+__global__ void __launch_bounds__(kSmallThreads) k_layer_small(const bf16 *__restrict__ X, int ldx, int batch,
+                                                                 const bf16 *__restrict__ W, int N, int K,
+                                                                 const float *__restrict__ bias, int mode, float *Cf,
+                                                                 int ldc, bf16 *Yb, int ldy) {
+  __shared__ float part[4][16][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int n0 = blockIdx.x * 8;
+  const int ksteps = K / 16, per = (ksteps + 3) / 4;
+  const int k_lo = warp * per, k_hi = min(ksteps, k_lo + per);
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const bool r0 = g < batch, r1 = g + 8 < batch;
+  const bool nok = n0 + g < N;
+  const uint32_t *xa = reinterpret_cast<const uint32_t *>(X + (size_t)g * ldx);
+  const uint32_t *xb = reinterpret_cast<const uint32_t *>(X + (size_t)(g + 8) * ldx);
+  const uint32_t *wr = reinterpret_cast<const uint32_t *>(W + (size_t)(n0 + g) * K);
+#pragma unroll 4
+  for (int ks = k_lo; ks < k_hi; ++ks) {
+    const int c = (ks * 16) / 2 + t;            // 32-bit word of columns 2t, 2t+1 of this k-step
+    uint32_t a[4];
+    a[0] = r0 ? __ldg(xa + c) : 0u;
+    a[1] = r1 ? __ldg(xb + c) : 0u;
+    a[2] = r0 ? __ldg(xa + c + 4) : 0u;
+    a[3] = r1 ? __ldg(xb + c + 4) : 0u;
+    const uint32_t b0 = nok ? __ldg(wr + c) : 0u;
+    const uint32_t b1 = nok ? __ldg(wr + c + 4) : 0u;
+    mma_bf16(acc, a, b0, b1);
+  }
+  // accumulator layout of m16n8: (row g, cols 2t, 2t+1) and (row g+8, same cols)
+  part[warp][g][2 * t] = acc[0];
+  part[warp][g][2 * t + 1] = acc[1];
+  part[warp][g + 8][2 * t] = acc[2];
+  part[warp][g + 8][2 * t + 1] = acc[3];
+  __syncthreads();
+  const int m = threadIdx.x >> 3, n = threadIdx.x & 7;   // 128 threads = 16 rows x 8 columns
+  if (m < batch && n0 + n < N) {
+    float v = ((part[0][m][n] + part[1][m][n]) + part[2][m][n]) + part[3][m][n];
+    if (bias) v += bias[n0 + n];
+    if (mode == 0) {
+      Cf[(size_t)m * ldc + n0 + n] = v;
+    } else {
+      Yb[(size_t)m * ldy + n0 + n] = __float2bfloat16_rn(fmaxf(v, 0.0f));
+    }
+  }
+}
+
 // Transpose a [rows][cols] bfloat16 matrix into [cols][rows].
 __global__ void k_transpose_bf16(const bf16 *__restrict__ in, int rows, int cols, bf16 *__restrict__ out) {
   __shared__ bf16 tile[32][33];
@@ -230,6 +285,13 @@ cudaError_t launch_gemm_nt(const bf16 *A, int lda, const bf16 *B, int ldb, int M
                            int mode, float *Cf, int ldc, bf16 *Yb, int ldy, bf16 *Yt, int ldt, cudaStream_t s) {
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
   k_gemm_nt<<<grid, kGemmThreads, 0, s>>>(A, lda, B, ldb, M, N, K, bias, mode, Cf, ldc, Yb, ldy, Yt, ldt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_small(const bf16 *X, int ldx, int batch, const bf16 *W, int N, int K, const float *bias,
+                               int mode, float *Cf, int ldc, bf16 *Yb, int ldy, cudaStream_t s) {
+  if (batch < 1 || batch > 16 || K % 16 != 0) return cudaErrorInvalidValue;
+  k_layer_small<<<(N + 7) / 8, kSmallThreads, 0, s>>>(X, ldx, batch, W, N, K, bias, mode, Cf, ldc, Yb, ldy);
   return cudaGetLastError();
 }
 

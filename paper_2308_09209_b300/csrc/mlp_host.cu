@@ -19,6 +19,8 @@ namespace stitch {
 cudaError_t launch_gemm_nt(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias,
                            int mode, float *Cf, int ldc, bf16 *Yb, int ldy, bf16 *Yt, int ldt, cudaStream_t s);
 cudaError_t launch_transpose_bf16(const bf16 *in, int rows, int cols, bf16 *out, cudaStream_t s);
+cudaError_t launch_layer_small(const bf16 *X, int ldx, int batch, const bf16 *W, int N, int K, const float *bias,
+                               int mode, float *Cf, int ldc, bf16 *Yb, int ldy, cudaStream_t s);
 cudaError_t launch_mse(const float *y, int ldy, const float *t, int batch, int n_out, const float *mu, const float *sd,
                        bf16 *dz, bf16 *dzt, float *loss, cudaStream_t s);
 cudaError_t launch_relu_bwd(const float *dx, const bf16 *y, int batch, int n, bf16 *dz, bf16 *dzt, cudaStream_t s);
@@ -105,6 +107,18 @@ cudaError_t forward(stitch_mlp *n, const bf16 *x, int batch, bool keep_xt, cudaS
   cudaError_t e = cudaSuccess;
   if (keep_xt) e = launch_transpose_bf16(x, batch, kIn[0], n->xt, s);
   const bf16 *in = x;
+  if (!keep_xt && batch <= 16) {
+    // Inference on a few rows: the small-batch layer kernel (K split over warps).
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+      const float *bias = n->p + n->off[l] + (size_t)kOut[l] * kIn[l];
+      if (l < kLayers - 1)
+        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 1, nullptr, 0, n->y[l], kOut[l], s);
+      else
+        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 0, n->yf, kOut[l], nullptr, 0, s);
+      in = n->y[l];
+    }
+    return e;
+  }
   for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
     const float *bias = n->p + n->off[l] + (size_t)kOut[l] * kIn[l];
     if (l < kLayers - 1)

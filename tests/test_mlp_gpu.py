@@ -76,7 +76,7 @@ def test_forward_matches_oracle():
     mu = rng.normal(0, 0.1, N_OUT).astype(np.float32)
     sd = rng.uniform(0.05, 0.5, N_OUT).astype(np.float32)
     S.stitch_mlp_set_norm(net.h, mu, sd)
-    for batch in (1, 37, 256):
+    for batch in (1, 7, 16, 17, 37, 256):   # <= 16 rows take the small-batch kernel
         X = _features(rng, batch)
         x = _bf16_bits(X).cuda()
         y = torch.empty((batch, N_OUT), dtype=torch.float32, device="cuda")

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from gpu_common import (Pair, assert_pano_ok, compare_pano, compare_stats, ensure_built, flows_for, rel_err,
-                        M_REL_TOL)
+                        M_REL_TOL, MAX_ABS, FRAC_WITHIN_1)
 from oracle.pipeline import OracleStitcher
 from paper_2308_09209_b300 import stitch as S
 from synth import Scene, make_rig, render_camera_frames
@@ -81,6 +81,36 @@ def test_full_size_4x1080p_stats_and_sampled_pixels():
         g = out["pano"].cpu().numpy()[:, ys, xs].T.astype(np.int16)
         d = np.abs(g - vals.astype(np.int16)).max(1)[~near]
         assert d.max() <= 2 and (d <= 1).mean() >= 0.9999, (d.max(), (d <= 1).mean())
+
+
+def test_full_size_4x1080p_graph_sequence_as_benchmarked():
+    """The benchmark's launch form: a recorded multi-stream sequence of frames
+    of the 4 x 1080p workload (window 5, flow 8 px, moving objects); every
+    frame's panorama against the oracle on sampled pixels, and the colour
+    state after the sequence."""
+    pr = Pair("4x1920x1080", seed=3)
+    n = 6
+    ins = [pr.inputs(t) for t in range(n)]
+    panos = [pr.st.new_pano() for _ in range(n)]
+    S.stitch_sequence(pr.st.ctx, n, [f for fr, _, _ in ins for f in fr], [f for _, a, _ in ins for f in a],
+                      [f for _, _, b in ins for f in b], panos)
+    torch.cuda.synchronize()
+    rng = np.random.RandomState(1)
+    W, H = pr.rig.pano_w, pr.rig.pano_h
+    for t, (fr, a, b) in enumerate(ins):
+        fr_np = [f.cpu().numpy() for f in fr]
+        pr.oracle.estimate_color(fr_np)
+        xs = rng.randint(0, W, 20000)
+        ys = rng.randint(0, H, 20000)
+        for (x0, x1, y0, y1) in pr.st.bands.tolist():
+            xs = np.concatenate([xs, np.arange(x0, x1)])
+            ys = np.concatenate([ys, np.full(x1 - x0, (y0 + y1) // 2)])
+        vals, near = pr.oracle.pixels(fr_np, [f.cpu().numpy() for f in a], [f.cpu().numpy() for f in b], xs, ys)
+        g = panos[t].cpu().numpy()[:, ys, xs].T.astype(np.int16)
+        d = np.abs(g - vals.astype(np.int16)).max(1)[~near]
+        assert d.max() <= MAX_ABS and (d <= 1).mean() >= FRAC_WITHIN_1, (t, d.max(), (d <= 1).mean())
+    _check_color(pr)
+    pr.st.close()
 
 
 def _T(tx, ty):
