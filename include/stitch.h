@@ -295,6 +295,21 @@ typedef struct stitch_mlp stitch_mlp;
 
 int stitch_mlp_n_params(void);
 
+/* GEMM engines of the network's batched layers (training, and inference on
+ * more than 16 rows; up to 16 rows use a small-batch mma.sync kernel):
+ * tcgen05 (5th-generation tensor cores, accumulators in tensor memory; the
+ * default) or mma.sync (warp-level tensor-core instructions). Both compute
+ * in bfloat16 with float32 accumulation. */
+#define STITCH_MLP_GEMM_MMA_SYNC 0
+#define STITCH_MLP_GEMM_TCGEN05 1
+int stitch_mlp_set_gemm(stitch_mlp *mlp, int engine);
+
+/* Synchronise and report the network's device error word: STITCH_ETIMEOUT
+ * if a bounded tensor-core wait ran out since the last report (the affected
+ * outputs are not valid), else STITCH_OK. stitch_mlp_gradients and
+ * stitch_mlp_get_params report it too. */
+int stitch_mlp_status(stitch_mlp *mlp);
+
 /* Create a network with He-normal weights drawn from `seed` (a host
  * Mersenne-Twister stream) and buffers for batches up to max_batch (a
  * multiple of 32, at most 65536). Allocates device memory; synchronises. */

@@ -31,6 +31,10 @@ cudaError_t launch_to_bf16(const float *w, int n_out, int n_in, bf16 *wb, bf16 *
 cudaError_t launch_denorm(const float *y, int ldy, int batch, int n_out, const float *mu, const float *sd, float *out,
                           cudaStream_t s);
 cudaError_t launch_pair_label(const PairParams &p, cudaStream_t s);
+cudaError_t gemm_tc_setup();
+cudaError_t launch_gemm_tc(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias,
+                           int mode, float *Cf, int ldc, bf16 *Yb, int ldy, bf16 *Yt, int ldt, int *err,
+                           cudaStream_t s);
 void record_last_error(const std::string &msg);
 }  // namespace stitch
 
@@ -71,6 +75,8 @@ struct stitch_mlp {
   bf16 *dz[kLayers] = {}, *dzt[kLayers] = {};
   float *norm = nullptr;                                         // mu[16], sd[16]
   float *loss = nullptr;
+  int *err = nullptr;                                            // device error word (tensor-core waits)
+  int gemm = STITCH_MLP_GEMM_TCGEN05;                            // GEMM engine of the large-batch layers
 };
 
 namespace {
@@ -85,6 +91,7 @@ void free_mlp(stitch_mlp *n) {
   cudaFree(n->dx);
   cudaFree(n->norm);
   cudaFree(n->loss);
+  cudaFree(n->err);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(n->wb[l]);
     cudaFree(n->wt[l]);
@@ -93,6 +100,14 @@ void free_mlp(stitch_mlp *n) {
     cudaFree(n->dz[l]);
     cudaFree(n->dzt[l]);
   }
+}
+
+// C = A B^T with the network's GEMM engine (tcgen05 or mma.sync); same modes.
+cudaError_t gemm(stitch_mlp *n, const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias,
+                 int mode, float *Cf, int ldc, bf16 *Yb, int ldy, bf16 *Yt, int ldt, cudaStream_t s) {
+  if (n->gemm == STITCH_MLP_GEMM_TCGEN05)
+    return launch_gemm_tc(A, lda, B, ldb, M, N, K, bias, mode, Cf, ldc, Yb, ldy, Yt, ldt, n->err, s);
+  return launch_gemm_nt(A, lda, B, ldb, M, N, K, bias, mode, Cf, ldc, Yb, ldy, Yt, ldt, s);
 }
 
 cudaError_t refresh_bf16(stitch_mlp *n, cudaStream_t s) {
@@ -122,11 +137,11 @@ cudaError_t forward(stitch_mlp *n, const bf16 *x, int batch, bool keep_xt, cudaS
   for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
     const float *bias = n->p + n->off[l] + (size_t)kOut[l] * kIn[l];
     if (l < kLayers - 1)
-      e = launch_gemm_nt(in, kIn[l], n->wb[l], kIn[l], batch, kOut[l], kIn[l], bias, 1, nullptr, 0, n->y[l], kOut[l],
-                         keep_xt ? n->yt[l] : nullptr, batch, s);
+      e = gemm(n, in, kIn[l], n->wb[l], kIn[l], batch, kOut[l], kIn[l], bias, 1, nullptr, 0, n->y[l], kOut[l],
+               keep_xt ? n->yt[l] : nullptr, batch, s);
     else
-      e = launch_gemm_nt(in, kIn[l], n->wb[l], kIn[l], batch, kOut[l], kIn[l], bias, 0, n->yf, kOut[l], nullptr, 0,
-                         nullptr, 0, s);
+      e = gemm(n, in, kIn[l], n->wb[l], kIn[l], batch, kOut[l], kIn[l], bias, 0, n->yf, kOut[l], nullptr, 0, nullptr, 0,
+               s);
     in = n->y[l];
   }
   return e;
@@ -140,13 +155,12 @@ cudaError_t backward(stitch_mlp *n, const bf16 *x, int batch, cudaStream_t s) {
     float *gb = gW + (size_t)kOut[l] * kIn[l];
     const bf16 *inT = l == 0 ? n->xt : n->yt[l - 1];
     // dW[out][in] = sum_b dZ^T[out][b] X^T[in][b]
-    e = launch_gemm_nt(n->dzt[l], batch, inT, batch, kOut[l], kIn[l], batch, nullptr, 0, gW, kIn[l], nullptr, 0,
-                       nullptr, 0, s);
+    e = gemm(n, n->dzt[l], batch, inT, batch, kOut[l], kIn[l], batch, nullptr, 0, gW, kIn[l], nullptr, 0, nullptr, 0, s);
     if (e == cudaSuccess) e = launch_bias_grad(n->dzt[l], batch, kOut[l], gb, s);
     if (e == cudaSuccess && l > 0) {
       // dX[b][in] = sum_o dZ[b][o] W^T[in][o]
-      e = launch_gemm_nt(n->dz[l], kOut[l], n->wt[l], kOut[l], batch, kIn[l], kOut[l], nullptr, 0, n->dx, kIn[l],
-                         nullptr, 0, nullptr, 0, s);
+      e = gemm(n, n->dz[l], kOut[l], n->wt[l], kOut[l], batch, kIn[l], kOut[l], nullptr, 0, n->dx, kIn[l], nullptr, 0,
+               nullptr, 0, s);
       if (e == cudaSuccess) e = launch_relu_bwd(n->dx, n->y[l - 1], batch, kIn[l], n->dz[l - 1], n->dzt[l - 1], s);
     }
   }
@@ -156,9 +170,35 @@ cudaError_t backward(stitch_mlp *n, const bf16 *x, int batch, cudaStream_t s) {
 
 }  // namespace
 
+// Device error word of the network's tensor-core kernels (read and cleared).
+static int take_err(stitch_mlp *n) {
+  int h = 0;
+  if (cudaMemcpy(&h, n->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return STITCH_ECUDA;
+  if (h) {
+    cudaMemset(n->err, 0, 4);
+    record_last_error("a tensor-core wait timed out");
+    return STITCH_ETIMEOUT;
+  }
+  return STITCH_OK;
+}
+
 extern "C" {
 
 int stitch_mlp_n_params(void) { return (int)total_params(); }
+
+int stitch_mlp_set_gemm(stitch_mlp *n, int engine) {
+  if (!n || (engine != STITCH_MLP_GEMM_MMA_SYNC && engine != STITCH_MLP_GEMM_TCGEN05))
+    return fail(STITCH_EINVAL, "mlp is NULL or unknown GEMM engine");
+  n->gemm = engine;
+  return STITCH_OK;
+}
+
+int stitch_mlp_status(stitch_mlp *n) {
+  if (!n) return fail(STITCH_EINVAL, "mlp is NULL");
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(STITCH_ECUDA, cudaGetErrorString(e));
+  return take_err(n);
+}
 
 int stitch_mlp_create(int max_batch, unsigned long long seed, stitch_mlp **out) {
   if (!out) return fail(STITCH_EINVAL, "out is NULL");
@@ -188,6 +228,8 @@ int stitch_mlp_create(int max_batch, unsigned long long seed, stitch_mlp **out) 
   alloc((void **)&n->dx, (size_t)max_batch * 512 * 4);
   alloc((void **)&n->norm, 32 * 4);
   alloc((void **)&n->loss, 4);
+  alloc((void **)&n->err, 4);
+  if (e == cudaSuccess) e = gemm_tc_setup();
   for (int l = 0; l < kLayers; ++l) {
     alloc((void **)&n->wb[l], (size_t)kOut[l] * kIn[l] * 2);
     alloc((void **)&n->wt[l], (size_t)kOut[l] * kIn[l] * 2);
@@ -245,7 +287,8 @@ int stitch_mlp_get_params(stitch_mlp *n, float *host) {
   if (!n || !host) return fail(STITCH_EINVAL, "mlp and host buffer are required");
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(host, n->p, total_params() * 4, cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? STITCH_OK : fail(STITCH_ECUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(STITCH_ECUDA, cudaGetErrorString(e));
+  return take_err(n);
 }
 
 int stitch_mlp_set_params(stitch_mlp *n, const float *host) {
@@ -303,7 +346,8 @@ int stitch_mlp_gradients(stitch_mlp *n, const uint16_t *x_dev, const float *t_de
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(grads_host, n->g, total_params() * 4, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && loss_host) e = cudaMemcpy(loss_host, n->loss, 4, cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? STITCH_OK : fail(STITCH_ECUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(STITCH_ECUDA, cudaGetErrorString(e));
+  return take_err(n);
 }
 
 int stitch_pairs_label(const uint8_t *pairs_dev, int n_pairs, int patch_w, int patch_h, double lambda,

@@ -100,6 +100,8 @@ def lib():
             "stitch_mlp_n_params": (ip, []),
             "stitch_mlp_create": (ip, [ip, ctypes.c_ulonglong, ctypes.POINTER(vp)]),
             "stitch_mlp_destroy": (None, [vp]),
+            "stitch_mlp_set_gemm": (ip, [vp, ip]),
+            "stitch_mlp_status": (ip, [vp]),
             "stitch_mlp_set_norm": (ip, [vp, vp, vp]),
             "stitch_mlp_get_params": (ip, [vp, vp]),
             "stitch_mlp_set_params": (ip, [vp, vp]),
@@ -362,6 +364,18 @@ def stitch_mlp_create(max_batch: int, seed: int):
 def stitch_mlp_destroy(mlp) -> None:
     if mlp is not None and mlp.value:
         lib().stitch_mlp_destroy(mlp)
+
+
+STITCH_MLP_GEMM_MMA_SYNC = 0
+STITCH_MLP_GEMM_TCGEN05 = 1
+
+
+def stitch_mlp_set_gemm(mlp, engine: int) -> int:
+    return _check(lib().stitch_mlp_set_gemm(mlp, engine))
+
+
+def stitch_mlp_status(mlp) -> int:
+    return _check(lib().stitch_mlp_status(mlp))
 
 
 def stitch_mlp_set_norm(mlp, mu, sd) -> int:

@@ -140,6 +140,35 @@ def test_gradients_match_oracle_backward():
     net.close()
 
 
+def test_gemm_engines_agree():
+    """The tcgen05 GEMM (default) and the mma.sync GEMM give the same layer
+    outputs and gradients up to float32 accumulation order."""
+    ensure_built()
+    rng = np.random.default_rng(23)
+    net, params = _random_net(7)
+    S.stitch_mlp_set_norm(net.h, np.zeros(N_OUT, np.float32), np.full(N_OUT, 0.2, np.float32))
+    batch = 96
+    X = _features(rng, batch)
+    x = _bf16_bits(X).cuda()
+    t = torch.from_numpy(rng.normal(0, 0.2, (batch, N_OUT)).astype(np.float32)).cuda()
+    out = {}
+    for eng in (S.STITCH_MLP_GEMM_TCGEN05, S.STITCH_MLP_GEMM_MMA_SYNC):
+        S.stitch_mlp_set_gemm(net.h, eng)
+        y = torch.empty((batch, N_OUT), dtype=torch.float32, device="cuda")
+        S.stitch_mlp_forward(net.h, x, batch, y)
+        g, loss = S.stitch_mlp_gradients(net.h, x, t, batch)
+        S.stitch_mlp_status(net.h)
+        out[eng] = (y.cpu().numpy(), g.astype(np.float64), loss)
+    ya, ga, la = out[S.STITCH_MLP_GEMM_TCGEN05]
+    yb, gb, lb = out[S.STITCH_MLP_GEMM_MMA_SYNC]
+    assert np.linalg.norm(ya - yb) <= 2e-3 * np.linalg.norm(yb)
+    assert abs(la - lb) <= 1e-4 * lb
+    for li, (ws, bs) in enumerate(_layer_slices()):
+        err = np.linalg.norm(ga[ws] - gb[ws]) / np.linalg.norm(gb[ws])
+        assert err < 1e-2, (li, err)
+    net.close()
+
+
 def test_training_reduces_loss():
     ensure_built()
     from paper_2308_09209_b300 import learned
