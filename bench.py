@@ -361,7 +361,12 @@ def run_extras(args, dev, stream, ctxs):
     train_s = time.perf_counter() - t0
     del pairs
     gain = learned.evaluate_gain(net, seeds=(201, 202), n_frames=8, objects=6)
-    out["learned"] = {"train_pairs": 65536, "epochs": 20, "final_loss": hist[-1], "train_s": train_s, **gain}
+    # training arithmetic: forward + two backward GEMMs per layer, 2 flops per multiply-add
+    macs = 1536 * 512 + 512 * 512 + 512 * 256 + 256 * 16
+    steps_pairs = (int((flags == 0).sum()) // 512) * 512 * 20
+    out["learned"] = {"train_pairs": 65536, "epochs": 20, "final_loss": hist[-1], "train_s": train_s,
+                      "gemm_engine": "tcgen05", "train_tflops_incl_data": 3 * 2 * macs * steps_pairs / train_s / 1e12,
+                      **gain}
 
     # cylindrical large rig: full form vs plain form on the same frames
     F = 4

@@ -2,14 +2,17 @@
 // C[m][n] = sum_k A[m][k] B[n][k] (both operands K-contiguous bfloat16),
 // float32 accumulation in tensor memory.
 //
-// One CTA (128 threads) owns a 128 x 64 tile of C. K advances 64 at a time
-// through two shared-memory stages: all threads copy a stage (A: 128 x 64,
-// B: 64 x 64) from global memory into the canonical K-major layout without
-// swizzle (8-row x 16-byte core matrices; core matrices adjacent along K
-// are 128 bytes apart, 8-row groups 1024 bytes apart), one thread issues
-// four tcgen05.mma (M = 128, N = 64, K = 16 each) into the tile's 64
-// tensor-memory columns and commits them to the stage's mbarrier, and the
-// copy of the next stage overlaps the MMAs. The epilogue reads the
+// One CTA (128 threads) owns a 128 x 32 tile of C. K advances 64 at a time
+// through a ring of kStages shared-memory stages: all threads copy a stage
+// (A: 128 x 64, B: 32 x 64) from global memory with cp.async into the
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices;
+// core matrices adjacent along K are 128 bytes apart, 8-row groups 1024 bytes
+// apart), one thread issues four tcgen05.mma (M = 128, N = 32, K = 16 each)
+// into the tile's 32 tensor-memory columns and commits them to the stage's
+// mbarrier. Copies run kAhead tiles ahead of the MMAs, and a stage is only
+// refilled once the MMAs that read it (kStages - kAhead tiles earlier) are
+// done, so neither the copy latency nor the MMA latency is waited on in
+// step. The epilogue reads the
 // accumulators with tcgen05.ld (warp w owns rows 32w..32w+31) and applies
 // the same modes as k_gemm_nt: float32 out (+bias), or ReLU(acc + bias) to
 // bfloat16 (and optionally its transpose).
@@ -26,15 +29,17 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int BM = 128, BN = 32, BK = 64;
 constexpr int kThreads = 128;
 constexpr int kTileA = BM * BK * 2;            // 16 KB
-constexpr int kTileB = BN * BK * 2;            // 8 KB
-constexpr int kStage = kTileA + kTileB;        // 24 KB
-constexpr uint32_t kTmemCols = 64;             // BN float32 accumulators per row
+constexpr int kTileB = BN * BK * 2;            // 4 KB
+constexpr int kStage = kTileA + kTileB;        // 20 KB
+constexpr uint32_t kTmemCols = 32;             // BN float32 accumulators per row
 constexpr uint32_t kLBO = 128, kSBO = 1024;    // core-matrix strides (bytes): along K, along M / N
 constexpr int kWaitLimit = 1 << 22;
-constexpr size_t kSmemBytes = 2 * kStage + 64 + 1024;   // stages, barriers, alignment slack
+constexpr int kStages = 4;
+constexpr int kAhead = 2;   // tiles copied ahead of the MMAs; a stage is refilled kStages - kAhead tiles after its MMAs
+constexpr size_t kSmemBytes = kStages * kStage + 64 + 1024;   // stages, barriers, alignment slack
 
 // Instruction descriptor, kind::f16: float32 accumulate (bits 4-5 = 1), A and
 // B bfloat16 (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bit 17,
@@ -68,9 +73,13 @@ __device__ __forceinline__ uint32_t chunk_off(int row, int j) {
   return (uint32_t)((row >> 3) * kSBO + j * kLBO + (row & 7) * 16);
 }
 
-__device__ __forceinline__ uint4 load_chunk(const bf16 *__restrict__ g, int ld, int row, int rows, int k, int K) {
-  if (row < rows && k < K) return __ldg(reinterpret_cast<const uint4 *>(g + (size_t)row * ld + k));
-  return make_uint4(0u, 0u, 0u, 0u);
+// Asynchronous 16-byte copy global -> shared; a chunk outside the matrix is
+// zero-filled (source size 0, the source address then only needs to be valid).
+__device__ __forceinline__ void copy_chunk(uint32_t dst, const bf16 *__restrict__ g, int ld, int row, int rows, int k,
+                                           int K) {
+  const bool in = row < rows && k < K;
+  const bf16 *src = in ? g + (size_t)row * ld + k : g;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
 }
 
 }  // namespace
@@ -81,8 +90,8 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
                                                       int *err) {
   extern __shared__ uint8_t dsm[];
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * kStage);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(base + kStages * kStage);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + kStages);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nk = (K + BK - 1) / BK;
@@ -93,8 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar[0])), "r"(1u));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar[1])), "r"(1u));
+    for (int i = 0; i < kStages; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bar[i])), "r"(1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -102,55 +110,42 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  // Register copy of one stage: A 8 chunks, B 4 chunks per thread.
-  uint4 ra[8], rb[4];
+  // Copy tile kt into its stage: A 8 chunks, B 2 chunks per thread.
   auto fetch = [&](int kt) {
+    const uint32_t sa = su32(base + (kt % kStages) * kStage), sb = sa + kTileA;
     const int k0 = kt * BK;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int c = tid + i * kThreads, row = c >> 3, j = c & 7;
-      ra[i] = load_chunk(A, lda, m0 + row, M, k0 + 8 * j, K);
+      copy_chunk(sa + chunk_off(row, j), A, lda, m0 + row, M, k0 + 8 * j, K);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < BN * 8 / kThreads; ++i) {
       const int c = tid + i * kThreads, row = c >> 3, j = c & 7;
-      rb[i] = load_chunk(B, ldb, n0 + row, N, k0 + 8 * j, K);
+      copy_chunk(sb + chunk_off(row, j), B, ldb, n0 + row, N, k0 + 8 * j, K);
     }
   };
-  fetch(0);
+  for (int t = 0; t < kAhead; ++t) {
+    if (t < nk) fetch(t);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   bool bad = false;
   int last = -1;   // the last tile whose MMAs were committed
   for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt & 1;
-    uint8_t *sa = base + s * kStage, *sb = sa + kTileA;
-    if (kt >= 2) {
-      // the MMAs of tile kt - 2 read this stage: wait for their commit
-      const bool ok = mbar_wait(su32(&bar[s]), (uint32_t)(((kt - 2) >> 1) & 1));
-      if (__syncthreads_or(!ok)) {
-        bad = true;
-        break;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int c = tid + i * kThreads;
-      *reinterpret_cast<uint4 *>(sa + chunk_off(c >> 3, c & 7)) = ra[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = tid + i * kThreads;
-      *reinterpret_cast<uint4 *>(sb + chunk_off(c >> 3, c & 7)) = rb[i];
-    }
-    // make the generic-proxy stores visible to the tensor core (async proxy)
+    const int s = kt % kStages;
+    // this thread's copies of tile kt are done (kAhead - 1 younger groups may still fly)
+    asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 1) : "memory");
+    // make the copies visible to the tensor core (async proxy), then to the issuing thread
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = su32(base + s * kStage), sb = sa + kTileA;
 #pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks) {
-        const uint64_t ad = smem_desc(su32(sa) + (uint32_t)ks * 2 * kLBO);
-        const uint64_t bd = smem_desc(su32(sb) + (uint32_t)ks * 2 * kLBO);
-        const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+      for (int q = 0; q < BK / 16; ++q) {
+        const uint64_t ad = smem_desc(sa + (uint32_t)q * 2 * kLBO);
+        const uint64_t bd = smem_desc(sb + (uint32_t)q * 2 * kLBO);
+        const uint32_t acc = (kt > 0 || q > 0) ? 1u : 0u;
         asm volatile(
             "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
             "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
@@ -159,13 +154,27 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
                    : "memory");
     }
     last = kt;
-    if (kt + 1 < nk) fetch(kt + 1);
+    // copy tile kt + kAhead into the stage that tile kt + kAhead - kStages read, once its MMAs are done
+    const int nt = kt + kAhead;
+    if (nt < nk) {
+      if (nt >= kStages) {
+        const int pt = nt - kStages;
+        const bool ok = mbar_wait(su32(&bar[pt % kStages]), (uint32_t)((pt / kStages) & 1));
+        if (__syncthreads_or(!ok)) {
+          bad = true;
+          break;
+        }
+      }
+      fetch(nt);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 
   // The last commit covers every MMA issued before it (after a timeout this
   // is the drain of the MMAs still in flight).
   if (last >= 0) {
-    const bool done = mbar_wait(su32(&bar[last & 1]), (uint32_t)((last >> 1) & 1));
+    const bool done = mbar_wait(su32(&bar[last % kStages]), (uint32_t)((last / kStages) & 1));
     if (__syncthreads_or(!done)) bad = true;
   }
   if (bad) {
