@@ -210,14 +210,14 @@ def traffic_from_profile(workload):
 # --------------------------------------------------------------------------- #
 # CPU baseline / reference arm: the FP64 oracle, as it stands
 # --------------------------------------------------------------------------- #
-def oracle_frames(wl, frame_ids, keep=False):
+def oracle_frames(wl, frame_ids, keep=False, flags=0):
     """Run the oracle on the given frames; returns (seconds, output pixels,
     [(planes, near-edge mask)] when keep)."""
     from oracle.pipeline import OracleStitcher
     rig, seq = wl["rig"], wl["seq"]
     ex = rig.extra or {}
     o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
-                       max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"))
+                       max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"), flags=flags)
     host = [([f.cpu().numpy() for f in wl["frames"][t]], [f.cpu().numpy() for f in wl["fij"][t]],
              [f.cpu().numpy() for f in wl["fji"][t]]) for t in frame_ids]
     outs = []
@@ -229,6 +229,31 @@ def oracle_frames(wl, frame_ids, keep=False):
             outs.append((planes, near))
     dt = time.perf_counter() - t0
     return dt, len(frame_ids) * wl["pano_px"], outs
+
+
+def oracle_check_rigs(items, n_samples=40000):
+    """Frame 0 of each batched rig against the oracle on sampled pixels (half
+    of them in the blend bands)."""
+    import numpy as np
+    from oracle.pipeline import OracleStitcher
+    res = []
+    rng = np.random.default_rng(0)
+    for it in items:
+        rig, seq = it["rig"], it["seq"]
+        o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
+                           max_flow=seq["max_flow"], flags=it["flags"])
+        o.estimate_color(it["frames"])
+        xs = rng.integers(0, rig.pano_w, n_samples)
+        ys = rng.integers(0, rig.pano_h, n_samples)
+        for i in range(n_samples // 2):
+            x0, x1, y0, y1 = o.geom.bands[i % len(o.geom.bands)]
+            xs[i], ys[i] = rng.integers(x0, x1), rng.integers(y0, y1)
+        vals, near = o.pixels(it["frames"], it["fij"], it["fji"], xs, ys)
+        d = np.abs(it["pano"][:, ys, xs].T.astype(np.int16) - vals.astype(np.int16)).max(1)[~near]
+        res.append({"rig": "x".join(map(str, (len(rig.cam_w), rig.pano_w, rig.pano_h))), "max_abs": int(d.max()),
+                    "frac_within_1": float((d <= 1).mean()), "frac_exact": float((d == 0).mean()),
+                    "samples": int(d.size)})
+    return res
 
 
 def oracle_error(gpu_panos, oracle_outs, pano_w):
@@ -343,6 +368,20 @@ def run_extras(args, dev, stream, ctxs):
 
     ms_p = _time(seq_all, stream, 5)
     px = F * sum(w["pano_px"] for w in wls)
+    # frame 0 of every rig through a fresh batch, for the oracle check of the CPU-baseline leg
+    fresh = [S.Stitcher(w["cfg"]) for w in wls]
+    ctxs.extend(fresh)
+    bf0 = S.stitch_batch_create([st.ctx for st in fresh])
+    p0 = [torch.empty((3, w["cfg"].pano_h, w["cfg"].pitch), dtype=torch.uint8, device=dev) for w in wls]
+    S.stitch_batch_sequence(bf0, 1, fr[:sum(len(w["frames"][0]) for w in wls)], fij[:sum(len(w["fij"][0]) for w in wls)],
+                            fji[:sum(len(w["fji"][0]) for w in wls)], p0, stream)
+    stream.synchronize()
+    S.stitch_batch_destroy(bf0)
+    out["_batched_check"] = [dict(rig=w["rig"], seq=w["seq"], flags=w["cfg"].flags,
+                                  frames=[f.cpu().numpy() for f in w["frames"][0]],
+                                  fij=[f.cpu().numpy() for f in w["fij"][0]],
+                                  fji=[f.cpu().numpy() for f in w["fji"][0]], pano=p.cpu().numpy())
+                             for w, p in zip(wls, p0)]
     out["batched"] = {"rigs": list(BATCH_RIGS), "frames_per_step": F, "intermediate": "fp16",
                       "tile_shape": S.TILE_SHAPES[shape], "autotune_ms": [round(float(m), 4) for m in ms_shapes],
                       "batched_mpix_s": px / (ms_b / 1e3) / 1e6, "one_rig_at_a_time_mpix_s": px / (ms_p / 1e3) / 1e6,
@@ -508,6 +547,11 @@ def _run_ours(args, dist, ctxs):
     h2d = n_e2e * (wl["in_bytes"] + wl["flow_bytes"])
     d2h = n_e2e * 3 * cfg.pitch * cfg.pano_h
 
+    extras = {}
+    if dist.rank == 0 and dist.world == 1 and not args.no_extras:
+        del panos, h_frames, h_fij, h_fji, h_out
+        extras = run_extras(args, dev, stream, ctxs)
+
     cpu_baseline = None
     err = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -524,11 +568,21 @@ def _run_ours(args, dist, ctxs):
             g.append(st3.frame(wl["frames"][t], wl["fij"][t], wl["fji"][t]))
         torch.cuda.synchronize()
         err = oracle_error(g, outs, cfg.pano_w)
+        # the same frames with FP16 band intermediates, against the oracle in that mode
+        cfg16 = S.Config(cfg.cam_w, cfg.cam_h, cfg.H, cfg.pano_w, cfg.pano_h, window=cfg.window,
+                         max_flow=cfg.max_flow, flags=S.STITCH_FP16_INTERMEDIATE)
+        st4 = S.Stitcher(cfg16)
+        ctxs.append(st4)
+        g16 = []
+        for t in (0, 1):
+            st4.estimate_color(wl["frames"][t])
+            g16.append(st4.frame(wl["frames"][t], wl["fij"][t], wl["fji"][t]))
+        torch.cuda.synchronize()
+        _, _, outs16 = oracle_frames(wl, [0, 1], keep=True, flags=S.STITCH_FP16_INTERMEDIATE)
+        err = {"fp32_intermediates": err, "fp16_intermediates": oracle_error(g16, outs16, cfg.pano_w)}
+        if "_batched_check" in extras:
+            err["batched_rigs_frame0"] = oracle_check_rigs(extras["_batched_check"])
 
-    extras = {}
-    if dist.rank == 0 and dist.world == 1 and not args.no_extras:
-        del panos, h_frames, h_fij, h_fji, h_out
-        extras = run_extras(args, dev, stream, ctxs)
 
     launches = args.steps * F * 4     # stats, estimate, band pre-warp, fuse per frame
     if dist.rank == 0:
@@ -559,6 +613,7 @@ def _run_ours(args, dist, ctxs):
             "clocks": clk,
             "gpu_launches": launches,
         }
+        line["config"].pop("_batched_check", None)
         print(json.dumps(line), flush=True)
 
 
