@@ -1051,8 +1051,8 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
       if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kE][(t - 2) % 8], 0));
       rc = launch_stats_for(ctx, fr, T0 + t, sA);
       chk(cudaEventRecord(ev[kS][t % 8], sA));
-      // band pre-warp: its slot was last read by the fuse of frame t-2
-      if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kF][(t - 2) % 8], 0));
+      // band pre-warp: its slot was last read by the fuse of frame t - kPwSlots
+      if (t >= kPwSlots) chk(cudaStreamWaitEvent(sA, ev[kF][(t - kPwSlots) % 8], 0));
       if (rc == STITCH_OK) rc = launch_prewarp_for(ctx, fp, sA);
       chk(cudaEventRecord(ev[kW][t % 8], sA));
       // estimate: after this frame's statistics; its colour slot was last read by fuse t-4
@@ -1716,7 +1716,7 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       for (int r = 0; r < R && rc == STITCH_OK; ++r)
         rc = launch_stats_for(b->ctx[r], frames_dev + (size_t)t * b->cams + b->cam_off[r], b->ctx[r]->host_T + t, sA);
       chk(cudaEventRecord(ev[kS][t % 8], sA));
-      if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kF][(t - 2) % 8], 0));
+      if (t >= kPwSlots) chk(cudaStreamWaitEvent(sA, ev[kF][(t - kPwSlots) % 8], 0));
       MultiParams mp{bg.params, t * R, b->n_pw_items, b->pw_items, nullptr};
       chk(launch_prewarp_multi(mp, b->half, sA));
       chk(cudaEventRecord(ev[kW][t % 8], sA));

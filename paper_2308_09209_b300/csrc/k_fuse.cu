@@ -315,34 +315,19 @@ __device__ void load_block_color(const FuseParams &P, BlockColor &bc) {
   }
 }
 
-// Hot per-channel balance parameters, kept in registers.
-struct Hot {
-  float mid[3], half[3], A[3], B[3];
-};
-
-__device__ __forceinline__ Hot load_hot(const BlockColor &bc) {
-  Hot h;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    h.mid[c] = bc.mid[c];
-    h.half[c] = bc.half[c];
-    h.A[c] = bc.A[c];
-    h.B[c] = bc.B[c];
-  }
-  return h;
-}
-
 // One channel: clamp (saturate), balance (Eq. 5), round half to even; the low
-// byte of the result is the output byte.
-__device__ __forceinline__ uint32_t finish(const Hot &h, const BlockColor &bc, int c, float v) {
+// byte of the result is the output byte. The curve's parameters are read from
+// shared memory (keeping them in registers costs more in spills than the
+// loads).
+__device__ __forceinline__ uint32_t finish(const BlockColor &bc, int c, float v) {
   const float u = __saturatef(v);
-  float F = fmaf(h.B[c], u, h.A[c]);
-  if (fabsf(u - h.mid[c]) > h.half[c]) {
+  float F = fmaf(bc.B[c], u, bc.A[c]);
+  if (fabsf(u - bc.mid[c]) > bc.half[c]) {
     // The side comes from the midpoint: mid -/+ half need not round to the
     // knots exactly, and a value next to a knot must take that knot's tail
     // (both pieces meet there).
     const Tail &t = bc.tail[c];
-    F = (u < h.mid[c]) ? t.d1 * __powf(u * t.k1, t.g1)
+    F = (u < bc.mid[c]) ? t.d1 * __powf(u * t.k1, t.g1)
                        : 255.0f - t.e2 * __powf((1.0f - u) * t.k2, t.g2);
   }
   return (uint32_t)__float_as_int(F + kMagicRound);
@@ -428,13 +413,13 @@ __device__ __forceinline__ float3 pw_bilinear(const typename PwT<kHalf>::T *pw, 
 }
 
 template <int TW, int TH>
-__device__ __forceinline__ void put_px(uint8_t (*s_out)[TH][TW], int lx, int ly, const Hot &h, const BlockColor &bc,
-                                       bool cov, float3 v) {
+__device__ __forceinline__ void put_px(uint8_t (*s_out)[TH][TW], int lx, int ly, const BlockColor &bc, bool cov,
+                                       float3 v) {
   uint32_t o0 = 0u, o1 = 0u, o2 = 0u;
   if (cov) {
-    o0 = finish(h, bc, 0, v.x);
-    o1 = finish(h, bc, 1, v.y);
-    o2 = finish(h, bc, 2, v.z);
+    o0 = finish(bc, 0, v.x);
+    o1 = finish(bc, 1, v.y);
+    o2 = finish(bc, 2, v.z);
   }
   s_out[0][ly][lx] = (uint8_t)o0;
   s_out[1][ly][lx] = (uint8_t)o1;
@@ -513,7 +498,6 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
   if (W0.ok) stage_window(P.src[t.idx], P.cam[t.idx], W0, sm.s_win[0]);
   if (W1.ok) stage_window(P.src[t.idx + 1], P.cam[t.idx + 1], W1, sm.s_win[1]);
   __syncthreads();
-  const Hot hot = load_hot(bc);
 
   if (t.kind == 0) {
     // Fully covered own tile: no coverage test, no fallback.
@@ -528,7 +512,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
         const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
         float sx, sy;
         cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
-        put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, true, mulM(M, win_bilinear(sm.s_win[0], W0, sx, sy)));
+        put_px<TW, TH>(sm.s_out, lx, ly, bc, true, mulM(M, win_bilinear(sm.s_win[0], W0, sx, sy)));
       }
     } else {
 #pragma unroll 2
@@ -538,7 +522,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
         cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
         const float3 v =
             mulM(M, W0.ok ? win_bilinear(sm.s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
-        put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, true, v);
+        put_px<TW, TH>(sm.s_out, lx, ly, bc, true, v);
       }
     }
   } else if (t.kind == 2) {
@@ -556,7 +540,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
         if (!cov && k > 0) cov = cam_value_g(P, bc, k - 1, x, y, v);
         if (!cov && k < P.n_cams - 1) cov = cam_value_g(P, bc, k + 1, x, y, v);
       }
-      put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, cov, v);
+      put_px<TW, TH>(sm.s_out, lx, ly, bc, cov, v);
     }
   } else {
     const int p = t.idx;
@@ -620,7 +604,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
           }
         }
       }
-      put_px<TW, TH>(sm.s_out, lx, ly, hot, bc, cov, v);
+      put_px<TW, TH>(sm.s_out, lx, ly, bc, cov, v);
     }
   }
   __syncthreads();
