@@ -333,11 +333,6 @@ __device__ __forceinline__ uint32_t finish(const BlockColor &bc, int c, float v)
   return (uint32_t)__float_as_int(F + kMagicRound);
 }
 
-__device__ __forceinline__ void load_M(const BlockColor &bc, int k, float (&M)[9]) {
-#pragma unroll
-  for (int e = 0; e < 9; ++e) M[e] = bc.M[k][e];
-}
-
 // ---------------------------------------------------------------------------
 // Per-pixel general paths (global memory).
 // ---------------------------------------------------------------------------
@@ -352,8 +347,9 @@ __device__ __forceinline__ bool cam_value_g(const FuseParams &P, const BlockColo
   return true;
 }
 
-// Camera k's value at q, from its staged window when there is one.
-__device__ __forceinline__ bool cam_value_w(const FuseParams &P, const float (&M)[9], int k, const Window &W,
+// Camera k's value at q, from its staged window when there is one (M points
+// at the block's shared copy of the camera's matrix).
+__device__ __forceinline__ bool cam_value_w(const FuseParams &P, const float *M, int k, const Window &W,
                                             const uint32_t *s, int x, int y, float3 &v) {
   const CamDev &c = P.cam[k];
   float sx, sy, nw;
@@ -503,8 +499,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
     // Fully covered own tile: no coverage test, no fallback.
     const int k = t.idx;
     const CamDev &c = P.cam[k];
-    float M[9];
-    load_M(bc, k, M);
+    const float *M = bc.M[k];
     const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
     if (c.affine && W0.ok) {
 #pragma unroll 2
@@ -527,8 +522,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
     }
   } else if (t.kind == 2) {
     const int k = t.idx;
-    float M[9];
-    load_M(bc, k, M);
+    const float *M = bc.M[k];
 #pragma unroll 2
     for (int j = 0; j < MP::kPix; ++j) {
       const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
@@ -545,9 +539,8 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
   } else {
     const int p = t.idx;
     const BandDev B = P.band[p];
-    float Ma[9], Mb[9];
-    load_M(bc, p, Ma);
-    load_M(bc, p + 1, Mb);
+    const float *Ma = bc.M[p];
+    const float *Mb = bc.M[p + 1];
     const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
     const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
     const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
