@@ -470,6 +470,13 @@ def _run_ours(args, dist, ctxs):
     frames = [f for fr in wl["frames"] for f in fr]
     fij = [f for fl in wl["fij"] for f in fl]
     fji = [f for fl in wl["fji"] for f in fl]
+    # pick the fuse tile shape for this rig with the library's autotuner (one frame, outside the timed region)
+    S.stitch_estimate_color(st.ctx, wl["frames"][0], stream)
+    shape, shape_ms = S.stitch_autotune(st.ctx, wl["frames"][0], wl["fij"][0], wl["fji"][0], panos[0], reps=5)
+    st.close()
+    ctxs.remove(st)
+    st = S.Stitcher(cfg)                 # a fresh context with the tuned shape recorded for this rig
+    ctxs.append(st)
     torch.cuda.synchronize()
 
     def step():
@@ -602,6 +609,8 @@ def _run_ours(args, dist, ctxs):
                                               "fuse": fuse_ms},
                        "stage_timing": stage_timing,
                        "status": rc, "parallelism": f"replicas x{dist.world}",
+                       "tile_shape": list(S.stitch_tile_shape(st.ctx)[1]),
+                       "autotune_ms": [round(float(m), 4) for m in shape_ms],
                        "oracle_error": err, **extras},
             "roofline": {"bound": "hbm", "kernel": "fused warp stage of a frame (k_prewarp_band + k_fuse)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
