@@ -609,7 +609,8 @@ bool check_ptrs(const void *const *p, int n) {
 // (kind 1); others belong to the one camera whose own columns hold them: kind
 // 0 when that camera covers the whole tile with a margin (coverage is convex,
 // so the four corners decide) and no pixel needs a coverage test or a fallback
-// camera, kind 2 for partial coverage. Band tiles come first. Returns false
+// camera, kind 2 for partial coverage. Band tiles come first, and among the
+// own tiles the partly covered ones precede the fully covered. Returns false
 // (with a message) when a tile would touch two bands.
 bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &band_tiles, std::vector<TileDesc> &own_tiles,
                  std::string &err) {
@@ -664,7 +665,15 @@ bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &band_tiles, std
       }
     }
   }
+  // partly covered own tiles first: the fully covered ones close the list
+  std::stable_partition(own_tiles.begin(), own_tiles.end(), [](const TileDesc &t) { return t.kind != 0; });
   return true;
+}
+
+int count_full(const std::vector<TileDesc> &own) {
+  int n = 0;
+  for (const TileDesc &t : own) n += t.kind == 0 ? 1 : 0;
+  return n;
 }
 
 // Tiles of the smallest shape (at least 32 x 16): room for any shape's list.
@@ -908,6 +917,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   fp.halo = ctx->halo;
   fp.max_flow = ctx->max_flow;
   fp.n_tiles = ctx->n_band_tiles + ctx->n_own_tiles;
+  fp.n_full = count_full(own_tiles);
   fp.tiles = ctx->tiles;
   fp.n_pw_tiles = (int)pw_tiles.size();
   fp.pw_tiles = ctx->pw_tiles;
@@ -1420,10 +1430,12 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
     bt.clear();
     ot.clear();
     if (!build_tiles(ctx->g, sh, bt, ot, err)) continue;
+    const int nfull = count_full(ot);
     bt.insert(bt.end(), ot.begin(), ot.end());
     e = cudaMemcpyAsync(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s);
     fp.tiles = ctx->tiles;
     fp.n_tiles = (int)bt.size();
+    fp.n_full = nfull;
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_fuse(fp, sh, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fuse(fp, sh, s);
@@ -1446,6 +1458,7 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
     build_tiles(ctx->g, best, bt, ot, err);
     ctx->n_band_tiles = (int)bt.size();
     ctx->n_own_tiles = (int)ot.size();
+    ctx->fp.n_full = count_full(ot);
     bt.insert(bt.end(), ot.begin(), ot.end());
     e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
     ctx->fp.n_tiles = (int)bt.size();
@@ -1476,10 +1489,12 @@ int stitch_set_tile_shape(stitch_ctx *ctx, int shape) {
   cudaError_t e = cudaDeviceSynchronize();
   ctx->n_band_tiles = (int)bt.size();
   ctx->n_own_tiles = (int)ot.size();
+  const int nfull = count_full(ot);
   bt.insert(bt.end(), ot.begin(), ot.end());
   if (e == cudaSuccess) e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_err(ctx, e, "tile list upload");
   ctx->fp.n_tiles = (int)bt.size();
+  ctx->fp.n_full = nfull;
   ctx->shape = shape;
   for (auto &ge : ctx->graphs) {
     if (ge.exec) cudaGraphExecDestroy(ge.exec);

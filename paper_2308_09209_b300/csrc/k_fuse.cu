@@ -9,7 +9,9 @@
 //   STITCH_FP16_INTERMEDIATE). It does not depend on the colour estimate.
 //
 // k_fuse: one block per panorama tile (64 x 32 by default; the shape is a
-//   template parameter the autotuner picks per rig).
+//   template parameter the autotuner picks per rig). The fully covered own
+//   tiles (about three quarters of a rig's tiles) run in a second launch,
+//   k_fuse_own, whose one-camera code needs fewer registers and no spills.
 //   * Own tiles (columns of one camera k): the source window that the tile
 //     maps to through H_k^-1 (planar) or through the cylinder's ray and H_k^-1
 //     (cylindrical panorama) is staged in shared memory as one RGBX word per
@@ -604,6 +606,60 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
   store_tile<TW, TH>(P, tx0, ty0, sm.s_out);
 }
 
+// Shared memory of a fully covered own tile: one camera, one window.
+template <int TW, int TH>
+struct FuseOwnSmem {
+  BlockColor bc;
+  Window sW;
+  __align__(16) uint32_t s_win[kWinCap];
+  __align__(16) uint8_t s_out[3][TH][TW];
+};
+
+// A fully covered own tile (kind 0) on its own: no band, no coverage test, no
+// fallback camera; the same arithmetic as that case of fuse_tile, with the
+// registers and shared memory of one camera only.
+template <int TW, int TH>
+__device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDesc t, FuseOwnSmem<TW, TH> &sm) {
+  using MP = Map<TW, TH>;
+  BlockColor &bc = sm.bc;
+  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
+  const int tx1 = min(tx0 + TW, P.pano_w) - 1, ty1 = min(ty0 + TH, P.pano_h) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = t.idx;
+  const CamDev &c = P.cam[k];
+  load_block_color(P, bc);
+  if (warp == 0) {
+    const Window W = warp_window(c, tx0, ty0, tx1, ty1);
+    if (lane == 0) sm.sW = W;
+  }
+  __syncthreads();
+  const Window W0 = sm.sW;
+  if (W0.ok) stage_window(P.src[k], c, W0, sm.s_win);
+  __syncthreads();
+  const float *M = bc.M[k];
+  const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
+  if (c.affine && W0.ok) {
+#pragma unroll 2
+    for (int j = 0; j < MP::kPix; ++j) {
+      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+      float sx, sy;
+      cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
+      put_px<TW, TH>(sm.s_out, lx, ly, bc, true, mulM(M, win_bilinear(sm.s_win, W0, sx, sy)));
+    }
+  } else {
+#pragma unroll 2
+    for (int j = 0; j < MP::kPix; ++j) {
+      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+      float sx, sy, nw;
+      cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
+      const float3 v = mulM(M, W0.ok ? win_bilinear(sm.s_win, W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
+      put_px<TW, TH>(sm.s_out, lx, ly, bc, true, v);
+    }
+  }
+  __syncthreads();
+  store_tile<TW, TH>(P, tx0, ty0, sm.s_out);
+}
+
 // One band pre-warp piece (kTileW x kTileH) of pair pt.pair, both cameras.
 template <bool kHalf>
 __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, uint32_t (*s_win)[kWinCap],
@@ -673,6 +729,13 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const FuseParams P) {
   fuse_tile<kHalf, TW, TH>(P, P.tiles[blockIdx.x], sm);
 }
 
+// The fully covered own tiles, which close the tile list (P.n_full of them).
+template <int TW, int TH>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own(const FuseParams P) {
+  __shared__ FuseOwnSmem<TW, TH> sm;
+  fuse_own_tile<TW, TH>(P, P.tiles[P.n_tiles - P.n_full + blockIdx.x], sm);
+}
+
 // Band pre-warp of several rigs in one launch: block b takes item b.
 template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParams M) {
@@ -725,12 +788,18 @@ cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s) {
 
 namespace {
 
+// The tiles that touch a band or are partly covered (k_fuse), then the fully
+// covered own tiles (k_fuse_own), in one stream.
 template <int TW, int TH>
 void fuse_by_half(const FuseParams &p, cudaStream_t s) {
-  if (p.flags & STITCH_FP16_INTERMEDIATE)
-    k_fuse<true, TW, TH><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
-  else
-    k_fuse<false, TW, TH><<<p.n_tiles, kFuseThreads, 0, s>>>(p);
+  const int mixed = p.n_tiles - p.n_full;
+  if (mixed > 0) {
+    if (p.flags & STITCH_FP16_INTERMEDIATE)
+      k_fuse<true, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
+    else
+      k_fuse<false, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
+  }
+  if (p.n_full > 0) k_fuse_own<TW, TH><<<p.n_full, kFuseThreads, 0, s>>>(p);
 }
 
 template <int TW, int TH>

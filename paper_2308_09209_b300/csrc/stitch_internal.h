@@ -113,6 +113,7 @@ struct alignas(16) FuseParams {
   int halo;
   float max_flow;
   int n_tiles;
+  int n_full;                         // the last n_full tiles are fully covered own tiles (kind 0)
   const TileDesc *tiles;
   int n_pw_tiles;
   const PwTile *pw_tiles;
