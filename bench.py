@@ -591,7 +591,7 @@ def _run_ours(args, dist, ctxs):
             err["batched_rigs_frame0"] = oracle_check_rigs(extras["_batched_check"])
 
 
-    launches = args.steps * F * 4     # stats, estimate, band pre-warp, fuse per frame
+    launches = args.steps * F * 5     # stats, estimate, band pre-warp, fuse (band / partly covered tiles), fuse (full own tiles)
     if dist.rank == 0:
         rig = wl["rig"]
         line = {
@@ -612,7 +612,7 @@ def _run_ours(args, dist, ctxs):
                        "tile_shape": list(S.stitch_tile_shape(st.ctx)[1]),
                        "autotune_ms": [round(float(m), 4) for m in shape_ms],
                        "oracle_error": err, **extras},
-            "roofline": {"bound": "hbm", "kernel": "fused warp stage of a frame (k_prewarp_band + k_fuse)",
+            "roofline": {"bound": "hbm", "kernel": "fused warp stage of a frame (k_prewarp_band + k_fuse + k_fuse_own)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": fuse_bytes},
