@@ -556,8 +556,17 @@ def _run_ours(args, dist, ctxs):
 
     extras = {}
     if dist.rank == 0 and dist.world == 1 and not args.no_extras:
+        # the same workload with FP16 band intermediates (coordinates and arithmetic stay FP32)
+        cfg16 = S.Config(cfg.cam_w, cfg.cam_h, cfg.H, cfg.pano_w, cfg.pano_h, window=cfg.window,
+                         max_flow=cfg.max_flow, flags=S.STITCH_FP16_INTERMEDIATE)
+        st16 = S.Stitcher(cfg16)
+        ctxs.append(st16)
+        ms16 = _time(lambda: S.stitch_sequence(st16.ctx, F, frames, fij, fji, panos, stream), stream,
+                     max(3, min(args.steps, 20)), 2)
+        extras["fp16_intermediates"] = {"value": F * wl["pano_px"] / (ms16 / 1e3) / 1e6, "unit": UNIT,
+                                        "ms_per_step": ms16}
         del panos, h_frames, h_fij, h_fji, h_out
-        extras = run_extras(args, dev, stream, ctxs)
+        extras.update(run_extras(args, dev, stream, ctxs))
 
     cpu_baseline = None
     err = None
