@@ -420,8 +420,9 @@ int stitch_tile_shape(const stitch_ctx *ctx, int *tile_w, int *tile_h);
  * Batched launch of several independent rigs (streams of uneven geometry).
  * A batch drives up to STITCH_BATCH_MAX_RIGS contexts together: every frame
  * runs each rig's statistics and estimate, then ONE band pre-warp launch and
- * ONE persistent fuse launch over the tiles of all rigs (blocks take tiles
- * from a work counter; band tiles first), recorded in a CUDA graph and
+ * two persistent fuse launches over the tiles of all rigs (band and partly
+ * covered tiles, then the fully covered ones; blocks take tiles from a work
+ * counter, band tiles first), recorded in a CUDA graph and
  * replayed like stitch_sequence. The paper stitches one rig; this is the
  * serving form. The contexts keep their own state and may still be used
  * alone between batch calls. All contexts must share the device and the

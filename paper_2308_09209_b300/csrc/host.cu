@@ -1525,7 +1525,7 @@ struct BatchGraph {
   int n_frames = 0;
   cudaGraphExec_t exec = nullptr;
   FuseParams *params = nullptr;       // n_frames x n_rigs parameter blocks
-  int *counters = nullptr;            // one work counter per frame
+  int *counters = nullptr;            // two work counters per frame (band / partly covered, fully covered)
 };
 
 struct stitch_batch {
@@ -1534,8 +1534,11 @@ struct stitch_batch {
   bool half = false;
   int cams = 0, pairs = 0;            // totals over the rigs
   std::vector<int> cam_off, pair_off;
-  MultiItem *fuse_items = nullptr;
+  MultiItem *fuse_items = nullptr;    // band and partly covered tiles of every rig
   int n_fuse_items = 0;
+  MultiItem *own_items = nullptr;     // fully covered own tiles of every rig
+  int n_own_items = 0;
+  int grid_own = 0;
   MultiItem *pw_items = nullptr;
   int n_pw_items = 0;
   int grid = 0;                       // persistent fuse blocks
@@ -1563,9 +1566,10 @@ void free_batch_graph(BatchGraph &g) {
   g.counters = nullptr;
 }
 
-// Work lists of the batch for a tile shape: every rig's fuse tiles (band
-// tiles first, the costliest, so that the dynamic schedule ends evenly) and
-// band pre-warp pieces.
+// Work lists of the batch for a tile shape: every rig's band and partly
+// covered tiles (band tiles first, the costliest, so that the dynamic
+// schedule ends evenly), its fully covered own tiles (the one-camera kernel),
+// and its band pre-warp pieces.
 int batch_items(stitch_batch *b, int shape) {
   std::vector<MultiItem> band, part, full, pw;
   std::string err;
@@ -1580,25 +1584,32 @@ int batch_items(stitch_batch *b, int shape) {
         for (int x = g.band[p][0]; x < g.band[p][1]; x += kTileW) pw.push_back(MultiItem{r, TileDesc{}, PwTile{p, x, y}});
   }
   band.insert(band.end(), part.begin(), part.end());
-  band.insert(band.end(), full.begin(), full.end());
   cudaFree(b->fuse_items);
+  cudaFree(b->own_items);
   cudaFree(b->pw_items);
   b->fuse_items = nullptr;
+  b->own_items = nullptr;
   b->pw_items = nullptr;
   cudaError_t e = cudaMalloc(&b->fuse_items, band.size() * sizeof(MultiItem) + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&b->own_items, full.size() * sizeof(MultiItem) + 16);
   if (e == cudaSuccess) e = cudaMalloc(&b->pw_items, pw.size() * sizeof(MultiItem) + 16);
   if (e == cudaSuccess && !band.empty())
     e = cudaMemcpy(b->fuse_items, band.data(), band.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !full.empty())
+    e = cudaMemcpy(b->own_items, full.data(), full.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !pw.empty())
     e = cudaMemcpy(b->pw_items, pw.data(), pw.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return batch_err(b, STITCH_ECUDA, std::string("batch work lists: ") + cudaGetErrorString(e));
   b->n_fuse_items = (int)band.size();
+  b->n_own_items = (int)full.size();
   b->n_pw_items = (int)pw.size();
   int sms = 148, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, shape));
   b->grid = std::max(1, std::min(b->n_fuse_items, per_sm * sms));
+  const int per_sm_own = std::max(1, fuse_own_multi_blocks_per_sm(shape));
+  b->grid_own = std::max(1, std::min(b->n_own_items, per_sm_own * sms));
   b->shape = shape;
   for (auto &g : b->graphs) free_batch_graph(g);
   b->graphs.clear();
@@ -1690,7 +1701,7 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
     bg.key = key;
     bg.n_frames = n_frames;
     cudaError_t e = cudaMalloc(&bg.params, (size_t)n_frames * R * sizeof(FuseParams));
-    if (e == cudaSuccess) e = cudaMalloc(&bg.counters, (size_t)n_frames * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&bg.counters, (size_t)n_frames * 2 * sizeof(int));
     std::vector<FuseParams> hp((size_t)n_frames * R);
     for (int t = 0; t < n_frames; ++t)
       for (int r = 0; r < R; ++r) {
@@ -1741,9 +1752,11 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       chk(cudaEventRecord(ev[kE][t % 8], sB));
       chk(cudaStreamWaitEvent(sC, ev[kE][t % 8], 0));
       chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
-      chk(cudaMemsetAsync(bg.counters + t, 0, sizeof(int), sC));
-      MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + t};
+      chk(cudaMemsetAsync(bg.counters + 2 * t, 0, 2 * sizeof(int), sC));
+      MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + 2 * t};
       chk(launch_fuse_multi(mf, b->half, b->shape, b->grid, sC));
+      MultiParams mo{bg.params, t * R, b->n_own_items, b->own_items, bg.counters + 2 * t + 1};
+      chk(launch_fuse_own_multi(mo, b->shape, b->grid_own, sC));
       chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
     chk(cudaEventRecord(ev[kS][0], sA));
@@ -1791,7 +1804,7 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
   FuseParams *params = nullptr;
   int *counter = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&params, R * sizeof(FuseParams));
-  if (e == cudaSuccess) e = cudaMalloc(&counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&counter, 2 * sizeof(int));
   std::vector<FuseParams> hp(R);
   for (int r = 0; r < R; ++r) {
     stitch_ctx *c = b->ctx[r];
@@ -1812,15 +1825,16 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
     MultiParams pw{params, 0, b->n_pw_items, b->pw_items, nullptr};
     e = launch_prewarp_multi(pw, b->half, b->cap);
     MultiParams mf{params, 0, b->n_fuse_items, b->fuse_items, counter};
-    for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
-      e = cudaMemsetAsync(counter, 0, sizeof(int), b->cap);
-      if (e == cudaSuccess) e = launch_fuse_multi(mf, b->half, sh, b->grid, b->cap);
-    }
+    MultiParams mo{params, 0, b->n_own_items, b->own_items, counter + 1};
+    auto both = [&]() {
+      cudaError_t x = cudaMemsetAsync(counter, 0, 2 * sizeof(int), b->cap);
+      if (x == cudaSuccess) x = launch_fuse_multi(mf, b->half, sh, b->grid, b->cap);
+      if (x == cudaSuccess) x = launch_fuse_own_multi(mo, sh, b->grid_own, b->cap);
+      return x;
+    };
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = both();
     if (e == cudaSuccess) e = cudaEventRecord(e0, b->cap);
-    for (int k = 0; k < reps && e == cudaSuccess; ++k) {
-      e = cudaMemsetAsync(counter, 0, sizeof(int), b->cap);
-      if (e == cudaSuccess) e = launch_fuse_multi(mf, b->half, sh, b->grid, b->cap);
-    }
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = both();
     if (e == cudaSuccess) e = cudaEventRecord(e1, b->cap);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float t = 0.0f;
@@ -1849,6 +1863,7 @@ void stitch_batch_destroy(stitch_batch *b) {
   cudaDeviceSynchronize();
   for (auto &g : b->graphs) free_batch_graph(g);
   cudaFree(b->fuse_items);
+  cudaFree(b->own_items);
   cudaFree(b->pw_items);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (int i = 0; i < 3; ++i)

@@ -38,9 +38,9 @@
 // rows, so a warp touches 32 consecutive pixels of a row at a time and its
 // shared-memory tap reads fall in distinct banks.
 //
-// k_prewarp_multi / k_fuse_multi: the same work over the tiles of several
-// independent rigs in one launch; the fuse is persistent (one block per
-// resident slot, tiles taken from a work counter).
+// k_prewarp_multi / k_fuse_multi / k_fuse_own_multi: the same work over the
+// tiles of several independent rigs in one launch each; the fuse kernels are
+// persistent (one block per resident slot, tiles taken from a work counter).
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -773,6 +773,29 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi(const MultiParam
   }
 }
 
+// Persistent fuse over the fully covered own tiles of several rigs.
+template <int TW, int TH>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi(const MultiParams M) {
+  __shared__ FuseOwnSmem<TW, TH> sm;
+  __shared__ FuseParams sp;
+  __shared__ int s_item;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= M.n_items) break;
+    const MultiItem it = M.items[item];
+    if (it.rig != cur) {
+      copy_params(sp, M.params + M.base + it.rig);
+      cur = it.rig;
+    }
+    __syncthreads();
+    fuse_own_tile<TW, TH>(sp, it.tile, sm);
+    __syncthreads();
+  }
+}
+
 size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
 
 cudaError_t fuse_setup_attributes(int) { return cudaSuccess; }
@@ -808,6 +831,13 @@ void fuse_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t 
     k_fuse_multi<true, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
   else
     k_fuse_multi<false, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
+}
+
+template <int TW, int TH>
+int occupancy_own() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<TW, TH>, kFuseThreads, 0);
+  return n;
 }
 
 template <int TW, int TH>
@@ -858,6 +888,28 @@ cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int gr
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s) {
+  if (m.n_items <= 0) return cudaSuccess;
+  switch (shape) {
+    case 0: k_fuse_own_multi<64, 32><<<grid, kFuseThreads, 0, s>>>(m); break;
+    case 1: k_fuse_own_multi<64, 16><<<grid, kFuseThreads, 0, s>>>(m); break;
+    case 2: k_fuse_own_multi<32, 32><<<grid, kFuseThreads, 0, s>>>(m); break;
+    case 3: k_fuse_own_multi<128, 16><<<grid, kFuseThreads, 0, s>>>(m); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int fuse_own_multi_blocks_per_sm(int shape) {
+  switch (shape) {
+    case 0: return occupancy_own<64, 32>();
+    case 1: return occupancy_own<64, 16>();
+    case 2: return occupancy_own<32, 32>();
+    case 3: return occupancy_own<128, 16>();
+    default: return 0;
+  }
 }
 
 int fuse_multi_blocks_per_sm(bool half, int shape) {

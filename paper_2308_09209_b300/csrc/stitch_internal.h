@@ -213,6 +213,8 @@ cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s);
 cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s);
 cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s);
 int fuse_multi_blocks_per_sm(bool half, int shape);
+cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);
+int fuse_own_multi_blocks_per_sm(int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
 size_t stats_smem_bytes();
 size_t prewarp_elem_bytes(bool fp16);

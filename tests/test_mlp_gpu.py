@@ -254,3 +254,52 @@ def test_learned_context_matches_oracle_learned_mode():
     assert np.allclose(Mg, pr.oracle.M_cam, rtol=0, atol=M_REL_TOL * 3)
     pr.st.close()
     net.close()
+
+
+def test_mlp_argument_errors():
+    ensure_built()
+    with pytest.raises(S.StitchError):
+        S.stitch_mlp_create(48, 0)          # not a multiple of 32
+    net = S.Mlp(max_batch=64, seed=0)
+    x = torch.zeros((80, S.STITCH_MLP_IN), dtype=torch.int16, device="cuda")
+    y = torch.zeros((80, N_OUT), dtype=torch.float32, device="cuda")
+    t = torch.zeros((80, N_OUT), dtype=torch.float32, device="cuda")
+    with pytest.raises(S.StitchError):
+        S.stitch_mlp_forward(net.h, x, 65, y)            # above max_batch
+    with pytest.raises(S.StitchError):
+        S.stitch_mlp_train_step(net.h, x, t, 40, 1e-3)   # not a multiple of 32
+    xs = x.view(-1)[1:1 + 16 * S.STITCH_MLP_IN].view(16, S.STITCH_MLP_IN)   # 2-byte offset: misaligned
+    with pytest.raises(S.StitchError):
+        S.stitch_mlp_forward(net.h, xs, 16, y)
+    with pytest.raises(S.StitchError):
+        S.stitch_mlp_set_gemm(net.h, 7)
+    S.stitch_mlp_status(net.h)
+    net.close()
+
+
+def test_learned_context_eight_cameras_and_state_round_trip():
+    """Seven pairs through the small-batch network path, and a saved learned
+    context (its window of histograms included) resumes identically."""
+    ensure_built()
+    net = S.Mlp(max_batch=32, seed=11)
+    S.stitch_mlp_set_norm(net.h, np.zeros(N_OUT, np.float32), np.full(N_OUT, 0.05, np.float32))
+    pa = Pair("6x1920x1080+2x1280x720", seed=5, flags=S.STITCH_LEARNED)
+    pb = Pair("6x1920x1080+2x1280x720", seed=5, flags=S.STITCH_LEARNED)
+    S.stitch_attach_mlp(pa.st.ctx, net.h)
+    S.stitch_attach_mlp(pb.st.ctx, net.h)
+    ins = [pa.inputs(t) for t in range(4)]
+    for t in range(2):
+        pa.st.estimate_color(ins[t][0])
+        pb.st.estimate_color(ins[t][0])
+    blob = S.stitch_save_state(pa.st.ctx)
+    S.stitch_load_state(pb.st.ctx, blob)
+    for t in range(2, 4):
+        pa.st.estimate_color(ins[t][0])
+        pb.st.estimate_color(ins[t][0])
+    Ma, ra, ua = S.stitch_get_learned(pa.st.ctx, 7)
+    Mb, rb, ub = S.stitch_get_learned(pb.st.ctx, 7)
+    assert np.array_equal(Ma, Mb) and np.array_equal(ra, rb) and np.array_equal(ua, ub)
+    assert np.all(np.isfinite(ra))
+    pa.st.close()
+    pb.st.close()
+    net.close()
