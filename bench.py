@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--workload", default="4x1920x1080")
     ap.add_argument("--frames", type=int, default=60)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--e2e-frames", type=int, default=8)
+    ap.add_argument("--e2e-frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched / learned / cylindrical comparisons (rank 0 of a 1-GPU run only)")

@@ -156,9 +156,13 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
 /*
  * stitch_sequence_host -- as stitch_sequence, but every array is HOST memory:
  * the library copies each frame's images and flows to its own device staging
- * buffers, runs the frame and copies the panorama back, all on `stream`, and
- * returns after the stream has drained. Host frames are read with the
- * configured row pitch; host flows are dense band_w x band_h float2.
+ * buffers (two frames' worth), runs the frame on `stream` and copies the
+ * panorama back. The copies run on two library-owned streams so that the
+ * inputs of frame t + 1 and the panorama of frame t - 1 move while frame t
+ * computes; events order them against `stream`. Returns after all of it has
+ * drained (on an error too). Host frames are read with the configured row
+ * pitch; host flows are dense band_w x band_h float2. Page-locked host memory
+ * is needed for the copies to overlap.
  */
 int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_host,
                          const float *const *flow_ij_host, const float *const *flow_ji_host,

@@ -415,6 +415,19 @@ struct GraphEntry {
   std::vector<ProfPair> pairs;        // events owned by this graph (profiling only)
 };
 
+// One slot of the host-memory sequence path: device copies of a frame's
+// images and flows and of its panorama, with the events that order the copy
+// streams against the compute stream.
+struct HostStage {
+  uint8_t *frames[kMaxCams] = {};
+  float *fij[kMaxPairs] = {};
+  float *fji[kMaxPairs] = {};
+  uint8_t *pano = nullptr;
+  cudaEvent_t in_ready = nullptr;     // inputs copied
+  cudaEvent_t computed = nullptr;     // frame computed: inputs free, panorama ready
+  cudaEvent_t out_done = nullptr;     // panorama copied out: panorama buffer free
+};
+
 struct stitch_ctx {
   Geo g;
   int flags = 0;
@@ -445,10 +458,9 @@ struct stitch_ctx {
   std::vector<ProfPair> *prof_sink = nullptr;   // where new pairs go (a graph while capturing)
   std::vector<ProfPair> pending;      // pairs whose times the next stitch_profile_read sums
   std::vector<ProfPair> owned;        // per-call pairs, destroyed after they are read
-  uint8_t *stage_frames[kMaxCams] = {};
-  float *stage_fij[kMaxPairs] = {};
-  float *stage_fji[kMaxPairs] = {};
-  uint8_t *stage_pano = nullptr;
+  HostStage stage[2];                 // device staging of stitch_sequence_host, two frames in flight
+  cudaStream_t copy_in = nullptr;     // host-to-device copies of stitch_sequence_host
+  cudaStream_t copy_out = nullptr;    // device-to-host copies of stitch_sequence_host
   int shape = 0;                      // fuse tile shape (index into kTileShapes)
   LearnedState *ls = nullptr;         // learned estimator state (STITCH_LEARNED contexts)
   stitch_mlp *mlp = nullptr;          // attached network (not owned)
@@ -1136,42 +1148,72 @@ int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *fr
       !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_host), n_frames * np) ||
       !check_ptrs(reinterpret_cast<const void *const *>(pano_host), n_frames))
     return set_err(ctx, STITCH_EINVAL, "sequence pointer arrays must be complete and non-NULL");
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < n && e == cudaSuccess; ++k)
-    if (!ctx->stage_frames[k]) e = cudaMalloc(&ctx->stage_frames[k], (size_t)g.pitch[k] * g.h[k]);
-  for (int p = 0; p < np && e == cudaSuccess; ++p) {
-    if (!ctx->stage_fij[p]) e = cudaMalloc(&ctx->stage_fij[p], band_elems(g, p) * 8);
-    if (e == cudaSuccess && !ctx->stage_fji[p]) e = cudaMalloc(&ctx->stage_fji[p], band_elems(g, p) * 8);
-  }
   const size_t pano_bytes = (size_t)3 * g.pano_pitch * g.pano_h;
-  if (e == cudaSuccess && !ctx->stage_pano) e = cudaMalloc(&ctx->stage_pano, pano_bytes);
+  cudaError_t e = cudaSuccess;
+  for (HostStage &hs : ctx->stage) {
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+      if (!hs.frames[k]) e = cudaMalloc(&hs.frames[k], (size_t)g.pitch[k] * g.h[k]);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+      if (!hs.fij[p]) e = cudaMalloc(&hs.fij[p], band_elems(g, p) * 8);
+      if (e == cudaSuccess && !hs.fji[p]) e = cudaMalloc(&hs.fji[p], band_elems(g, p) * 8);
+    }
+    if (e == cudaSuccess && !hs.pano) e = cudaMalloc(&hs.pano, pano_bytes);
+    for (cudaEvent_t *ev : {&hs.in_ready, &hs.computed, &hs.out_done})
+      if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && !ctx->copy_in) e = cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->copy_out) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_err(ctx, e, "staging allocation");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const uint8_t *fr[kMaxCams];
-  const float *fi[kMaxPairs], *fj[kMaxPairs];
-  for (int k = 0; k < n; ++k) fr[k] = ctx->stage_frames[k];
-  for (int p = 0; p < np; ++p) {
-    fi[p] = ctx->stage_fij[p];
-    fj[p] = ctx->stage_fji[p];
-  }
+  cudaStream_t si = ctx->copy_in, so = ctx->copy_out;
+  // Two frames in flight: the inputs of frame t + 1 copy in on `si` and the
+  // panorama of frame t - 1 copies out on `so` while frame t computes on `s`.
+  // A slot's inputs are rewritten only after the frame that read them has
+  // computed, and its panorama only after the previous copy-out has finished.
+  // On an error the three streams are drained before returning, so that no
+  // copy of this call is still in flight at the next one.
+  auto fail = [&](int rc) {
+    cudaStreamSynchronize(si);
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(so);
+    return rc;
+  };
   for (int t = 0; t < n_frames; ++t) {
+    HostStage &hs = ctx->stage[t & 1];
+    if (t >= 2) e = cudaStreamWaitEvent(si, hs.computed, 0);
     for (int k = 0; k < n && e == cudaSuccess; ++k)
-      e = cudaMemcpyAsync(ctx->stage_frames[k], frames_host[(size_t)t * n + k], (size_t)g.pitch[k] * g.h[k],
-                          cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(hs.frames[k], frames_host[(size_t)t * n + k], (size_t)g.pitch[k] * g.h[k],
+                          cudaMemcpyHostToDevice, si);
     for (int p = 0; p < np && e == cudaSuccess; ++p) {
-      e = cudaMemcpyAsync(ctx->stage_fij[p], flow_ij_host[(size_t)t * np + p], band_elems(g, p) * 8,
-                          cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(hs.fij[p], flow_ij_host[(size_t)t * np + p], band_elems(g, p) * 8,
+                          cudaMemcpyHostToDevice, si);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->stage_fji[p], flow_ji_host[(size_t)t * np + p], band_elems(g, p) * 8,
-                            cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(hs.fji[p], flow_ji_host[(size_t)t * np + p], band_elems(g, p) * 8,
+                            cudaMemcpyHostToDevice, si);
     }
-    if (e != cudaSuccess) return cuda_err(ctx, e, "host-to-device copy");
+    if (e == cudaSuccess) e = cudaEventRecord(hs.in_ready, si);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hs.in_ready, 0);
+    if (e == cudaSuccess && t >= 2) e = cudaStreamWaitEvent(s, hs.out_done, 0);
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "host-to-device copy"));
+    const uint8_t *fr[kMaxCams];
+    const float *fi[kMaxPairs], *fj[kMaxPairs];
+    for (int k = 0; k < n; ++k) fr[k] = hs.frames[k];
+    for (int p = 0; p < np; ++p) {
+      fi[p] = hs.fij[p];
+      fj[p] = hs.fji[p];
+    }
     int rc = launch_estimate_color(ctx, fr, s);
-    if (rc == STITCH_OK) rc = launch_frame(ctx, fr, fi, fj, ctx->stage_pano, s);
-    if (rc != STITCH_OK) return rc;
-    e = cudaMemcpyAsync(pano_host[t], ctx->stage_pano, pano_bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_err(ctx, e, "device-to-host copy");
+    if (rc == STITCH_OK) rc = launch_frame(ctx, fr, fi, fj, hs.pano, s);
+    if (rc != STITCH_OK) return fail(rc);
+    e = cudaEventRecord(hs.computed, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(so, hs.computed, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pano_host[t], hs.pano, pano_bytes, cudaMemcpyDeviceToHost, so);
+    if (e == cudaSuccess) e = cudaEventRecord(hs.out_done, so);
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "device-to-host copy"));
   }
+  // Join the copy-out stream back into `stream`.
+  for (int q = 0; q < 2 && q < n_frames && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(s, ctx->stage[q].out_done, 0);
+  if (e != cudaSuccess) return fail(cuda_err(ctx, e, "stream join"));
   return stitch_sync(ctx, stream);
 }
 
@@ -1906,12 +1948,19 @@ void stitch_destroy(stitch_ctx *ctx) {
   cudaFree(ctx->tiles);
   cudaFree(ctx->pw_tiles);
   cudaFree(ctx->pw);
-  for (int k = 0; k < kMaxCams; ++k) cudaFree(ctx->stage_frames[k]);
-  for (int p = 0; p < kMaxPairs; ++p) {
-    cudaFree(ctx->stage_fij[p]);
-    cudaFree(ctx->stage_fji[p]);
+  for (HostStage &hs : ctx->stage) {
+    for (int k = 0; k < kMaxCams; ++k) cudaFree(hs.frames[k]);
+    for (int p = 0; p < kMaxPairs; ++p) {
+      cudaFree(hs.fij[p]);
+      cudaFree(hs.fji[p]);
+    }
+    cudaFree(hs.pano);
+    if (hs.in_ready) cudaEventDestroy(hs.in_ready);
+    if (hs.computed) cudaEventDestroy(hs.computed);
+    if (hs.out_done) cudaEventDestroy(hs.out_done);
   }
-  cudaFree(ctx->stage_pano);
+  if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+  if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
   delete ctx;
 }
 

@@ -169,21 +169,30 @@ def test_sequence_graph_matches_per_call():
     assert pa.st.color()[3] == pb.st.color()[3] == 8
 
 
-def test_sequence_host_matches_device():
+@pytest.mark.parametrize("pinned", [True, False])
+def test_sequence_host_matches_device(pinned):
+    """The host-memory path keeps two frames in flight over two staging slots:
+    seven distinct frames in two calls (3 + 4) reuse each slot several times
+    and must give the device path's panoramas exactly."""
+    n = 7
     pa = Pair("2x640x360", seed=5)
     pb = Pair("2x640x360", seed=5)
-    ins = [pa.inputs(t) for t in range(3)]
+    ins = [pa.inputs(t) for t in range(n)]
     ref = []
     for fr, fij, fji in ins:
         pa.st.estimate_color(fr)
         ref.append(pa.st.frame(fr, fij, fji).cpu())
-    frames = [f.cpu().pin_memory() for fr, _, _ in ins for f in fr]
-    fij = [f.cpu().pin_memory() for _, fi, _ in ins for f in fi]
-    fji = [f.cpu().pin_memory() for _, _, fj in ins for f in fj]
-    outs = [torch.zeros_like(r).pin_memory() for r in ref]
-    S.stitch_sequence_host(pb.st.ctx, 3, frames, fij, fji, outs)
+    host = (lambda x: x.cpu().pin_memory()) if pinned else (lambda x: x.cpu().clone())
+    frames = [host(f) for fr, _, _ in ins for f in fr]
+    fij = [host(f) for _, fi, _ in ins for f in fi]
+    fji = [host(f) for _, _, fj in ins for f in fj]
+    outs = [host(torch.zeros_like(r)) for r in ref]
+    nc, npair = len(ins[0][0]), len(ins[0][1])
+    S.stitch_sequence_host(pb.st.ctx, 3, frames[:3 * nc], fij[:3 * npair], fji[:3 * npair], outs[:3])
+    S.stitch_sequence_host(pb.st.ctx, 4, frames[3 * nc:], fij[3 * npair:], fji[3 * npair:], outs[3:])
     for a, b in zip(ref, outs):
         assert torch.equal(a, b)
+    assert pb.st.color()[3] == n
 
 
 def test_save_and_load_state_resume_identically():
