@@ -29,6 +29,10 @@ import sys
 import threading
 import time
 
+# numpy's bundled OpenBLAS reads this when numpy is first imported (bench.py
+# imports numpy lazily): the oracle's timings are of one host core.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -212,16 +216,45 @@ def traffic_from_profile(workload):
 # --------------------------------------------------------------------------- #
 # CPU baseline / reference arm: the FP64 oracle, as it stands
 # --------------------------------------------------------------------------- #
+def host_link_gbs(dev, stream, mib=256, reps=5):
+    """Pinned host <-> device copy bandwidth of one large cudaMemcpyAsync per
+    direction (CUDA events on the copying stream), the bound of any
+    host-buffer path."""
+    import torch
+    h = torch.empty(mib << 20, dtype=torch.uint8).pin_memory()
+    d = torch.empty(mib << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("h2d_gbs", lambda: d.copy_(h, non_blocking=True)),
+                         ("d2h_gbs", lambda: h.copy_(d, non_blocking=True))):
+            fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            out[name] = reps * (mib << 20) / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del h, d
+    return out
+
+
 def one_thread():
     """Context that holds numpy's BLAS / OpenMP pools to one thread, so that
-    the oracle's timing is that of one host core."""
-    from threadpoolctl import threadpool_limits
+    the oracle's timing is that of one host core (threadpoolctl when it is
+    installed; otherwise OPENBLAS_NUM_THREADS, set above, does it)."""
+    import contextlib
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        return contextlib.nullcontext()
     return threadpool_limits(limits=1)
 
 
 def oracle_frames(wl, frame_ids, keep=False, flags=0):
     """Run the oracle on the given frames; returns (seconds, output pixels,
-    [(planes, near-edge mask)] when keep)."""
+    [(planes, near-edge mask)] when keep, process CPU seconds)."""
     from oracle.pipeline import OracleStitcher
     rig, seq = wl["rig"], wl["seq"]
     ex = rig.extra or {}
@@ -231,6 +264,7 @@ def oracle_frames(wl, frame_ids, keep=False, flags=0):
              [f.cpu().numpy() for f in wl["fji"][t]]) for t in frame_ids]
     outs = []
     with one_thread():
+        c0 = time.process_time()
         t0 = time.perf_counter()
         for fr, a, b in host:
             o.estimate_color(fr)
@@ -238,7 +272,8 @@ def oracle_frames(wl, frame_ids, keep=False, flags=0):
             if keep:
                 outs.append((planes, near))
         dt = time.perf_counter() - t0
-    return dt, len(frame_ids) * wl["pano_px"], outs
+        cpu = time.process_time() - c0
+    return dt, len(frame_ids) * wl["pano_px"], outs, cpu
 
 
 def oracle_check_rigs(items, n_samples=40000):
@@ -332,7 +367,8 @@ def run_reference(args, dist):
               f"{min(strips)}-{max(strips)} of its {H} rows (all {Wp} columns), strip time scaled to "
               f"{H} rows; {len(times)} timed steps over {n_gen} generated frames, {spent:.1f} s measured, "
               f"process CPU time / wall time {cpu_s / max(spent, 1e-9):.2f}")
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    cpu = {"value": value, "unit": UNIT, "cores": max(1, round(cpu_s / max(spent, 1e-9))), "kind": "oracle",
+           "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -599,6 +635,11 @@ def _run_ours(args, dist, ctxs):
     e2e_value = dist.world * n_e2e * wl["pano_px"] / e2e_s / 1e6
     h2d = n_e2e * (wl["in_bytes"] + wl["flow_bytes"])
     d2h = n_e2e * 3 * cfg.pitch * cfg.pano_h
+    link = host_link_gbs(dev, stream)
+    # the copies bound e2e: per frame, the larger of copy-in and copy-out time
+    frame_copy_s = max(h2d / n_e2e / (link["h2d_gbs"] * 1e9), d2h / n_e2e / (link["d2h_gbs"] * 1e9))
+    link["e2e_bound_mpix_s"] = dist.world * wl["pano_px"] / frame_copy_s / 1e6
+    link["e2e_frac_of_bound"] = e2e_value / link["e2e_bound_mpix_s"]
 
     extras = {}
     if dist.rank == 0 and dist.world == 1 and not args.no_extras:
@@ -617,10 +658,11 @@ def _run_ours(args, dist, ctxs):
     cpu_baseline = None
     err = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        dt, px, outs = oracle_frames(wl, [0, 1], keep=True)
-        cpu_baseline = {"value": px / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+        dt, px, outs, cpu_s = oracle_frames(wl, [0, 1], keep=True)
+        cpu_baseline = {"value": px / dt / 1e6, "unit": UNIT, "cores": max(1, round(cpu_s / dt)), "kind": "oracle",
                         "sample": f"frames 0-1 of the workload: estimate + full {wl['rig'].pano_w}x"
-                                  f"{wl['rig'].pano_h} panorama each, numpy float64, one thread"}
+                                  f"{wl['rig'].pano_h} panorama each, numpy float64, one thread (process CPU time / "
+                                  f"wall time {cpu_s / dt:.2f})"}
         # the same two frames from a fresh context, compared with the oracle's panoramas
         st3 = S.Stitcher(cfg)
         ctxs.append(st3)
@@ -640,7 +682,7 @@ def _run_ours(args, dist, ctxs):
             st4.estimate_color(wl["frames"][t])
             g16.append(st4.frame(wl["frames"][t], wl["fij"][t], wl["fji"][t]))
         torch.cuda.synchronize()
-        _, _, outs16 = oracle_frames(wl, [0, 1], keep=True, flags=S.STITCH_FP16_INTERMEDIATE)
+        _, _, outs16, _ = oracle_frames(wl, [0, 1], keep=True, flags=S.STITCH_FP16_INTERMEDIATE)
         err = {"fp32_intermediates": err, "fp16_intermediates": oracle_error(g16, outs16, cfg.pano_w)}
         if "_batched_check" in extras:
             err["batched_rigs_frame0"] = oracle_check_rigs(extras["_batched_check"])
@@ -673,7 +715,7 @@ def _run_ours(args, dist, ctxs):
                          "algorithmic_bytes_per_launch": fuse_bytes},
             "cpu_baseline": cpu_baseline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "frames_per_step": n_e2e},
+                    "frames_per_step": n_e2e, "host_link": link},
             "clocks": clk,
             "gpu_launches": launches,
         }
