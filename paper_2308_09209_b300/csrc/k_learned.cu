@@ -22,46 +22,40 @@ using namespace est;
 
 constexpr double kResidLimit = 1e-3;
 
+// One block per (pair, side, channel), one thread per bin: the float64
+// divisions spread over 6 blocks per pair instead of one (FP64 throughput is
+// low on this part). Each block also pools its side's channel 0 for the pixel
+// count.
 __global__ void __launch_bounds__(256) k_learned_features(const LearnedParams P) {
   const int p = blockIdx.x;
+  const int side = blockIdx.y / 3, ch = blockIdx.y % 3;
+  const int v = threadIdx.x;
   const int frame = P.state->T - 1;
   const int slot = frame % kMaxWindow;
   const RawStats *raw = P.raw + (frame % P.raw_slots);
   LearnedState *L = P.ls;
   const int nw = min(frame + 1, P.window);
-  __shared__ uint32_t H[2][768];
-  __shared__ unsigned long long n[2];
-  if (threadIdx.x < 2) n[threadIdx.x] = 0ull;
-  for (int i = threadIdx.x; i < 768; i += blockDim.x) {
-    const uint32_t hi = (&raw->Hi[p][0][0])[i], hj = (&raw->Hj[p][0][0])[i];
-    L->H_ring[slot][p][0][i] = hi;
-    L->H_ring[slot][p][1][i] = hj;
-    uint32_t si = hi, sj = hj;
-    for (int k = 1; k < nw; ++k) {
-      const int sl = (frame - k) % kMaxWindow;
-      si += L->H_ring[sl][p][0][i];
-      sj += L->H_ring[sl][p][1][i];
-    }
-    H[0][i] = si;
-    H[1][i] = sj;
+  const uint32_t *cur = side == 0 ? &raw->Hi[p][0][0] : &raw->Hj[p][0][0];
+  __shared__ unsigned long long part[8];
+  // window sums of bin v of this channel and of channel 0 (the count)
+  const int i = ch * 256 + v;
+  const uint32_t h = cur[i], h0 = cur[v];
+  L->H_ring[slot][p][side][i] = h;
+  uint32_t s = h, s0 = h0;
+  for (int k = 1; k < nw; ++k) {
+    const int sl = (frame - k) % kMaxWindow;
+    s += L->H_ring[sl][p][side][i];
+    s0 += L->H_ring[sl][p][side][v];
   }
+  const unsigned long long w = warp_sum((unsigned long long)s0);
+  if ((v & 31) == 0) part[v >> 5] = w;
   __syncthreads();
-  // pixel counts: the sum of channel 0 of each side (one warp per side)
-  const int warp = threadIdx.x >> 5;
-  if (warp < 2) {
-    unsigned long long s = 0ull;
-    for (int v = threadIdx.x & 31; v < 256; v += 32) s += H[warp][v];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) n[warp] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 1536; i += blockDim.x) {
-    const int side = i / 768;
-    const unsigned long long c = n[side];
-    // (H * 256) / n in float64, then float32, then bfloat16 (both round to nearest even)
-    const double f = c ? ((double)H[side][i % 768] * 256.0) / (double)c : 0.0;
-    L->feat[p][i] = __float2bfloat16_rn(__double2float_rn(f));
-  }
+  unsigned long long c = 0ull;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) c += part[q];
+  // (H * 256) / n in float64, then float32, then bfloat16 (both round to nearest even)
+  const double f = c ? ((double)s * 256.0) / (double)c : 0.0;
+  L->feat[p][side * 768 + i] = __float2bfloat16_rn(__double2float_rn(f));
 }
 
 __global__ void __launch_bounds__(256) k_learned_select(const LearnedParams P) {
@@ -137,7 +131,7 @@ __global__ void __launch_bounds__(256) k_learned_select(const LearnedParams P) {
 
 cudaError_t launch_learned_features(const LearnedParams &p, cudaStream_t s) {
   if (p.n_pairs <= 0) return cudaSuccess;
-  k_learned_features<<<p.n_pairs, 256, 0, s>>>(p);
+  k_learned_features<<<dim3(p.n_pairs, 6), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -132,22 +132,27 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_nt(const bf16 *__restrict
 
 // One layer for a small batch (at most 16 rows, e.g. the pairs of one rig at
 // inference): Y = act(X W^T + b). Block b owns output columns [8 b, 8 b + 8);
-// its four warps split K into four ranges and each runs one m16n8k16 tile
-// (rows >= batch read as zero) with fragments loaded straight from global
-// memory (X is a few KB and stays in L1; each k-step reads one 32-byte
-// sector of eight W rows). The four partial tiles are summed in a fixed order
-// in shared memory, so results do not depend on scheduling.
-constexpr int kSmallThreads = 128;
+// its sixteen warps split K into sixteen ranges and each runs one m16n8k16
+// tile (rows >= batch read as zero) with fragments loaded straight from
+// global memory (X is a few KB and stays in L1; each k-step reads one 32-byte
+// sector of eight W rows). With at most six k-steps per warp, all of a
+// block's weight loads are in flight at once: the layer costs about one
+// memory latency. The sixteen partial tiles are summed in a fixed order in
+// shared memory, so results do not depend on scheduling.
+constexpr int kSmallWarps = 16;
+constexpr int kSmallThreads = 32 * kSmallWarps;
 
 __global__ void __launch_bounds__(kSmallThreads) k_layer_small(const bf16 *__restrict__ X, int ldx, int batch,
                                                                  const bf16 *__restrict__ W, int N, int K,
                                                                  const float *__restrict__ bias, int mode, float *Cf,
-                                                                 int ldc, bf16 *Yb, int ldy) {
-  __shared__ float part[4][16][8];
+                                                                 int ldc, bf16 *Yb, int ldy,
+                                                                 const float *__restrict__ mu,
+                                                                 const float *__restrict__ sd, int n_used) {
+  __shared__ float part[kSmallWarps][16][8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
   const int n0 = blockIdx.x * 8;
-  const int ksteps = K / 16, per = (ksteps + 3) / 4;
+  const int ksteps = K / 16, per = (ksteps + kSmallWarps - 1) / kSmallWarps;
   const int k_lo = warp * per, k_hi = min(ksteps, k_lo + per);
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   const bool r0 = g < batch, r1 = g + 8 < batch;
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_layer_small(const bf16 *__res
   const uint32_t *xa = reinterpret_cast<const uint32_t *>(X + (size_t)g * ldx);
   const uint32_t *xb = reinterpret_cast<const uint32_t *>(X + (size_t)(g + 8) * ldx);
   const uint32_t *wr = reinterpret_cast<const uint32_t *>(W + (size_t)(n0 + g) * K);
-#pragma unroll 4
+#pragma unroll 6
   for (int ks = k_lo; ks < k_hi; ++ks) {
     const int c = (ks * 16) / 2 + t;            // 32-bit word of columns 2t, 2t+1 of this k-step
     uint32_t a[4];
@@ -173,12 +178,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_layer_small(const bf16 *__res
   part[warp][g + 8][2 * t] = acc[2];
   part[warp][g + 8][2 * t + 1] = acc[3];
   __syncthreads();
-  const int m = threadIdx.x >> 3, n = threadIdx.x & 7;   // 128 threads = 16 rows x 8 columns
-  if (m < batch && n0 + n < N) {
-    float v = ((part[0][m][n] + part[1][m][n]) + part[2][m][n]) + part[3][m][n];
+  const int m = threadIdx.x >> 3, n = threadIdx.x & 7;   // the first 128 threads: 16 rows x 8 columns
+  if (threadIdx.x < 128 && m < batch && n0 + n < N) {
+    float v = part[0][m][n];
+#pragma unroll
+    for (int w = 1; w < kSmallWarps; ++w) v += part[w][m][n];
     if (bias) v += bias[n0 + n];
     if (mode == 0) {
       Cf[(size_t)m * ldc + n0 + n] = v;
+    } else if (mode == 2) {
+      // denormalised output of the last layer: v sd + mu, columns below n_used
+      if (n0 + n < n_used) Cf[(size_t)m * ldc + n0 + n] = fmaf(v, sd[n0 + n], mu[n0 + n]);
     } else {
       Yb[(size_t)m * ldy + n0 + n] = __float2bfloat16_rn(fmaxf(v, 0.0f));
     }
@@ -278,7 +288,7 @@ __global__ void k_denorm(const float *__restrict__ y, int ldy, int batch, int n_
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= batch * n_out) return;
   const int b = i / n_out, n = i % n_out;
-  out[i] = y[(size_t)b * ldy + n] * sd[n] + mu[n];
+  out[i] = fmaf(y[(size_t)b * ldy + n], sd[n], mu[n]);
 }
 
 cudaError_t launch_gemm_nt(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias,
@@ -289,9 +299,12 @@ cudaError_t launch_gemm_nt(const bf16 *A, int lda, const bf16 *B, int ldb, int M
 }
 
 cudaError_t launch_layer_small(const bf16 *X, int ldx, int batch, const bf16 *W, int N, int K, const float *bias,
-                               int mode, float *Cf, int ldc, bf16 *Yb, int ldy, cudaStream_t s) {
+                               int mode, float *Cf, int ldc, bf16 *Yb, int ldy, const float *mu, const float *sd,
+                               int n_used, cudaStream_t s) {
   if (batch < 1 || batch > 16 || K % 16 != 0) return cudaErrorInvalidValue;
-  k_layer_small<<<(N + 7) / 8, kSmallThreads, 0, s>>>(X, ldx, batch, W, N, K, bias, mode, Cf, ldc, Yb, ldy);
+  if (mode == 2 && (!mu || !sd)) return cudaErrorInvalidValue;
+  k_layer_small<<<(N + 7) / 8, kSmallThreads, 0, s>>>(X, ldx, batch, W, N, K, bias, mode, Cf, ldc, Yb, ldy, mu, sd,
+                                                       n_used);
   return cudaGetLastError();
 }
 

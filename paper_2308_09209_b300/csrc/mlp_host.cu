@@ -20,7 +20,8 @@ cudaError_t launch_gemm_nt(const bf16 *A, int lda, const bf16 *B, int ldb, int M
                            int mode, float *Cf, int ldc, bf16 *Yb, int ldy, bf16 *Yt, int ldt, cudaStream_t s);
 cudaError_t launch_transpose_bf16(const bf16 *in, int rows, int cols, bf16 *out, cudaStream_t s);
 cudaError_t launch_layer_small(const bf16 *X, int ldx, int batch, const bf16 *W, int N, int K, const float *bias,
-                               int mode, float *Cf, int ldc, bf16 *Yb, int ldy, cudaStream_t s);
+                               int mode, float *Cf, int ldc, bf16 *Yb, int ldy, const float *mu, const float *sd,
+                               int n_used, cudaStream_t s);
 cudaError_t launch_mse(const float *y, int ldy, const float *t, int batch, int n_out, const float *mu, const float *sd,
                        bf16 *dz, bf16 *dzt, float *loss, cudaStream_t s);
 cudaError_t launch_relu_bwd(const float *dx, const bf16 *y, int batch, int n, bf16 *dz, bf16 *dzt, cudaStream_t s);
@@ -117,9 +118,14 @@ cudaError_t refresh_bf16(stitch_mlp *n, cudaStream_t s) {
   return e;
 }
 
-// Forward pass; the last layer's float32 output goes to n->yf (normalised units).
-cudaError_t forward(stitch_mlp *n, const bf16 *x, int batch, bool keep_xt, cudaStream_t s) {
+// Forward pass; the last layer's float32 output goes to n->yf (normalised
+// units). Inference on at most 16 rows with y_out given writes the
+// denormalised outputs [batch][12] to y_out directly instead (and sets
+// *denormed).
+cudaError_t forward(stitch_mlp *n, const bf16 *x, int batch, bool keep_xt, cudaStream_t s, float *y_out = nullptr,
+                    bool *denormed = nullptr) {
   cudaError_t e = cudaSuccess;
+  if (denormed) *denormed = false;
   if (keep_xt) e = launch_transpose_bf16(x, batch, kIn[0], n->xt, s);
   const bf16 *in = x;
   if (!keep_xt && batch <= 16) {
@@ -127,11 +133,17 @@ cudaError_t forward(stitch_mlp *n, const bf16 *x, int batch, bool keep_xt, cudaS
     for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
       const float *bias = n->p + n->off[l] + (size_t)kOut[l] * kIn[l];
       if (l < kLayers - 1)
-        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 1, nullptr, 0, n->y[l], kOut[l], s);
+        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 1, nullptr, 0, n->y[l], kOut[l],
+                               nullptr, nullptr, 0, s);
+      else if (y_out)
+        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 2, y_out, kOutUsed, nullptr, 0,
+                               n->norm, n->norm + 16, kOutUsed, s);
       else
-        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 0, n->yf, kOut[l], nullptr, 0, s);
+        e = launch_layer_small(in, kIn[l], batch, n->wb[l], kOut[l], kIn[l], bias, 0, n->yf, kOut[l], nullptr, 0,
+                               nullptr, nullptr, 0, s);
       in = n->y[l];
     }
+    if (e == cudaSuccess && y_out && denormed) *denormed = true;
     return e;
   }
   for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
@@ -305,8 +317,9 @@ int stitch_mlp_forward(stitch_mlp *n, const uint16_t *x_dev, int batch, float *y
   if (batch < 1 || batch > n->max_batch) return fail(STITCH_EINVAL, "batch out of range");
   if (reinterpret_cast<uintptr_t>(x_dev) & 15u) return fail(STITCH_EINVAL, "x must be 16-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = forward(n, reinterpret_cast<const bf16 *>(x_dev), batch, false, s);
-  if (e == cudaSuccess) e = launch_denorm(n->yf, 16, batch, kOutUsed, n->norm, n->norm + 16, y_dev, s);
+  bool denormed = false;
+  cudaError_t e = forward(n, reinterpret_cast<const bf16 *>(x_dev), batch, false, s, y_dev, &denormed);
+  if (e == cudaSuccess && !denormed) e = launch_denorm(n->yf, 16, batch, kOutUsed, n->norm, n->norm + 16, y_dev, s);
   return e == cudaSuccess ? STITCH_OK : fail(STITCH_ECUDA, cudaGetErrorString(e));
 }
 
