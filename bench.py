@@ -430,14 +430,14 @@ def run_extras(args, dev, stream, ctxs):
     panos = [torch.empty((3, w["cfg"].pano_h, w["cfg"].pitch), dtype=torch.uint8, device=dev)
              for _ in range(F) for w in wls]
     fr, fij, fji = _flat_seq(wls, F)
-    shape, ms_shapes = S.stitch_batch_autotune(b, fr[:sum(len(w["frames"][0]) for w in wls)],
+    shapes, ms_shapes = S.stitch_batch_autotune(b, fr[:sum(len(w["frames"][0]) for w in wls)],
                                                fij[:sum(len(w["fij"][0]) for w in wls)],
                                                fji[:sum(len(w["fji"][0]) for w in wls)], panos[:len(wls)], reps=3)
     ms_b = _time(lambda: S.stitch_batch_sequence(b, F, fr, fij, fji, panos, stream), stream, 5)
     alone = [S.Stitcher(w["cfg"]) for w in wls]
     ctxs.extend(alone)
-    for st in alone:
-        S.stitch_set_tile_shape(st.ctx, shape)
+    for st, sh in zip(alone, shapes):
+        S.stitch_set_tile_shape(st.ctx, sh)
     per = []
     for w, st in zip(wls, alone):
         pp = [torch.empty((3, w["cfg"].pano_h, w["cfg"].pitch), dtype=torch.uint8, device=dev) for _ in range(F)]
@@ -465,7 +465,8 @@ def run_extras(args, dev, stream, ctxs):
                                   fji=[f.cpu().numpy() for f in w["fji"][0]], pano=p.cpu().numpy())
                              for w, p in zip(wls, p0)]
     out["batched"] = {"rigs": list(BATCH_RIGS), "frames_per_step": F, "intermediate": "fp16",
-                      "tile_shape": S.TILE_SHAPES[shape], "autotune_ms": [round(float(m), 4) for m in ms_shapes],
+                      "tile_shapes": [S.TILE_SHAPES[sh] for sh in shapes],
+                      "autotune_ms": [[round(float(m), 4) for m in row] for row in ms_shapes],
                       "batched_mpix_s": px / (ms_b / 1e3) / 1e6, "one_rig_at_a_time_mpix_s": px / (ms_p / 1e3) / 1e6,
                       "speedup": ms_p / ms_b}
     S.stitch_batch_destroy(b)
@@ -504,7 +505,7 @@ def run_extras(args, dev, stream, ctxs):
     ctxs.append(full)
     S.stitch_attach_mlp(full.ctx, net.h)
     bf = S.stitch_batch_create([full.ctx])
-    shape, _ = S.stitch_batch_autotune(bf, fr[:8], a[:7], c[:7], pp[:1], reps=2)
+    shapes_full, _ = S.stitch_batch_autotune(bf, fr[:8], a[:7], c[:7], pp[:1], reps=2)
     ms_full = _time(lambda: S.stitch_batch_sequence(bf, F, fr, a, c, pp, stream), stream, 3)
     n_l, n_f = S.stitch_learned_stats(full.ctx)
     px = F * wl["pano_px"]
@@ -515,7 +516,7 @@ def run_extras(args, dev, stream, ctxs):
                           "plain_mpix_s": px / (ms_plain / 1e3) / 1e6,
                           "full_form_mpix_s": px / (ms_full / 1e3) / 1e6,
                           "full_form": "learned estimate with fallback, fp16 intermediates, batched launch, "
-                                       f"tile {S.TILE_SHAPES[shape]}",
+                                       f"tile {S.TILE_SHAPES[shapes_full[0]]}",
                           "learned_fallback_rate": n_f / max(n_l + n_f, 1),
                           "path_bytes_per_frame": wl["in_bytes"] + wl["flow_bytes"] + wl["out_bytes"]}
     S.stitch_batch_destroy(bf)

@@ -427,11 +427,13 @@ int stitch_tile_shape(const stitch_ctx *ctx, int *tile_w, int *tile_h);
  * two persistent fuse launches over the tiles of all rigs (band and partly
  * covered tiles, then the fully covered ones; blocks take tiles from a work
  * counter, band tiles first), recorded in a CUDA graph and
- * replayed like stitch_sequence. The paper stitches one rig; this is the
- * serving form. The contexts keep their own state and may still be used
- * alone between batch calls. All contexts must share the device and the
- * STITCH_FP16_INTERMEDIATE flag. The batch does not own the contexts:
- * destroy the batch first.
+ * replayed like stitch_sequence. Every rig's tiles keep that rig's own tile
+ * shape: at creation the shape recorded for the rig in a batched launch (see
+ * stitch_batch_autotune), else the shape its context runs with. The paper
+ * stitches one rig; this is the serving form. The contexts keep their own
+ * state and may still be used alone between batch calls. All contexts must
+ * share the device and the STITCH_FP16_INTERMEDIATE flag. The batch does not
+ * own the contexts: destroy the batch first.
  */
 #define STITCH_BATCH_MAX_RIGS 16
 typedef struct stitch_batch stitch_batch;
@@ -446,12 +448,22 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
                           const float *const *flow_ij_dev, const float *const *flow_ji_dev, uint8_t *const *pano_dev,
                           stitch_stream_t stream);
 
-/* The batch's own tile shape autotune over one frame of every rig (arrays as
- * stitch_batch_sequence with n_frames = 1); the panoramas are written.
- * Synchronous. */
+/* The batch's own tile-shape autotune over one frame of every rig (arrays as
+ * stitch_batch_sequence with n_frames = 1; the panoramas are written),
+ * one rig at a time: with the other rigs at their current shapes, both fuse
+ * launches of the batch are timed (`reps` times each) with every shape that
+ * fits rig r, and the fastest is kept before the next rig. The chosen shapes
+ * are recorded per rig like stitch_autotune's (process table and
+ * STITCH_TUNE_CACHE), under a key marked as batched. shapes_out (optional):
+ * one int per rig. ms_out (optional): n_rigs x STITCH_TILE_SHAPES floats,
+ * ms_out[r * STITCH_TILE_SHAPES + s] = mean ms of the batch's fuse launches
+ * with rig r at shape s, -1 where that shape does not fit. Synchronous. */
 int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
-                          const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shape_out,
+                          const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shapes_out,
                           float *ms_out);
+/* The batch's tile shape of every rig (n_rigs ints); returns n_rigs, or
+ * STITCH_EINVAL for a NULL argument. */
+int stitch_batch_tile_shapes(const stitch_batch *b, int *shapes_out);
 void stitch_batch_destroy(stitch_batch *b);
 const char *stitch_batch_last_error(const stitch_batch *b);
 

@@ -701,7 +701,10 @@ std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_file_read = false;
 
-std::string tune_key(const Geo &g, int flags) {
+// Cache key of a rig's tuned fuse tile shape: device, cameras, panorama,
+// bands, intermediate precision, and whether the rig runs alone or inside a
+// batched persistent launch (tuned separately).
+std::string tune_key(const Geo &g, int flags, bool batched = false) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceProp prop{};
@@ -719,6 +722,7 @@ std::string tune_key(const Geo &g, int flags) {
   k << "|" << g.pano_w << "x" << g.pano_h << "|";
   for (int p = 0; p + 1 < g.n; ++p) k << (g.band[p][1] - g.band[p][0]) << "x" << (g.band[p][3] - g.band[p][2]) << ",";
   k << "|fp16=" << ((flags & STITCH_FP16_INTERMEDIATE) ? 1 : 0);
+  if (batched) k << "|batched";
   return k.str();
 }
 
@@ -737,16 +741,16 @@ void tune_file_read_locked() {
   }
 }
 
-int tuned_shape(const Geo &g, int flags) {
-  const std::string key = tune_key(g, flags);
+int tuned_shape(const Geo &g, int flags, bool batched = false, int fallback = 0) {
+  const std::string key = tune_key(g, flags, batched);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_file_read_locked();
   const auto it = g_tune.find(key);
-  return it == g_tune.end() ? 0 : it->second;
+  return it == g_tune.end() ? fallback : it->second;
 }
 
-void tune_record(const Geo &g, int flags, int shape) {
-  const std::string key = tune_key(g, flags);
+void tune_record(const Geo &g, int flags, int shape, bool batched = false) {
+  const std::string key = tune_key(g, flags, batched);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_file_read_locked();
   g_tune[key] = shape;
@@ -1572,7 +1576,8 @@ struct BatchGraph {
 
 struct stitch_batch {
   std::vector<stitch_ctx *> ctx;
-  int shape = 0;
+  std::vector<int> shapes;            // fuse tile shape of every rig
+  int uniform = 0;                    // the common shape of all rigs, or -1 when they differ
   bool half = false;
   int cams = 0, pairs = 0;            // totals over the rigs
   std::vector<int> cam_off, pair_off;
@@ -1608,22 +1613,25 @@ void free_batch_graph(BatchGraph &g) {
   g.counters = nullptr;
 }
 
-// Work lists of the batch for a tile shape: every rig's band and partly
-// covered tiles (band tiles first, the costliest, so that the dynamic
+// Work lists of the batch for one tile shape per rig: every rig's band and
+// partly covered tiles (band tiles first, the costliest, so that the dynamic
 // schedule ends evenly), its fully covered own tiles (the one-camera kernel),
 // and its band pre-warp pieces.
-int batch_items(stitch_batch *b, int shape) {
+int batch_items(stitch_batch *b, const std::vector<int> &shapes) {
   std::vector<MultiItem> band, part, full, pw;
   std::string err;
   for (int r = 0; r < (int)b->ctx.size(); ++r) {
+    const int sh = shapes[r];
+    if (sh < 0 || sh >= kNumTileShapes) return batch_err(b, STITCH_EINVAL, "tile shape out of range");
     std::vector<TileDesc> bt, ot;
-    if (!build_tiles(b->ctx[r]->g, shape, bt, ot, err)) return batch_err(b, STITCH_EINVAL, err);
-    for (const TileDesc &t : bt) band.push_back(MultiItem{r, t, PwTile{}});
-    for (const TileDesc &t : ot) (t.kind == 0 ? full : part).push_back(MultiItem{r, t, PwTile{}});
+    if (!build_tiles(b->ctx[r]->g, sh, bt, ot, err)) return batch_err(b, STITCH_EINVAL, err);
+    for (const TileDesc &t : bt) band.push_back(MultiItem{r, sh, t, PwTile{}});
+    for (const TileDesc &t : ot) (t.kind == 0 ? full : part).push_back(MultiItem{r, sh, t, PwTile{}});
     const Geo &g = b->ctx[r]->g;
     for (int p = 0; p + 1 < g.n; ++p)
       for (int y = g.band[p][2]; y < g.band[p][3]; y += kTileH)
-        for (int x = g.band[p][0]; x < g.band[p][1]; x += kTileW) pw.push_back(MultiItem{r, TileDesc{}, PwTile{p, x, y}});
+        for (int x = g.band[p][0]; x < g.band[p][1]; x += kTileW)
+          pw.push_back(MultiItem{r, 0, TileDesc{}, PwTile{p, x, y}});
   }
   band.insert(band.end(), part.begin(), part.end());
   cudaFree(b->fuse_items);
@@ -1648,11 +1656,15 @@ int batch_items(stitch_batch *b, int shape) {
   int sms = 148, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, shape));
+  int uniform = shapes.empty() ? 0 : shapes[0];
+  for (int sh : shapes)
+    if (sh != uniform) uniform = -1;
+  const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, uniform));
   b->grid = std::max(1, std::min(b->n_fuse_items, per_sm * sms));
-  const int per_sm_own = std::max(1, fuse_own_multi_blocks_per_sm(shape));
+  const int per_sm_own = std::max(1, fuse_own_multi_blocks_per_sm(uniform));
   b->grid_own = std::max(1, std::min(b->n_own_items, per_sm_own * sms));
-  b->shape = shape;
+  b->shapes = shapes;
+  b->uniform = uniform;
   for (auto &g : b->graphs) free_batch_graph(g);
   b->graphs.clear();
   return STITCH_OK;
@@ -1705,8 +1717,12 @@ int stitch_batch_create(stitch_ctx *const *ctxs, int n_ctx, stitch_batch **out) 
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&b->pipe[i], cudaStreamNonBlocking);
   for (int a = 0; a < 4 && e == cudaSuccess; ++a)
     for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev[a][k], cudaEventDisableTiming);
-  int rc = e == cudaSuccess ? batch_items(b, ctxs[0]->shape) : batch_err(b, STITCH_ECUDA, cudaGetErrorString(e));
-  if (rc != STITCH_OK && ctxs[0]->shape != 0) rc = batch_items(b, 0);
+  // Each rig starts from its batched-launch shape in the tune cache, else the
+  // shape its own context runs with.
+  std::vector<int> sh(n_ctx, 0);
+  for (int r = 0; r < n_ctx; ++r) sh[r] = tuned_shape(ctxs[r]->g, ctxs[r]->flags, true, ctxs[r]->shape);
+  int rc = e == cudaSuccess ? batch_items(b, sh) : batch_err(b, STITCH_ECUDA, cudaGetErrorString(e));
+  if (rc != STITCH_OK && e == cudaSuccess) rc = batch_items(b, std::vector<int>(n_ctx, 0));
   if (rc != STITCH_OK) {
     const std::string m = b->err;
     stitch_batch_destroy(b);
@@ -1796,9 +1812,9 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
       chk(cudaMemsetAsync(bg.counters + 2 * t, 0, 2 * sizeof(int), sC));
       MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + 2 * t};
-      chk(launch_fuse_multi(mf, b->half, b->shape, b->grid, sC));
+      chk(launch_fuse_multi(mf, b->half, b->uniform, b->grid, sC));
       MultiParams mo{bg.params, t * R, b->n_own_items, b->own_items, bg.counters + 2 * t + 1};
-      chk(launch_fuse_own_multi(mo, b->shape, b->grid_own, sC));
+      chk(launch_fuse_own_multi(mo, b->uniform, b->grid_own, sC));
       chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
     chk(cudaEventRecord(ev[kS][0], sA));
@@ -1835,7 +1851,7 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
 }
 
 int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
-                          const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shape_out,
+                          const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shapes_out,
                           float *ms_out) {
   if (!b) return batch_err(nullptr, STITCH_EINVAL, "batch is NULL");
   if (reps < 1 || reps > 1000) return batch_err(b, STITCH_EINVAL, "reps must be in 1..1000");
@@ -1858,46 +1874,73 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  float ms[kNumTileShapes];
-  int best = -1;
-  const int keep = b->shape;
-  for (int sh = 0; sh < kNumTileShapes && e == cudaSuccess; ++sh) {
-    ms[sh] = -1.0f;
-    if (batch_items(b, sh) != STITCH_OK) continue;
+  // The band intermediates of the frame (they do not depend on the shapes).
+  if (e == cudaSuccess) {
     MultiParams pw{params, 0, b->n_pw_items, b->pw_items, nullptr};
     e = launch_prewarp_multi(pw, b->half, b->cap);
+  }
+  // Both fuse launches of the frame with the current work lists, timed.
+  auto timed = [&](float &ms) {
     MultiParams mf{params, 0, b->n_fuse_items, b->fuse_items, counter};
     MultiParams mo{params, 0, b->n_own_items, b->own_items, counter + 1};
     auto both = [&]() {
       cudaError_t x = cudaMemsetAsync(counter, 0, 2 * sizeof(int), b->cap);
-      if (x == cudaSuccess) x = launch_fuse_multi(mf, b->half, sh, b->grid, b->cap);
-      if (x == cudaSuccess) x = launch_fuse_own_multi(mo, sh, b->grid_own, b->cap);
+      if (x == cudaSuccess) x = launch_fuse_multi(mf, b->half, b->uniform, b->grid, b->cap);
+      if (x == cudaSuccess) x = launch_fuse_own_multi(mo, b->uniform, b->grid_own, b->cap);
       return x;
     };
-    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = both();
-    if (e == cudaSuccess) e = cudaEventRecord(e0, b->cap);
-    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = both();
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->cap);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    cudaError_t x = cudaSuccess;
+    for (int w = 0; w < 2 && x == cudaSuccess; ++w) x = both();
+    if (x == cudaSuccess) x = cudaEventRecord(e0, b->cap);
+    for (int k = 0; k < reps && x == cudaSuccess; ++k) x = both();
+    if (x == cudaSuccess) x = cudaEventRecord(e1, b->cap);
+    if (x == cudaSuccess) x = cudaEventSynchronize(e1);
     float t = 0.0f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-    if (e == cudaSuccess) {
-      ms[sh] = t / (float)reps;
-      if (best < 0 || ms[sh] < ms[best]) best = sh;
+    if (x == cudaSuccess) x = cudaEventElapsedTime(&t, e0, e1);
+    ms = t / (float)reps;
+    return x;
+  };
+  // One rig at a time (coordinate descent): try every shape for rig r with the
+  // other rigs at their current shapes, keep the fastest batch.
+  std::vector<int> cur = b->shapes;
+  std::vector<float> ms((size_t)R * kNumTileShapes, -1.0f);
+  for (int r = 0; r < R && e == cudaSuccess; ++r) {
+    int best = cur[r];
+    float best_ms = -1.0f;
+    for (int sh = 0; sh < kNumTileShapes && e == cudaSuccess; ++sh) {
+      std::vector<int> trial = cur;
+      trial[r] = sh;
+      if (batch_items(b, trial) != STITCH_OK) continue;   // a tile would touch two bands
+      float t = 0.0f;
+      e = timed(t);
+      if (e != cudaSuccess) break;
+      ms[(size_t)r * kNumTileShapes + sh] = t;
+      if (best_ms < 0.0f || t < best_ms) {
+        best_ms = t;
+        best = sh;
+      }
     }
+    cur[r] = best;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(params);
   cudaFree(counter);
-  const int chosen = best >= 0 ? best : keep;
-  const int rc = batch_items(b, chosen);
+  const int rc = batch_items(b, e == cudaSuccess ? cur : b->shapes);
   if (e != cudaSuccess) return batch_err(b, STITCH_ECUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
   if (rc != STITCH_OK) return rc;
-  if (shape_out) *shape_out = chosen;
+  for (int r = 0; r < R; ++r) tune_record(b->ctx[r]->g, b->ctx[r]->flags, cur[r], true);
+  if (shapes_out)
+    for (int r = 0; r < R; ++r) shapes_out[r] = cur[r];
   if (ms_out)
-    for (int sh = 0; sh < kNumTileShapes; ++sh) ms_out[sh] = ms[sh];
+    for (size_t i = 0; i < ms.size(); ++i) ms_out[i] = ms[i];
   return STITCH_OK;
+}
+
+int stitch_batch_tile_shapes(const stitch_batch *b, int *shapes_out) {
+  if (!b || !shapes_out) return batch_err(nullptr, STITCH_EINVAL, "batch and shapes_out are required");
+  for (size_t r = 0; r < b->shapes.size(); ++r) shapes_out[r] = b->shapes[r];
+  return (int)b->shapes.size();
 }
 
 void stitch_batch_destroy(stitch_batch *b) {

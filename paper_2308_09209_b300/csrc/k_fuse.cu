@@ -41,6 +41,8 @@
 // k_prewarp_multi / k_fuse_multi / k_fuse_own_multi: the same work over the
 // tiles of several independent rigs in one launch each; the fuse kernels are
 // persistent (one block per resident slot, tiles taken from a work counter).
+// When the rigs' tile shapes differ, the *_mixed forms run every tile with
+// its rig's shape.
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -748,9 +750,37 @@ __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParam
   prewarp_piece<kHalf>(sp, it.pw, s_win, sW);
 }
 
+// Shared memory of the persistent multi-rig kernels: room for any tile shape
+// (every rig's tiles use that rig's own shape).
+union MultiSmem {
+  FuseSmem<64, 32> s0;
+  FuseSmem<64, 16> s1;
+  FuseSmem<32, 32> s2;
+  FuseSmem<128, 16> s3;
+};
+union MultiOwnSmem {
+  FuseOwnSmem<64, 32> s0;
+  FuseOwnSmem<64, 16> s1;
+  FuseOwnSmem<32, 32> s2;
+  FuseOwnSmem<128, 16> s3;
+};
+
+// One tile of a multi-rig launch in its own call frame, so that each shape's
+// code gets its own register allocation inside the mixed-shape kernels.
+template <bool kHalf, int TW, int TH>
+__device__ __noinline__ void multi_tile(const FuseParams &P, const TileDesc t, FuseSmem<TW, TH> &sm) {
+  fuse_tile<kHalf, TW, TH>(P, t, sm);
+}
+template <int TW, int TH>
+__device__ __noinline__ void multi_own_tile(const FuseParams &P, const TileDesc t, FuseOwnSmem<TW, TH> &sm) {
+  fuse_own_tile<TW, TH>(P, t, sm);
+}
+
 // Persistent fuse over the tiles of several rigs: each block takes the next
 // item from a work counter until none is left (dynamic balance of uneven tile
 // costs), loading a rig's parameters into shared memory when the rig changes.
+// k_fuse_multi serves batches whose rigs share one tile shape;
+// k_fuse_multi_mixed runs every item with its rig's own shape.
 template <bool kHalf, int TW, int TH>
 __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi(const MultiParams M) {
   __shared__ FuseSmem<TW, TH> sm;
@@ -773,7 +803,35 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi(const MultiParam
   }
 }
 
-// Persistent fuse over the fully covered own tiles of several rigs.
+template <bool kHalf>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi_mixed(const MultiParams M) {
+  __shared__ MultiSmem sm;
+  __shared__ FuseParams sp;
+  __shared__ int s_item;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= M.n_items) break;
+    const MultiItem it = M.items[item];
+    if (it.rig != cur) {
+      copy_params(sp, M.params + M.base + it.rig);
+      cur = it.rig;
+    }
+    __syncthreads();
+    switch (it.shape) {
+      case 0: multi_tile<kHalf, 64, 32>(sp, it.tile, sm.s0); break;
+      case 1: multi_tile<kHalf, 64, 16>(sp, it.tile, sm.s1); break;
+      case 2: multi_tile<kHalf, 32, 32>(sp, it.tile, sm.s2); break;
+      default: multi_tile<kHalf, 128, 16>(sp, it.tile, sm.s3); break;
+    }
+    __syncthreads();
+  }
+}
+
+// Persistent fuse over the fully covered own tiles of several rigs (one shape
+// for all rigs, or each rig's own).
 template <int TW, int TH>
 __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi(const MultiParams M) {
   __shared__ FuseOwnSmem<TW, TH> sm;
@@ -796,6 +854,32 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi(const MultiP
   }
 }
 
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi_mixed(const MultiParams M) {
+  __shared__ MultiOwnSmem sm;
+  __shared__ FuseParams sp;
+  __shared__ int s_item;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= M.n_items) break;
+    const MultiItem it = M.items[item];
+    if (it.rig != cur) {
+      copy_params(sp, M.params + M.base + it.rig);
+      cur = it.rig;
+    }
+    __syncthreads();
+    switch (it.shape) {
+      case 0: multi_own_tile<64, 32>(sp, it.tile, sm.s0); break;
+      case 1: multi_own_tile<64, 16>(sp, it.tile, sm.s1); break;
+      case 2: multi_own_tile<32, 32>(sp, it.tile, sm.s2); break;
+      default: multi_own_tile<128, 16>(sp, it.tile, sm.s3); break;
+    }
+    __syncthreads();
+  }
+}
+
 size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
 
 cudaError_t fuse_setup_attributes(int) { return cudaSuccess; }
@@ -814,30 +898,11 @@ namespace {
 // The tiles that touch a band or are partly covered (k_fuse), then the fully
 // covered own tiles (k_fuse_own), in one stream.
 template <int TW, int TH>
-void fuse_by_half(const FuseParams &p, cudaStream_t s) {
-  const int mixed = p.n_tiles - p.n_full;
-  if (mixed > 0) {
-    if (p.flags & STITCH_FP16_INTERMEDIATE)
-      k_fuse<true, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
-    else
-      k_fuse<false, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
-  }
-  if (p.n_full > 0) k_fuse_own<TW, TH><<<p.n_full, kFuseThreads, 0, s>>>(p);
-}
-
-template <int TW, int TH>
 void fuse_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t s) {
   if (half)
     k_fuse_multi<true, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
   else
     k_fuse_multi<false, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
-}
-
-template <int TW, int TH>
-int occupancy_own() {
-  int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<TW, TH>, kFuseThreads, 0);
-  return n;
 }
 
 template <int TW, int TH>
@@ -849,6 +914,20 @@ int occupancy(bool half) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi<false, TW, TH>, kFuseThreads, 0);
   return n;
 }
+
+template <int TW, int TH>
+void fuse_by_half(const FuseParams &p, cudaStream_t s) {
+  const int mixed = p.n_tiles - p.n_full;
+  if (mixed > 0) {
+    if (p.flags & STITCH_FP16_INTERMEDIATE)
+      k_fuse<true, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
+    else
+      k_fuse<false, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
+  }
+  if (p.n_full > 0) k_fuse_own<TW, TH><<<p.n_full, kFuseThreads, 0, s>>>(p);
+}
+
+
 
 }  // namespace
 
@@ -881,6 +960,12 @@ cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s
 cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s) {
   if (m.n_items <= 0) return cudaSuccess;
   switch (shape) {
+    case -1:
+      if (half)
+        k_fuse_multi_mixed<true><<<grid, kFuseThreads, 0, s>>>(m);
+      else
+        k_fuse_multi_mixed<false><<<grid, kFuseThreads, 0, s>>>(m);
+      break;
     case 0: fuse_multi_by_half<64, 32>(m, half, grid, s); break;
     case 1: fuse_multi_by_half<64, 16>(m, half, grid, s); break;
     case 2: fuse_multi_by_half<32, 32>(m, half, grid, s); break;
@@ -893,6 +978,7 @@ cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int gr
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s) {
   if (m.n_items <= 0) return cudaSuccess;
   switch (shape) {
+    case -1: k_fuse_own_multi_mixed<<<grid, kFuseThreads, 0, s>>>(m); break;
     case 0: k_fuse_own_multi<64, 32><<<grid, kFuseThreads, 0, s>>>(m); break;
     case 1: k_fuse_own_multi<64, 16><<<grid, kFuseThreads, 0, s>>>(m); break;
     case 2: k_fuse_own_multi<32, 32><<<grid, kFuseThreads, 0, s>>>(m); break;
@@ -903,17 +989,28 @@ cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cud
 }
 
 int fuse_own_multi_blocks_per_sm(int shape) {
+  int n = 0;
   switch (shape) {
-    case 0: return occupancy_own<64, 32>();
-    case 1: return occupancy_own<64, 16>();
-    case 2: return occupancy_own<32, 32>();
-    case 3: return occupancy_own<128, 16>();
-    default: return 0;
+    case -1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi_mixed, kFuseThreads, 0); break;
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<64, 32>, kFuseThreads, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<64, 16>, kFuseThreads, 0); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<32, 32>, kFuseThreads, 0); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<128, 16>, kFuseThreads, 0); break;
+    default: break;
   }
+  return n;
 }
 
 int fuse_multi_blocks_per_sm(bool half, int shape) {
   switch (shape) {
+    case -1: {
+      int n = 0;
+      if (half)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi_mixed<true>, kFuseThreads, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi_mixed<false>, kFuseThreads, 0);
+      return n;
+    }
     case 0: return occupancy<64, 32>(half);
     case 1: return occupancy<64, 16>(half);
     case 2: return occupancy<32, 32>(half);

@@ -100,7 +100,7 @@ struct TileDesc {
   int16_t pad;
 };
 
-// One 64 x 16 piece of a band rectangle for the band pre-warp kernel.
+// One kTileW x kTileH piece of a band rectangle for the band pre-warp kernel.
 struct PwTile {
   int pair;
   int x0, y0;                         // panorama origin of the piece
@@ -132,6 +132,7 @@ struct alignas(16) FuseParams {
 // (or band pre-warp piece) with the parameters params[base + r].
 struct MultiItem {
   int rig;
+  int shape;                          // fuse items: the rig's tile shape (index into kTileShapes)
   TileDesc tile;                      // fuse items
   PwTile pw;                          // pre-warp items
 };
@@ -211,6 +212,8 @@ cudaError_t estimate_setup();
 cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s);
 cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s);
 cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s);
+// The persistent multi-rig fuse kernels: shape >= 0 when every rig uses that
+// tile shape, -1 to run every item with its MultiItem::shape.
 cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s);
 int fuse_multi_blocks_per_sm(bool half, int shape);
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);

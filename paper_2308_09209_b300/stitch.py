@@ -118,6 +118,7 @@ def lib():
             "stitch_batch_create": (ip, [pp, ip, ctypes.POINTER(vp)]),
             "stitch_batch_sequence": (ip, [vp, ip, pp, pp, pp, pp, vp]),
             "stitch_batch_autotune": (ip, [vp, pp, pp, pp, pp, ip, vp, vp]),
+            "stitch_batch_tile_shapes": (ip, [vp, vp]),
             "stitch_batch_destroy": (None, [vp]),
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
@@ -511,11 +512,22 @@ def stitch_batch_sequence(b, n_frames, frames, flows_ij, flows_ji, panos, stream
 
 
 def stitch_batch_autotune(b, frames, flows_ij, flows_ji, panos, reps: int = 5):
-    ms = np.zeros(STITCH_TILE_SHAPES, dtype=np.float32)
-    shape = ctypes.c_int(0)
+    """Per-rig tile shapes of the batch, tuned one rig at a time on one frame
+    (panos: one panorama per rig). Returns (shapes [n_rigs], ms [n_rigs, 4])."""
+    n = len(panos)
+    ms = np.zeros(n * STITCH_TILE_SHAPES, dtype=np.float32)
+    shapes = np.zeros(n, dtype=np.int32)
     _batch_check(lib().stitch_batch_autotune(b, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji), _ptrs(panos), reps,
-                                             ctypes.byref(shape), ms.ctypes.data), b)
-    return shape.value, ms
+                                             shapes.ctypes.data, ms.ctypes.data), b)
+    return [int(x) for x in shapes], ms.reshape(n, STITCH_TILE_SHAPES)
+
+
+def stitch_batch_tile_shapes(b):
+    """The batch's tile shape index of every rig."""
+    buf = np.zeros(STITCH_BATCH_MAX_RIGS, dtype=np.int32)
+    n = lib().stitch_batch_tile_shapes(b, buf.ctypes.data)
+    _batch_check(min(n, 0), b)
+    return [int(x) for x in buf[:n]]
 
 
 def stitch_batch_destroy(b) -> None:

@@ -89,9 +89,20 @@ def test_batch_equals_each_rig_alone(fp16):
             r["st"].close()
             r["cfg"].flags = S.STITCH_FP16_INTERMEDIATE
             r["st"] = S.Stitcher(r["cfg"])
+    # a different tile shape per rig: the persistent kernels run every rig's
+    # tiles with that rig's shape
+    want = []
+    for r, sh in zip(rigs, (2, 1, 3)):
+        try:
+            S.stitch_set_tile_shape(r["st"].ctx, sh)
+        except S.StitchError:
+            pass
+        want.append(S.stitch_tile_shape(r["st"].ctx)[0])
+    assert len(set(want)) >= 2
     for r in rigs:
         r["panos"] = [r["st"].new_pano() for _ in range(n_frames)]
     b = S.stitch_batch_create([r["st"].ctx for r in rigs])
+    assert S.stitch_batch_tile_shapes(b) == want
     fr, fij, fji, pano = _flat(rigs, n_frames)
     S.stitch_batch_sequence(b, n_frames, fr, fij, fji, pano)
     torch.cuda.synchronize()
@@ -127,8 +138,11 @@ def test_full_batch_against_the_oracle_on_sampled_pixels():
         r["panos"] = [r["st"].new_pano() for _ in range(n_frames)]
     b = S.stitch_batch_create([r["st"].ctx for r in rigs])
     fr, fij, fji, pano = _flat(rigs, 1)
-    shape, ms = S.stitch_batch_autotune(b, fr, fij, fji, pano, reps=2)
-    assert ms[shape] > 0
+    shapes, ms = S.stitch_batch_autotune(b, fr, fij, fji, pano, reps=2)
+    assert S.stitch_batch_tile_shapes(b) == shapes and ms.shape == (len(rigs), S.STITCH_TILE_SHAPES)
+    for r, sh in enumerate(shapes):
+        # every rig's chosen shape is its fastest fitting one (the other rigs at their shapes then)
+        assert ms[r, sh] > 0 and ms[r, sh] == ms[r][ms[r] > 0].min()
     fr, fij, fji, pano = _flat(rigs, n_frames)
     S.stitch_batch_sequence(b, n_frames, fr, fij, fji, pano)
     torch.cuda.synchronize()
