@@ -24,6 +24,8 @@ reordering beyond what the definition states. Modules:
 * ``warp``      -- pre-warp, optical-flow local warping and weighted-mean
   fusion (section 3.1, section 3.2, Eq. 15-18), per pixel.
 * ``pipeline``  -- the per-frame sequence with its temporal state.
+* ``refine``    -- homography refinement from the band flows (section 3.1,
+  Eq. 13-14, with the supplied flow fields in place of SURF matches).
 
 Parity pins: each function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force or a library routine (see each test
