@@ -169,6 +169,33 @@ int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *fr
                          uint8_t *const *pano_host, stitch_stream_t stream);
 
 /*
+ * stitch_refine_homographies -- revised camera homographies from one frame's
+ * band flows (section 3.1, Eq. 13-14: the skew matrix M and the scale matrix
+ * N, with the flow fields in place of SURF matches). Planar panoramas only.
+ *   flow_ij_dev / flow_ji_dev: n_pairs device pointers laid out as for
+ *       stitch_frame (band_w x band_h float2, 8-byte aligned); read only.
+ *   params_out (optional, host): n_pairs x 4 doubles (t_x, t_y, s_x, s_y),
+ *       the correction of the pair's camera farther from the reference:
+ *       q -> c + s (q - c) + t in panorama pixels, c the band centre
+ *       ((x0 + x1 - 1) / 2, (y0 + y1 - 1) / 2).
+ *   H_out (optional, host): n_cams x 9 doubles, row-major camera -> panorama
+ *       homographies C_k H_k, the corrections composed outward from the
+ *       reference camera (C_ref = I, C_k = C_(k+1) A_k to its left and
+ *       C_(k-1) A_(k-1) to its right); pass them to a new stitch_init.
+ * Per pair the left camera's content sits displaced by d = (median flow_ij -
+ * median flow_ji) / 2 against the right camera's and grows across the band by
+ * g = (median forward difference of flow_ij - the same of flow_ji) / 2 (x
+ * differences of x, y differences of y; float32 subtractions); the outer
+ * camera gets (t, s) = (-d, 1 - g) on the left of the reference and (+d, 1 + g)
+ * on its right. A median is the ((n - 1) / 2)-th smallest finite value, exact
+ * (radix selection on the GPU); with none it is 0. The context itself is not
+ * changed. Synchronous (waits for the device first). STITCH_EINVAL for a
+ * cylindrical context, fewer than two cameras or bad pointers.
+ */
+int stitch_refine_homographies(stitch_ctx *ctx, const float *const *flow_ij_dev, const float *const *flow_ji_dev,
+                               double *params_out, double *H_out);
+
+/*
  * stitch_sync -- wait for `stream`, then report (and clear) the device-side
  * condition word: STITCH_ESINGULAR if a colour fit kept its previous M since
  * the last report, else STITCH_OK.

@@ -2,6 +2,7 @@
 // geometry (paper section 2.1 step 1, section 3.1), device state, launches and
 // the C ABI declared in include/stitch.h.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1219,6 +1220,84 @@ int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *fr
   for (int q = 0; q < 2 && q < n_frames && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(s, ctx->stage[q].out_done, 0);
   if (e != cudaSuccess) return fail(cuda_err(ctx, e, "stream join"));
   return stitch_sync(ctx, stream);
+}
+
+int stitch_refine_homographies(stitch_ctx *ctx, const float *const *flow_ij_dev, const float *const *flow_ji_dev,
+                               double *params_out, double *H_out) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  const Geo &g = ctx->g;
+  const int np = g.n - 1;
+  if (np < 1) return set_err(ctx, STITCH_EINVAL, "refinement needs at least two cameras");
+  if (g.cyl) return set_err(ctx, STITCH_EINVAL, "refinement is defined for planar panoramas only");
+  if (!check_ptrs(reinterpret_cast<const void *const *>(flow_ij_dev), np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_dev), np))
+    return set_err(ctx, STITCH_EINVAL, "flow pointer arrays must be complete and non-NULL");
+  for (int p = 0; p < np; ++p)
+    if ((reinterpret_cast<uintptr_t>(flow_ij_dev[p]) | reinterpret_cast<uintptr_t>(flow_ji_dev[p])) & 7u)
+      return set_err(ctx, STITCH_EINVAL, "flows must be 8-byte aligned");
+  RefineParams rp{};
+  rp.n_pairs = np;
+  for (int p = 0; p < np; ++p) {
+    rp.fij[p] = reinterpret_cast<const float2 *>(flow_ij_dev[p]);
+    rp.fji[p] = reinterpret_cast<const float2 *>(flow_ji_dev[p]);
+    rp.bw[p] = g.band[p][1] - g.band[p][0];
+    rp.bh[p] = g.band[p][3] - g.band[p][2];
+  }
+  const int n_prob = 8 * np;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMalloc(&rp.state, n_prob * sizeof(RefineState));
+  if (e == cudaSuccess) e = cudaMalloc(&rp.hist, (size_t)n_prob * 256 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(rp.state, 0, n_prob * sizeof(RefineState));
+  if (e == cudaSuccess) e = cudaMemset(rp.hist, 0, (size_t)n_prob * 256 * sizeof(uint32_t));
+  for (int shift = 24; shift >= 0 && e == cudaSuccess; shift -= 8) e = launch_refine_pass(rp, shift, nullptr);
+  std::vector<RefineState> st(n_prob);
+  if (e == cudaSuccess) e = cudaMemcpy(st.data(), rp.state, n_prob * sizeof(RefineState), cudaMemcpyDeviceToHost);
+  cudaFree(rp.state);
+  cudaFree(rp.hist);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "refinement");
+  // The medians (0 where a statistic has no finite value).
+  std::vector<double> med(n_prob, 0.0);
+  for (int i = 0; i < n_prob; ++i) {
+    if (st[i].bad) return set_err(ctx, STITCH_EINVAL, "the flows changed during the refinement");
+    if (st[i].n == 0) continue;
+    const uint32_t key = st[i].prefix;
+    const uint32_t u = (key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key;
+    float v;
+    std::memcpy(&v, &u, 4);
+    med[i] = (double)v;
+  }
+  // Per pair: displacement d and growth g of the left content against the
+  // right; the outer camera's correction (t, s) about the band centre; then
+  // the corrections composed outward from the reference camera.
+  auto mul = [](const double *A, const double *B, double *C) {
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) C[r * 3 + c] = A[r * 3] * B[c] + A[r * 3 + 1] * B[3 + c] + A[r * 3 + 2] * B[6 + c];
+  };
+  std::vector<std::array<double, 9>> A(np);
+  for (int p = 0; p < np; ++p) {
+    const double *a = &med[8 * p], *b = &med[8 * p + 4];
+    const double dx = (a[0] - b[0]) / 2.0, dy = (a[1] - b[1]) / 2.0;
+    const double gx = (a[2] - b[2]) / 2.0, gy = (a[3] - b[3]) / 2.0;
+    const double sign = p < g.ref ? -1.0 : 1.0;
+    const double tx = sign * dx, ty = sign * dy, sx = 1.0 + sign * gx, sy = 1.0 + sign * gy;
+    const double cx = (g.band[p][0] + g.band[p][1] - 1) / 2.0, cy = (g.band[p][2] + g.band[p][3] - 1) / 2.0;
+    if (params_out) {
+      params_out[4 * p] = tx;
+      params_out[4 * p + 1] = ty;
+      params_out[4 * p + 2] = sx;
+      params_out[4 * p + 3] = sy;
+    }
+    const double M[9] = {1.0, 0.0, tx, 0.0, 1.0, ty, 0.0, 0.0, 1.0};                      // Eq. 13, skew
+    const double N[9] = {sx, 0.0, cx - sx * cx, 0.0, sy, cy - sy * cy, 0.0, 0.0, 1.0};      // scale about c
+    mul(M, N, A[p].data());
+  }
+  std::vector<std::array<double, 9>> C(g.n);
+  C[g.ref] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0};
+  for (int k = g.ref - 1; k >= 0; --k) mul(C[k + 1].data(), A[k].data(), C[k].data());
+  for (int k = g.ref + 1; k < g.n; ++k) mul(C[k - 1].data(), A[k - 1].data(), C[k].data());
+  if (H_out)
+    for (int k = 0; k < g.n; ++k) mul(C[k].data(), g.H[k], H_out + 9 * k);
+  return STITCH_OK;
 }
 
 int stitch_sync(stitch_ctx *ctx, stitch_stream_t stream) {

@@ -205,6 +205,24 @@ struct LearnedParams {
   LearnedState *ls;
 };
 
+// Homography refinement (k_refine.cu): radix-selection state of one median.
+struct RefineState {
+  uint32_t prefix, mask;              // key bits chosen so far
+  uint32_t k;                         // rank still wanted among the keys that match them
+  uint32_t n;                         // finite values
+  uint32_t bad;                       // counts changed between passes
+  uint32_t pad[3];
+};
+
+struct RefineParams {
+  const float2 *fij[kMaxPairs];
+  const float2 *fji[kMaxPairs];
+  int bw[kMaxPairs], bh[kMaxPairs];
+  int n_pairs;
+  RefineState *state;                 // [n_pairs * 8], zeroed before the first pass
+  uint32_t *hist;                     // [n_pairs * 8][256], zeroed before the first pass
+};
+
 // Launchers (defined in the kernel files).
 cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
@@ -219,6 +237,8 @@ int fuse_multi_blocks_per_sm(bool half, int shape);
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);
 int fuse_own_multi_blocks_per_sm(int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
+// One radix pass (key bits [shift, shift + 8)) of every band-flow median.
+cudaError_t launch_refine_pass(const RefineParams &p, int shift, cudaStream_t s);
 size_t stats_smem_bytes();
 size_t prewarp_elem_bytes(bool fp16);
 cudaError_t launch_learned_features(const LearnedParams &p, cudaStream_t s);

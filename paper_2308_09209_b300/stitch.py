@@ -119,6 +119,7 @@ def lib():
             "stitch_batch_sequence": (ip, [vp, ip, pp, pp, pp, pp, vp]),
             "stitch_batch_autotune": (ip, [vp, pp, pp, pp, pp, ip, vp, vp]),
             "stitch_batch_tile_shapes": (ip, [vp, vp]),
+            "stitch_refine_homographies": (ip, [vp, pp, pp, vp, vp]),
             "stitch_batch_destroy": (None, [vp]),
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
@@ -528,6 +529,17 @@ def stitch_batch_tile_shapes(b):
     n = lib().stitch_batch_tile_shapes(b, buf.ctypes.data)
     _batch_check(min(n, 0), b)
     return [int(x) for x in buf[:n]]
+
+
+def stitch_refine_homographies(ctx, flows_ij, flows_ji, n_cams: int):
+    """Refined camera -> panorama homographies (n_cams, 3, 3) and the per-pair
+    correction parameters (n_cams - 1, 4) = (t_x, t_y, s_x, s_y) from one
+    frame's band flows (device tensors, as for stitch_frame)."""
+    H = np.zeros((n_cams, 9), dtype=np.float64)
+    prm = np.zeros((max(n_cams - 1, 1), 4), dtype=np.float64)
+    _check(lib().stitch_refine_homographies(ctx, _ptrs(flows_ij), _ptrs(flows_ji), prm.ctypes.data, H.ctypes.data),
+           ctx)
+    return H.reshape(n_cams, 3, 3), prm[:n_cams - 1]
 
 
 def stitch_batch_destroy(b) -> None:
