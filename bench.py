@@ -213,6 +213,29 @@ def traffic_from_profile(workload):
     return int(m.group(1))
 
 
+def issue_from_profiles(workload):
+    """Warp instructions per frame of the whole path (k_stats, k_estimate,
+    k_prewarp_band, k_fuse, k_fuse_own) from the committed ncu summaries of
+    one capture, if none of their sources changed since (else None)."""
+    names = ("fuse", "stats", "estimate")
+    paths = [os.path.join(ROOT, "profiles", f"{n}_{workload}.md") for n in names]
+    if not all(os.path.exists(p) for p in paths):
+        return None
+    txt = open(paths[0]).read()
+    shas = dict(re.findall(r"(k_\w+\.cu) sha1:\s*([0-9a-f]+)", txt))
+    for src in ("k_fuse.cu", "k_stats.cu", "k_estimate.cu"):
+        f = os.path.join(ROOT, "paper_2308_09209_b300", "csrc", src)
+        if shas.get(src) != hashlib.sha1(open(f, "rb").read()).hexdigest():
+            return None
+    total = 0.0
+    for p in paths:
+        vals = re.findall(r"warp instructions \(`smsp__inst_executed\.sum`\) \| ([0-9.]+) inst", open(p).read())
+        if not vals:
+            return None
+        total += sum(float(v) for v in vals)
+    return total
+
+
 # --------------------------------------------------------------------------- #
 # CPU baseline / reference arm: the FP64 oracle, as it stands
 # --------------------------------------------------------------------------- #
@@ -615,6 +638,7 @@ def _run_ours(args, dist, ctxs):
     peak, peak_kind = measured_peaks()
     achieved = fuse_bytes / (warp_ms / 1e3) / 1e9
     traffic = traffic_from_profile(args.workload)
+    issue_instr = issue_from_profiles(args.workload)
     path_bytes = wl["in_bytes"] + wl["flow_bytes"] + wl["out_bytes"]
     path_gbs = F * path_bytes / (ms / 1e3) / 1e9
 
@@ -732,6 +756,19 @@ def _run_ours(args, dist, ctxs):
             "gpu_launches": launches,
         }
         line["config"].pop("_batched_check", None)
+        if issue_instr and clk and clk.get("sm_mhz"):
+            # The path is bound by instruction issue rather than HBM: warp
+            # instructions of all five kernels per frame (ncu, one capture of
+            # this workload) over the live frame time, against 148 SMs x 4
+            # schedulers x one warp instruction per clock at the sampled clock.
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak_issue = sms * 4 * clk["sm_mhz"] * 1e6
+            achieved_issue = issue_instr / (ms / F / 1e3)
+            line["config"]["issue"] = {"warp_instructions_per_frame": issue_instr,
+                                       "achieved_warp_inst_per_s": achieved_issue,
+                                       "peak_warp_inst_per_s": peak_issue, "frac": achieved_issue / peak_issue,
+                                       "source": "ncu smsp__inst_executed.sum per kernel from profiles/"
+                                                 f"{{fuse,stats,estimate}}_{args.workload}.md"}
         print(json.dumps(line), flush=True)
 
 
