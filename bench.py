@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=60)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-frames", type=int, default=16)
+    ap.add_argument("--tile-shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="fuse tile shape index (-1: the library's autotuner picks it)")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="reference arm: seconds of oracle work for all warm-up and timed steps together")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -213,15 +215,19 @@ def traffic_from_profile(workload):
     return int(m.group(1))
 
 
-def issue_from_profiles(workload):
+def issue_from_profiles(workload, tile):
     """Warp instructions per frame of the whole path (k_stats, k_estimate,
     k_prewarp_band, k_fuse, k_fuse_own) from the committed ncu summaries of
-    one capture, if none of their sources changed since (else None)."""
+    one capture, if none of their sources changed since and the capture ran
+    the fuse with the same tile shape (w, h) (else None)."""
     names = ("fuse", "stats", "estimate")
     paths = [os.path.join(ROOT, "profiles", f"{n}_{workload}.md") for n in names]
     if not all(os.path.exists(p) for p in paths):
         return None
     txt = open(paths[0]).read()
+    m = re.search(r"## k_fuse_own<(\d+), (\d+)>", txt)
+    if not m or (int(m.group(1)), int(m.group(2))) != tuple(tile):
+        return None
     shas = dict(re.findall(r"(k_\w+\.cu) sha1:\s*([0-9a-f]+)", txt))
     for src in ("k_fuse.cu", "k_stats.cu", "k_estimate.cu"):
         f = os.path.join(ROOT, "paper_2308_09209_b300", "csrc", src)
@@ -577,12 +583,16 @@ def _run_ours(args, dist, ctxs):
     fij = [f for fl in wl["fij"] for f in fl]
     fji = [f for fl in wl["fji"] for f in fl]
     # pick the fuse tile shape for this rig with the library's autotuner (one frame, outside the timed region)
-    S.stitch_estimate_color(st.ctx, wl["frames"][0], stream)
-    shape, shape_ms = S.stitch_autotune(st.ctx, wl["frames"][0], wl["fij"][0], wl["fji"][0], panos[0], reps=5)
+    shape_ms = []
+    if args.tile_shape < 0:
+        S.stitch_estimate_color(st.ctx, wl["frames"][0], stream)
+        shape, shape_ms = S.stitch_autotune(st.ctx, wl["frames"][0], wl["fij"][0], wl["fji"][0], panos[0], reps=5)
     st.close()
     ctxs.remove(st)
     st = S.Stitcher(cfg)                 # a fresh context with the tuned shape recorded for this rig
     ctxs.append(st)
+    if args.tile_shape >= 0:
+        S.stitch_set_tile_shape(st.ctx, args.tile_shape)
     torch.cuda.synchronize()
 
     def step():
@@ -638,7 +648,7 @@ def _run_ours(args, dist, ctxs):
     peak, peak_kind = measured_peaks()
     achieved = fuse_bytes / (warp_ms / 1e3) / 1e9
     traffic = traffic_from_profile(args.workload)
-    issue_instr = issue_from_profiles(args.workload)
+    issue_instr = issue_from_profiles(args.workload, S.stitch_tile_shape(st.ctx)[1])
     path_bytes = wl["in_bytes"] + wl["flow_bytes"] + wl["out_bytes"]
     path_gbs = F * path_bytes / (ms / 1e3) / 1e9
 
@@ -686,6 +696,8 @@ def _run_ours(args, dist, ctxs):
         for _ in range(10):
             S.stitch_refine_homographies(st.ctx, wl["fij"][0], wl["fji"][0], n_cams)
         band_px = int(sum(int(f.shape[0]) * int(f.shape[1]) for f in wl["fij"][0]))
+        from paper_2308_09209_b300.study import window_study
+        extras["window_study"] = window_study()
         extras["refine_homographies"] = {"ms_per_call": (time.perf_counter() - t0) / 10 * 1e3, "pairs": n_cams - 1,
                                          "band_px": band_px,
                                          "what": "8 exact medians per pair (radix selection, 4 passes), "

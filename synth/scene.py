@@ -104,8 +104,11 @@ def _photometric(rgb: torch.Tensor, gain, gamma, offset, cast) -> torch.Tensor:
 
 
 def render_camera_frames(rig, scene: Scene, t: int = 0, device="cpu",
-                         photometric=True, rows_per_chunk=540):
-    """Render every camera's frame at time t: a list of uint8 [h, w, 3] tensors."""
+                         photometric=True, rows_per_chunk=540, noise=0.0, noise_seed=0):
+    """Render every camera's frame at time t: a list of uint8 [h, w, 3] tensors.
+    noise > 0 adds seeded Gaussian sensor noise of that standard deviation
+    (grey levels) to the scene radiance of every pixel, drawn independently
+    per frame, camera and row chunk (seeded from noise_seed, t, k)."""
     frames = []
     for k in range(rig.n_cams):
         w, h = rig.cam_w[k], rig.cam_h[k]
@@ -129,6 +132,10 @@ def render_camera_frames(rig, scene: Scene, t: int = 0, device="cpu",
                 X = ((G[0, 0] * U + G[0, 1] * V + G[0, 2]) / den).float()
                 Y = ((G[1, 0] * U + G[1, 1] * V + G[1, 2]) / den).float()
             rgb = scene.render(X, Y, t)
+            if noise > 0:
+                gen = torch.Generator(device=device)
+                gen.manual_seed(((int(noise_seed) * 1000003 + int(t)) * 64 + k) * 4096 + r0 // rows_per_chunk)
+                rgb = rgb + float(noise) * torch.randn(rgb.shape, generator=gen, device=device, dtype=rgb.dtype)
             if photometric:
                 img[r0:r1] = _photometric(rgb, rig.gain[k], rig.gamma[k], rig.offset[k], rig.cast[k])
             else:

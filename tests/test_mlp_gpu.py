@@ -303,3 +303,16 @@ def test_learned_context_eight_cameras_and_state_round_trip():
     pa.st.close()
     pb.st.close()
     net.close()
+
+
+def test_temporal_window_study():
+    """The window study (Tables 2-3's comparison): finite figures for every
+    window, and the temporal window lowers M's frame-to-frame variation."""
+    ensure_built()
+    from paper_2308_09209_b300.study import window_study
+    r = window_study("2x640x360", windows=(1, 3), n_frames=10, seed=3)
+    a, b = r["per_window"]["1"], r["per_window"]["3"]
+    for v in (a, b):
+        assert np.isfinite(v["psnr_mu"]) and v["psnr_mu"] > 10 and np.isfinite(v["psnr_sigma"])
+    assert a["frames_used"] == 10 and b["frames_used"] == 8
+    assert b["sigma_M"] < a["sigma_M"]
