@@ -183,6 +183,9 @@ def evaluate_gain(net, config="2x640x360", seeds=(101, 102, 103, 104), n_frames=
     out = {k: dict(rms_colour_error=float(np.mean(v["err"])), sigma_M=float(np.mean(v["M"]))) for k, v in res.items()}
     out["plain"]["estimate_ms_per_frame"] = t_plain / max(n_est, 1)
     out["learned_used"]["estimate_ms_per_frame"] = t_learned / max(n_est, 1)
+    out["estimate_timing"] = ("GPU time between the stage events around each direct stitch_estimate_color call "
+                              "(one call per frame, so the gaps while the host launches the next kernel count: "
+                              "2 launches for the plain estimate, 8 for the learned one)")
     out["fallback_rate"] = n_f / max(n_l + n_f, 1)
     out["rigs"] = f"{len(seeds)} x {config}, {n_frames} frames each"
     return out
