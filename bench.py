@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--e2e-frames", type=int, default=16)
     ap.add_argument("--tile-shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="fuse tile shape index (-1: the library's autotuner picks it)")
-    ap.add_argument("--ref-budget", type=float, default=120.0,
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="reference arm: seconds of oracle work for all warm-up and timed steps together")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -353,7 +353,7 @@ def run_reference(args, dist):
     panorama on a strip of whole rows (computed pixel by pixel; the strip's
     output equals the same rows of its full-frame render), with the strip's
     time scaled to all rows. The strip height is set from the previous step's
-    timing so that all steps together take about --ref-budget seconds; frames
+    timing so that all steps together take about --ref-seconds seconds; frames
     cycle over at most four generated frames."""
     import numpy as np
     from oracle.pipeline import OracleStitcher
@@ -368,7 +368,7 @@ def run_reference(args, dist):
     host = [([f.numpy() for f in wl["frames"][t]], [f.numpy() for f in wl["fij"][t]],
              [f.numpy() for f in wl["fji"][t]]) for t in range(n_gen)]
     H, Wp = rig.pano_h, rig.pano_w
-    per_step = args.ref_budget / max(1, args.warmup + args.steps)
+    per_step = args.ref_seconds / max(1, args.warmup + args.steps)
     rows = min(H, 32)
     times, strips, spent, cpu_s = [], [], 0.0, 0.0
     pool = one_thread()
