@@ -26,6 +26,8 @@ reordering beyond what the definition states. Modules:
 * ``pipeline``  -- the per-frame sequence with its temporal state.
 * ``refine``    -- homography refinement from the band flows (section 3.1,
   Eq. 13-14, with the supplied flow fields in place of SURF matches).
+* ``flow``      -- optical flow between a pair's pre-warped images over its
+  blend band (section 3.2), a coarse-to-fine integer block matcher.
 
 Parity pins: each function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force or a library routine (see each test
