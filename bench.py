@@ -707,6 +707,13 @@ def _run_ours(args, dist, ctxs):
                                          "band_px": band_px,
                                          "what": "8 exact medians per pair (radix selection, 4 passes), "
                                                  "then the composed float64 homographies"}
+        # band optical flow of frame 0 (stream-ordered; CUDA events on the stream)
+        fl_ij = [torch.empty_like(f) for f in wl["fij"][0]]
+        fl_ji = [torch.empty_like(f) for f in wl["fji"][0]]
+        ms_flow = _time(lambda: S.stitch_estimate_flow(st.ctx, wl["frames"][0], fl_ij, fl_ji, stream), stream, 10, 2)
+        extras["estimate_flow"] = {"ms_per_frame": ms_flow, "pairs": n_cams - 1, "band_px": band_px,
+                                   "what": "float32 band pre-warp of both cameras, integer luminance, 3-level "
+                                           "7x7 block matching both ways, sub-pixel parabola"}
         # the temporal-window study (W = 1 vs 3 / 5 / 7), outside every timed region
         from paper_2308_09209_b300.study import window_study
         extras["window_study"] = window_study()

@@ -169,6 +169,29 @@ int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *fr
                          uint8_t *const *pano_host, stitch_stream_t stream);
 
 /*
+ * stitch_estimate_flow -- optical flow between the pre-warped images of every
+ * pair over its blend band (section 3.2), in the layout stitch_frame takes:
+ *   frames_dev:  n_cams device pointers (packed RGB, as for stitch_frame).
+ *   flow_ij_dev: n_pairs device pointers (8-byte aligned, band_w x band_h
+ *                float2), written: the left camera's pre-warped image sampled
+ *                at q + flow_ij(q) matches the right camera's at q.
+ *   flow_ji_dev: likewise, the right camera's image onto the left one's.
+ * Method (the paper leaves it to a library routine): both cameras are
+ * pre-warped over the band in float32 (the band pre-warp kernel, into the
+ * context's own buffer), reduced to integer luminance round((R + 2G + B) / 4),
+ * and matched coarse to fine over a 3-level 2 x 2 integer pyramid by the sum
+ * of absolute differences over 7 x 7 windows (coordinates clamped into the
+ * band): radius R = max(1, ceil(max_flow / 4)) at the coarsest level,
+ * 2 d + [-1, 1]^2 below, ties to the smaller |d - start|^2, then d_y, then
+ * d_x; a float32 parabola through the costs of the neighbours gives the
+ * sub-pixel step (at most half a pixel). Asynchronous on `stream`; calls on
+ * one context must be ordered by the caller. STITCH_EINVAL for fewer than two
+ * cameras, bad pointers or max_flow above 32 px.
+ */
+int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, float *const *flow_ij_dev,
+                         float *const *flow_ji_dev, stitch_stream_t stream);
+
+/*
  * stitch_refine_homographies -- revised camera homographies from one frame's
  * band flows (section 3.1, Eq. 13-14: the skew matrix M and the scale matrix
  * N, with the flow fields in place of SURF matches). Planar panoramas only.

@@ -460,6 +460,9 @@ struct stitch_ctx {
   std::vector<ProfPair> pending;      // pairs whose times the next stitch_profile_read sums
   std::vector<ProfPair> owned;        // per-call pairs, destroyed after they are read
   HostStage stage[2];                 // device staging of stitch_sequence_host, two frames in flight
+  float4 *flow_pw = nullptr;          // stitch_estimate_flow: float32 pre-warped bands
+  uint8_t *flow_Y = nullptr;          // its luminance pyramids
+  int16_t *flow_d = nullptr;          // its chosen displacements (dx then dy)
   cudaStream_t copy_in = nullptr;     // host-to-device copies of stitch_sequence_host
   cudaStream_t copy_out = nullptr;    // device-to-host copies of stitch_sequence_host
   int shape = 0;                      // fuse tile shape (index into kTileShapes)
@@ -1220,6 +1223,89 @@ int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *fr
   for (int q = 0; q < 2 && q < n_frames && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(s, ctx->stage[q].out_done, 0);
   if (e != cudaSuccess) return fail(cuda_err(ctx, e, "stream join"));
   return stitch_sync(ctx, stream);
+}
+
+int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, float *const *flow_ij_dev,
+                         float *const *flow_ji_dev, stitch_stream_t stream) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  const Geo &g = ctx->g;
+  const int np = g.n - 1;
+  if (np < 1) return set_err(ctx, STITCH_EINVAL, "flow needs at least two cameras");
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), g.n) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ij_dev), np) ||
+      !check_ptrs(reinterpret_cast<const void *const *>(flow_ji_dev), np))
+    return set_err(ctx, STITCH_EINVAL, "frame and flow pointer arrays must be complete and non-NULL");
+  for (int p = 0; p < np; ++p)
+    if ((reinterpret_cast<uintptr_t>(flow_ij_dev[p]) | reinterpret_cast<uintptr_t>(flow_ji_dev[p])) & 7u)
+      return set_err(ctx, STITCH_EINVAL, "flows must be 8-byte aligned");
+  const int radius = std::max(1, (int)std::ceil((double)ctx->max_flow / (double)(1 << (kFlowLevels - 1))));
+  if (radius > kFlowMaxRadius) return set_err(ctx, STITCH_EINVAL, "max_flow above 32 px is beyond the flow search");
+  // Level sizes and buffer layout.
+  FlowParams fl{};
+  fl.n_pairs = np;
+  size_t pw_elems = 0, y_bytes = 0, d_elems = 0;
+  for (int p = 0; p < np; ++p) {
+    int w = g.band[p][1] - g.band[p][0], h = g.band[p][3] - g.band[p][2];
+    fl.pw_off[p][0] = pw_elems;
+    fl.pw_off[p][1] = pw_elems + (size_t)w * h;
+    pw_elems += 2 * (size_t)w * h;
+    for (int l = 0; l < kFlowLevels; ++l) {
+      if (l > 0) {
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+      }
+      fl.lev[l].w[p] = w;
+      fl.lev[l].h[p] = h;
+      for (int k = 0; k < 2; ++k) {
+        fl.lev[l].y_off[p][k] = y_bytes;
+        y_bytes += (size_t)w * h;
+        fl.lev[l].d_off[p][k] = d_elems;
+        d_elems += (size_t)w * h;
+      }
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (!ctx->flow_pw) e = cudaMalloc(&ctx->flow_pw, pw_elems * sizeof(float4) + 16);
+  if (e == cudaSuccess && !ctx->flow_Y) e = cudaMalloc(&ctx->flow_Y, y_bytes + 16);
+  if (e == cudaSuccess && !ctx->flow_d) e = cudaMalloc(&ctx->flow_d, 2 * d_elems * sizeof(int16_t) + 16);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "flow buffers");
+  fl.pw = ctx->flow_pw;
+  fl.Y = ctx->flow_Y;
+  fl.dx = ctx->flow_d;
+  fl.dy = ctx->flow_d + d_elems;
+  for (int p = 0; p < np; ++p) {
+    fl.out_ij[p] = reinterpret_cast<float2 *>(flow_ij_dev[p]);
+    fl.out_ji[p] = reinterpret_cast<float2 *>(flow_ji_dev[p]);
+  }
+  // Candidates in the tie-break order: |e|^2, then e_y, then e_x.
+  auto order = [](int r, int8_t *out) {
+    std::vector<std::array<int, 2>> c;
+    for (int ey = -r; ey <= r; ++ey)
+      for (int ex = -r; ex <= r; ++ex) c.push_back({ex, ey});
+    std::stable_sort(c.begin(), c.end(), [](const std::array<int, 2> &a, const std::array<int, 2> &b) {
+      const int na = a[0] * a[0] + a[1] * a[1], nb = b[0] * b[0] + b[1] * b[1];
+      if (na != nb) return na < nb;
+      if (a[1] != b[1]) return a[1] < b[1];
+      return a[0] < b[0];
+    });
+    for (size_t i = 0; i < c.size(); ++i) {
+      out[2 * i] = (int8_t)c[i][0];
+      out[2 * i + 1] = (int8_t)c[i][1];
+    }
+    return (int)c.size();
+  };
+  fl.n_cand_top = order(radius, fl.cand_top);
+  order(1, fl.cand_fine);
+  // The float32 band pre-warp into the flow's own buffer, then the flow.
+  const float *none[kMaxPairs] = {};
+  FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
+  fp.flags &= ~STITCH_FP16_INTERMEDIATE;
+  fp.pw = ctx->flow_pw;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  e = launch_prewarp(fp, s);
+  if (e == cudaSuccess) e = launch_flow(fl, s);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "flow launch");
+  return STITCH_OK;
 }
 
 int stitch_refine_homographies(stitch_ctx *ctx, const float *const *flow_ij_dev, const float *const *flow_ji_dev,
@@ -2081,6 +2167,9 @@ void stitch_destroy(stitch_ctx *ctx) {
     if (hs.computed) cudaEventDestroy(hs.computed);
     if (hs.out_done) cudaEventDestroy(hs.out_done);
   }
+  cudaFree(ctx->flow_pw);
+  cudaFree(ctx->flow_Y);
+  cudaFree(ctx->flow_d);
   if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
   if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
   delete ctx;

@@ -2,6 +2,7 @@
 // public ABI). Layouts here are shared by the host code and the kernels.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -223,6 +224,30 @@ struct RefineParams {
   uint32_t *hist;                     // [n_pairs * 8][256], zeroed before the first pass
 };
 
+// Band optical flow (k_flow.cu): a coarse-to-fine block matcher over the
+// luminance of both cameras' pre-warped band images.
+constexpr int kFlowLevels = 3;
+constexpr int kFlowMaxRadius = 8;     // coarsest search radius: max_flow up to 32 px
+
+struct FlowLevelDev {
+  int w[kMaxPairs], h[kMaxPairs];     // level size of every band
+  size_t y_off[kMaxPairs][2];         // luminance of the left / right camera (bytes into Y)
+  size_t d_off[kMaxPairs][2];         // chosen displacements, direction 0 / 1 (elements into dx, dy)
+};
+
+struct FlowParams {
+  int n_pairs;
+  FlowLevelDev lev[kFlowLevels];
+  const float4 *pw;                   // float32 pre-warped bands (layout of FuseParams::pw)
+  size_t pw_off[kMaxPairs][2];
+  uint8_t *Y;
+  int16_t *dx, *dy;
+  float2 *out_ij[kMaxPairs], *out_ji[kMaxPairs];
+  int n_cand_top;                     // candidates of the coarsest level, in tie-break order
+  int8_t cand_top[2 * (2 * kFlowMaxRadius + 1) * (2 * kFlowMaxRadius + 1)];
+  int8_t cand_fine[18];               // the 3 x 3 refinement, in tie-break order
+};
+
 // Launchers (defined in the kernel files).
 cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
@@ -237,6 +262,8 @@ int fuse_multi_blocks_per_sm(bool half, int shape);
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);
 int fuse_own_multi_blocks_per_sm(int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
+// Every level of the band flow of every pair, both directions.
+cudaError_t launch_flow(const FlowParams &p, cudaStream_t s);
 // One radix pass (key bits [shift, shift + 8)) of every band-flow median.
 cudaError_t launch_refine_pass(const RefineParams &p, int shift, cudaStream_t s);
 size_t stats_smem_bytes();

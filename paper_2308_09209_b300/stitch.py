@@ -120,6 +120,7 @@ def lib():
             "stitch_batch_autotune": (ip, [vp, pp, pp, pp, pp, ip, vp, vp]),
             "stitch_batch_tile_shapes": (ip, [vp, vp]),
             "stitch_refine_homographies": (ip, [vp, pp, pp, vp, vp]),
+            "stitch_estimate_flow": (ip, [vp, pp, pp, pp, vp]),
             "stitch_batch_destroy": (None, [vp]),
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
@@ -529,6 +530,12 @@ def stitch_batch_tile_shapes(b):
     n = lib().stitch_batch_tile_shapes(b, buf.ctypes.data)
     _batch_check(min(n, 0), b)
     return [int(x) for x in buf[:n]]
+
+
+def stitch_estimate_flow(ctx, frames, flows_ij, flows_ji, stream=None) -> None:
+    """Band optical flow of one frame into the caller's float32 [bh, bw, 2]
+    device tensors flows_ij / flows_ji (one per pair)."""
+    _check(lib().stitch_estimate_flow(ctx, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji), _stream(stream)), ctx)
 
 
 def stitch_refine_homographies(ctx, flows_ij, flows_ji, n_cams: int):

@@ -1,0 +1,78 @@
+"""GPU parity of the band optical flow (stitch_estimate_flow; section 3.2)
+against the oracle (oracle/flow.py) on the same frames.
+
+Bar: every cost is an integer, so a pixel's flow is identical on both sides
+whenever the two luminance pyramids agree inside its matching windows. The
+luminance differs only where the float32 pre-warp and the float64 one fall on
+opposite sides of a rounding midpoint (a few pixels in 10^4), and each such
+pixel touches the windows of a small neighbourhood, so at least 99 % of the
+band pixels must carry bit-identical flows; the remaining ones must still be
+within the search reach."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.flow import pair_flows
+from paper_2308_09209_b300 import stitch as S
+
+from gpu_common import Pair, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+FRAC_IDENTICAL = 0.99
+
+
+def _gpu_flows(pr, frames):
+    fij, fji = [], []
+    for x0, x1, y0, y1 in pr.st.bands.tolist():
+        fij.append(torch.full((y1 - y0, x1 - x0, 2), float("nan"), dtype=torch.float32, device="cuda"))
+        fji.append(torch.full((y1 - y0, x1 - x0, 2), float("nan"), dtype=torch.float32, device="cuda"))
+    S.stitch_estimate_flow(pr.st.ctx, frames, fij, fji)
+    torch.cuda.synchronize()
+    return [f.cpu().numpy() for f in fij], [f.cpu().numpy() for f in fji]
+
+
+@pytest.mark.parametrize("config,seed", [("2x640x360", 0), ("4x640x360cyl", 1)])
+def test_flow_matches_the_oracle(config, seed):
+    pr = Pair(config, seed=seed)
+    frames, _, _ = pr.inputs(2)
+    gij, gji = _gpu_flows(pr, frames)
+    oij, oji = pair_flows([f.cpu().numpy() for f in frames], pr.oracle.geom, pr.seq["max_flow"])
+    reach = 4 * max(1, int(np.ceil(pr.seq["max_flow"] / 4))) + 2 + 1 + 0.5
+    for g, o in zip(gij + gji, oij + oji):
+        assert g.shape == o.shape and np.all(np.isfinite(g))
+        same = np.all(g == o, axis=2)
+        assert same.mean() >= FRAC_IDENTICAL, same.mean()
+        assert np.all(np.abs(g) <= reach)
+    pr.st.close()
+
+
+def test_flow_feeds_the_stitch():
+    """Estimated flows drive stitch_frame like supplied ones; the same call
+    twice gives the same flows."""
+    pr = Pair("2x640x360", seed=3)
+    frames, _, _ = pr.inputs(0)
+    a = _gpu_flows(pr, frames)
+    b = _gpu_flows(pr, frames)
+    assert all(np.array_equal(x, y) for x, y in zip(a[0] + a[1], b[0] + b[1]))
+    fij = [torch.from_numpy(f).cuda() for f in a[0]]
+    fji = [torch.from_numpy(f).cuda() for f in a[1]]
+    pr.st.estimate_color(frames)
+    pano = pr.st.frame(frames, fij, fji)
+    torch.cuda.synchronize()
+    assert pano.shape[0] == 3 and int(pano.max()) > 0
+    pr.st.close()
+
+
+def test_flow_argument_errors():
+    ensure_built()
+    pr = Pair("2x640x360", seed=0)
+    frames, fij, fji = pr.inputs(0)
+    with pytest.raises(S.StitchError):
+        S.stitch_estimate_flow(pr.st.ctx, frames, [0], fji)
+    bad = torch.empty(fij[0].numel() * 4 + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.StitchError):
+        S.stitch_estimate_flow(pr.st.ctx, frames, [bad.data_ptr() + 4], fji)
+    with pytest.raises(S.StitchError):
+        S.stitch_estimate_flow(pr.st.ctx, frames[:1] + [0], fij, fji)
+    pr.st.close()
