@@ -1303,7 +1303,7 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   fp.pw = ctx->flow_pw;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   e = launch_prewarp(fp, s);
-  if (e == cudaSuccess) e = launch_flow(fl, s);
+  if (e == cudaSuccess) e = launch_flow(fl, radius, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "flow launch");
   return STITCH_OK;
 }

@@ -19,7 +19,8 @@
 //               the denominator is positive, clamped to [-0.5, 0.5]); the
 //               flow is float(d) + off.
 //
-// One thread per pixel; blockIdx.y is (pair, camera) or (pair, direction):
+// One thread per pixel (the matcher: 32 x 8 pixel tiles with both images
+// staged in shared memory); blockIdx.y is (pair, camera) or (pair, direction):
 // direction 0 moves the left camera onto the right one (flow_ij), 1 the
 // right onto the left (flow_ji). All costs are integers, so the chosen
 // displacements follow from the luminance images alone.
@@ -33,23 +34,6 @@ constexpr int kFlowThreads = 256;
 constexpr int kWin = 3;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-__device__ __forceinline__ int window_cost(const uint8_t *__restrict__ A, const uint8_t *__restrict__ B, int w, int h,
-                                           int x, int y, int dx, int dy) {
-  int c = 0;
-#pragma unroll
-  for (int oy = -kWin; oy <= kWin; ++oy) {
-    const uint8_t *ra = A + (size_t)clampi(y + dy + oy, 0, h - 1) * w;
-    const uint8_t *rb = B + (size_t)clampi(y + oy, 0, h - 1) * w;
-#pragma unroll
-    for (int ox = -kWin; ox <= kWin; ++ox) {
-      const int a = __ldg(ra + clampi(x + dx + ox, 0, w - 1));
-      const int b = __ldg(rb + clampi(x + ox, 0, w - 1));
-      c += abs(a - b);
-    }
-  }
-  return c;
-}
 
 __global__ void __launch_bounds__(kFlowThreads) k_flow_luma(const FlowParams P) {
   const int pair = blockIdx.y >> 1, side = blockIdx.y & 1;
@@ -78,38 +62,96 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_down(const FlowParams P, 
   }
 }
 
-__global__ void __launch_bounds__(kFlowThreads) k_flow_match(const FlowParams P, int lev) {
+// Shared-memory tiles of the matcher: a 32 x 8 block of pixels, the target
+// image over the block plus the window's reach, and the moving image over
+// the block plus the window and the largest displacement the level can
+// test. Both are loaded with the same clamped coordinates as the plain
+// definition, so a tile read equals the clamped image read it replaces.
+constexpr int kTX = 32, kTY = 8;
+constexpr int kReach0 = 4 * kFlowMaxRadius + 2 + 1 + 1;   // |d| at the finest level, plus the sub-pixel neighbours
+constexpr int kHaloA = kWin + kReach0;
+constexpr int kAW = kTX + 2 * kHaloA, kAH = kTY + 2 * kHaloA;
+constexpr int kBW = kTX + 2 * kWin, kBH = kTY + 2 * kWin;
+
+struct MatchTile {
+  uint8_t a[kAH][kAW];
+  uint8_t b[kBH][kBW];
+};
+
+// Load the tiles of block (bx0, by0) with halo `ha` for the moving image.
+__device__ __forceinline__ void load_tiles(MatchTile &T, const uint8_t *__restrict__ A, const uint8_t *__restrict__ B,
+                                           int w, int h, int bx0, int by0, int ha) {
+  const int aw = kTX + 2 * ha, ah = kTY + 2 * ha;
+  for (int i = threadIdx.x; i < aw * ah; i += blockDim.x) {
+    const int ry = i / aw, rx = i - ry * aw;
+    T.a[ry][rx] = __ldg(A + (size_t)clampi(by0 + ry - ha, 0, h - 1) * w + clampi(bx0 + rx - ha, 0, w - 1));
+  }
+  for (int i = threadIdx.x; i < kBW * kBH; i += blockDim.x) {
+    const int ry = i / kBW, rx = i - ry * kBW;
+    T.b[ry][rx] = __ldg(B + (size_t)clampi(by0 + ry - kWin, 0, h - 1) * w + clampi(bx0 + rx - kWin, 0, w - 1));
+  }
+}
+
+// Cost of displacement (dx, dy) at local pixel (lx, ly); |dx|, |dy| <= ha - kWin.
+__device__ __forceinline__ int tile_cost(const MatchTile &T, int ha, int lx, int ly, int dx, int dy) {
+  int c = 0;
+#pragma unroll
+  for (int oy = 0; oy < 2 * kWin + 1; ++oy) {
+    const uint8_t *ra = &T.a[ly + ha - kWin + dy + oy][lx + ha - kWin + dx];
+    const uint8_t *rb = &T.b[ly + oy][lx];
+#pragma unroll
+    for (int ox = 0; ox < 2 * kWin + 1; ++ox) c += abs((int)ra[ox] - (int)rb[ox]);
+  }
+  return c;
+}
+
+__device__ __forceinline__ int level_reach(int lev, int radius) {
+  int r = radius;
+  for (int l = kFlowLevels - 1; l > lev; --l) r = 2 * r + 1;
+  return r;
+}
+
+__global__ void __launch_bounds__(kFlowThreads, 3) k_flow_match(const FlowParams P, int lev, int radius) {
   const int pair = blockIdx.y >> 1, dir = blockIdx.y & 1;
   const int w = P.lev[lev].w[pair], h = P.lev[lev].h[pair];
+  const int ntx = (w + kTX - 1) / kTX;
+  if ((int)blockIdx.x >= ntx * ((h + kTY - 1) / kTY)) return;     // block-uniform
+  const int bx0 = (blockIdx.x % ntx) * kTX, by0 = (blockIdx.x / ntx) * kTY;
   const uint8_t *A = P.Y + P.lev[lev].y_off[pair][dir];        // the image that moves
   const uint8_t *B = P.Y + P.lev[lev].y_off[pair][dir ^ 1];    // the target
-  int16_t *dxo = P.dx + P.lev[lev].d_off[pair][dir];
-  int16_t *dyo = P.dy + P.lev[lev].d_off[pair][dir];
   const bool top = lev == kFlowLevels - 1;
+  const int reach = level_reach(lev, radius);
+  const int ha = kWin + reach;
+  __shared__ MatchTile T;
+  load_tiles(T, A, B, w, h, bx0, by0, ha);
+  __syncthreads();
+  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  const int x = bx0 + lx, y = by0 + ly;
+  if (x >= w || y >= h) return;
+  int sx = 0, sy = 0;
+  if (!top) {
+    const int wu = P.lev[lev + 1].w[pair];
+    const size_t j = P.lev[lev + 1].d_off[pair][dir] + (size_t)(y >> 1) * wu + (x >> 1);
+    sx = 2 * P.dx[j];
+    sy = 2 * P.dy[j];
+  }
   const int n_cand = top ? P.n_cand_top : 9;
   const int8_t *cand = top ? P.cand_top : P.cand_fine;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w * h; i += gridDim.x * blockDim.x) {
-    const int y = i / w, x = i - y * w;
-    int sx = 0, sy = 0;
-    if (!top) {
-      const int wu = P.lev[lev + 1].w[pair];
-      const size_t j = P.lev[lev + 1].d_off[pair][dir] + (size_t)(y >> 1) * wu + (x >> 1);
-      sx = 2 * P.dx[j];
-      sy = 2 * P.dy[j];
+  const int lim = reach;
+  int best = INT_MAX, bx = sx, by = sy;
+  for (int c = 0; c < n_cand; ++c) {
+    // the search never leaves the reach; the clamp only guards the tile
+    const int dx = clampi(sx + cand[2 * c], -lim, lim), dy = clampi(sy + cand[2 * c + 1], -lim, lim);
+    const int cost = tile_cost(T, ha, lx, ly, dx, dy);
+    if (cost < best) {
+      best = cost;
+      bx = dx;
+      by = dy;
     }
-    int best = INT_MAX, bx = sx, by = sy;
-    for (int c = 0; c < n_cand; ++c) {
-      const int dx = sx + cand[2 * c], dy = sy + cand[2 * c + 1];
-      const int cost = window_cost(A, B, w, h, x, y, dx, dy);
-      if (cost < best) {
-        best = cost;
-        bx = dx;
-        by = dy;
-      }
-    }
-    dxo[i] = (int16_t)bx;
-    dyo[i] = (int16_t)by;
   }
+  const size_t i = (size_t)y * w + x;
+  P.dx[P.lev[lev].d_off[pair][dir] + i] = (int16_t)bx;
+  P.dy[P.lev[lev].d_off[pair][dir] + i] = (int16_t)by;
 }
 
 __device__ __forceinline__ float subpixel(int cm, int c0, int cp) {
@@ -119,22 +161,44 @@ __device__ __forceinline__ float subpixel(int cm, int c0, int cp) {
   return fminf(fmaxf(off, -0.5f), 0.5f);
 }
 
-__global__ void __launch_bounds__(kFlowThreads) k_flow_final(const FlowParams P) {
+__global__ void __launch_bounds__(kFlowThreads, 3) k_flow_final(const FlowParams P, int radius) {
   const int pair = blockIdx.y >> 1, dir = blockIdx.y & 1;
   const int w = P.lev[0].w[pair], h = P.lev[0].h[pair];
+  const int ntx = (w + kTX - 1) / kTX;
+  if ((int)blockIdx.x >= ntx * ((h + kTY - 1) / kTY)) return;     // block-uniform
+  const int bx0 = (blockIdx.x % ntx) * kTX, by0 = (blockIdx.x / ntx) * kTY;
   const uint8_t *A = P.Y + P.lev[0].y_off[pair][dir];
   const uint8_t *B = P.Y + P.lev[0].y_off[pair][dir ^ 1];
-  const int16_t *dxi = P.dx + P.lev[0].d_off[pair][dir];
-  const int16_t *dyi = P.dy + P.lev[0].d_off[pair][dir];
-  float2 *out = dir == 0 ? P.out_ij[pair] : P.out_ji[pair];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w * h; i += gridDim.x * blockDim.x) {
-    const int y = i / w, x = i - y * w;
-    const int dx = dxi[i], dy = dyi[i];
-    const int c0 = window_cost(A, B, w, h, x, y, dx, dy);
-    const float ox = subpixel(window_cost(A, B, w, h, x, y, dx - 1, dy), c0, window_cost(A, B, w, h, x, y, dx + 1, dy));
-    const float oy = subpixel(window_cost(A, B, w, h, x, y, dx, dy - 1), c0, window_cost(A, B, w, h, x, y, dx, dy + 1));
-    out[i] = make_float2(__fadd_rn((float)dx, ox), __fadd_rn((float)dy, oy));
+  const int reach = level_reach(0, radius) + 1;                 // the chosen d and its neighbours
+  const int ha = kWin + reach;
+  __shared__ MatchTile T;
+  load_tiles(T, A, B, w, h, bx0, by0, ha);
+  __syncthreads();
+  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  const int x = bx0 + lx, y = by0 + ly;
+  if (x >= w || y >= h) return;
+  const size_t i = (size_t)y * w + x;
+  const int lim = reach - 1;
+  const int dx = clampi(P.dx[P.lev[0].d_off[pair][dir] + i], -lim, lim);
+  const int dy = clampi(P.dy[P.lev[0].d_off[pair][dir] + i], -lim, lim);
+  // costs of d, d -/+ (1, 0), d -/+ (0, 1), one window at a time
+  int c[5];
+#pragma unroll 1
+  for (int k = 0; k < 5; ++k) {
+    const int ex = k == 1 ? -1 : (k == 2 ? 1 : 0), ey = k == 3 ? -1 : (k == 4 ? 1 : 0);
+    c[k] = tile_cost(T, ha, lx, ly, dx + ex, dy + ey);
   }
+  const float ox = subpixel(c[1], c[0], c[2]);
+  const float oy = subpixel(c[3], c[0], c[4]);
+  float2 *out = dir == 0 ? P.out_ij[pair] : P.out_ji[pair];
+  out[i] = make_float2(__fadd_rn((float)dx, ox), __fadd_rn((float)dy, oy));
+}
+
+dim3 flow_tiles(const FlowParams &p, int lev) {
+  int most = 0;
+  for (int i = 0; i < p.n_pairs; ++i)
+    most = std::max(most, ((p.lev[lev].w[i] + kTX - 1) / kTX) * ((p.lev[lev].h[i] + kTY - 1) / kTY));
+  return dim3(std::max(1, most), 2 * p.n_pairs);
 }
 
 dim3 flow_grid(const FlowParams &p, int lev) {
@@ -145,12 +209,15 @@ dim3 flow_grid(const FlowParams &p, int lev) {
 
 }  // namespace
 
-cudaError_t launch_flow(const FlowParams &p, cudaStream_t s) {
+cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s) {
   if (p.n_pairs <= 0) return cudaSuccess;
+  if (radius < 1 || radius > kFlowMaxRadius) return cudaErrorInvalidValue;
+  static_assert(kTX * kTY == kFlowThreads, "one pixel per thread");
   k_flow_luma<<<flow_grid(p, 0), kFlowThreads, 0, s>>>(p);
   for (int lev = 1; lev < kFlowLevels; ++lev) k_flow_down<<<flow_grid(p, lev), kFlowThreads, 0, s>>>(p, lev);
-  for (int lev = kFlowLevels - 1; lev >= 0; --lev) k_flow_match<<<flow_grid(p, lev), kFlowThreads, 0, s>>>(p, lev);
-  k_flow_final<<<flow_grid(p, 0), kFlowThreads, 0, s>>>(p);
+  for (int lev = kFlowLevels - 1; lev >= 0; --lev)
+    k_flow_match<<<flow_tiles(p, lev), kFlowThreads, 0, s>>>(p, lev, radius);
+  k_flow_final<<<flow_tiles(p, 0), kFlowThreads, 0, s>>>(p, radius);
   return cudaGetLastError();
 }
 

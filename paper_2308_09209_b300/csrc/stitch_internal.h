@@ -263,7 +263,7 @@ cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cud
 int fuse_own_multi_blocks_per_sm(int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
 // Every level of the band flow of every pair, both directions.
-cudaError_t launch_flow(const FlowParams &p, cudaStream_t s);
+cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s);
 // One radix pass (key bits [shift, shift + 8)) of every band-flow median.
 cudaError_t launch_refine_pass(const RefineParams &p, int shift, cudaStream_t s);
 size_t stats_smem_bytes();
