@@ -28,6 +28,8 @@ reordering beyond what the definition states. Modules:
   Eq. 13-14, with the supplied flow fields in place of SURF matches).
 * ``flow``      -- optical flow between a pair's pre-warped images over its
   blend band (section 3.2), a coarse-to-fine integer block matcher.
+* ``correspondence`` -- the one-frame colour transfer from pixel
+  correspondences that Tables 2-3 compare against (2D-M).
 
 Parity pins: each function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force or a library routine (see each test
