@@ -192,6 +192,21 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
                          float *const *flow_ji_dev, stitch_stream_t stream);
 
 /*
+ * stitch_pair_M_correspondence -- the one-frame colour transfer from pixel
+ * correspondences that the paper compares its 3D-M against (Tables 2-3, the
+ * 2D-M method): for every pair, with colour source i and target j oriented
+ * toward the reference camera, X and Y the two cameras' float32 pre-warped
+ * samples over the pair's blend band (rows of RGB at the same panorama
+ * positions), M = (X^T X)^-1 (X^T Y) with the sums in float64 (fixed-order
+ * reduction) and the 3 x 3 solve on the host.
+ *   frames_dev: n_cams device pointers (as for stitch_frame).
+ *   M_out (host): n_pairs x 9 doubles, row-major, row-vector convention.
+ * The context's colour state is not touched. Synchronous. STITCH_ESINGULAR
+ * (identity written for that pair) when a band's X^T X is singular.
+ */
+int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_dev, double *M_out);
+
+/*
  * stitch_refine_homographies -- revised camera homographies from one frame's
  * band flows (section 3.1, Eq. 13-14: the skew matrix M and the scale matrix
  * N, with the flow fields in place of SURF matches). Planar panoramas only.

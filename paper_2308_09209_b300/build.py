@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libstitch.so")
 SOURCES = ["host.cu", "k_stats.cu", "k_estimate.cu", "k_fuse.cu", "noalloc.cu", "k_pairs.cu", "k_mlp.cu", "k_learned.cu", "k_mlp_tc.cu",
-           "k_refine.cu", "k_flow.cu",
+           "k_refine.cu", "k_flow.cu", "k_corr.cu",
            "mlp_host.cu"]
 HEADERS = ["stitch_internal.h", "estimate_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

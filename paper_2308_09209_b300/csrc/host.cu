@@ -1308,6 +1308,74 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   return STITCH_OK;
 }
 
+int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_dev, double *M_out) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  const Geo &g = ctx->g;
+  const int np = g.n - 1;
+  if (np < 1) return set_err(ctx, STITCH_EINVAL, "a correspondence fit needs at least two cameras");
+  if (!M_out) return set_err(ctx, STITCH_EINVAL, "M_out is NULL");
+  if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), g.n))
+    return set_err(ctx, STITCH_EINVAL, "frame pointer array must be complete and non-NULL");
+  size_t pw_elems = 0;
+  for (int p = 0; p < np; ++p) pw_elems += 2 * (size_t)(g.band[p][1] - g.band[p][0]) * (g.band[p][3] - g.band[p][2]);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && !ctx->flow_pw) e = cudaMalloc(&ctx->flow_pw, pw_elems * sizeof(float4) + 16);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "correspondence buffers");
+  CorrParams cp{};
+  cp.n_pairs = np;
+  cp.pw = ctx->flow_pw;
+  for (int p = 0; p < np; ++p) {
+    const int left_is_i = g.pair_i[p] == p ? 1 : 0;
+    cp.off_i[p] = ctx->fp.pw_off[p][left_is_i ? 0 : 1];
+    cp.off_j[p] = ctx->fp.pw_off[p][left_is_i ? 1 : 0];
+    cp.n[p] = (g.band[p][1] - g.band[p][0]) * (g.band[p][3] - g.band[p][2]);
+  }
+  const int blocks = 128;
+  if (e == cudaSuccess) e = cudaMalloc(&cp.partial, (size_t)np * blocks * kCorrSums * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&cp.sums, (size_t)np * kCorrSums * sizeof(double));
+  // The float32 band pre-warp into the context's own buffer, then the sums.
+  const float *none[kMaxPairs] = {};
+  FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
+  fp.flags &= ~STITCH_FP16_INTERMEDIATE;
+  fp.pw = ctx->flow_pw;
+  if (e == cudaSuccess) e = launch_prewarp(fp, nullptr);
+  if (e == cudaSuccess) e = launch_corr(cp, blocks, nullptr);
+  std::vector<double> sums((size_t)np * kCorrSums);
+  if (e == cudaSuccess) e = cudaMemcpy(sums.data(), cp.sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(cp.partial);
+  cudaFree(cp.sums);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "correspondence fit");
+  int rc = STITCH_OK;
+  for (int p = 0; p < np; ++p) {
+    const double *t = &sums[(size_t)p * kCorrSums];
+    double A[3][4 + 3] = {{t[0], t[1], t[2]}, {t[1], t[3], t[4]}, {t[2], t[4], t[5]}};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) A[r][3 + c] = t[6 + 3 * r + c];
+    // Gaussian elimination with partial pivoting on [A | B].
+    bool ok = true;
+    for (int c = 0; c < 3 && ok; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 3; ++r)
+        if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+      if (!(std::fabs(A[piv][c]) > 0.0)) {
+        ok = false;
+        break;
+      }
+      if (piv != c)
+        for (int k = 0; k < 6; ++k) std::swap(A[c][k], A[piv][k]);
+      for (int r = 0; r < 3; ++r) {
+        if (r == c) continue;
+        const double f = A[r][c] / A[c][c];
+        for (int k = c; k < 6; ++k) A[r][k] -= f * A[c][k];
+      }
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) M_out[9 * p + 3 * r + c] = ok ? A[r][3 + c] / A[r][r] : (r == c ? 1.0 : 0.0);
+    if (!ok) rc = set_err(ctx, STITCH_ESINGULAR, "a band has no colour variation; the identity was returned for it");
+  }
+  return rc;
+}
+
 int stitch_refine_homographies(stitch_ctx *ctx, const float *const *flow_ij_dev, const float *const *flow_ji_dev,
                                double *params_out, double *H_out) {
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");

@@ -248,6 +248,19 @@ struct FlowParams {
   int8_t cand_fine[18];               // the 3 x 3 refinement, in tie-break order
 };
 
+// One-frame colour transfer from pixel correspondences (k_corr.cu).
+constexpr int kCorrSums = 15;         // A = X^T X (6 distinct entries), B = X^T Y (9)
+constexpr int kCorrMaxBlocks = 256;
+
+struct CorrParams {
+  int n_pairs;
+  const float4 *pw;                   // float32 pre-warped bands
+  size_t off_i[kMaxPairs], off_j[kMaxPairs];   // element offsets of the colour source / target band
+  int n[kMaxPairs];                   // band pixels
+  double *partial;                    // [n_pairs][blocks][kCorrSums]
+  double *sums;                       // [n_pairs][kCorrSums]
+};
+
 // Launchers (defined in the kernel files).
 cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
@@ -262,6 +275,8 @@ int fuse_multi_blocks_per_sm(bool half, int shape);
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);
 int fuse_own_multi_blocks_per_sm(int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
+// The correspondence sums of every pair (blocks per pair, fixed-order totals).
+cudaError_t launch_corr(const CorrParams &p, int blocks, cudaStream_t s);
 // Every level of the band flow of every pair, both directions.
 cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s);
 // One radix pass (key bits [shift, shift + 8)) of every band-flow median.

@@ -121,6 +121,7 @@ def lib():
             "stitch_batch_tile_shapes": (ip, [vp, vp]),
             "stitch_refine_homographies": (ip, [vp, pp, pp, vp, vp]),
             "stitch_estimate_flow": (ip, [vp, pp, pp, pp, vp]),
+            "stitch_pair_M_correspondence": (ip, [vp, pp, vp]),
             "stitch_batch_destroy": (None, [vp]),
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
@@ -530,6 +531,13 @@ def stitch_batch_tile_shapes(b):
     n = lib().stitch_batch_tile_shapes(b, buf.ctypes.data)
     _batch_check(min(n, 0), b)
     return [int(x) for x in buf[:n]]
+
+
+def stitch_pair_M_correspondence(ctx, frames, n_pairs: int):
+    """One-frame 2D-M of every pair from pixel correspondences (n_pairs, 3, 3)."""
+    M = np.zeros((max(n_pairs, 1), 9), dtype=np.float64)
+    _check(lib().stitch_pair_M_correspondence(ctx, _ptrs(frames), M.ctypes.data), ctx)
+    return M[:n_pairs].reshape(n_pairs, 3, 3)
 
 
 def stitch_estimate_flow(ctx, frames, flows_ij, flows_ji, stream=None) -> None:

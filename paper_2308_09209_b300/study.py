@@ -14,7 +14,10 @@ the same way: PSNR = 10 log10(255^2 / mean squared difference over the
 band's pixels and channels). Reported per window: the mean and the frame-to-frame standard
 deviation of the PSNR (Table 2's mu and sigma rows), and the mean
 frame-to-frame standard deviation of M's entries. The first W - 1 frames,
-where the window is not yet full, are left out of the statistics.
+where the window is not yet full, are left out of the statistics. The same
+figures for the 2D-M method the paper compares against (a one-frame least-
+squares map from the bands' pixel correspondences,
+stitch_pair_M_correspondence) are reported beside them.
 """
 from __future__ import annotations
 
@@ -61,6 +64,25 @@ def window_study(config: str = "3x1920x1080", windows=(1, 3, 5, 7), n_frames: in
         grids.append((xx.reshape(-1), yy.reshape(-1)))
     out = {"rig": config, "frames": n_frames, "moving_objects": objects, "object_speed_px": object_speed,
            "sensor_noise_sigma": noise, "per_window": {}}
+    def psnr_row(t, Mp):
+        row = []
+        for p in range(n - 1):
+            i = p if p < ref else p + 1              # colour source of the pair (away from the reference)
+            j = p + 1 if p < ref else p
+            xs, ys = grids[p]
+            Pi = _sample(frames[t][i], Hinv[i], xs, ys)
+            Pj = _sample(frames[t][j], Hinv[j], xs, ys)
+            Mt = torch.tensor(Mp[p], dtype=torch.float64, device=dev)
+            mse = float(((Pi @ Mt).clamp(0, 255) - Pj).pow(2).mean())
+            row.append(10.0 * np.log10(255.0 ** 2 / max(mse, 1e-12)))
+        return row
+
+    def summary(psnr, Ms):
+        psnr = np.asarray(psnr)                      # [frames, pairs]
+        Ms = np.asarray(Ms)                          # [frames, pairs, 3, 3]
+        return {"psnr_mu": float(psnr.mean()), "psnr_sigma": float(psnr.std(axis=0).mean()),
+                "sigma_M": float(Ms.std(axis=0).mean()), "frames_used": int(psnr.shape[0])}
+
     for W in windows:
         cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=W, max_flow=seq["max_flow"])
         st = S.Stitcher(cfg)
@@ -70,25 +92,16 @@ def window_study(config: str = "3x1920x1080", windows=(1, 3, 5, 7), n_frames: in
             Mp = S.stitch_get_pair_M(st.ctx, n - 1)
             if t < W - 1:
                 continue
-            row = []
-            for p in range(n - 1):
-                i = p if p < ref else p + 1          # colour source of the pair (away from the reference)
-                j = p + 1 if p < ref else p
-                xs, ys = grids[p]
-                Pi = _sample(frames[t][i], Hinv[i], xs, ys)
-                Pj = _sample(frames[t][j], Hinv[j], xs, ys)
-                Mt = torch.tensor(Mp[p], dtype=torch.float64, device=dev)
-                mse = float(((Pi @ Mt).clamp(0, 255) - Pj).pow(2).mean())
-                row.append(10.0 * np.log10(255.0 ** 2 / max(mse, 1e-12)))
-            psnr.append(row)
+            psnr.append(psnr_row(t, Mp))
             Ms.append(np.asarray(Mp, np.float64).copy())
+        if W == windows[0]:
+            # the 2D-M comparison: one-frame least squares over the pixel correspondences
+            p2, M2 = [], []
+            for t in range(n_frames):
+                Mc = S.stitch_pair_M_correspondence(st.ctx, frames[t], n - 1)
+                p2.append(psnr_row(t, Mc))
+                M2.append(np.asarray(Mc, np.float64).copy())
+            out["2d_m_correspondence"] = summary(p2, M2)
         st.close()
-        psnr = np.asarray(psnr)                      # [frames, pairs]
-        Ms = np.asarray(Ms)                          # [frames, pairs, 3, 3]
-        out["per_window"][str(W)] = {
-            "psnr_mu": float(psnr.mean()),
-            "psnr_sigma": float(psnr.std(axis=0).mean()),
-            "sigma_M": float(Ms.std(axis=0).mean()),
-            "frames_used": int(psnr.shape[0]),
-        }
+        out["per_window"][str(W)] = summary(psnr, Ms)
     return out
