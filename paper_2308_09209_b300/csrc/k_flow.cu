@@ -72,10 +72,13 @@ constexpr int kReach0 = 4 * kFlowMaxRadius + 2 + 1 + 1;   // |d| at the finest l
 constexpr int kHaloA = kWin + kReach0;
 constexpr int kAW = kTX + 2 * kHaloA, kAH = kTY + 2 * kHaloA;
 constexpr int kBW = kTX + 2 * kWin, kBH = kTY + 2 * kWin;
+// Rows padded to whole 32-bit words with room for the third word a 7-byte
+// window at any offset reads (the bytes beyond a row's data are never used).
+constexpr int kAWP = (kAW + 8) & ~3, kBWP = (kBW + 8) & ~3;
 
 struct MatchTile {
-  uint8_t a[kAH][kAW];
-  uint8_t b[kBH][kBW];
+  __align__(16) uint8_t a[kAH][kAWP];
+  __align__(16) uint8_t b[kBH][kBWP];
 };
 
 // Load the tiles of block (bx0, by0) with halo `ha` for the moving image.
@@ -92,17 +95,39 @@ __device__ __forceinline__ void load_tiles(MatchTile &T, const uint8_t *__restri
   }
 }
 
+// The seven bytes [o, o + 7) of a tile row as two words (the eighth byte
+// zero), from three aligned 32-bit loads and two funnel shifts.
+__device__ __forceinline__ uint2 row7(const uint8_t *row, int o) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(row) + (o >> 2);
+  const uint32_t sh = (uint32_t)(o & 3) * 8u;
+  const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+  return make_uint2(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh) & 0x00FFFFFFu);
+}
+
+// The target's 7 x 7 window of local pixel (lx, ly), kept in registers.
+struct BWin {
+  uint2 r[2 * kWin + 1];
+};
+
+__device__ __forceinline__ BWin target_window(const MatchTile &T, int lx, int ly) {
+  BWin b;
+#pragma unroll
+  for (int oy = 0; oy < 2 * kWin + 1; ++oy) b.r[oy] = row7(T.b[ly + oy], lx);
+  return b;
+}
+
 // Cost of displacement (dx, dy) at local pixel (lx, ly); |dx|, |dy| <= ha - kWin.
-__device__ __forceinline__ int tile_cost(const MatchTile &T, int ha, int lx, int ly, int dx, int dy) {
-  int c = 0;
+// Byte-wise absolute differences summed four at a time (the same integer).
+__device__ __forceinline__ int tile_cost(const MatchTile &T, const BWin &b, int ha, int lx, int ly, int dx, int dy) {
+  unsigned c = 0u;
+  const int o = lx + ha - kWin + dx;
 #pragma unroll
   for (int oy = 0; oy < 2 * kWin + 1; ++oy) {
-    const uint8_t *ra = &T.a[ly + ha - kWin + dy + oy][lx + ha - kWin + dx];
-    const uint8_t *rb = &T.b[ly + oy][lx];
-#pragma unroll
-    for (int ox = 0; ox < 2 * kWin + 1; ++ox) c += abs((int)ra[ox] - (int)rb[ox]);
+    const uint2 a = row7(T.a[ly + ha - kWin + dy + oy], o);
+    c = __dp4a(__vabsdiffu4(a.x, b.r[oy].x), 0x01010101u, c);
+    c = __dp4a(__vabsdiffu4(a.y, b.r[oy].y), 0x01010101u, c);
   }
-  return c;
+  return (int)c;
 }
 
 __device__ __forceinline__ int level_reach(int lev, int radius) {
@@ -138,11 +163,12 @@ __global__ void __launch_bounds__(kFlowThreads, 3) k_flow_match(const FlowParams
   const int n_cand = top ? P.n_cand_top : 9;
   const int8_t *cand = top ? P.cand_top : P.cand_fine;
   const int lim = reach;
+  const BWin bw = target_window(T, lx, ly);
   int best = INT_MAX, bx = sx, by = sy;
   for (int c = 0; c < n_cand; ++c) {
     // the search never leaves the reach; the clamp only guards the tile
     const int dx = clampi(sx + cand[2 * c], -lim, lim), dy = clampi(sy + cand[2 * c + 1], -lim, lim);
-    const int cost = tile_cost(T, ha, lx, ly, dx, dy);
+    const int cost = tile_cost(T, bw, ha, lx, ly, dx, dy);
     if (cost < best) {
       best = cost;
       bx = dx;
@@ -181,12 +207,13 @@ __global__ void __launch_bounds__(kFlowThreads, 3) k_flow_final(const FlowParams
   const int lim = reach - 1;
   const int dx = clampi(P.dx[P.lev[0].d_off[pair][dir] + i], -lim, lim);
   const int dy = clampi(P.dy[P.lev[0].d_off[pair][dir] + i], -lim, lim);
-  // costs of d, d -/+ (1, 0), d -/+ (0, 1), one window at a time
+  // costs of d, d -/+ (1, 0), d -/+ (0, 1)
+  const BWin bw = target_window(T, lx, ly);
   int c[5];
-#pragma unroll 1
+#pragma unroll
   for (int k = 0; k < 5; ++k) {
     const int ex = k == 1 ? -1 : (k == 2 ? 1 : 0), ey = k == 3 ? -1 : (k == 4 ? 1 : 0);
-    c[k] = tile_cost(T, ha, lx, ly, dx + ex, dy + ey);
+    c[k] = tile_cost(T, bw, ha, lx, ly, dx + ex, dy + ey);
   }
   const float ox = subpixel(c[1], c[0], c[2]);
   const float oy = subpixel(c[3], c[0], c[4]);
