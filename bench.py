@@ -711,9 +711,25 @@ def _run_ours(args, dist, ctxs):
         fl_ij = [torch.empty_like(f) for f in wl["fij"][0]]
         fl_ji = [torch.empty_like(f) for f in wl["fji"][0]]
         ms_flow = _time(lambda: S.stitch_estimate_flow(st.ctx, wl["frames"][0], fl_ij, fl_ji, stream), stream, 10, 2)
+        # the whole per-frame method with the library's own flow: flow, colour estimate, stitch
+        stf = S.Stitcher(cfg)
+        ctxs.append(stf)
+        pano1 = torch.empty((3, cfg.pano_h, cfg.pitch), dtype=torch.uint8, device=dev)
+        nf = min(F, 8)
+
+        def with_flow():
+            for t in range(nf):
+                S.stitch_estimate_flow(stf.ctx, wl["frames"][t], fl_ij, fl_ji, stream)
+                S.stitch_estimate_color(stf.ctx, wl["frames"][t], stream)
+                S.stitch_frame(stf.ctx, wl["frames"][t], fl_ij, fl_ji, pano1, stream)
+
+        ms_wf = _time(with_flow, stream, 3, 1) / nf
         extras["estimate_flow"] = {"ms_per_frame": ms_flow, "pairs": n_cams - 1, "band_px": band_px,
                                    "what": "float32 band pre-warp of both cameras, integer luminance, 3-level "
-                                           "7x7 block matching both ways, sub-pixel parabola"}
+                                           "7x7 block matching both ways, sub-pixel parabola",
+                                   "with_stitch_mpix_s": wl["pano_px"] / (ms_wf / 1e3) / 1e6,
+                                   "with_stitch": "per frame: stitch_estimate_flow, stitch_estimate_color, "
+                                                  "stitch_frame with those flows (direct calls, one stream)"}
         # the temporal-window study (W = 1 vs 3 / 5 / 7), outside every timed region
         from paper_2308_09209_b300.study import window_study
         extras["window_study"] = window_study()

@@ -379,6 +379,14 @@ int stitch_mlp_set_gemm(stitch_mlp *mlp, int engine);
  * stitch_mlp_get_params report it too. */
 int stitch_mlp_status(stitch_mlp *mlp);
 
+/* Diagnostic of the library's bounded device waits (failure detection
+ * without a fault): one thread polls an mbarrier with the same bounded loop
+ * the tensor-core GEMM uses, `limit` polls at most (1 .. 2^22). With
+ * arrive = 0 nothing ever arrives, the wait gives up and the call returns
+ * STITCH_ETIMEOUT with the device still usable; with arrive = 1 the arrival
+ * comes first and the call returns STITCH_OK. Synchronous. */
+int stitch_selftest_wait(int arrive, int limit);
+
 /* Create a network with He-normal weights drawn from `seed` (a host
  * Mersenne-Twister stream) and buffers for batches up to max_batch (a
  * multiple of 32, at most 65536). Allocates device memory; synchronises. */

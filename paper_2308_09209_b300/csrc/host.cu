@@ -1,6 +1,8 @@
 // Host side of the stitching library: configuration checks, float64 overlap
 // geometry (paper section 2.1 step 1, section 3.1), device state, launches and
 // the C ABI declared in include/stitch.h.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -67,6 +69,15 @@ void proj(const double *H, double x, double y, double &X, double &Y, double &W) 
   X = a / W;
   Y = b / W;
 }
+
+// A named NVTX range over a public call (header-only NVTX: a no-op unless a
+// profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Geo {
   int n = 0;
@@ -999,6 +1010,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
 }
 
 int stitch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames_dev, stitch_stream_t stream) {
+  NvtxRange nvtx_("stitch_estimate_color");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), ctx->g.n))
     return set_err(ctx, STITCH_EINVAL, "frames_dev must hold n_cams non-NULL pointers");
@@ -1007,6 +1019,7 @@ int stitch_estimate_color(stitch_ctx *ctx, const uint8_t *const *frames_dev, sti
 
 int stitch_frame(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
                  const float *const *flow_ji_dev, uint8_t *pano_dev, stitch_stream_t stream) {
+  NvtxRange nvtx_("stitch_frame");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   const int np = ctx->g.n - 1;
   if (!check_ptrs(reinterpret_cast<const void *const *>(frames_dev), ctx->g.n))
@@ -1025,6 +1038,7 @@ int stitch_frame(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float 
 int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_dev,
                     const float *const *flow_ij_dev, const float *const *flow_ji_dev,
                     uint8_t *const *pano_dev, stitch_stream_t stream) {
+  NvtxRange nvtx_("stitch_sequence");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   if (n_frames < 1) return set_err(ctx, STITCH_EINVAL, "n_frames must be >= 1");
   const int n = ctx->g.n, np = n - 1;
@@ -1147,6 +1161,7 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
 int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_host,
                          const float *const *flow_ij_host, const float *const *flow_ji_host,
                          uint8_t *const *pano_host, stitch_stream_t stream) {
+  NvtxRange nvtx_("stitch_sequence_host");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   if (n_frames < 1) return set_err(ctx, STITCH_EINVAL, "n_frames must be >= 1");
   const Geo &g = ctx->g;
@@ -1227,6 +1242,7 @@ int stitch_sequence_host(stitch_ctx *ctx, int n_frames, const uint8_t *const *fr
 
 int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, float *const *flow_ij_dev,
                          float *const *flow_ji_dev, stitch_stream_t stream) {
+  NvtxRange nvtx_("stitch_estimate_flow");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   const Geo &g = ctx->g;
   const int np = g.n - 1;
@@ -1309,6 +1325,7 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
 }
 
 int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_dev, double *M_out) {
+  NvtxRange nvtx_("stitch_pair_M_correspondence");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   const Geo &g = ctx->g;
   const int np = g.n - 1;
@@ -1378,6 +1395,7 @@ int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_d
 
 int stitch_refine_homographies(stitch_ctx *ctx, const float *const *flow_ij_dev, const float *const *flow_ji_dev,
                                double *params_out, double *H_out) {
+  NvtxRange nvtx_("stitch_refine_homographies");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   const Geo &g = ctx->g;
   const int np = g.n - 1;
@@ -1680,6 +1698,7 @@ int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
 
 int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
                     const float *const *flow_ji_dev, uint8_t *pano_dev, int reps, int *shape_out, float *ms_out) {
+  NvtxRange nvtx_("stitch_autotune");
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   const int np = ctx->g.n - 1;
   if (reps < 1 || reps > 1000) return set_err(ctx, STITCH_EINVAL, "reps must be in 1..1000");
@@ -1968,6 +1987,7 @@ int stitch_batch_create(stitch_ctx *const *ctxs, int n_ctx, stitch_batch **out) 
 int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *frames_dev,
                           const float *const *flow_ij_dev, const float *const *flow_ji_dev, uint8_t *const *pano_dev,
                           stitch_stream_t stream) {
+  NvtxRange nvtx_("stitch_batch_sequence");
   if (!b) return batch_err(nullptr, STITCH_EINVAL, "batch is NULL");
   if (n_frames < 1) return batch_err(b, STITCH_EINVAL, "n_frames must be >= 1");
   if (!batch_ptrs_ok(b, n_frames, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev))
@@ -2086,6 +2106,7 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
 int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
                           const float *const *flow_ji_dev, uint8_t *const *pano_dev, int reps, int *shapes_out,
                           float *ms_out) {
+  NvtxRange nvtx_("stitch_batch_autotune");
   if (!b) return batch_err(nullptr, STITCH_EINVAL, "batch is NULL");
   if (reps < 1 || reps > 1000) return batch_err(b, STITCH_EINVAL, "reps must be in 1..1000");
   if (!batch_ptrs_ok(b, 1, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev))

@@ -55,8 +55,8 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = kWaitLimit) {
+  for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -83,6 +83,25 @@ __device__ __forceinline__ void copy_chunk(uint32_t dst, const bf16 *__restrict_
 }
 
 }  // namespace
+
+// Diagnostic of the bounded waits: thread 0 initialises an mbarrier that
+// expects one arrival and polls for its phase with the same bounded loop the
+// GEMM uses. Without the arrival the poll gives up after `limit` tries and
+// the kernel records that in *err, as k_gemm_tc does for a stalled pipeline;
+// with it the wait succeeds at once. Nothing else waits, so it cannot stall.
+__global__ void k_wait_selftest(int arrive, int limit, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = su32(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  if (arrive) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(b) : "memory");
+    (void)state;
+  }
+  if (!mbar_wait(b, 0u, limit)) atomicExch(err, 1);
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(b) : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B,
                                                       int ldb, int M, int N, int K, const float *__restrict__ bias,
@@ -212,6 +231,12 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+cudaError_t launch_wait_selftest(int arrive, int limit, int *err, cudaStream_t s) {
+  if (limit < 1 || limit > kWaitLimit) return cudaErrorInvalidValue;
+  k_wait_selftest<<<1, 32, 0, s>>>(arrive, limit, err);
+  return cudaGetLastError();
 }
 
 cudaError_t gemm_tc_setup() {

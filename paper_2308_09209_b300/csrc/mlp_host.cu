@@ -33,6 +33,7 @@ cudaError_t launch_denorm(const float *y, int ldy, int batch, int n_out, const f
                           cudaStream_t s);
 cudaError_t launch_pair_label(const PairParams &p, cudaStream_t s);
 cudaError_t gemm_tc_setup();
+cudaError_t launch_wait_selftest(int arrive, int limit, int *err, cudaStream_t s);
 cudaError_t launch_gemm_tc(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const float *bias,
                            int mode, float *Cf, int ldc, bf16 *Yb, int ldy, bf16 *Yt, int ldt, int *err,
                            cudaStream_t s);
@@ -210,6 +211,19 @@ int stitch_mlp_status(stitch_mlp *n) {
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(STITCH_ECUDA, cudaGetErrorString(e));
   return take_err(n);
+}
+
+int stitch_selftest_wait(int arrive, int limit) {
+  if (limit < 1 || limit > (1 << 22)) return fail(STITCH_EINVAL, "limit must be in [1, 2^22]");
+  int *err = nullptr;
+  cudaError_t e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_wait_selftest(arrive ? 1 : 0, limit, err, nullptr);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  if (e != cudaSuccess) return fail(STITCH_ECUDA, cudaGetErrorString(e));
+  return h ? fail(STITCH_ETIMEOUT, "the bounded wait gave up, as expected without an arrival") : STITCH_OK;
 }
 
 int stitch_mlp_create(int max_batch, unsigned long long seed, stitch_mlp **out) {

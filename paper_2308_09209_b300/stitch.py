@@ -122,6 +122,7 @@ def lib():
             "stitch_refine_homographies": (ip, [vp, pp, pp, vp, vp]),
             "stitch_estimate_flow": (ip, [vp, pp, pp, pp, vp]),
             "stitch_pair_M_correspondence": (ip, [vp, pp, vp]),
+            "stitch_selftest_wait": (ip, [ip, ip]),
             "stitch_batch_destroy": (None, [vp]),
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
@@ -531,6 +532,12 @@ def stitch_batch_tile_shapes(b):
     n = lib().stitch_batch_tile_shapes(b, buf.ctypes.data)
     _batch_check(min(n, 0), b)
     return [int(x) for x in buf[:n]]
+
+
+def stitch_selftest_wait(arrive: bool, limit: int = 1 << 16) -> int:
+    """Status of the bounded-wait diagnostic: STITCH_ETIMEOUT without an
+    arrival, STITCH_OK with one (no exception either way)."""
+    return lib().stitch_selftest_wait(1 if arrive else 0, limit)
 
 
 def stitch_pair_M_correspondence(ctx, frames, n_pairs: int):
