@@ -474,6 +474,9 @@ struct stitch_ctx {
   float4 *flow_pw = nullptr;          // stitch_estimate_flow: float32 pre-warped bands
   uint8_t *flow_Y = nullptr;          // its luminance pyramids
   int16_t *flow_d = nullptr;          // its chosen displacements (dx then dy)
+  RefineState *refine_state = nullptr;  // stitch_refine_homographies: radix-selection state
+  uint32_t *refine_hist = nullptr;      // and histograms (8 medians per pair)
+  double *corr_buf = nullptr;         // stitch_pair_M_correspondence: block partials, then the totals
   cudaStream_t copy_in = nullptr;     // host-to-device copies of stitch_sequence_host
   cudaStream_t copy_out = nullptr;    // device-to-host copies of stitch_sequence_host
   int shape = 0;                      // fuse tile shape (index into kTileShapes)
@@ -1348,8 +1351,10 @@ int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_d
     cp.n[p] = (g.band[p][1] - g.band[p][0]) * (g.band[p][3] - g.band[p][2]);
   }
   const int blocks = 128;
-  if (e == cudaSuccess) e = cudaMalloc(&cp.partial, (size_t)np * blocks * kCorrSums * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&cp.sums, (size_t)np * kCorrSums * sizeof(double));
+  // one buffer of the context, allocated on the first call: block partials, then the totals
+  if (e == cudaSuccess && !ctx->corr_buf) e = cudaMalloc(&ctx->corr_buf, (size_t)np * (blocks + 1) * kCorrSums * sizeof(double));
+  cp.partial = ctx->corr_buf;
+  cp.sums = ctx->corr_buf + (size_t)np * blocks * kCorrSums;
   // The float32 band pre-warp into the context's own buffer, then the sums.
   const float *none[kMaxPairs] = {};
   FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
@@ -1359,8 +1364,6 @@ int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_d
   if (e == cudaSuccess) e = launch_corr(cp, blocks, nullptr);
   std::vector<double> sums((size_t)np * kCorrSums);
   if (e == cudaSuccess) e = cudaMemcpy(sums.data(), cp.sums, sums.size() * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(cp.partial);
-  cudaFree(cp.sums);
   if (e != cudaSuccess) return cuda_err(ctx, e, "correspondence fit");
   int rc = STITCH_OK;
   for (int p = 0; p < np; ++p) {
@@ -1417,15 +1420,16 @@ int stitch_refine_homographies(stitch_ctx *ctx, const float *const *flow_ij_dev,
   }
   const int n_prob = 8 * np;
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMalloc(&rp.state, n_prob * sizeof(RefineState));
-  if (e == cudaSuccess) e = cudaMalloc(&rp.hist, (size_t)n_prob * 256 * sizeof(uint32_t));
+  // buffers of the context, allocated on the first call (the geometry is fixed)
+  if (e == cudaSuccess && !ctx->refine_state) e = cudaMalloc(&ctx->refine_state, n_prob * sizeof(RefineState));
+  if (e == cudaSuccess && !ctx->refine_hist) e = cudaMalloc(&ctx->refine_hist, (size_t)n_prob * 256 * sizeof(uint32_t));
+  rp.state = ctx->refine_state;
+  rp.hist = ctx->refine_hist;
   if (e == cudaSuccess) e = cudaMemset(rp.state, 0, n_prob * sizeof(RefineState));
   if (e == cudaSuccess) e = cudaMemset(rp.hist, 0, (size_t)n_prob * 256 * sizeof(uint32_t));
   for (int shift = 24; shift >= 0 && e == cudaSuccess; shift -= 8) e = launch_refine_pass(rp, shift, nullptr);
   std::vector<RefineState> st(n_prob);
   if (e == cudaSuccess) e = cudaMemcpy(st.data(), rp.state, n_prob * sizeof(RefineState), cudaMemcpyDeviceToHost);
-  cudaFree(rp.state);
-  cudaFree(rp.hist);
   if (e != cudaSuccess) return cuda_err(ctx, e, "refinement");
   // The medians (0 where a statistic has no finite value).
   std::vector<double> med(n_prob, 0.0);
@@ -2259,6 +2263,9 @@ void stitch_destroy(stitch_ctx *ctx) {
   cudaFree(ctx->flow_pw);
   cudaFree(ctx->flow_Y);
   cudaFree(ctx->flow_d);
+  cudaFree(ctx->refine_state);
+  cudaFree(ctx->refine_hist);
+  cudaFree(ctx->corr_buf);
   if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
   if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
   delete ctx;
