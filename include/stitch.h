@@ -544,6 +544,19 @@ const char *stitch_batch_last_error(const stitch_batch *b);
 int stitch_n_pairs(const stitch_ctx *ctx);
 
 /*
+ * stitch_window_fallbacks -- diagnostic counter of the fuse and band
+ * pre-warp kernels (section 3.1's pre-warp reads each tile's source window
+ * from shared memory): the number of tiles, over every launch on this context
+ * since stitch_init or the last reset, whose source window did not fit the
+ * kernel's staging capacity (about 1.5 x the tile width by the tile height
+ * + 16 rows) and therefore sampled the frame with per-pixel global loads
+ * instead. The result is the same either way; only the speed differs.
+ * *count (required) receives the counter; reset != 0 clears it afterwards.
+ * Synchronises the device. Returns STITCH_OK, STITCH_EINVAL or STITCH_ECUDA.
+ */
+int stitch_window_fallbacks(stitch_ctx *ctx, unsigned long long *count, int reset);
+
+/*
  * stitch_last_error -- message of the last failing call on ctx, or of the
  * last failing stitch_geometry / stitch_init when ctx is NULL. The string is
  * owned by the library and valid until the next call on the same context.

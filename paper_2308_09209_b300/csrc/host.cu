@@ -455,9 +455,10 @@ struct stitch_ctx {
   RawStats *raw = nullptr;            // kRawSlots slots
   ColorState *state = nullptr;
   TileDesc *tiles = nullptr;
-  int n_band_tiles = 0, n_own_tiles = 0;
   PwTile *pw_tiles = nullptr;
   void *pw = nullptr;                 // band pre-warp intermediate
+  uint8_t *lut = nullptr;             // output tables of the colour slots (kColorSlots x kLutBytes)
+  unsigned int *win_fallback = nullptr;   // fuse tiles whose source window did not fit (counter)
   int stats_grid_x = 1;
   StatsParams sp{};
   EstimateParams ep{};
@@ -587,7 +588,11 @@ FuseParams frame_params(stitch_ctx *ctx, const uint8_t *const *frames, const flo
     fp.flow_ji[p] = reinterpret_cast<const float2 *>(fji[p]);
   }
   fp.out = pano;
-  fp.color = &ctx->state->out[((colour_T % kColorSlots) + kColorSlots) % kColorSlots];
+  const int slot = ((colour_T % kColorSlots) + kColorSlots) % kColorSlots;
+  fp.color = &ctx->state->out[slot];
+  fp.lut = ctx->lut + (size_t)slot * kLutBytes;
+  fp.win_fallback = ctx->win_fallback;
+  fp.flags |= kFlagPwOffset;
   fp.pw = static_cast<char *>(ctx->pw) + (size_t)(F % kPwSlots) * ctx->pw_slot_bytes;
   return fp;
 }
@@ -635,24 +640,67 @@ bool check_ptrs(const void *const *p, int n) {
   return true;
 }
 
-// Fuse tiles of one shape. A tile touching a band's columns is a band tile
-// (kind 1); others belong to the one camera whose own columns hold them: kind
-// 0 when that camera covers the whole tile with a margin (coverage is convex,
-// so the four corners decide) and no pixel needs a coverage test or a fallback
-// camera, kind 2 for partial coverage. Band tiles come first, and among the
-// own tiles the partly covered ones precede the fully covered. Returns false
-// (with a message) when a tile would touch two bands.
-bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &band_tiles, std::vector<TileDesc> &own_tiles,
-                 std::string &err) {
+// Fuse tile pieces of one shape. A tile is cut at 16-column boundaries into
+// pieces of one kind each: the chunks of the band rectangle's columns
+// (kTileBand, when the tile's rows lie inside the band rectangle), the chunk
+// holding a band edge and band columns outside the band rows (kTileBandPart),
+// and own columns of one camera, kTileOwn when that camera covers every
+// pixel of the piece with a margin (coverage is convex on the plane, so the
+// corners decide; on the cylinder every border pixel is tested), else
+// kTileOwnPart. The list holds the general pieces (kinds 2 and 3) first, then
+// the band pieces, then the fully covered own pieces. Returns false (with a
+// message) when a tile would touch two bands.
+struct TileCounts {
+  int n_band = 0, n_full = 0;
+};
+
+bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &tiles, TileCounts &cnt, std::string &err) {
   const int TW = kTileShapes[shape].w, TH = kTileShapes[shape].h;
   const int ntx = (g.pano_w + TW - 1) / TW, nty = (g.pano_h + TH - 1) / TH;
   if (ntx > 32767 || nty > 32767) {
     err = "panorama too large for the tile index";
     return false;
   }
+  std::vector<TileDesc> gen, band, full;
+  auto own_piece = [&](int k, int tx, int ty, int x0, int x1) {
+    // columns [x0, x1) of tile (tx, ty), owned by camera k
+    if (x0 >= x1) return;
+    const int r0 = ty * TH, r1 = std::min(r0 + TH, g.pano_h) - 1;
+    auto inside = [&](int x, int y) {
+      double sx, sy, sw;
+      pano_to_cam(g, k, x, y, sx, sy, sw);
+      return sw > 0 && sx >= 0.01 && sx <= g.w[k] - 1.01 && sy >= 0.01 && sy <= g.h[k] - 1.01;
+    };
+    bool ok = x1 <= g.pano_w && r0 + TH <= g.pano_h;
+    if (!g.cyl) {
+      ok = ok && inside(x0, r0) && inside(x1 - 1, r0) && inside(x0, r1) && inside(x1 - 1, r1);
+    } else {
+      for (int x = x0; x < x1 && ok; ++x) ok = inside(x, r0) && inside(x, r1);
+      for (int y = r0; y <= r1 && ok; ++y) ok = inside(x0, y) && inside(x1 - 1, y);
+    }
+    TileDesc t{};
+    t.tx = (int16_t)tx;
+    t.ty = (int16_t)ty;
+    t.kind = (int8_t)(ok ? kTileOwn : kTileOwnPart);
+    t.idx = (int8_t)k;
+    t.c0 = (uint8_t)((x0 - tx * TW) / 16);
+    t.c1 = (uint8_t)((x1 - tx * TW + 15) / 16);
+    (ok ? full : gen).push_back(t);
+  };
+  auto band_piece = [&](int p, int kind, int tx, int ty, int x0, int x1) {
+    if (x0 >= x1) return;
+    TileDesc t{};
+    t.tx = (int16_t)tx;
+    t.ty = (int16_t)ty;
+    t.kind = (int8_t)kind;
+    t.idx = (int8_t)p;
+    t.c0 = (uint8_t)((x0 - tx * TW) / 16);
+    t.c1 = (uint8_t)((x1 - tx * TW + 15) / 16);
+    (kind == kTileBand ? band : gen).push_back(t);
+  };
   for (int ty = 0; ty < nty; ++ty) {
     for (int tx = 0; tx < ntx; ++tx) {
-      const int c0 = tx * TW, c1 = c0 + TW;
+      const int c0 = tx * TW, c1 = std::min(c0 + TW, g.pano_pitch);
       int hit = -1, nhit = 0;
       for (int p = 0; p + 1 < g.n; ++p)
         if (c0 < g.band[p][1] && c1 > g.band[p][0]) {
@@ -663,51 +711,42 @@ bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &band_tiles, std
         err = "a camera's own columns are narrower than a fuse tile (" + std::to_string(TW) + " pixels)";
         return false;
       }
-      TileDesc t{};
-      t.tx = (int16_t)tx;
-      t.ty = (int16_t)ty;
-      if (hit >= 0) {
-        t.kind = 1;
-        t.idx = (int8_t)hit;
-        band_tiles.push_back(t);
-      } else {
+      if (hit < 0) {
         int k = 0;
         while (k < g.n - 1 && c0 >= g.own_hi[k]) ++k;
-        const int r0 = ty * TH, r1 = std::min(r0 + TH, g.pano_h) - 1;
-        const int q1 = std::min(c1, g.pano_w) - 1;
-        bool full = c1 <= g.pano_w && r0 + TH <= g.pano_h;
-        auto inside = [&](int x, int y) {
-          double sx, sy, sw;
-          pano_to_cam(g, k, x, y, sx, sy, sw);
-          return sw > 0 && sx >= 0.01 && sx <= g.w[k] - 1.01 && sy >= 0.01 && sy <= g.h[k] - 1.01;
-        };
-        if (!g.cyl) {
-          // planar coverage is convex: the four corners decide
-          full = full && inside(c0, r0) && inside(q1, r0) && inside(c0, r1) && inside(q1, r1);
-        } else {
-          // the cylinder bends the coverage border: test every border pixel
-          for (int x = c0; x <= q1 && full; ++x) full = inside(x, r0) && inside(x, r1);
-          for (int y = r0; y <= r1 && full; ++y) full = inside(c0, y) && inside(q1, y);
-        }
-        t.kind = full ? 0 : 2;
-        t.idx = (int8_t)k;
-        own_tiles.push_back(t);
+        own_piece(k, tx, ty, c0, c1);
+        continue;
+      }
+      const int p = hit;
+      const int bx0 = g.band[p][0], bx1 = g.band[p][1];
+      const int a = bx0 & ~15, b = (bx0 + 15) & ~15;     // chunk holding the left band edge: [a, b)
+      const int a2 = bx1 & ~15, b2 = (bx1 + 15) & ~15;   // chunk holding the right band edge: [a2, b2)
+      // every row of the tile, also past a partial last tile row, inside the band rectangle
+      const int r0 = ty * TH;
+      const bool rows_in = r0 >= g.band[p][2] && r0 + TH <= g.band[p][3];
+      auto clip0 = [&](int v) { return std::min(std::max(v, c0), c1); };
+      own_piece(p, tx, ty, c0, clip0(a));
+      own_piece(p + 1, tx, ty, clip0(b2), c1);
+      if (b <= a2) {
+        band_piece(p, kTileBandPart, tx, ty, clip0(a), clip0(b));
+        band_piece(p, rows_in ? kTileBand : kTileBandPart, tx, ty, clip0(b), clip0(a2));
+        band_piece(p, kTileBandPart, tx, ty, clip0(a2), clip0(b2));
+      } else {
+        band_piece(p, kTileBandPart, tx, ty, clip0(a), clip0(b2));
       }
     }
   }
-  // partly covered own tiles first: the fully covered ones close the list
-  std::stable_partition(own_tiles.begin(), own_tiles.end(), [](const TileDesc &t) { return t.kind != 0; });
+  cnt.n_band = (int)band.size();
+  cnt.n_full = (int)full.size();
+  tiles = gen;
+  tiles.insert(tiles.end(), band.begin(), band.end());
+  tiles.insert(tiles.end(), full.begin(), full.end());
   return true;
 }
 
-int count_full(const std::vector<TileDesc> &own) {
-  int n = 0;
-  for (const TileDesc &t : own) n += t.kind == 0 ? 1 : 0;
-  return n;
-}
-
-// Tiles of the smallest shape (at least 32 x 16): room for any shape's list.
-size_t max_tiles(const Geo &g) { return (size_t)((g.pano_w + 31) / 32) * (size_t)((g.pano_h + 15) / 16); }
+// Pieces of the smallest shape (at least 32 x 16, at most five pieces per
+// tile): room for any shape's list.
+size_t max_tiles(const Geo &g) { return 5 * (size_t)((g.pano_w + 31) / 32) * (size_t)((g.pano_h + 15) / 16); }
 
 // ---------------------------------------------------------------------------
 // Autotuner results: the fastest fuse tile shape per (GPU, rig geometry,
@@ -815,24 +854,26 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   ctx->halo = (int)std::ceil((double)cfg->max_flow) + 1;
 
   ctx->shape = tuned_shape(g, cfg->flags);
-  std::vector<TileDesc> band_tiles, own_tiles;
-  if (!build_tiles(g, ctx->shape, band_tiles, own_tiles, err)) {
+  std::vector<TileDesc> tiles;
+  TileCounts tcnt;
+  if (!build_tiles(g, ctx->shape, tiles, tcnt, err)) {
     if (ctx->shape != 0) {
       ctx->shape = 0;
-      band_tiles.clear();
-      own_tiles.clear();
+      tiles.clear();
     }
-    if (ctx->shape != 0 || !build_tiles(g, 0, band_tiles, own_tiles, err)) {
+    if (ctx->shape != 0 || !build_tiles(g, 0, tiles, tcnt, err)) {
       delete ctx;
       return set_err(nullptr, STITCH_EINVAL, err);
     }
   }
-  ctx->n_band_tiles = (int)band_tiles.size();
-  ctx->n_own_tiles = (int)own_tiles.size();
 
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = estimate_setup();
+  if (e == cudaSuccess) e = fuse_setup_attributes(0);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->raw, kRawSlots * sizeof(RawStats));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->lut, (size_t)kColorSlots * kLutBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->win_fallback, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->win_fallback, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->state, sizeof(ColorState));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, max_tiles(g) * sizeof(TileDesc) + 16);
   if (e == cudaSuccess) e = cudaMemset(ctx->raw, 0, kRawSlots * sizeof(RawStats));
@@ -859,12 +900,8 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->pw, kPwSlots * ctx->pw_slot_bytes + 16);
   if (e == cudaSuccess && !pw_tiles.empty())
     e = cudaMemcpy(ctx->pw_tiles, pw_tiles.data(), pw_tiles.size() * sizeof(PwTile), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    std::vector<TileDesc> all(band_tiles);
-    all.insert(all.end(), own_tiles.begin(), own_tiles.end());
-    if (!all.empty())
-      e = cudaMemcpy(ctx->tiles, all.data(), all.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
-  }
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpy(ctx->tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     ColorState *h = new ColorState();
     std::memset(h, 0, sizeof(ColorState));
@@ -879,6 +916,10 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
       for (int c = 0; c < 3; ++c) h->out[s].curve[c].ident = 1.0f;
     e = cudaMemcpy(ctx->state, h, sizeof(ColorState), cudaMemcpyHostToDevice);
     delete h;
+    // the identity curve's output table in every colour slot
+    for (int sl = 0; sl < kColorSlots && e == cudaSuccess; ++sl)
+      e = launch_curve_lut(&ctx->state->out[sl], cfg->flags, ctx->lut + (size_t)sl * kLutBytes, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
@@ -940,6 +981,8 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   ep.raw = ctx->raw;
   ep.raw_slots = kRawSlots;
   ep.state = ctx->state;
+  ep.flags = ctx->flags;
+  ep.lut = ctx->lut;
 
   FuseParams &fp = ctx->fp;
   fp = FuseParams{};
@@ -950,8 +993,9 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   fp.pano_pitch = g.pano_pitch;
   fp.halo = ctx->halo;
   fp.max_flow = ctx->max_flow;
-  fp.n_tiles = ctx->n_band_tiles + ctx->n_own_tiles;
-  fp.n_full = count_full(own_tiles);
+  fp.n_tiles = (int)tiles.size();
+  fp.n_band = tcnt.n_band;
+  fp.n_full = tcnt.n_full;
   fp.tiles = ctx->tiles;
   fp.n_pw_tiles = (int)pw_tiles.size();
   fp.pw_tiles = ctx->pw_tiles;
@@ -976,6 +1020,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
       }
       const double sc = 1.0 / hs[8];
       for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(hs[e2] * sc);
+      for (int e2 = 0; e2 < 9; ++e2) c.hm[e2] = (float)((hs[e2] - (e2 < 6 ? 0.5 * hs[6 + e2 % 3] : 0.0)) * sc);
       c.affine = (hs[6] == 0.0 && hs[7] == 0.0) ? 1 : 0;
       c.cyl = 0;
     } else {
@@ -986,6 +1031,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
       const double *A = g.Hi[k];
       const double sc = 1.0 / std::sqrt(A[6] * A[6] + A[7] * A[7] + A[8] * A[8]);
       for (int e2 = 0; e2 < 9; ++e2) c.h[e2] = (float)(A[e2] * sc);
+      for (int e2 = 0; e2 < 9; ++e2) c.hm[e2] = (float)((A[e2] - (e2 < 6 ? 0.5 * A[6 + e2 % 3] : 0.0)) * sc);
       c.affine = 0;
       c.cyl = 1;
       c.cyl_finv = (float)(1.0 / g.f);
@@ -1318,7 +1364,7 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   // The float32 band pre-warp into the flow's own buffer, then the flow.
   const float *none[kMaxPairs] = {};
   FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
-  fp.flags &= ~STITCH_FP16_INTERMEDIATE;
+  fp.flags &= ~(STITCH_FP16_INTERMEDIATE | kFlagPwOffset);
   fp.pw = ctx->flow_pw;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   e = launch_prewarp(fp, s);
@@ -1358,7 +1404,7 @@ int stitch_pair_M_correspondence(stitch_ctx *ctx, const uint8_t *const *frames_d
   // The float32 band pre-warp into the context's own buffer, then the sums.
   const float *none[kMaxPairs] = {};
   FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
-  fp.flags &= ~STITCH_FP16_INTERMEDIATE;
+  fp.flags &= ~(STITCH_FP16_INTERMEDIATE | kFlagPwOffset);
   fp.pw = ctx->flow_pw;
   if (e == cudaSuccess) e = launch_prewarp(fp, nullptr);
   if (e == cudaSuccess) e = launch_corr(cp, blocks, nullptr);
@@ -1615,6 +1661,10 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
     else
       e = cudaMemset(ctx->ls, 0, sizeof(LearnedState));
   }
+  // the output tables follow the restored curves
+  for (int sl = 0; sl < kColorSlots && e == cudaSuccess; ++sl)
+    e = launch_curve_lut(&ctx->state->out[sl], ctx->flags, ctx->lut + (size_t)sl * kLutBytes, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, e, "state write");
   ctx->host_T = hd.host_T;
   return STITCH_OK;
@@ -1700,6 +1750,17 @@ int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used)
 
 int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
 
+int stitch_window_fallbacks(stitch_ctx *ctx, unsigned long long *count, int reset) {
+  if (!ctx || !count) return set_err(ctx, STITCH_EINVAL, "ctx and count are required");
+  unsigned int v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->win_fallback, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(ctx->win_fallback, 0, sizeof(unsigned int));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "window fallback counter");
+  *count = v;
+  return STITCH_OK;
+}
+
 int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
                     const float *const *flow_ji_dev, uint8_t *pano_dev, int reps, int *shape_out, float *ms_out) {
   NvtxRange nvtx_("stitch_autotune");
@@ -1725,19 +1786,18 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   float ms[kNumTileShapes];
   int best = -1;
-  std::vector<TileDesc> bt, ot;
+  std::vector<TileDesc> bt;
+  TileCounts tc;
   std::string err;
   for (int sh = 0; sh < kNumTileShapes && e == cudaSuccess; ++sh) {
     ms[sh] = -1.0f;
     bt.clear();
-    ot.clear();
-    if (!build_tiles(ctx->g, sh, bt, ot, err)) continue;
-    const int nfull = count_full(ot);
-    bt.insert(bt.end(), ot.begin(), ot.end());
+    if (!build_tiles(ctx->g, sh, bt, tc, err)) continue;
     e = cudaMemcpyAsync(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s);
     fp.tiles = ctx->tiles;
     fp.n_tiles = (int)bt.size();
-    fp.n_full = nfull;
+    fp.n_band = tc.n_band;
+    fp.n_full = tc.n_full;
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_fuse(fp, sh, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fuse(fp, sh, s);
@@ -1756,14 +1816,11 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
   // Keep the winner: its tile list goes back into the context.
   if (e == cudaSuccess) {
     bt.clear();
-    ot.clear();
-    build_tiles(ctx->g, best, bt, ot, err);
-    ctx->n_band_tiles = (int)bt.size();
-    ctx->n_own_tiles = (int)ot.size();
-    ctx->fp.n_full = count_full(ot);
-    bt.insert(bt.end(), ot.begin(), ot.end());
+    build_tiles(ctx->g, best, bt, tc, err);
     e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
     ctx->fp.n_tiles = (int)bt.size();
+    ctx->fp.n_band = tc.n_band;
+    ctx->fp.n_full = tc.n_full;
     ctx->shape = best;
   }
   if (e != cudaSuccess) return cuda_err(ctx, e, "autotune");
@@ -1785,18 +1842,16 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
 int stitch_set_tile_shape(stitch_ctx *ctx, int shape) {
   if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
   if (shape < 0 || shape >= kNumTileShapes) return set_err(ctx, STITCH_EINVAL, "no such tile shape");
-  std::vector<TileDesc> bt, ot;
+  std::vector<TileDesc> bt;
+  TileCounts tc;
   std::string err;
-  if (!build_tiles(ctx->g, shape, bt, ot, err)) return set_err(ctx, STITCH_EINVAL, err);
+  if (!build_tiles(ctx->g, shape, bt, tc, err)) return set_err(ctx, STITCH_EINVAL, err);
   cudaError_t e = cudaDeviceSynchronize();
-  ctx->n_band_tiles = (int)bt.size();
-  ctx->n_own_tiles = (int)ot.size();
-  const int nfull = count_full(ot);
-  bt.insert(bt.end(), ot.begin(), ot.end());
   if (e == cudaSuccess) e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_err(ctx, e, "tile list upload");
   ctx->fp.n_tiles = (int)bt.size();
-  ctx->fp.n_full = nfull;
+  ctx->fp.n_band = tc.n_band;
+  ctx->fp.n_full = tc.n_full;
   ctx->shape = shape;
   for (auto &ge : ctx->graphs) {
     if (ge.exec) cudaGraphExecDestroy(ge.exec);
@@ -1879,17 +1934,20 @@ int batch_items(stitch_batch *b, const std::vector<int> &shapes) {
   for (int r = 0; r < (int)b->ctx.size(); ++r) {
     const int sh = shapes[r];
     if (sh < 0 || sh >= kNumTileShapes) return batch_err(b, STITCH_EINVAL, "tile shape out of range");
-    std::vector<TileDesc> bt, ot;
-    if (!build_tiles(b->ctx[r]->g, sh, bt, ot, err)) return batch_err(b, STITCH_EINVAL, err);
-    for (const TileDesc &t : bt) band.push_back(MultiItem{r, sh, t, PwTile{}});
-    for (const TileDesc &t : ot) (t.kind == 0 ? full : part).push_back(MultiItem{r, sh, t, PwTile{}});
+    std::vector<TileDesc> bt;
+    TileCounts tc;
+    if (!build_tiles(b->ctx[r]->g, sh, bt, tc, err)) return batch_err(b, STITCH_EINVAL, err);
+    for (const TileDesc &t : bt)
+      (t.kind == kTileOwn ? full : t.kind == kTileBand ? band : part).push_back(MultiItem{r, sh, t, PwTile{}});
     const Geo &g = b->ctx[r]->g;
     for (int p = 0; p + 1 < g.n; ++p)
       for (int y = g.band[p][2]; y < g.band[p][3]; y += kTileH)
         for (int x = g.band[p][0]; x < g.band[p][1]; x += kTileW)
           pw.push_back(MultiItem{r, 0, TileDesc{}, PwTile{p, x, y}});
   }
-  band.insert(band.end(), part.begin(), part.end());
+  // the general pieces (costliest per pixel) first, so that the dynamic schedule ends evenly
+  part.insert(part.end(), band.begin(), band.end());
+  band.swap(part);
   cudaFree(b->fuse_items);
   cudaFree(b->own_items);
   cudaFree(b->pw_items);
@@ -2249,6 +2307,8 @@ void stitch_destroy(stitch_ctx *ctx) {
   cudaFree(ctx->tiles);
   cudaFree(ctx->pw_tiles);
   cudaFree(ctx->pw);
+  cudaFree(ctx->lut);
+  cudaFree(ctx->win_fallback);
   for (HostStage &hs : ctx->stage) {
     for (int k = 0; k < kMaxCams; ++k) cudaFree(hs.frames[k]);
     for (int p = 0; p < kMaxPairs; ++p) {

@@ -34,6 +34,31 @@ namespace {
 using namespace est;
 
 constexpr int kT = 1024;
+
+// One entry of the output table: the fused, clamped value x = n / 16 through
+// the balance curve F (Eq. 5, as read for the oracle: linear between the
+// knots, the gamma tails outside them, identity for a degenerate span or with
+// the balance off), clamped to [0, 255] and rounded half to even.
+__device__ __forceinline__ uint32_t lut_entry(const Curve &cv, bool off, int n) {
+  const float x = fminf((float)n * (1.0f / 16.0f), 255.0f);
+  float F = x;
+  if (!off && cv.ident == 0.0f) {
+    F = cv.d1 + cv.s * (x - cv.m1);
+    if (cv.m1 > 0.0f && x < cv.m1) F = cv.d1 * powf(x * cv.inv_m1, cv.g1);
+    if (cv.m2 < 255.0f && x > cv.m2) F = 255.0f - (255.0f - cv.d2) * powf((255.0f - x) * cv.inv_bm, cv.g2);
+  }
+  return (uint32_t)__float2int_rn(fminf(fmaxf(F, 0.0f), 255.0f));
+}
+
+// The three channel tables (kLutEntries bytes each), four entries per store.
+__device__ void write_lut(const Curve *cv, bool off, uint8_t *lut) {
+  uint32_t *L = reinterpret_cast<uint32_t *>(lut);
+  for (int i = threadIdx.x; i < kLutBytes / 4; i += blockDim.x) {
+    const int c = (4 * i) / kLutEntries, n = (4 * i) % kLutEntries;
+    L[i] = lut_entry(cv[c], off, n) | (lut_entry(cv[c], off, n + 1) << 8) | (lut_entry(cv[c], off, n + 2) << 16) |
+           (lut_entry(cv[c], off, n + 3) << 24);
+  }
+}
 constexpr int kWarps = kT / 32;
 constexpr int kScanTasksMax = kMaxPairs * 6 + 3;
 
@@ -44,6 +69,7 @@ struct EstSmem {
   double M_cam[kMaxCams][9];
   int knot[3][2];
   int sing;
+  Curve curve[3];
 };
 
 __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
@@ -209,6 +235,7 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
     cv.inv_bm = m2 < 255.0f ? 1.0f / (255.0f - m2) : 0.0f;
     cv.ident = ident ? 1.0f : 0.0f;
     S->out[T % kColorSlots].curve[c] = cv;
+    sm.curve[c] = cv;
   } else if (warp >= 2) {
     // 7. Clear the slot of frame T - 1 (already consumed): the stats pass of
     //    frame T + raw_slots - 1 accumulates into it. Warps 2..31 only, so the
@@ -218,7 +245,16 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
     for (int i = tid - 64; i < n16; i += kT - 64) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
+  // 8. The output table of this frame's curve (read by the fuse kernels).
+  if (P.lut) write_lut(sm.curve, (P.flags & STITCH_BALANCE_OFF) != 0, P.lut + (size_t)(T % kColorSlots) * kLutBytes);
   if (tid == 0) S->T = T + 1;
+}
+
+__global__ void __launch_bounds__(256) k_curve_lut(const ColorOut *slot, int flags, uint8_t *lut) {
+  __shared__ Curve cv[3];
+  if (threadIdx.x < 3) cv[threadIdx.x] = slot->curve[threadIdx.x];
+  __syncthreads();
+  write_lut(cv, (flags & STITCH_BALANCE_OFF) != 0, lut);
 }
 
 }  // namespace
@@ -248,6 +284,11 @@ cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_estimate, p);
+}
+
+cudaError_t launch_curve_lut(const ColorOut *slot, int flags, uint8_t *lut, cudaStream_t s) {
+  k_curve_lut<<<1, 256, 0, s>>>(slot, flags, lut);
+  return cudaGetLastError();
 }
 
 }  // namespace stitch

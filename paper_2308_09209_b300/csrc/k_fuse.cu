@@ -1,48 +1,59 @@
 // K3 -- pre-warp, local warping, colour transfer, blend and balance
 // (paper section 3.1 pre-warp; section 3.2 Eq. 15-18; Eq. 4; Eq. 5).
 //
-// Two kernels per frame:
+// Kernels of one frame:
 //
 // k_prewarp_band: the pre-warped image of section 3.1 over each pair's blend
 //   band, for BOTH cameras of the pair, computed once per band pixel and kept
 //   in a small intermediate (float32 RGB, or float16 with
-//   STITCH_FP16_INTERMEDIATE). It does not depend on the colour estimate.
+//   STITCH_FP16_INTERMEDIATE). It does not depend on the colour estimate. In
+//   the frame path the intermediate holds v - 128 (the offset form below).
 //
-// k_fuse: one block per panorama tile (64 x 32 by default; the shape is a
-//   template parameter the autotuner picks per rig). The fully covered own
-//   tiles (about three quarters of a rig's tiles) run in a second launch,
-//   k_fuse_own, whose one-camera code needs fewer registers and no spills.
-//   * Own tiles (columns of one camera k): the source window that the tile
-//     maps to through H_k^-1 (planar) or through the cylinder's ray and H_k^-1
-//     (cylindrical panorama) is staged in shared memory as one RGBX word per
-//     pixel; every pixel then computes s = H_k^-1 q (float32, relative to the
-//     camera's panorama origin), tests coverage 0 <= s <= (w-1, h-1), reads its
-//     four bilinear taps from shared memory and forms v = P . M_k. Pixels that
-//     camera k does not cover fall back to k-1, then k+1 (Eq. 15's one-image
-//     cases), else 0.
-//   * Band tiles: pixels of the band rectangle compute
-//       theta_j = (x - x0 + 0.5) / (x1 - x0), theta_i = 1 - theta_j (Eq. 16 read
-//       as a ramp), X_i = q + theta_j clamp(flow_ij), X_j = q + theta_i
-//       clamp(flow_ji) (Eq. 17, continuous reading; the printed weights under
-//       STITCH_FLOW_WEIGHTS_PRINTED), clamp X into the band and sample the
-//       pre-warped intermediate bilinearly (Eq. 18):
-//       out = theta_i P_i(X_i) M_i + theta_j P_j(X_j) M_j.
-//     The tile's other pixels (own columns beside the band, band columns
-//     outside the band rows) use the staged windows of both cameras as above,
-//     blending both cameras without flow where both cover a band-column pixel.
-//   * Each channel is clamped to [0, 255], passed through the piecewise balance
-//     curve F (Eq. 5: gamma, linear, gamma) and rounded half to even; pixels
-//     go to a shared-memory tile and leave as 16-byte stores per plane.
+// k_fuse_own: the fully covered own tiles (columns of one camera k, every
+//   pixel seen by k with a margin), about three quarters of a rig's tiles.
+//   The source window that a tile maps to through H_k^-1 (planar) or through
+//   the cylinder's ray and H_k^-1 is staged in shared memory as one RGBX word
+//   per pixel whose fourth byte is 0x64, so that one byte permute turns the
+//   same channel of two pixels into a half2 pair (1024 + v0, 1024 + v1).
+//   A thread takes its pixels two at a time:
+//   * s = H_k^-1 q for both in packed float32 (f32x2 FMA), relative to the
+//     window and shifted by half a pixel, one reciprocal per pixel;
+//   * integer tap and fraction by the round-to-nearest magic constant;
+//   * the bilinear sample (Eq. 18's kernel, section 3.1) in half2 on v - 128:
+//     a + fx (b - a) + fy ((d - a) + fx ((e - d) - (b - a))), exact tap
+//     differences, every rounding within 1/32 of a grey level of the exact
+//     interpolant for the fraction rounded to half precision;
+//   * v . M (Eq. 4) in packed float32 with the offset folded into a per-
+//     channel bias, the last product saturating to [0, 1] (M is pre-scaled by
+//     1/255), which is the clamp to [0, 255];
+//   * balance (Eq. 5) and rounding through the colour slot's output table:
+//     byte = table[round(4080 u)], the curve evaluated at the fused value
+//     rounded to a sixteenth of a grey level.
 //
-// Thread mapping: lane l of a warp handles columns l + 32 a of the warp's
-// rows, so a warp touches 32 consecutive pixels of a row at a time and its
-// shared-memory tap reads fall in distinct banks.
+// k_fuse: the band tiles and the partly covered own tiles.
+//   * Pixels of a band rectangle: theta_j = (x - x0 + 0.5) / (x1 - x0),
+//     theta_i = 1 - theta_j (Eq. 16 read as a ramp), X_i = q + theta_j
+//     clamp(flow_ij), X_j = q + theta_i clamp(flow_ji) (Eq. 17, continuous
+//     reading; the printed weights under STITCH_FLOW_WEIGHTS_PRINTED), X
+//     clamped into the band (skipped for tiles whose reach stays inside it),
+//     the bilinear sample of the pre-warped intermediate (Eq. 18), then
+//     out = theta_i P_i(X_i) M_i + theta_j P_j(X_j) M_j through the table.
+//   * Other pixels (own columns beside the band, band columns outside the
+//     band rows, partly covered tiles) take the general float32 path: staged
+//     windows of both cameras, coverage tests, Eq. 15's one-image fallbacks
+//     (k, then k - 1, then k + 1), blending both cameras without flow where
+//     both cover a band-column pixel, uncovered pixels 0.
+//   Pixels go to a shared-memory tile and leave as 16-byte stores per plane.
+//
+// Both fuse kernels are persistent: a block loads the colour matrices and
+// the 12 KB output table once and then takes tiles with a fixed stride.
 //
 // k_prewarp_multi / k_fuse_multi / k_fuse_own_multi: the same work over the
-// tiles of several independent rigs in one launch each; the fuse kernels are
-// persistent (one block per resident slot, tiles taken from a work counter).
-// When the rigs' tile shapes differ, the *_mixed forms run every tile with
-// its rig's shape.
+// tiles of several independent rigs in one launch each; the fuse kernels
+// take tiles from a work counter and reload the colour constants when the
+// rig changes. When the rigs' tile shapes differ, the *_mixed forms run
+// every tile with its rig's shape.
+#include <algorithm>
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -52,12 +63,39 @@ namespace stitch {
 namespace {
 
 constexpr float kMagicRound = 12582912.0f;   // 1.5 * 2^23: x + kMagicRound rounds x to an integer (RNE)
-constexpr int kMagicRoundBits = 0x4B400000;
+constexpr uint32_t kMagicRoundBits = 0x4B400000u;
 constexpr float kMagicByte = 8388608.0f;     // 2^23: the float with bits 0x4B0000bb is 2^23 + bb
-constexpr int kWinCap = 3840;                // staged source pixels per window (15 KB)
+constexpr uint32_t kXByte = 0x64u;           // fourth byte of a staged word: [v, 0x64] is the half 1024 + v
+constexpr float kHalfOffset = 1152.0f;       // 1024 + 128: half (1024 + v) minus this is v - 128
 
-// Approximate reciprocal (CUDA's fast division intrinsic: a few ulp).
-__device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
+// Source windows: a fixed row stride per tile shape (tap offsets become
+// immediates); windows wider or taller than the capacity fall back to
+// per-pixel global gathers and are counted.
+template <int TW, int TH>
+struct WinGeom {
+  static constexpr int kStride = TW + TW / 2;          // words per staged row
+  static constexpr int kRows = TH + 16 + (TW >= 128 ? 8 : 0);   // a wide tile spans more rotated rows
+  static constexpr int kAlloc = kStride * kRows + kStride + 8;   // + a guard row for zero-weight taps
+  static_assert(kStride % 4 == 0, "window rows are staged four pixels at a time");
+};
+
+// Approximate reciprocal (the hardware's one-instruction rcp.approx, flushing
+// subnormals: within one ulp; a camera's w is near 1 wherever it is used).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ __half2 as_h2(uint32_t v) {
+  __half2 h;
+  *reinterpret_cast<uint32_t *>(&h) = v;
+  return h;
+}
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<const uint32_t *>(&h); }
 
 // s = H^-1 q for panorama point (x, y) given as floats relative to the origin.
 // Cylindrical panorama: q stands for the ray (sin theta, h, cos theta) with
@@ -82,22 +120,12 @@ __device__ __forceinline__ void cam_map_f(const CamDev &c, float dx, float dy, f
   sy = ny * r;
 }
 
-// Affine camera (no perspective row): s = H^-1 q without a divide.
-__device__ __forceinline__ void cam_map_aff(const CamDev &c, float dx, float dy, float &sx, float &sy) {
-  sx = fmaf(c.h[0], dx, fmaf(c.h[1], dy, c.h[2]));
-  sy = fmaf(c.h[3], dx, fmaf(c.h[4], dy, c.h[5]));
-}
-
-__device__ __forceinline__ bool covered(const CamDev &c, float sx, float sy, float nw) {
-  return nw > 0.0f && sx >= 0.0f && sx <= c.wm1 && sy >= 0.0f && sy <= c.hm1;
-}
-
 // Integer part and fraction of s with fraction in [0, 1]; for integer s the
 // pair (s - 1, 1) may come back instead of (s, 0): both give the same bilinear
 // sample, and the right-hand tap then never passes the last row / column.
 __device__ __forceinline__ void split(float s, int &i, float &f) {
   const float r = (s - 0.5f) + kMagicRound;
-  i = __float_as_int(r) - kMagicRoundBits;
+  i = __float_as_int(r) - (int)kMagicRoundBits;
   f = s - (r - kMagicRound);
 }
 
@@ -106,7 +134,7 @@ __device__ __forceinline__ float mbyte(uint32_t w, int c) {
   return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + c));
 }
 
-// Bilinear of four RGBX words with fractions (fx, fy): (1-fy)((1-fx) a + fx b) + fy((1-fx) d + fx e).
+// Bilinear of four RGBX words with fractions (fx, fy), float32.
 __device__ __forceinline__ float3 bilerp_words(uint32_t a, uint32_t b, uint32_t d, uint32_t e, float fx, float fy) {
   float o[3];
 #pragma unroll
@@ -144,21 +172,12 @@ __device__ __forceinline__ float3 src_bilinear(const uint8_t *__restrict__ src, 
   return o;
 }
 
-// Row-vector product v . M (Eq. 4).
-__device__ __forceinline__ float3 mulM(const float *M, float3 v) {
-  float3 o;
-  o.x = fmaf(v.x, M[0], fmaf(v.y, M[3], v.z * M[6]));
-  o.y = fmaf(v.x, M[1], fmaf(v.y, M[4], v.z * M[7]));
-  o.z = fmaf(v.x, M[2], fmaf(v.y, M[5], v.z * M[8]));
-  return o;
-}
-
 // ---------------------------------------------------------------------------
 // Source windows in shared memory.
 // ---------------------------------------------------------------------------
 
 struct Window {
-  int x0, y0, w, h, stride, ok;
+  int x0, y0, w, h, ok;
 };
 
 // Source window of the panorama rectangle [rx0, rx1] x [ry0, ry1] (inclusive)
@@ -166,6 +185,7 @@ struct Window {
 // and the right / bottom tap, clipped to the frame. Computed by one warp (lane
 // & 3 picks a corner); every lane returns the same window. ok = 0 when a corner
 // maps behind the camera, the box is empty or it exceeds the capacity.
+template <int kStride, int kRows>
 __device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry1) {
   const int k = threadIdx.x & 3;
   const int px = (k & 1) ? rx1 : rx0;
@@ -193,69 +213,72 @@ __device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry
   const int y1 = min(c.h_px - 1, (int)floorf(hi_y) + 2);
   W.w = x1 - W.x0 + 1;
   W.h = y1 - W.y0 + 1;
-  W.stride = (W.w + 3) & ~3;
-  W.ok = (front && W.w >= 2 && W.h >= 2 && W.stride * W.h <= kWinCap) ? 1 : 0;
+  W.ok = (front && W.w >= 2 && W.h >= 2 && W.w <= kStride && W.h <= kRows) ? 1 : 0;
   return W;
 }
 
 __device__ __forceinline__ Window no_window() {
   Window W;
-  W.x0 = W.y0 = W.w = W.h = W.stride = W.ok = 0;
+  W.x0 = W.y0 = W.w = W.h = W.ok = 0;
   return W;
 }
 
-// Stage the window as RGBX words: four pixels (12 bytes) per step, read as
-// aligned 32-bit words and realigned with funnel shifts.
+// Stage the window as RGBX words (fourth byte 0x64): four pixels (12 bytes)
+// per step, read as aligned 32-bit words and realigned with funnel shifts.
+// Every row also gets the word just past the window (a real pixel, or 0x64
+// past the frame) and the row below the window is filled with 0x64 words:
+// a tap with zero weight there still reads a finite value.
+template <int kStride>
 __device__ void stage_window(const uint8_t *__restrict__ src, const CamDev &c, const Window &W, uint32_t *s) {
-  const int G = W.stride >> 2;
-  const uintptr_t end = reinterpret_cast<uintptr_t>(src) + (uintptr_t)c.pitch * (uintptr_t)(c.h_px - 1) +
-                        (uintptr_t)(3 * c.w);
-  const int nt = blockDim.x;
-  const bool rows = G <= nt;
-  const int rpi = rows ? nt / G : 0;
-  if (rows && (int)threadIdx.x >= rpi * G) return;
-  int r = rows ? (int)threadIdx.x / G : 0;
-  int g = rows ? (int)threadIdx.x - r * G : 0;
-  int i = threadIdx.x;
-  while (true) {
-    if (!rows) {
-      if (i >= G * W.h) break;
-      r = i / G;
-      g = i - r * G;
-    } else if (r >= W.h) {
-      break;
-    }
-    const int px = W.x0 + 4 * g;
-    const uint8_t *b = src + (size_t)(W.y0 + r) * c.pitch + 3 * px;
-    const uintptr_t B = reinterpret_cast<uintptr_t>(b);
-    const uintptr_t A = B & ~(uintptr_t)3;
+  const int G = min((W.w + 4) >> 2, kStride >> 2);
+  for (int i = threadIdx.x; i < kStride + 4; i += blockDim.x) s[W.h * kStride + i] = kXByte << 24;
+  // G <= kStride / 4 <= blockDim.x: thread i takes group i % G of rows i / G,
+  // i / G + rows_per_pass, ... (one division per window)
+  const int rpp = blockDim.x / G;
+  const int r_first = threadIdx.x / G;
+  const int g = threadIdx.x - r_first * G;
+  if (r_first >= rpp || r_first >= W.h) return;
+  const int px = W.x0 + 4 * g;
+  const int nvalid = min(4, c.w - px);              // pixels of the group inside the frame
+  const uint32_t col = 3u * (uint32_t)px;           // byte offset of the group in its row
+  // With a pitch that is a multiple of 4, every row's group has the same
+  // misalignment; the four aligned words from there hold its 12 bytes.
+  const uintptr_t B = reinterpret_cast<uintptr_t>(src + (size_t)(W.y0 + r_first) * c.pitch + col);
+  const uint32_t lead = (uint32_t)(B & 3u), sh = lead * 8u;
+  const uint32_t *wrow = reinterpret_cast<const uint32_t *>(B - lead);
+  const size_t wstep = (size_t)rpp * (size_t)c.pitch / 4;
+  const bool vec_ok = nvalid == 4 && (c.pitch & 3) == 0;
+  // On the frame's last row the 16 bytes read must end inside its 3 w bytes.
+  const int last_vec_row = (col - lead + 16u <= 3u * (uint32_t)c.w) ? c.h_px - 1 : c.h_px - 2;
+  uint32_t *dst = s + r_first * kStride + 4 * g;
+  for (int r = r_first; r < W.h; r += rpp, wrow += wstep, dst += rpp * kStride) {
     uint32_t p0, p1, p2, p3;
-    if (px + 4 <= c.w && A + 16 <= end) {
-      const uint32_t *wp = reinterpret_cast<const uint32_t *>(A);
-      const uint32_t w0 = __ldg(wp), w1 = __ldg(wp + 1), w2 = __ldg(wp + 2), w3 = __ldg(wp + 3);
-      const uint32_t sh = (uint32_t)(B - A) * 8u;
+    if (vec_ok && W.y0 + r <= last_vec_row) {
+      const uint32_t w0 = __ldg(wrow), w1 = __ldg(wrow + 1), w2 = __ldg(wrow + 2), w3 = __ldg(wrow + 3);
       const uint32_t q0 = __funnelshift_r(w0, w1, sh);
       const uint32_t q1 = __funnelshift_r(w1, w2, sh);
       const uint32_t q2 = __funnelshift_r(w2, w3, sh);
-      p0 = __byte_perm(q0, 0u, 0x4210u);
-      p1 = __byte_perm(q0, q1, 0x4543u);
-      p2 = __byte_perm(q1, q2, 0x4432u);
-      p3 = __byte_perm(q2, 0u, 0x4321u);
+      p0 = __byte_perm(q0, kXByte, 0x4210u);
+      p1 = (__byte_perm(q0, q1, 0x0543u) & 0x00ffffffu) | (kXByte << 24);
+      p2 = (__byte_perm(q1, q2, 0x0432u) & 0x00ffffffu) | (kXByte << 24);
+      p3 = __byte_perm(q2, kXByte, 0x4321u);
     } else {
+      const uint8_t *b = src + (size_t)(W.y0 + r) * c.pitch + col;
       uint32_t q[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        if (px + k < c.w)
+        if (k < nvalid)
           q[k] = (uint32_t)__ldg(b + 3 * k) | ((uint32_t)__ldg(b + 3 * k + 1) << 8) |
                  ((uint32_t)__ldg(b + 3 * k + 2) << 16);
-      p0 = q[0]; p1 = q[1]; p2 = q[2]; p3 = q[3];
+      p0 = q[0] | (kXByte << 24); p1 = q[1] | (kXByte << 24);
+      p2 = q[2] | (kXByte << 24); p3 = q[3] | (kXByte << 24);
     }
-    *reinterpret_cast<uint4 *>(s + r * W.stride + 4 * g) = make_uint4(p0, p1, p2, p3);
-    if (rows) r += rpi; else i += nt;
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(p0, p1, p2, p3);
   }
 }
 
-// Bilinear sample from a staged window (taps clamped into the window).
+// Bilinear sample from a staged window (taps clamped into the window), float32.
+template <int kStride>
 __device__ __forceinline__ float3 win_bilinear(const uint32_t *s, const Window &W, float sx, float sy) {
   int ix, iy;
   float fx, fy;
@@ -268,404 +291,761 @@ __device__ __forceinline__ float3 win_bilinear(const uint32_t *s, const Window &
   if (ly > W.h - 2) { ly = W.h - 2; fy = 1.0f; }
   lx = max(lx, 0);
   ly = max(ly, 0);
-  const uint32_t *p = s + ly * W.stride + lx;
-  return bilerp_words(p[0], p[1], p[W.stride], p[W.stride + 1], fx, fy);
+  const uint32_t *p = s + ly * kStride + lx;
+  return bilerp_words(p[0], p[1], p[kStride], p[kStride + 1], fx, fy);
 }
 
 // ---------------------------------------------------------------------------
-// Colour and balance, prepared once per block.
+// Shared memory common to every fuse kernel: colour constants, window
+// descriptors, the output table and (multi-rig kernels) the rig's parameters.
 // ---------------------------------------------------------------------------
-
-struct Tail {       // gamma tails of Eq. 5 on u = v / 255
-  float d1, k1, g1; // dark:   F = d1 (u k1)^g1
-  float e2, k2, g2; // bright: F = 255 - e2 ((1 - u) k2)^g2
-};
 
 struct BlockColor {
-  float M[kMaxCams][9];   // M / 255, so fused values land in [0, 1]
-  float lo[3], hi[3];     // knots m1/255, m2/255 (outside [0, 1] when there is no tail)
-  float mid[3], half[3];  // (lo + hi) / 2, (hi - lo) / 2: a tail is |u - mid| > half
-  float A[3], B[3];       // linear part F = A + B u
-  Tail tail[3];
+  float M[kMaxCams][9];      // M / 255, so fused values land in [0, 1]
+  float bias[kMaxCams][3];   // 128 * sum_c M[c][k] / 255: the correction for taps held as v - 128
+  // per camera and output channel k, as register pairs for the f32x2 path:
+  // (M[6+k], M[6+k], bias[k], bias[k]) and (M[3+k], M[3+k], M[k], M[k])
+  float4 pr[kMaxCams][3][2];
+  // per camera and output channel k: (M[k], M[3+k], M[6+k], bias[k])
+  float4 col[kMaxCams][3];
 };
 
-__device__ void load_block_color(const FuseParams &P, BlockColor &bc) {
+struct __align__(16) SmemHead {
+  FuseParams sp;             // multi-rig kernels: the current rig's parameters
+  BlockColor bc;
+  Window sW[2];
+  int item;
+  int rig;
+  __align__(16) uint8_t lut[kLutBytes];
+};
+
+template <int TW, int TH, int NW>
+struct __align__(16) SmemTile {
+  __align__(16) uint32_t win[NW][WinGeom<TW, TH>::kAlloc];
+  __align__(16) uint8_t out[3][TH][TW];
+};
+
+template <int TW, int TH, int NW>
+constexpr size_t smem_bytes() {
+  return (sizeof(SmemHead) + 15) / 16 * 16 + sizeof(SmemTile<TW, TH, NW>);
+}
+
+template <int TW, int TH, int NW>
+__device__ __forceinline__ SmemTile<TW, TH, NW> &tile_smem(unsigned char *base) {
+  return *reinterpret_cast<SmemTile<TW, TH, NW> *>(base + (sizeof(SmemHead) + 15) / 16 * 16);
+}
+
+// The colour constants and the output table of a rig (all threads; the
+// caller synchronises before use).
+__device__ void load_color(const FuseParams &P, SmemHead &h) {
   const int t = threadIdx.x;
-  if (t < kMaxCams * 9) bc.M[t / 9][t % 9] = P.color->M[t / 9][t % 9] * (1.0f / 255.0f);
-  if (t >= 96 && t < 99) {
-    const int c = t - 96;
-    const Curve cv = P.color->curve[c];
-    if ((P.flags & STITCH_BALANCE_OFF) || cv.ident != 0.0f) {
-      bc.lo[c] = -1.0f;
-      bc.hi[c] = 2.0f;
-      bc.A[c] = 0.0f;
-      bc.B[c] = 255.0f;
-    } else {
-      bc.lo[c] = cv.m1 * (1.0f / 255.0f);
-      bc.hi[c] = cv.m2 * (1.0f / 255.0f);
-      bc.A[c] = cv.d1 - cv.s * cv.m1;
-      bc.B[c] = 255.0f * cv.s;
-    }
-    bc.mid[c] = 0.5f * (bc.lo[c] + bc.hi[c]);
-    bc.half[c] = 0.5f * (bc.hi[c] - bc.lo[c]);
-    Tail tl;
-    tl.d1 = cv.d1;
-    tl.k1 = 255.0f * cv.inv_m1;
-    tl.g1 = cv.g1;
-    tl.e2 = 255.0f - cv.d2;
-    tl.k2 = 255.0f * cv.inv_bm;
-    tl.g2 = cv.g2;
-    bc.tail[c] = tl;
+  if (t < kMaxCams * 9) h.bc.M[t / 9][t % 9] = P.color->M[t / 9][t % 9] * (1.0f / 255.0f);
+  if (t >= 96 && t < 96 + kMaxCams * 3) {
+    const int k = (t - 96) / 3, c = (t - 96) % 3;
+    const float *M = P.color->M[k];
+    const float m0 = M[c] * (1.0f / 255.0f), m3 = M[3 + c] * (1.0f / 255.0f), m6 = M[6 + c] * (1.0f / 255.0f);
+    const float b = (128.0f / 255.0f) * (M[c] + M[3 + c] + M[6 + c]);
+    h.bc.bias[k][c] = b;
+    h.bc.pr[k][c][0] = make_float4(m6, m6, b, b);
+    h.bc.pr[k][c][1] = make_float4(m3, m3, m0, m0);
+    h.bc.col[k][c] = make_float4(m0, m3, m6, b);
   }
+  const uint4 *src = reinterpret_cast<const uint4 *>(P.lut);
+  uint4 *dst = reinterpret_cast<uint4 *>(h.lut);
+  for (int i = t; i < kLutBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
-// One channel: clamp (saturate), balance (Eq. 5), round half to even; the low
-// byte of the result is the output byte. The curve's parameters are read from
-// shared memory (keeping them in registers costs more in spills than the
-// loads).
-__device__ __forceinline__ uint32_t finish(const BlockColor &bc, int c, float v) {
-  const float u = __saturatef(v);
-  float F = fmaf(bc.B[c], u, bc.A[c]);
-  if (fabsf(u - bc.mid[c]) > bc.half[c]) {
-    // The side comes from the midpoint: mid -/+ half need not round to the
-    // knots exactly, and a value next to a knot must take that knot's tail
-    // (both pieces meet there).
-    const Tail &t = bc.tail[c];
-    F = (u < bc.mid[c]) ? t.d1 * __powf(u * t.k1, t.g1)
-                       : 255.0f - t.e2 * __powf((1.0f - u) * t.k2, t.g2);
-  }
-  return (uint32_t)__float_as_int(F + kMagicRound);
+// Table index of a fused value u in [0, 1]: round(4080 u), as the low bits of
+// u * 4080 + 1.5 * 2^23.
+__device__ __forceinline__ uint32_t lut_index(float u) {
+  return __float_as_uint(fmaf(u, kLutTop, kMagicRound)) - kMagicRoundBits;
 }
 
-// ---------------------------------------------------------------------------
-// Per-pixel general paths (global memory).
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ bool cam_value_g(const FuseParams &P, const BlockColor &bc, int k, int x, int y,
-                                            float3 &v) {
-  const CamDev &c = P.cam[k];
-  float sx, sy, nw;
-  cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
-  if (!covered(c, sx, sy, nw)) return false;
-  v = mulM(bc.M[k], src_bilinear(P.src[k], c, sx, sy));
-  return true;
-}
-
-// Camera k's value at q, from its staged window when there is one (M points
-// at the block's shared copy of the camera's matrix).
-__device__ __forceinline__ bool cam_value_w(const FuseParams &P, const float *M, int k, const Window &W,
-                                            const uint32_t *s, int x, int y, float3 &v) {
-  const CamDev &c = P.cam[k];
-  float sx, sy, nw;
-  cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
-  if (!covered(c, sx, sy, nw)) return false;
-  v = mulM(M, W.ok ? win_bilinear(s, W, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
-  return true;
-}
-
-template <bool kHalf>
-struct PwT;
-template <>
-struct PwT<false> {
-  using T = float4;
-  __device__ static void put(float4 *p, size_t i, float3 v) { p[i] = make_float4(v.x, v.y, v.z, 0.0f); }
-  __device__ static float3 get(const float4 *p, size_t i) {
-    const float4 q = __ldg(p + i);
-    return make_float3(q.x, q.y, q.z);
-  }
-};
-template <>
-struct PwT<true> {
-  using T = uint2;   // four halves
-  __device__ static void put(uint2 *p, size_t i, float3 v) {
-    const __half2 a = __floats2half2_rn(v.x, v.y);
-    const __half2 b = __floats2half2_rn(v.z, 0.0f);
-    p[i] = make_uint2(*reinterpret_cast<const uint32_t *>(&a), *reinterpret_cast<const uint32_t *>(&b));
-  }
-  __device__ static float3 get(const uint2 *p, size_t i) {
-    const uint2 q = __ldg(p + i);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
-    return make_float3(a.x, a.y, b.x);
-  }
-};
-
-// Bilinear sample of a band's pre-warped intermediate at X (already inside the band).
-template <bool kHalf>
-__device__ __forceinline__ float3 pw_bilinear(const typename PwT<kHalf>::T *pw, const BandDev &B, float X, float Y) {
-  int ix, iy;
-  float gx, gy;
-  split(X, ix, gx);
-  split(Y, iy, gy);
-  // X == x0 (odd) may come back as (x0 - 1, 1): take the tap at x0 instead.
-  if (ix < B.x0) { ix = B.x0; gx = 0.0f; }
-  if (iy < B.y0) { iy = B.y0; gy = 0.0f; }
-  const int bw = B.x1 - B.x0, bh = B.y1 - B.y0;
-  const int lx = min(ix - B.x0, bw - 1), ly = min(iy - B.y0, bh - 1);
-  const int lx1 = min(lx + 1, bw - 1), ly1 = min(ly + 1, bh - 1);
-  const float3 a = PwT<kHalf>::get(pw, (size_t)ly * bw + lx), b = PwT<kHalf>::get(pw, (size_t)ly * bw + lx1);
-  const float3 d = PwT<kHalf>::get(pw, (size_t)ly1 * bw + lx), e = PwT<kHalf>::get(pw, (size_t)ly1 * bw + lx1);
-  float3 t, u, o;
-  t.x = fmaf(gx, b.x - a.x, a.x); t.y = fmaf(gx, b.y - a.y, a.y); t.z = fmaf(gx, b.z - a.z, a.z);
-  u.x = fmaf(gx, e.x - d.x, d.x); u.y = fmaf(gx, e.y - d.y, d.y); u.z = fmaf(gx, e.z - d.z, d.z);
-  o.x = fmaf(gy, u.x - t.x, t.x); o.y = fmaf(gy, u.y - t.y, t.y); o.z = fmaf(gy, u.z - t.z, t.z);
-  return o;
-}
-
+// One pixel's bytes from its fused value v (already scaled by 1/255): the
+// saturation is the clamp to [0, 255], the table applies Eq. 5 and rounds.
 template <int TW, int TH>
-__device__ __forceinline__ void put_px(uint8_t (*s_out)[TH][TW], int lx, int ly, const BlockColor &bc, bool cov,
-                                       float3 v) {
+__device__ __forceinline__ void put_px(uint8_t (*out)[TH][TW], const uint8_t *lut, int lx, int ly, bool cov, float3 v) {
   uint32_t o0 = 0u, o1 = 0u, o2 = 0u;
   if (cov) {
-    o0 = finish(bc, 0, v.x);
-    o1 = finish(bc, 1, v.y);
-    o2 = finish(bc, 2, v.z);
+    o0 = lut[lut_index(__saturatef(v.x))];
+    o1 = lut[kLutEntries + lut_index(__saturatef(v.y))];
+    o2 = lut[2 * kLutEntries + lut_index(__saturatef(v.z))];
   }
-  s_out[0][ly][lx] = (uint8_t)o0;
-  s_out[1][ly][lx] = (uint8_t)o1;
-  s_out[2][ly][lx] = (uint8_t)o2;
+  out[0][ly][lx] = (uint8_t)o0;
+  out[1][ly][lx] = (uint8_t)o1;
+  out[2][ly][lx] = (uint8_t)o2;
 }
 
+// The piece's chunks of the tile (columns [16 c0, 16 c1)) as 16-byte stores.
 template <int TW, int TH>
-__device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0, const uint8_t (*s_out)[TH][TW]) {
-  // 3 planes x TH rows x TW / 16 sixteen-byte pieces.
+__device__ __forceinline__ void store_tile(const FuseParams &P, int tx0, int ty0, const uint8_t (*s_out)[TH][TW],
+                                           int c0, int c1) {
   constexpr int kPieces = TW / 16;
   for (int t = threadIdx.x; t < 3 * TH * kPieces; t += blockDim.x) {
     const int c = t / (TH * kPieces);
     const int r = (t / kPieces) % TH;
     const int q = t % kPieces;
     const int y = ty0 + r, x = tx0 + 16 * q;
-    if (y >= P.pano_h || x >= P.pano_pitch) continue;
+    if (q < c0 || q >= c1 || y >= P.pano_h || x >= P.pano_pitch) continue;
     const uint4 v = *reinterpret_cast<const uint4 *>(&s_out[c][r][16 * q]);
     *reinterpret_cast<uint4 *>(P.out + (size_t)c * P.pano_pitch * P.pano_h + (size_t)y * P.pano_pitch + x) = v;
   }
 }
 
-// Shared memory of one fuse tile.
+// ---------------------------------------------------------------------------
+// The paired fast path: two pixels per step, half2 / f32x2 arithmetic.
+// ---------------------------------------------------------------------------
+
+// Thread -> pixel pairs of a TW x TH tile. Warp w owns rows
+// [w TH / 8, (w + 1) TH / 8). With TW >= 64 a pair is columns (l + 64 cp,
+// l + 64 cp + 32) of one row (lane l; bank-conflict-free tap reads); with TW =
+// 32 it is column l of two consecutive rows.
 template <int TW, int TH>
-struct FuseSmem {
-  BlockColor bc;
-  Window sW[2];
-  __align__(16) uint32_t s_win[2][kWinCap];
-  __align__(16) uint8_t s_out[3][TH][TW];
+struct PairMap {
+  static constexpr int kG = TW / 32;
+  static constexpr int kRPW = TH / 8;
+  static constexpr bool kRowPairs = kG == 1;
+  static constexpr int kCP = kRowPairs ? 1 : kG / 2;
+  static constexpr int kSteps = kRowPairs ? kRPW / 2 : kRPW;
+  static constexpr float kDy = kRowPairs ? 2.0f : 1.0f;
+  static_assert(TW % 32 == 0 && TH % 16 == 0 && (kG == 1 || kG % 2 == 0), "tile shape");
+  __device__ static int lx0(int lane, int cp) { return kRowPairs ? lane : lane + 64 * cp; }
+  __device__ static int lx1(int lane, int cp) { return kRowPairs ? lane : lane + 64 * cp + 32; }
+  __device__ static int ly0(int warp, int s) { return kRPW * warp + (kRowPairs ? 2 * s : s); }
+  __device__ static int ly1(int warp, int s) { return ly0(warp, s) + (kRowPairs ? 1 : 0); }
 };
 
-// Thread -> pixel mapping of a TW x TH tile: warp w owns rows
-// [w TH / 8, (w + 1) TH / 8), lane l the columns l + 32 a; pixel j of a thread
-// is column group j % (TW / 32) of row j / (TW / 32) of its warp's rows.
-template <int TW, int TH>
-struct Map {
-  static constexpr int kGroups = TW / 32;
-  static constexpr int kRowsPerWarp = TH / 8;
-  static constexpr int kPix = kGroups * kRowsPerWarp;
-  static_assert(TW % 32 == 0 && TH % 8 == 0, "tile shape");
-  __device__ static int lx(int lane, int j) { return lane + 32 * (j % kGroups); }
-  __device__ static int ly(int warp, int j) { return kRowsPerWarp * warp + j / kGroups; }
+// The half-shifted camera map (hm) of a pixel pair: n = col + row * hy with
+// components (x, y, w) and s' = (n.x / n.w, n.y / n.w) = s - (1/2, 1/2), the
+// same products in the same order as cam_point. col holds a column's share
+// (planar: the camera-relative panorama column; cylinder: its sin / cos),
+// row the row coordinate (planar: the camera-relative row, exact; cylinder:
+// (y - cy) / f, formed from the exact row for every step).
+struct PairCoords {
+  float2 cx[2], cy[2], cw[2];   // per column pair: both pixels' column shares
+  float2 y0;                    // both pixels' panorama row at step 0 (exact)
 };
 
-// One panorama tile (see the file header): source windows, per-pixel work,
-// then the tile's three planes leave as 16-byte stores.
-template <bool kHalf, int TW, int TH>
-__device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t, FuseSmem<TW, TH> &sm) {
-  using PT = typename PwT<kHalf>::T;
-  using MP = Map<TW, TH>;
-  BlockColor &bc = sm.bc;
-  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
-  const int tx1 = min(tx0 + TW, P.pano_w) - 1, ty1 = min(ty0 + TH, P.pano_h) - 1;
+template <int TW, int TH>
+__device__ __forceinline__ PairCoords pair_coords(const CamDev &c, int tx0, int ty0, int lane, int warp) {
+  using PM = PairMap<TW, TH>;
+  PairCoords pc;
+#pragma unroll
+  for (int cp = 0; cp < 2; ++cp) {
+    if (cp >= PM::kCP) break;
+    float a0, b0, a1, b1;   // (first, second) column factors of both pixels
+    const int x0 = tx0 + PM::lx0(lane, cp), x1 = tx0 + PM::lx1(lane, cp);
+    if (c.cyl) {
+      sincosf(((float)x0 - c.cyl_cx) * c.cyl_finv, &a0, &b0);
+      sincosf(((float)x1 - c.cyl_cx) * c.cyl_finv, &a1, &b1);
+    } else {
+      a0 = (float)(x0 - c.ox);
+      a1 = (float)(x1 - c.ox);
+      b0 = b1 = 1.0f;
+    }
+    pc.cx[cp] = f2(fmaf(c.hm[0], a0, c.hm[2] * b0), fmaf(c.hm[0], a1, c.hm[2] * b1));
+    pc.cy[cp] = f2(fmaf(c.hm[3], a0, c.hm[5] * b0), fmaf(c.hm[3], a1, c.hm[5] * b1));
+    pc.cw[cp] = f2(fmaf(c.hm[6], a0, c.hm[8] * b0), fmaf(c.hm[6], a1, c.hm[8] * b1));
+  }
+  pc.y0 = f2((float)(ty0 + PM::ly0(warp, 0)), (float)(ty0 + PM::ly1(warp, 0)));
+  return pc;
+}
+
+// Row coordinate of both pixels from their exact panorama rows.
+__device__ __forceinline__ float2 pair_row(const CamDev &c, float2 y) {
+  if (c.cyl) return __fmul2_rn(__fadd2_rn(y, f2(-c.cyl_cy)), f2(c.cyl_finv));
+  return __fadd2_rn(y, f2(-(float)c.oy));
+}
+
+// s' of a pixel pair (the division skipped for an affine camera).
+__device__ __forceinline__ void pair_point(const CamDev &c, const PairCoords &pc, int cp, float2 row, float2 &ux,
+                                           float2 &uy) {
+  const float2 nx = __ffma2_rn(row, f2(c.hm[1]), pc.cx[cp]);
+  const float2 ny = __ffma2_rn(row, f2(c.hm[4]), pc.cy[cp]);
+  if (c.affine) {
+    ux = nx;
+    uy = ny;
+  } else {
+    const float2 nw = __ffma2_rn(row, f2(c.hm[7]), pc.cw[cp]);
+    const float2 rw = f2(rcp_approx(nw.x), rcp_approx(nw.y));
+    ux = __fmul2_rn(nx, rw);
+    uy = __fmul2_rn(ny, rw);
+  }
+}
+
+// Half-shifted source points um of a pixel pair -> the magic-rounded floats
+// (whose bits are kMagicRoundBits + tap index) and the fractions in half
+// precision.
+__device__ __forceinline__ void split_pair(float2 um, float2 &r, __half2 &f) {
+  r = __fadd2_rn(um, f2(kMagicRound));
+  const float2 n = __fadd2_rn(r, f2(-kMagicRound));
+  const float2 d = __ffma2_rn(n, f2(-1.0f), um);   // um - round(um), in [-1/2, 1/2], exact
+  f = __float22half2_rn(__fadd2_rn(d, f2(0.5f)));
+}
+
+// Half2 channel pair (1024 + v of pixel 0, 1024 + v of pixel 1) from two RGBX
+// words with the fourth byte 0x64.
+template <int C>
+__device__ __forceinline__ __half2 chan_pair(uint32_t w0, uint32_t w1) {
+  return as_h2(__byte_perm(w0, w1, 0x7430u + 0x0101u * C));
+}
+
+// Bilinear of a pixel pair per channel, in half2 on v - 128:
+// a + fx (b - a) + fy ((d - a) + fx ((e - d) - (b - a))).
+__device__ __forceinline__ void bilerp_pair(const uint32_t (&t0)[4], const uint32_t (&t1)[4], __half2 fx, __half2 fy,
+                                            float2 (&v)[3]) {
+  const __half2 off = __float2half2_rn(kHalfOffset);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    __half2 A, B, D, E;
+    if (c == 0) {
+      A = chan_pair<0>(t0[0], t1[0]); B = chan_pair<0>(t0[1], t1[1]);
+      D = chan_pair<0>(t0[2], t1[2]); E = chan_pair<0>(t0[3], t1[3]);
+    } else if (c == 1) {
+      A = chan_pair<1>(t0[0], t1[0]); B = chan_pair<1>(t0[1], t1[1]);
+      D = chan_pair<1>(t0[2], t1[2]); E = chan_pair<1>(t0[3], t1[3]);
+    } else {
+      A = chan_pair<2>(t0[0], t1[0]); B = chan_pair<2>(t0[1], t1[1]);
+      D = chan_pair<2>(t0[2], t1[2]); E = chan_pair<2>(t0[3], t1[3]);
+    }
+    const __half2 dx = __hsub2(B, A);
+    const __half2 dy = __hsub2(D, A);
+    const __half2 dxy = __hsub2(__hsub2(E, D), dx);
+    const __half2 a = __hsub2(A, off);
+    const __half2 u = __hfma2(fx, dxy, dy);
+    const __half2 t = __hfma2(fx, dx, a);
+    v[c] = __half22float2(__hfma2(fy, u, t));
+  }
+}
+
+// The four taps of a pixel at word index i of a window with row stride S.
+// The index is clamped to the window's allocation (kMax = kAlloc - S - 2), so
+// that no coordinate, however wrong, reads outside it.
+template <int S, int kMax>
+__device__ __forceinline__ void taps(const uint32_t *w, uint32_t i, uint32_t (&t)[4]) {
+  i = min(i, (uint32_t)kMax);
+  t[0] = w[i];
+  t[1] = w[i + 1];
+  t[2] = w[i + S];
+  t[3] = w[i + S + 1];
+}
+
+// v . M + bias through the table for a pixel pair (v held as v - 128), the
+// products in cam_value's order; pr holds the camera's colour pairs.
+template <int TW, int TH>
+__device__ __forceinline__ void finish_pair(const float2 (&v)[3], const float4 (*pr)[2], const uint8_t *lut,
+                                            uint8_t (*out)[TH][TW], int lx0, int ly0, int lx1, int ly1, bool in0,
+                                            bool in1) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 a = pr[k][0], b = pr[k][1];
+    float2 acc = __ffma2_rn(v[2], f2(a.x, a.y), f2(a.z, a.w));
+    acc = __ffma2_rn(v[1], f2(b.x, b.y), acc);
+    const float u0 = __saturatef(fmaf(v[0].x, b.z, acc.x));
+    const float u1 = __saturatef(fmaf(v[0].y, b.w, acc.y));
+    const float2 q = __ffma2_rn(f2(u0, u1), f2(kLutTop), f2(kMagicRound));
+    if (in0) out[k][ly0][lx0] = lut[k * kLutEntries + (__float_as_uint(q.x) - kMagicRoundBits)];
+    if (in1) out[k][ly1][lx1] = lut[k * kLutEntries + (__float_as_uint(q.y) - kMagicRoundBits)];
+  }
+}
+
+// Every pixel of a fully covered own tile from its staged window (W.ok): the
+// tile lies inside camera k with a margin, so every tap is a frame pixel of
+// the window and the result equals cam_value's for each pixel.
+template <int TW, int TH>
+__device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, const uint32_t *win, const BlockColor &bc,
+                                          int k, const uint8_t *lut, uint8_t (*out)[TH][TW], int tx0, int ty0,
+                                          int cx0, int cx1) {
+  using PM = PairMap<TW, TH>;
+  constexpr int S = WinGeom<TW, TH>::kStride;
+  constexpr int kMax = WinGeom<TW, TH>::kAlloc - S - 2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool empty = tx0 > tx1 || ty0 > ty1;
-  load_block_color(P, bc);
+  // word index of tap (ix, iy) = bits(ry) S + bits(rx) - off
+  const uint32_t off = kMagicRoundBits * (uint32_t)(S + 1) + (uint32_t)W.y0 * (uint32_t)S + (uint32_t)W.x0;
+  const PairCoords pc = pair_coords<TW, TH>(c, tx0, ty0, lane, warp);
+  float2 y = pc.y0;
+#pragma unroll 2
+  for (int s = 0; s < PM::kSteps; ++s) {
+    const float2 row = pair_row(c, y);
+#pragma unroll
+    for (int cp = 0; cp < PM::kCP; ++cp) {
+      float2 ux, uy;
+      pair_point(c, pc, cp, row, ux, uy);
+      float2 rx, ry;
+      __half2 fx, fy;
+      split_pair(ux, rx, fx);
+      split_pair(uy, ry, fy);
+      const uint32_t i0 = __float_as_uint(ry.x) * (uint32_t)S + __float_as_uint(rx.x) - off;
+      const uint32_t i1 = __float_as_uint(ry.y) * (uint32_t)S + __float_as_uint(rx.y) - off;
+      uint32_t t0[4], t1[4];
+      taps<S, kMax>(win, i0, t0);
+      taps<S, kMax>(win, i1, t1);
+      float2 v[3];
+      bilerp_pair(t0, t1, fx, fy, v);
+      const int lx0 = PM::lx0(lane, cp), lx1 = PM::lx1(lane, cp);
+      finish_pair<TW, TH>(v, bc.pr[k], lut, out, lx0, PM::ly0(warp, s), lx1, PM::ly1(warp, s),
+                          lx0 >= cx0 && lx0 < cx1, lx1 >= cx0 && lx1 < cx1);
+    }
+    y = __fadd2_rn(y, f2(PM::kDy));
+  }
+}
 
-  // Source windows: warp 0 for the tile's camera (or a band's left camera),
-  // warp 1 for a band's right camera, only where tile pixels need them.
+// ---------------------------------------------------------------------------
+// Per-pixel general path: the same arithmetic as the paired path, one pixel
+// at a time (its second half2 lane repeats the first), so that a pixel's
+// bytes do not depend on the tile shape, the tile kind or the batch.
+// ---------------------------------------------------------------------------
+
+// Half-shifted source point s' = s - (1/2, 1/2) of panorama pixel (x, y) in
+// camera c, from the half-shifted map hm (the paired path evaluates the same
+// products in the same order: column share first, then the row).
+__device__ __forceinline__ void cam_point(const CamDev &c, int x, int y, float &sx, float &sy, float &nw) {
+  float a, b, rc;
+  if (c.cyl) {
+    sincosf(((float)x - c.cyl_cx) * c.cyl_finv, &a, &b);
+    rc = ((float)y - c.cyl_cy) * c.cyl_finv;
+  } else {
+    a = (float)(x - c.ox);
+    b = 1.0f;
+    rc = (float)(y - c.oy);
+  }
+  const float cx = fmaf(c.hm[0], a, c.hm[2] * b);
+  const float cy = fmaf(c.hm[3], a, c.hm[5] * b);
+  const float cw = fmaf(c.hm[6], a, c.hm[8] * b);
+  const float nx = fmaf(rc, c.hm[1], cx), ny = fmaf(rc, c.hm[4], cy);
+  nw = fmaf(rc, c.hm[7], cw);
+  if (c.affine) {
+    sx = nx;
+    sy = ny;
+  } else {
+    const float r = rcp_approx(nw);
+    sx = nx * r;
+    sy = ny * r;
+  }
+}
+
+// Coverage of Eq. 15 in half-shifted coordinates: 0 <= s <= (w - 1, h - 1).
+__device__ __forceinline__ bool covered_m(const CamDev &c, float sx, float sy, float nw) {
+  return nw > 0.0f && sx >= -0.5f && sx <= c.wm1 - 0.5f && sy >= -0.5f && sy <= c.hm1 - 0.5f;
+}
+
+// One RGBX word (fourth byte 0x64) of frame pixel (x, y) from global memory.
+__device__ __forceinline__ uint32_t gword(const uint8_t *__restrict__ src, const CamDev &c, int x, int y) {
+  const uint8_t *p = src + (size_t)y * c.pitch + 3 * x;
+  return (uint32_t)__ldg(p) | ((uint32_t)__ldg(p + 1) << 8) | ((uint32_t)__ldg(p + 2) << 16) | (kXByte << 24);
+}
+
+// Camera k's colour-transferred value at panorama pixel (x, y) in the offset
+// form (bias + (P - 128) . M / 255, not yet saturated), or false where k does
+// not cover the pixel. Taps: floor(s) and floor(s) + 1, the far tap clamped
+// to the last row / column; read from the staged window when all four lie in
+// it, else from the frame.
+template <int S>
+__device__ bool cam_value(const FuseParams &P, const BlockColor &bc, int k, const Window &W, const uint32_t *win,
+                          int x, int y, float3 &o) {
+  const CamDev &c = P.cam[k];
+  float sx, sy, nw;
+  cam_point(c, x, y, sx, sy, nw);
+  if (!covered_m(c, sx, sy, nw)) return false;
+  const float rx = sx + kMagicRound, ry = sy + kMagicRound;
+  const float fx = (sx - (rx - kMagicRound)) + 0.5f, fy = (sy - (ry - kMagicRound)) + 0.5f;
+  const int ix = max((int)(__float_as_uint(rx) - kMagicRoundBits), 0);
+  const int iy = max((int)(__float_as_uint(ry) - kMagicRoundBits), 0);
+  const int ix1 = min(ix + 1, c.w - 1), iy1 = min(iy + 1, c.h_px - 1);
+  uint32_t t[4];
+  const int lx = ix - W.x0, ly = iy - W.y0;
+  if (W.ok && lx >= 0 && ly >= 0 && ix1 - W.x0 < W.w && iy1 - W.y0 < W.h) {
+    const int dx = ix1 - ix, dy = (iy1 - iy) * S;
+    const uint32_t *q = win + ly * S + lx;
+    t[0] = q[0]; t[1] = q[dx]; t[2] = q[dy]; t[3] = q[dy + dx];
+  } else {
+    const uint8_t *src = P.src[k];
+    t[0] = gword(src, c, ix, iy); t[1] = gword(src, c, ix1, iy);
+    t[2] = gword(src, c, ix, iy1); t[3] = gword(src, c, ix1, iy1);
+  }
+  float2 v[3];
+  bilerp_pair(t, t, __float2half2_rn(fx), __float2half2_rn(fy), v);
+  const float *M = bc.M[k], *bias = bc.bias[k];
+  o.x = fmaf(v[0].x, M[0], fmaf(v[1].x, M[3], fmaf(v[2].x, M[6], bias[0])));
+  o.y = fmaf(v[0].x, M[1], fmaf(v[1].x, M[4], fmaf(v[2].x, M[7], bias[1])));
+  o.z = fmaf(v[0].x, M[2], fmaf(v[1].x, M[5], fmaf(v[2].x, M[8], bias[2])));
+  return true;
+}
+
+// Camera k's value with the one-image fallbacks of Eq. 15 (k, then k - 1,
+// then k + 1 when those exist): true when any of them covers the pixel.
+template <int S>
+__device__ __forceinline__ bool own_value(const FuseParams &P, const BlockColor &bc, int k, int first, int second,
+                                          const Window &W, const uint32_t *win, int x, int y, float3 &o) {
+  if (cam_value<S>(P, bc, k, W, win, x, y, o)) return true;
+  const Window none = no_window();
+  if (first >= 0 && first < P.n_cams && cam_value<S>(P, bc, first, none, win, x, y, o)) return true;
+  return second >= 0 && second < P.n_cams && cam_value<S>(P, bc, second, none, win, x, y, o);
+}
+
+// ---------------------------------------------------------------------------
+// Band intermediate: float32 RGB_ or half RGB_ per band pixel and side.
+// ---------------------------------------------------------------------------
+
+template <bool kHalf>
+struct PwT;
+template <>
+struct PwT<false> {
+  using T = float4;
+};
+template <>
+struct PwT<true> {
+  using T = uint2;   // four halves
+};
+
+// Bilinear of the intermediate at band-relative tap (lx, ly) with fractions
+// (gx, gy); the neighbours are (lx1, ly1). Returns the three channels.
+__device__ __forceinline__ float3 pw_lerp(const float4 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
+                                          float gy) {
+  const float4 a = __ldg(pw + (size_t)ly * bw + lx), b = __ldg(pw + (size_t)ly * bw + lx1);
+  const float4 d = __ldg(pw + (size_t)ly1 * bw + lx), e = __ldg(pw + (size_t)ly1 * bw + lx1);
+  const float2 A = f2(a.x, a.y), B = f2(b.x, b.y), D = f2(d.x, d.y), E = f2(e.x, e.y);
+  const float2 dx = __ffma2_rn(A, f2(-1.0f), B);
+  const float2 dy = __ffma2_rn(A, f2(-1.0f), D);
+  const float2 dxy = __ffma2_rn(dx, f2(-1.0f), __ffma2_rn(D, f2(-1.0f), E));
+  const float2 o = __ffma2_rn(f2(gy), __ffma2_rn(f2(gx), dxy, dy), __ffma2_rn(f2(gx), dx, A));
+  const float bx = b.z - a.z, by = d.z - a.z, bxy = (e.z - d.z) - bx;
+  const float oz = fmaf(gy, fmaf(gx, bxy, by), fmaf(gx, bx, a.z));
+  return make_float3(o.x, o.y, oz);
+}
+
+__device__ __forceinline__ float3 pw_lerp(const uint2 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
+                                          float gy) {
+  const uint2 a = __ldg(pw + (size_t)ly * bw + lx), b = __ldg(pw + (size_t)ly * bw + lx1);
+  const uint2 d = __ldg(pw + (size_t)ly1 * bw + lx), e = __ldg(pw + (size_t)ly1 * bw + lx1);
+  const __half2 hx = __float2half2_rn(gx), hy = __float2half2_rn(gy);
+  float2 o[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const __half2 A = as_h2(h ? a.y : a.x), B = as_h2(h ? b.y : b.x);
+    const __half2 D = as_h2(h ? d.y : d.x), E = as_h2(h ? e.y : e.x);
+    const __half2 dx = __hsub2(B, A), dy = __hsub2(D, A);
+    const __half2 dxy = __hsub2(__hsub2(E, D), dx);
+    o[h] = __half22float2(__hfma2(hy, __hfma2(hx, dxy, dy), __hfma2(hx, dx, A)));
+  }
+  return make_float3(o[0].x, o[0].y, o[1].x);
+}
+
+// Remap sample P_k(X) (Eq. 18) of a band's intermediate at the band-relative,
+// half-shifted point qm = X - (x0, y0) - 1/2. kClamp: X may lie outside the
+// band (clamped into it first) and taps may fall on its last row / column.
+template <bool kHalf, bool kClamp>
+__device__ __forceinline__ float3 band_sample(const typename PwT<kHalf>::T *pw, int bw, int bh, float2 qm) {
+  if (kClamp) {
+    qm.x = fminf(fmaxf(qm.x, -0.5f), (float)bw - 1.5f);
+    qm.y = fminf(fmaxf(qm.y, -0.5f), (float)bh - 1.5f);
+  }
+  const float2 r = __fadd2_rn(qm, f2(kMagicRound));
+  const float2 d = __ffma2_rn(__fadd2_rn(r, f2(-kMagicRound)), f2(-1.0f), qm);
+  int lx = (int)(__float_as_uint(r.x) - kMagicRoundBits), ly = (int)(__float_as_uint(r.y) - kMagicRoundBits);
+  float gx = d.x + 0.5f, gy = d.y + 0.5f;
+  int lx1 = lx + 1, ly1 = ly + 1;
+  if (kClamp) {
+    // X == x0 may come back as (x0 - 1, 1): take the tap at x0 instead.
+    if (lx < 0) { lx = 0; gx = 0.0f; }
+    if (ly < 0) { ly = 0; gy = 0.0f; }
+    lx = min(lx, bw - 1);
+    ly = min(ly, bh - 1);
+    lx1 = min(lx + 1, bw - 1);
+    ly1 = min(ly + 1, bh - 1);
+  }
+  return pw_lerp(pw, bw, lx, ly, lx1, ly1, gx, gy);
+}
+
+// A band pixel (x, y) inside the band rectangle of pair p (Eq. 16-18 and the
+// weighted mean of Eq. 15), as the fused value scaled by 1/255.
+template <bool kHalf, bool kClamp>
+__device__ __forceinline__ float3 band_pixel(const FuseParams &P, const BlockColor &bc, int p, int x, int y,
+                                             bool printed) {
+  using PT = typename PwT<kHalf>::T;
+  const BandDev B = P.band[p];
+  const int bw = B.x1 - B.x0, bh = B.y1 - B.y0;
+  const float mf = P.max_flow;
+  const size_t fi = (size_t)(y - B.y0) * bw + (x - B.x0);
+  float2 fa = __ldg(P.flow_ij[p] + fi);
+  float2 fb = __ldg(P.flow_ji[p] + fi);
+  fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
+  fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
+  const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
+  const float ta = 1.0f - tb;
+  const float wa = printed ? ta : tb;
+  const float wb = printed ? tb : ta;
+  const float2 base = f2((float)(x - B.x0) - 0.5f, (float)(y - B.y0) - 0.5f);
+  const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
+  const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
+  const float3 Pa = band_sample<kHalf, kClamp>(pwa, bw, bh, __ffma2_rn(f2(wa), fa, base));
+  const float3 Pb = band_sample<kHalf, kClamp>(pwb, bw, bh, __ffma2_rn(f2(wb), fb, base));
+  const float *Ma = bc.M[p], *Mb = bc.M[p + 1];
+  const float *ba = bc.bias[p], *bb = bc.bias[p + 1];
+  float3 o;
+  o.x = fmaf(tb, fmaf(Pb.x, Mb[0], fmaf(Pb.y, Mb[3], fmaf(Pb.z, Mb[6], bb[0]))),
+             ta * fmaf(Pa.x, Ma[0], fmaf(Pa.y, Ma[3], fmaf(Pa.z, Ma[6], ba[0]))));
+  o.y = fmaf(tb, fmaf(Pb.x, Mb[1], fmaf(Pb.y, Mb[4], fmaf(Pb.z, Mb[7], bb[1]))),
+             ta * fmaf(Pa.x, Ma[1], fmaf(Pa.y, Ma[4], fmaf(Pa.z, Ma[7], ba[1]))));
+  o.z = fmaf(tb, fmaf(Pb.x, Mb[2], fmaf(Pb.y, Mb[5], fmaf(Pb.z, Mb[8], bb[2]))),
+             ta * fmaf(Pa.x, Ma[2], fmaf(Pa.y, Ma[5], fmaf(Pa.z, Ma[8], ba[2]))));
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Tiles.
+// ---------------------------------------------------------------------------
+
+// Shared memory of a band piece: only the output tile.
+template <int TW, int TH>
+struct __align__(16) SmemBand {
+  __align__(16) uint8_t out[3][TH][TW];
+};
+
+template <int TW, int TH>
+constexpr size_t band_smem_bytes() {
+  return (sizeof(SmemHead) + 15) / 16 * 16 + sizeof(SmemBand<TW, TH>);
+}
+
+// A fully covered own piece (kTileOwn): window of its columns, staging,
+// paired per-pixel work, stores. Pieces whose window does not fit take the
+// general per-pixel path with taps from the frame.
+template <int TW, int TH>
+__device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDesc t, SmemHead &h,
+                                              SmemTile<TW, TH, 1> &st) {
+  using G = WinGeom<TW, TH>;
+  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
+  const int cx0 = 16 * t.c0, cx1 = 16 * t.c1;
+  const int ty1 = min(ty0 + TH, P.pano_h) - 1;
+  const int warp = threadIdx.x >> 5;
+  const int k = t.idx;
+  const CamDev &c = P.cam[k];
+  if (warp == 0) {
+    const Window W = warp_window<G::kStride, G::kRows>(c, tx0 + cx0, ty0, tx0 + cx1 - 1, ty1);
+    if ((threadIdx.x & 31) == 0) {
+      h.sW[0] = W;
+      if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
+    }
+  }
+  __syncthreads();
+  const Window W0 = h.sW[0];
+  if (W0.ok) {
+    stage_window<G::kStride>(P.src[k], c, W0, st.win[0]);
+    __syncthreads();
+    own_pairs<TW, TH>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1);
+  } else {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < (TW / 32) * (TH / 8); ++j) {
+      const int lx = lane + 32 * (j % (TW / 32)), ly = (TH / 8) * warp + j / (TW / 32);
+      if (lx < cx0 || lx >= cx1) continue;
+      float3 v = make_float3(0.0f, 0.0f, 0.0f);
+      const bool cov = cam_value<G::kStride>(P, h.bc, k, W0, st.win[0], tx0 + lx, ty0 + ly, v);
+      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v);
+    }
+  }
+  __syncthreads();
+  store_tile<TW, TH>(P, tx0, ty0, st.out, t.c0, t.c1);
+}
+
+// One remap sample (Eq. 18) of a band's intermediate at the band-relative,
+// half-shifted point qm (inside the band when !kClamp), returned in the
+// intermediate's units; the same arithmetic as band_sample.
+template <bool kHalf, bool kClamp>
+__device__ __forceinline__ float3 band_tap(const typename PwT<kHalf>::T *pw, int bw, int bh, float2 qm) {
+  return band_sample<kHalf, kClamp>(pw, bw, bh, qm);
+}
+
+// Every pixel of a piece inside a band rectangle (kTileBand): a band pixel of
+// Eq. 16-18 from the band's pre-warped intermediate; no windows. A thread
+// walks its columns (theta, the flow column and the band-relative column are
+// fixed there) down its rows, with the next pixel's flows loaded before the
+// current pixel's remap taps; both cameras' colour constants stay in
+// registers. The clamps into the band are skipped when the piece's reach
+// (max_flow + 1 pixels around it) stays inside the band.
+template <bool kHalf, bool kClamp, int TW, int TH>
+__device__ __forceinline__ void band_rows(const FuseParams &P, const BlockColor &bc, int p, int tx0, int ty0, int cx0,
+                                          int cx1, const uint8_t *lut, uint8_t (*out)[TH][TW]) {
+  using PT = typename PwT<kHalf>::T;
+  constexpr int kGroups = TW / 32, kRPW = TH / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const BandDev B = P.band[p];
+  const int bw = B.x1 - B.x0, bh = B.y1 - B.y0;
+  const float mf = P.max_flow;
+  const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
+  const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
+  const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
+  const float4 *ca = bc.col[p], *cb = bc.col[p + 1];
+  const int ly0 = kRPW * warp;
+  const int row0 = ty0 + ly0 - B.y0;       // band-relative row of the thread's first pixel
+#pragma unroll 1
+  for (int gi = 0; gi < kGroups; ++gi) {
+    const int lx = lane + 32 * gi;
+    if (lx < cx0 || lx >= cx1) continue;
+    const int col = tx0 + lx - B.x0;       // band-relative column
+    const float tb = ((float)col + 0.5f) * B.inv_bw;
+    const float ta = 1.0f - tb;
+    const float wa = printed ? ta : tb;
+    const float wb = printed ? tb : ta;
+    const float2 *fa_p = P.flow_ij[p] + (size_t)row0 * bw + col;
+    const float2 *fb_p = P.flow_ji[p] + (size_t)row0 * bw + col;
+    float2 base = f2((float)col - 0.5f, (float)row0 - 0.5f);
+    float2 fa = __ldg(fa_p), fb = __ldg(fb_p);
+#pragma unroll
+    for (int r = 0; r < kRPW; ++r) {
+      float2 na, nb;
+      if (r + 1 < kRPW) {
+        na = __ldg(fa_p + (size_t)(r + 1) * bw);
+        nb = __ldg(fb_p + (size_t)(r + 1) * bw);
+      }
+      fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
+      fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
+      const float3 Pa = band_tap<kHalf, kClamp>(pwa, bw, bh, __ffma2_rn(f2(wa), fa, base));
+      const float3 Pb = band_tap<kHalf, kClamp>(pwb, bw, bh, __ffma2_rn(f2(wb), fb, base));
+      float o[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float4 A = ca[k], Bq = cb[k];
+        o[k] = fmaf(tb, fmaf(Pb.x, Bq.x, fmaf(Pb.y, Bq.y, fmaf(Pb.z, Bq.z, Bq.w))),
+                    ta * fmaf(Pa.x, A.x, fmaf(Pa.y, A.y, fmaf(Pa.z, A.z, A.w))));
+      }
+      put_px<TW, TH>(out, lut, lx, ly0 + r, true, make_float3(o[0], o[1], o[2]));
+      base.y += 1.0f;
+      if (r + 1 < kRPW) {
+        fa = na;
+        fb = nb;
+      }
+    }
+  }
+}
+
+template <bool kHalf, int TW, int TH>
+__device__ __forceinline__ void fuse_band_piece(const FuseParams &P, const TileDesc t, SmemHead &h,
+                                                uint8_t (*out)[TH][TW]) {
+  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
+  const int cx0 = 16 * t.c0, cx1 = 16 * t.c1;
+  const int p = t.idx;
+  const BandDev B = P.band[p];
+  const int reach = (int)ceilf(P.max_flow) + 1;
+  const bool interior = tx0 + cx0 - reach >= B.x0 && tx0 + cx1 - 1 + reach + 1 < B.x1 && ty0 - reach >= B.y0 &&
+                        ty0 + TH - 1 + reach + 1 < B.y1;
+  if (interior)
+    band_rows<kHalf, false, TW, TH>(P, h.bc, p, tx0, ty0, cx0, cx1, h.lut, out);
+  else
+    band_rows<kHalf, true, TW, TH>(P, h.bc, p, tx0, ty0, cx0, cx1, h.lut, out);
+  __syncthreads();
+  store_tile<TW, TH>(P, tx0, ty0, out, t.c0, t.c1);
+}
+
+// A general piece: own columns of camera idx seen only in part
+// (kTileOwnPart), or band columns of pair idx with other pixels
+// (kTileBandPart: the chunk holding a band edge, rows outside the band
+// rectangle). Every pixel takes the per-pixel general path.
+template <bool kHalf, int TW, int TH>
+__device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t, SmemHead &h,
+                                          SmemTile<TW, TH, 2> &st) {
+  using G = WinGeom<TW, TH>;
+  constexpr int S = G::kStride;
+  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
+  const int cx0 = 16 * t.c0, cx1 = 16 * t.c1;
+  const int px0 = tx0 + cx0;
+  const int px1 = min(tx0 + cx1, P.pano_w) - 1, ty1 = min(ty0 + TH, P.pano_h) - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool empty = px0 > px1 || ty0 > ty1;
+  const BlockColor &bc = h.bc;
+
+  // Source windows: warp 0 for the piece's camera (or a band's left camera),
+  // warp 1 for a band's right camera, only where its pixels need them.
   if (warp < 2) {
     Window W = no_window();
+    bool need = false;
     if (!empty) {
-      if (t.kind != 1) {
-        if (warp == 0) W = warp_window(P.cam[t.idx], tx0, ty0, tx1, ty1);
+      if (t.kind == kTileOwnPart) {
+        need = warp == 0;
+        if (need) W = warp_window<S, G::kRows>(P.cam[t.idx], px0, ty0, px1, ty1);
       } else {
         const BandDev B = P.band[t.idx];
         const bool rows_out = ty0 < B.y0 || ty1 >= B.y1;
-        const bool need = warp == 0 ? (tx0 < B.x0 || (rows_out && tx1 >= B.x0))
-                                    : (tx1 >= B.x1 || (rows_out && tx0 < B.x1));
-        if (need) W = warp_window(P.cam[t.idx + warp], tx0, ty0, tx1, ty1);
+        need = warp == 0 ? (px0 < B.x0 || (rows_out && px1 >= B.x0)) : (px1 >= B.x1 || (rows_out && px0 < B.x1));
+        if (need) W = warp_window<S, G::kRows>(P.cam[t.idx + warp], px0, ty0, px1, ty1);
       }
     }
-    if (lane == 0) sm.sW[warp] = W;
+    if (lane == 0) {
+      h.sW[warp] = W;
+      if (need && !W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
+    }
   }
   __syncthreads();
-  const Window W0 = sm.sW[0], W1 = sm.sW[1];
-  if (W0.ok) stage_window(P.src[t.idx], P.cam[t.idx], W0, sm.s_win[0]);
-  if (W1.ok) stage_window(P.src[t.idx + 1], P.cam[t.idx + 1], W1, sm.s_win[1]);
+  const Window W0 = h.sW[0], W1 = h.sW[1];
+  if (W0.ok) stage_window<S>(P.src[t.idx], P.cam[t.idx], W0, st.win[0]);
+  if (W1.ok) stage_window<S>(P.src[t.idx + 1], P.cam[t.idx + 1], W1, st.win[1]);
   __syncthreads();
 
-  if (t.kind == 0) {
-    // Fully covered own tile: no coverage test, no fallback.
+  constexpr int kGroups = TW / 32, kRPW = TH / 8;
+  if (t.kind == kTileOwnPart) {
     const int k = t.idx;
-    const CamDev &c = P.cam[k];
-    const float *M = bc.M[k];
-    const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
-    if (c.affine && W0.ok) {
-#pragma unroll 2
-      for (int j = 0; j < MP::kPix; ++j) {
-        const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
-        float sx, sy;
-        cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
-        put_px<TW, TH>(sm.s_out, lx, ly, bc, true, mulM(M, win_bilinear(sm.s_win[0], W0, sx, sy)));
-      }
-    } else {
-#pragma unroll 2
-      for (int j = 0; j < MP::kPix; ++j) {
-        const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
-        float sx, sy, nw;
-        cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
-        const float3 v =
-            mulM(M, W0.ok ? win_bilinear(sm.s_win[0], W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
-        put_px<TW, TH>(sm.s_out, lx, ly, bc, true, v);
-      }
-    }
-  } else if (t.kind == 2) {
-    const int k = t.idx;
-    const float *M = bc.M[k];
-#pragma unroll 2
-    for (int j = 0; j < MP::kPix; ++j) {
-      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+    for (int j = 0; j < kGroups * kRPW; ++j) {
+      const int lx = lane + 32 * (j % kGroups), ly = kRPW * warp + j / kGroups;
+      if (lx < cx0 || lx >= cx1) continue;
       const int x = tx0 + lx, y = ty0 + ly;
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       bool cov = false;
-      if (x < P.pano_w && y < P.pano_h) {
-        cov = cam_value_w(P, M, k, W0, sm.s_win[0], x, y, v);
-        if (!cov && k > 0) cov = cam_value_g(P, bc, k - 1, x, y, v);
-        if (!cov && k < P.n_cams - 1) cov = cam_value_g(P, bc, k + 1, x, y, v);
-      }
-      put_px<TW, TH>(sm.s_out, lx, ly, bc, cov, v);
+      if (x < P.pano_w && y < P.pano_h) cov = own_value<S>(P, bc, k, k - 1, k + 1, W0, st.win[0], x, y, v);
+      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v);
     }
   } else {
     const int p = t.idx;
     const BandDev B = P.band[p];
-    const float *Ma = bc.M[p];
-    const float *Mb = bc.M[p + 1];
-    const PT *pwa = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][0];
-    const PT *pwb = reinterpret_cast<const PT *>(P.pw) + P.pw_off[p][1];
     const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
-    const float mf = P.max_flow;
-    const int bw = B.x1 - B.x0;
-#pragma unroll 2
-    for (int j = 0; j < MP::kPix; ++j) {
-      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
+    for (int j = 0; j < kGroups * kRPW; ++j) {
+      const int lx = lane + 32 * (j % kGroups), ly = kRPW * warp + j / kGroups;
+      if (lx < cx0 || lx >= cx1) continue;
       const int x = tx0 + lx, y = ty0 + ly;
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       bool cov = false;
       if (x < P.pano_w && y < P.pano_h) {
         if (x < B.x0) {
-          cov = cam_value_w(P, Ma, p, W0, sm.s_win[0], x, y, v);
-          if (!cov && p > 0) cov = cam_value_g(P, bc, p - 1, x, y, v);
-          if (!cov) cov = cam_value_g(P, bc, p + 1, x, y, v);
+          cov = own_value<S>(P, bc, p, p - 1, p + 1, W0, st.win[0], x, y, v);
         } else if (x >= B.x1) {
-          cov = cam_value_w(P, Mb, p + 1, W1, sm.s_win[1], x, y, v);
-          if (!cov) cov = cam_value_g(P, bc, p, x, y, v);
-          if (!cov && p + 2 < P.n_cams) cov = cam_value_g(P, bc, p + 2, x, y, v);
-        } else {
+          cov = own_value<S>(P, bc, p + 1, p, p + 2, W1, st.win[1], x, y, v);
+        } else if (y < B.y0 || y >= B.y1) {
           const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
           const float ta = 1.0f - tb;
-          if (y < B.y0 || y >= B.y1) {
-            float3 va, vb;
-            const bool ca = cam_value_w(P, Ma, p, W0, sm.s_win[0], x, y, va);
-            const bool cb = cam_value_w(P, Mb, p + 1, W1, sm.s_win[1], x, y, vb);
-            if (ca && cb) {
-              v = make_float3(fmaf(ta, va.x, tb * vb.x), fmaf(ta, va.y, tb * vb.y), fmaf(ta, va.z, tb * vb.z));
-            } else if (ca) {
-              v = va;
-            } else if (cb) {
-              v = vb;
-            }
-            cov = ca || cb;
-          } else {
-            const size_t fi = (size_t)(y - B.y0) * bw + (x - B.x0);
-            float2 fa = __ldg(P.flow_ij[p] + fi);
-            float2 fb = __ldg(P.flow_ji[p] + fi);
-            fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
-            fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
-            const float wa = printed ? ta : tb;
-            const float wb = printed ? tb : ta;
-            const float lo_x = (float)B.x0, hi_x = (float)(B.x1 - 1);
-            const float lo_y = (float)B.y0, hi_y = (float)(B.y1 - 1);
-            const float Xa = fminf(fmaxf(fmaf(wa, fa.x, (float)x), lo_x), hi_x);
-            const float Ya = fminf(fmaxf(fmaf(wa, fa.y, (float)y), lo_y), hi_y);
-            const float Xb = fminf(fmaxf(fmaf(wb, fb.x, (float)x), lo_x), hi_x);
-            const float Yb = fminf(fmaxf(fmaf(wb, fb.y, (float)y), lo_y), hi_y);
-            const float3 Pa = mulM(Ma, pw_bilinear<kHalf>(pwa, B, Xa, Ya));
-            const float3 Pb = mulM(Mb, pw_bilinear<kHalf>(pwb, B, Xb, Yb));
-            v = make_float3(fmaf(ta, Pa.x, tb * Pb.x), fmaf(ta, Pa.y, tb * Pb.y), fmaf(ta, Pa.z, tb * Pb.z));
-            cov = true;
+          float3 va, vb;
+          const bool ca = cam_value<S>(P, bc, p, W0, st.win[0], x, y, va);
+          const bool cb = cam_value<S>(P, bc, p + 1, W1, st.win[1], x, y, vb);
+          if (ca && cb) {
+            v = make_float3(fmaf(ta, va.x, tb * vb.x), fmaf(ta, va.y, tb * vb.y), fmaf(ta, va.z, tb * vb.z));
+          } else if (ca) {
+            v = va;
+          } else if (cb) {
+            v = vb;
           }
+          cov = ca || cb;
+        } else {
+          v = band_pixel<kHalf, true>(P, bc, p, x, y, printed);
+          cov = true;
         }
       }
-      put_px<TW, TH>(sm.s_out, lx, ly, bc, cov, v);
+      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v);
     }
   }
   __syncthreads();
-  store_tile<TW, TH>(P, tx0, ty0, sm.s_out);
+  store_tile<TW, TH>(P, tx0, ty0, st.out, t.c0, t.c1);
 }
 
-// Shared memory of a fully covered own tile: one camera, one window.
-template <int TW, int TH>
-struct FuseOwnSmem {
-  BlockColor bc;
-  Window sW;
-  __align__(16) uint32_t s_win[kWinCap];
-  __align__(16) uint8_t s_out[3][TH][TW];
-};
-
-// A fully covered own tile (kind 0) on its own: no band, no coverage test, no
-// fallback camera; the same arithmetic as that case of fuse_tile, with the
-// registers and shared memory of one camera only.
-template <int TW, int TH>
-__device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDesc t, FuseOwnSmem<TW, TH> &sm) {
-  using MP = Map<TW, TH>;
-  BlockColor &bc = sm.bc;
-  const int tx0 = t.tx * TW, ty0 = t.ty * TH;
-  const int tx1 = min(tx0 + TW, P.pano_w) - 1, ty1 = min(ty0 + TH, P.pano_h) - 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k = t.idx;
-  const CamDev &c = P.cam[k];
-  load_block_color(P, bc);
-  if (warp == 0) {
-    const Window W = warp_window(c, tx0, ty0, tx1, ty1);
-    if (lane == 0) sm.sW = W;
-  }
-  __syncthreads();
-  const Window W0 = sm.sW;
-  if (W0.ok) stage_window(P.src[k], c, W0, sm.s_win);
-  __syncthreads();
-  const float *M = bc.M[k];
-  const float bx = (float)(tx0 - c.ox), by = (float)(ty0 - c.oy);
-  if (c.affine && W0.ok) {
-#pragma unroll 2
-    for (int j = 0; j < MP::kPix; ++j) {
-      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
-      float sx, sy;
-      cam_map_aff(c, bx + (float)lx, by + (float)ly, sx, sy);
-      put_px<TW, TH>(sm.s_out, lx, ly, bc, true, mulM(M, win_bilinear(sm.s_win, W0, sx, sy)));
-    }
-  } else {
-#pragma unroll 2
-    for (int j = 0; j < MP::kPix; ++j) {
-      const int lx = MP::lx(lane, j), ly = MP::ly(warp, j);
-      float sx, sy, nw;
-      cam_map_f(c, bx + (float)lx, by + (float)ly, sx, sy, nw);
-      const float3 v = mulM(M, W0.ok ? win_bilinear(sm.s_win, W0, sx, sy) : src_bilinear(P.src[k], c, sx, sy));
-      put_px<TW, TH>(sm.s_out, lx, ly, bc, true, v);
-    }
-  }
-  __syncthreads();
-  store_tile<TW, TH>(P, tx0, ty0, sm.s_out);
-}
-
-// One band pre-warp piece (kTileW x kTileH) of pair pt.pair, both cameras.
+// One band pre-warp piece (kTileW x kTileH) of pair pt.pair, both cameras,
+// s clamped into the frame (the band lies inside both cameras' coverage, so
+// the clamp only removes float32 noise). Under kFlagPwOffset (the frame path)
+// the samples are the paired half2 bilinear of the staged windows and the
+// intermediate holds v - 128; otherwise (the flow and the correspondence fit,
+// which want the plain pre-warped image) a float32 bilinear of v.
 template <bool kHalf>
-__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, uint32_t (*s_win)[kWinCap],
-                                              Window *sW) {
+__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, SmemHead &h,
+                                              SmemTile<kTileW, kTileH, 2> &st) {
+  using G = WinGeom<kTileW, kTileH>;
+  using PM = PairMap<kTileW, kTileH>;
+  constexpr int S = G::kStride;
+  constexpr int kMax = G::kAlloc - S - 2;
   using PT = typename PwT<kHalf>::T;
   const BandDev B = P.band[pt.pair];
   const int bw = B.x1 - B.x0;
@@ -673,34 +1053,105 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
   const int rx1 = min(rx0 + kTileW, B.x1) - 1, ry1 = min(ry0 + kTileH, B.y1) - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < 2) {
-    const Window W = warp_window(P.cam[pt.pair + warp], rx0, ry0, rx1, ry1);
-    if (lane == 0) sW[warp] = W;
+    const Window W = warp_window<S, G::kRows>(P.cam[pt.pair + warp], rx0, ry0, rx1, ry1);
+    if (lane == 0) {
+      h.sW[warp] = W;
+      if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
+    }
   }
   __syncthreads();
-  const Window Wa = sW[0], Wb = sW[1];
-  if (Wa.ok) stage_window(P.src[pt.pair], P.cam[pt.pair], Wa, s_win[0]);
-  if (Wb.ok) stage_window(P.src[pt.pair + 1], P.cam[pt.pair + 1], Wb, s_win[1]);
-  __syncthreads();
-  PT *da = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][0];
-  PT *db = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][1];
-  const CamDev &ca = P.cam[pt.pair];
-  const CamDev &cb = P.cam[pt.pair + 1];
+  const bool offset = (P.flags & kFlagPwOffset) != 0;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const Window W = h.sW[side];
+    const int k = pt.pair + side;
+    const CamDev &c = P.cam[k];
+    if (W.ok) stage_window<S>(P.src[k], c, W, st.win[side]);
+    __syncthreads();
+    PT *dst = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][side];
+    if (offset && W.ok) {
+      // Every clamped point of the piece lies in the window (clipped to the
+      // frame); a far tap past the frame reads the staged 0x64 column / row
+      // with weight zero.
+      const uint32_t off = kMagicRoundBits * (uint32_t)(S + 1) + (uint32_t)W.y0 * (uint32_t)S + (uint32_t)W.x0;
+      const float hx = c.wm1 - 0.5f, hy = c.hm1 - 0.5f;
+      const PairCoords pc = pair_coords<kTileW, kTileH>(c, rx0, ry0, lane, warp);
+      float2 yy = pc.y0;
 #pragma unroll 2
-  for (int j = 0; j < 8; ++j) {
-    const int x = rx0 + lane + 32 * (j & 1);
-    const int y = ry0 + 4 * warp + (j >> 1);
-    if (x > rx1 || y > ry1) continue;
-    const size_t o = (size_t)(y - B.y0) * bw + (x - B.x0);
-    float sx, sy, nw;
-    // The band lies inside both cameras' coverage: clamp float32 noise away.
-    cam_map_f(ca, (float)(x - ca.ox), (float)(y - ca.oy), sx, sy, nw);
-    sx = fminf(fmaxf(sx, 0.0f), ca.wm1);
-    sy = fminf(fmaxf(sy, 0.0f), ca.hm1);
-    PwT<kHalf>::put(da, o, Wa.ok ? win_bilinear(s_win[0], Wa, sx, sy) : src_bilinear(P.src[pt.pair], ca, sx, sy));
-    cam_map_f(cb, (float)(x - cb.ox), (float)(y - cb.oy), sx, sy, nw);
-    sx = fminf(fmaxf(sx, 0.0f), cb.wm1);
-    sy = fminf(fmaxf(sy, 0.0f), cb.hm1);
-    PwT<kHalf>::put(db, o, Wb.ok ? win_bilinear(s_win[1], Wb, sx, sy) : src_bilinear(P.src[pt.pair + 1], cb, sx, sy));
+      for (int s = 0; s < PM::kSteps; ++s) {
+        float2 ux, uy;
+        pair_point(c, pc, 0, pair_row(c, yy), ux, uy);
+        ux = f2(fminf(fmaxf(ux.x, -0.5f), hx), fminf(fmaxf(ux.y, -0.5f), hx));
+        uy = f2(fminf(fmaxf(uy.x, -0.5f), hy), fminf(fmaxf(uy.y, -0.5f), hy));
+        float2 rx, ry;
+        __half2 fx, fy;
+        split_pair(ux, rx, fx);
+        split_pair(uy, ry, fy);
+        const uint32_t i0 = __float_as_uint(ry.x) * (uint32_t)S + __float_as_uint(rx.x) - off;
+        const uint32_t i1 = __float_as_uint(ry.y) * (uint32_t)S + __float_as_uint(rx.y) - off;
+        uint32_t t0[4], t1[4];
+        taps<S, kMax>(st.win[side], i0, t0);
+        taps<S, kMax>(st.win[side], i1, t1);
+        float2 v[3];
+        bilerp_pair(t0, t1, fx, fy, v);
+        const int y = ry0 + PM::ly0(warp, s);
+        const int x0 = rx0 + PM::lx0(lane, 0), x1 = rx0 + PM::lx1(lane, 0);
+        if (y <= ry1) {
+          const size_t o = (size_t)(y - B.y0) * bw;
+          if (kHalf) {
+            uint2 *d2 = reinterpret_cast<uint2 *>(dst);
+            if (x0 <= rx1)
+              d2[o + (x0 - B.x0)] = make_uint2(h2_bits(__floats2half2_rn(v[0].x, v[1].x)),
+                                              h2_bits(__floats2half2_rn(v[2].x, 0.0f)));
+            if (x1 <= rx1)
+              d2[o + (x1 - B.x0)] = make_uint2(h2_bits(__floats2half2_rn(v[0].y, v[1].y)),
+                                              h2_bits(__floats2half2_rn(v[2].y, 0.0f)));
+          } else {
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+            if (x0 <= rx1) d4[o + (x0 - B.x0)] = make_float4(v[0].x, v[1].x, v[2].x, 0.0f);
+            if (x1 <= rx1) d4[o + (x1 - B.x0)] = make_float4(v[0].y, v[1].y, v[2].y, 0.0f);
+          }
+        }
+        yy = __fadd2_rn(yy, f2(PM::kDy));
+      }
+    } else {
+      for (int j = 0; j < 8; ++j) {
+        const int x = rx0 + lane + 32 * (j & 1);
+        const int y = ry0 + 4 * warp + (j >> 1);
+        if (x > rx1 || y > ry1) continue;
+        const size_t o = (size_t)(y - B.y0) * bw + (x - B.x0);
+        float3 v;
+        if (offset) {
+          // window did not fit: the same arithmetic with taps from the frame
+          float sx, sy, nw;
+          cam_point(c, x, y, sx, sy, nw);
+          sx = fminf(fmaxf(sx, -0.5f), c.wm1 - 0.5f);
+          sy = fminf(fmaxf(sy, -0.5f), c.hm1 - 0.5f);
+          const float rxs = sx + kMagicRound, rys = sy + kMagicRound;
+          const float fx = (sx - (rxs - kMagicRound)) + 0.5f, fy = (sy - (rys - kMagicRound)) + 0.5f;
+          const int ix = max((int)(__float_as_uint(rxs) - kMagicRoundBits), 0);
+          const int iy = max((int)(__float_as_uint(rys) - kMagicRoundBits), 0);
+          const int ix1 = min(ix + 1, c.w - 1), iy1 = min(iy + 1, c.h_px - 1);
+          uint32_t t[4] = {gword(P.src[k], c, ix, iy), gword(P.src[k], c, ix1, iy), gword(P.src[k], c, ix, iy1),
+                           gword(P.src[k], c, ix1, iy1)};
+          float2 vv[3];
+          bilerp_pair(t, t, __float2half2_rn(fx), __float2half2_rn(fy), vv);
+          v = make_float3(vv[0].x, vv[1].x, vv[2].x);
+        } else {
+          float sx, sy, nw;
+          cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
+          sx = fminf(fmaxf(sx, 0.0f), c.wm1);
+          sy = fminf(fmaxf(sy, 0.0f), c.hm1);
+          v = W.ok ? win_bilinear<S>(st.win[side], W, sx, sy) : src_bilinear(P.src[k], c, sx, sy);
+        }
+        if (kHalf) {
+          reinterpret_cast<uint2 *>(dst)[o] =
+              make_uint2(h2_bits(__floats2half2_rn(v.x, v.y)), h2_bits(__floats2half2_rn(v.z, 0.0f)));
+        } else {
+          reinterpret_cast<float4 *>(dst)[o] = make_float4(v.x, v.y, v.z, 0.0f);
+        }
+      }
+    }
   }
 }
 
@@ -720,113 +1171,127 @@ __device__ __forceinline__ void copy_params(FuseParams &dst, const FuseParams *s
 
 template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams P) {
-  __shared__ __align__(16) uint32_t s_win[2][kWinCap];
-  __shared__ Window sW[2];
-  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], s_win, sW);
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], h, tile_smem<kTileW, kTileH, 2>(smem));
 }
 
+// General pieces (the first n_tiles - n_band - n_full of the list),
+// persistent: block b takes pieces b, b + grid, ...
 template <bool kHalf, int TW, int TH>
-__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse(const FuseParams P) {
-  __shared__ FuseSmem<TW, TH> sm;
-  fuse_tile<kHalf, TW, TH>(P, P.tiles[blockIdx.x], sm);
+__global__ void __launch_bounds__(kFuseThreads, 3) k_fuse(const FuseParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  load_color(P, h);
+  const int n = P.n_tiles - P.n_band - P.n_full;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    __syncthreads();
+    fuse_tile<kHalf, TW, TH>(P, P.tiles[i], h, tile_smem<TW, TH, 2>(smem));
+  }
 }
 
-// The fully covered own tiles, which close the tile list (P.n_full of them).
+// Band pieces (the n_band before the fully covered ones), persistent.
+template <bool kHalf, int TW, int TH>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_band(const FuseParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  SmemBand<TW, TH> &sb = *reinterpret_cast<SmemBand<TW, TH> *>(smem + (sizeof(SmemHead) + 15) / 16 * 16);
+  load_color(P, h);
+  const int base = P.n_tiles - P.n_full - P.n_band;
+  for (int i = blockIdx.x; i < P.n_band; i += gridDim.x) {
+    __syncthreads();
+    fuse_band_piece<kHalf, TW, TH>(P, P.tiles[base + i], h, sb.out);
+  }
+}
+
+// The fully covered own pieces, which close the list (P.n_full of them).
 template <int TW, int TH>
 __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own(const FuseParams P) {
-  __shared__ FuseOwnSmem<TW, TH> sm;
-  fuse_own_tile<TW, TH>(P, P.tiles[P.n_tiles - P.n_full + blockIdx.x], sm);
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  load_color(P, h);
+  const int base = P.n_tiles - P.n_full;
+  for (int i = blockIdx.x; i < P.n_full; i += gridDim.x) {
+    __syncthreads();
+    fuse_own_tile<TW, TH>(P, P.tiles[base + i], h, tile_smem<TW, TH, 1>(smem));
+  }
 }
 
 // Band pre-warp of several rigs in one launch: block b takes item b.
 template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParams M) {
-  __shared__ __align__(16) uint32_t s_win[2][kWinCap];
-  __shared__ Window sW[2];
-  __shared__ FuseParams sp;
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
   const MultiItem it = M.items[blockIdx.x];
-  copy_params(sp, M.params + M.base + it.rig);
+  copy_params(h.sp, M.params + M.base + it.rig);
   __syncthreads();
-  prewarp_piece<kHalf>(sp, it.pw, s_win, sW);
+  prewarp_piece<kHalf>(h.sp, it.pw, h, tile_smem<kTileW, kTileH, 2>(smem));
 }
 
-// Shared memory of the persistent multi-rig kernels: room for any tile shape
-// (every rig's tiles use that rig's own shape).
-union MultiSmem {
-  FuseSmem<64, 32> s0;
-  FuseSmem<64, 16> s1;
-  FuseSmem<32, 32> s2;
-  FuseSmem<128, 16> s3;
-};
-union MultiOwnSmem {
-  FuseOwnSmem<64, 32> s0;
-  FuseOwnSmem<64, 16> s1;
-  FuseOwnSmem<32, 32> s2;
-  FuseOwnSmem<128, 16> s3;
-};
+// Next item of a persistent multi-rig launch; reloads the rig's parameters
+// and colour constants when the rig changes. Returns false when none is left.
+__device__ __forceinline__ bool next_item(const MultiParams &M, SmemHead &h, MultiItem &it) {
+  __syncthreads();
+  if (threadIdx.x == 0) h.item = atomicAdd(M.counter, 1);
+  __syncthreads();
+  const int item = h.item;
+  if (item >= M.n_items) return false;
+  it = M.items[item];
+  if (it.rig != h.rig) {
+    copy_params(h.sp, M.params + M.base + it.rig);
+    __syncthreads();
+    load_color(h.sp, h);
+    __syncthreads();
+    if (threadIdx.x == 0) h.rig = it.rig;
+    __syncthreads();
+  }
+  return true;
+}
 
 // One tile of a multi-rig launch in its own call frame, so that each shape's
 // code gets its own register allocation inside the mixed-shape kernels.
 template <bool kHalf, int TW, int TH>
-__device__ __noinline__ void multi_tile(const FuseParams &P, const TileDesc t, FuseSmem<TW, TH> &sm) {
-  fuse_tile<kHalf, TW, TH>(P, t, sm);
+__device__ __forceinline__ void any_tile(SmemHead &h, const TileDesc t, unsigned char *smem) {
+  if (t.kind == kTileBand)
+    fuse_band_piece<kHalf, TW, TH>(h.sp, t, h, tile_smem<TW, TH, 2>(smem).out);
+  else
+    fuse_tile<kHalf, TW, TH>(h.sp, t, h, tile_smem<TW, TH, 2>(smem));
+}
+template <bool kHalf, int TW, int TH>
+__device__ __noinline__ void multi_tile(SmemHead &h, const TileDesc t, unsigned char *smem) {
+  any_tile<kHalf, TW, TH>(h, t, smem);
 }
 template <int TW, int TH>
-__device__ __noinline__ void multi_own_tile(const FuseParams &P, const TileDesc t, FuseOwnSmem<TW, TH> &sm) {
-  fuse_own_tile<TW, TH>(P, t, sm);
+__device__ __noinline__ void multi_own_tile(SmemHead &h, const TileDesc t, unsigned char *smem) {
+  fuse_own_tile<TW, TH>(h.sp, t, h, tile_smem<TW, TH, 1>(smem));
 }
 
 // Persistent fuse over the tiles of several rigs: each block takes the next
 // item from a work counter until none is left (dynamic balance of uneven tile
-// costs), loading a rig's parameters into shared memory when the rig changes.
-// k_fuse_multi serves batches whose rigs share one tile shape;
+// costs). k_fuse_multi serves batches whose rigs share one tile shape;
 // k_fuse_multi_mixed runs every item with its rig's own shape.
 template <bool kHalf, int TW, int TH>
-__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi(const MultiParams M) {
-  __shared__ FuseSmem<TW, TH> sm;
-  __shared__ FuseParams sp;
-  __shared__ int s_item;
-  int cur = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= M.n_items) break;
-    const MultiItem it = M.items[item];
-    if (it.rig != cur) {
-      copy_params(sp, M.params + M.base + it.rig);
-      cur = it.rig;
-    }
-    __syncthreads();
-    fuse_tile<kHalf, TW, TH>(sp, it.tile, sm);
-    __syncthreads();
-  }
+__global__ void __launch_bounds__(kFuseThreads, 3) k_fuse_multi(const MultiParams M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  if (threadIdx.x == 0) h.rig = -1;
+  MultiItem it;
+  while (next_item(M, h, it)) any_tile<kHalf, TW, TH>(h, it.tile, smem);
 }
 
 template <bool kHalf>
-__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi_mixed(const MultiParams M) {
-  __shared__ MultiSmem sm;
-  __shared__ FuseParams sp;
-  __shared__ int s_item;
-  int cur = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= M.n_items) break;
-    const MultiItem it = M.items[item];
-    if (it.rig != cur) {
-      copy_params(sp, M.params + M.base + it.rig);
-      cur = it.rig;
-    }
-    __syncthreads();
+__global__ void __launch_bounds__(kFuseThreads, 3) k_fuse_multi_mixed(const MultiParams M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  if (threadIdx.x == 0) h.rig = -1;
+  MultiItem it;
+  while (next_item(M, h, it)) {
     switch (it.shape) {
-      case 0: multi_tile<kHalf, 64, 32>(sp, it.tile, sm.s0); break;
-      case 1: multi_tile<kHalf, 64, 16>(sp, it.tile, sm.s1); break;
-      case 2: multi_tile<kHalf, 32, 32>(sp, it.tile, sm.s2); break;
-      default: multi_tile<kHalf, 128, 16>(sp, it.tile, sm.s3); break;
+      case 0: multi_tile<kHalf, 64, 32>(h, it.tile, smem); break;
+      case 1: multi_tile<kHalf, 64, 16>(h, it.tile, smem); break;
+      case 2: multi_tile<kHalf, 32, 32>(h, it.tile, smem); break;
+      default: multi_tile<kHalf, 128, 16>(h, it.tile, smem); break;
     }
-    __syncthreads();
   }
 }
 
@@ -834,100 +1299,123 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_multi_mixed(const Mult
 // for all rigs, or each rig's own).
 template <int TW, int TH>
 __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi(const MultiParams M) {
-  __shared__ FuseOwnSmem<TW, TH> sm;
-  __shared__ FuseParams sp;
-  __shared__ int s_item;
-  int cur = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= M.n_items) break;
-    const MultiItem it = M.items[item];
-    if (it.rig != cur) {
-      copy_params(sp, M.params + M.base + it.rig);
-      cur = it.rig;
-    }
-    __syncthreads();
-    fuse_own_tile<TW, TH>(sp, it.tile, sm);
-    __syncthreads();
-  }
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  if (threadIdx.x == 0) h.rig = -1;
+  MultiItem it;
+  while (next_item(M, h, it)) fuse_own_tile<TW, TH>(h.sp, it.tile, h, tile_smem<TW, TH, 1>(smem));
 }
 
 __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi_mixed(const MultiParams M) {
-  __shared__ MultiOwnSmem sm;
-  __shared__ FuseParams sp;
-  __shared__ int s_item;
-  int cur = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(M.counter, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= M.n_items) break;
-    const MultiItem it = M.items[item];
-    if (it.rig != cur) {
-      copy_params(sp, M.params + M.base + it.rig);
-      cur = it.rig;
-    }
-    __syncthreads();
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  if (threadIdx.x == 0) h.rig = -1;
+  MultiItem it;
+  while (next_item(M, h, it)) {
     switch (it.shape) {
-      case 0: multi_own_tile<64, 32>(sp, it.tile, sm.s0); break;
-      case 1: multi_own_tile<64, 16>(sp, it.tile, sm.s1); break;
-      case 2: multi_own_tile<32, 32>(sp, it.tile, sm.s2); break;
-      default: multi_own_tile<128, 16>(sp, it.tile, sm.s3); break;
+      case 0: multi_own_tile<64, 32>(h, it.tile, smem); break;
+      case 1: multi_own_tile<64, 16>(h, it.tile, smem); break;
+      case 2: multi_own_tile<32, 32>(h, it.tile, smem); break;
+      default: multi_own_tile<128, 16>(h, it.tile, smem); break;
     }
-    __syncthreads();
   }
 }
 
-size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
-
-cudaError_t fuse_setup_attributes(int) { return cudaSuccess; }
-
-cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s) {
-  if (p.n_pw_tiles <= 0) return cudaSuccess;
-  if (p.flags & STITCH_FP16_INTERMEDIATE)
-    k_prewarp_band<true><<<p.n_pw_tiles, kFuseThreads, 0, s>>>(p);
-  else
-    k_prewarp_band<false><<<p.n_pw_tiles, kFuseThreads, 0, s>>>(p);
-  return cudaGetLastError();
-}
+// ---------------------------------------------------------------------------
+// Host side: shared-memory sizes, attributes, launches.
+// ---------------------------------------------------------------------------
 
 namespace {
 
-// The tiles that touch a band or are partly covered (k_fuse), then the fully
-// covered own tiles (k_fuse_own), in one stream.
-template <int TW, int TH>
-void fuse_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t s) {
-  if (half)
-    k_fuse_multi<true, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
-  else
-    k_fuse_multi<false, TW, TH><<<grid, kFuseThreads, 0, s>>>(m);
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kPwSmem = smem_bytes<kTileW, kTileH, 2>();
+constexpr size_t kMixSmem =
+    cmax(cmax(smem_bytes<64, 32, 2>(), smem_bytes<64, 16, 2>()), cmax(smem_bytes<32, 32, 2>(), smem_bytes<128, 16, 2>()));
+constexpr size_t kMixOwnSmem =
+    cmax(cmax(smem_bytes<64, 32, 1>(), smem_bytes<64, 16, 1>()), cmax(smem_bytes<32, 32, 1>(), smem_bytes<128, 16, 1>()));
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int TW, int TH>
-int occupancy(bool half) {
+cudaError_t setup_shape() {
+  cudaError_t e = set_smem(k_fuse<false, TW, TH>, smem_bytes<TW, TH, 2>());
+  if (e == cudaSuccess) e = set_smem(k_fuse<true, TW, TH>, smem_bytes<TW, TH, 2>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_band<false, TW, TH>, band_smem_bytes<TW, TH>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_band<true, TW, TH>, band_smem_bytes<TW, TH>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_own<TW, TH>, smem_bytes<TW, TH, 1>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_multi<false, TW, TH>, smem_bytes<TW, TH, 2>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_multi<true, TW, TH>, smem_bytes<TW, TH, 2>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_own_multi<TW, TH>, smem_bytes<TW, TH, 1>());
+  return e;
+}
+
+// Resident blocks per SM of a persistent kernel, cached per kernel.
+template <typename K>
+int per_sm(K kernel, size_t smem) {
   int n = 0;
-  if (half)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi<true, TW, TH>, kFuseThreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi<false, TW, TH>, kFuseThreads, 0);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kFuseThreads, smem) != cudaSuccess) n = 1;
+  return n < 1 ? 1 : n;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
   return n;
 }
 
-template <int TW, int TH>
-void fuse_by_half(const FuseParams &p, cudaStream_t s) {
-  const int mixed = p.n_tiles - p.n_full;
-  if (mixed > 0) {
-    if (p.flags & STITCH_FP16_INTERMEDIATE)
-      k_fuse<true, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
-    else
-      k_fuse<false, TW, TH><<<mixed, kFuseThreads, 0, s>>>(p);
-  }
-  if (p.n_full > 0) k_fuse_own<TW, TH><<<p.n_full, kFuseThreads, 0, s>>>(p);
+// Persistent grid for n tiles: one full wave of resident blocks (every SM
+// holds as many blocks as fit, which hides the kernels' load latency).
+int persistent_grid(int n, int resident) {
+  if (n <= 0) return 0;
+  return std::min(n, resident * sm_count());
 }
 
+// The three fuse launches of a frame (general pieces, band pieces, fully
+// covered own pieces), each a persistent grid of at most one resident wave.
+template <int TW, int TH>
+void fuse_by_half(const FuseParams &p, cudaStream_t s) {
+  static int res_gen[2] = {0, 0}, res_band[2] = {0, 0}, res_own = 0;
+  const int gen = p.n_tiles - p.n_band - p.n_full;
+  const bool half = (p.flags & STITCH_FP16_INTERMEDIATE) != 0;
+  constexpr size_t kGen = smem_bytes<TW, TH, 2>(), kBand = band_smem_bytes<TW, TH>(), kOwn = smem_bytes<TW, TH, 1>();
+  if (gen > 0) {
+    if (half) {
+      if (!res_gen[1]) res_gen[1] = per_sm(k_fuse<true, TW, TH>, kGen);
+      k_fuse<true, TW, TH><<<persistent_grid(gen, res_gen[1]), kFuseThreads, kGen, s>>>(p);
+    } else {
+      if (!res_gen[0]) res_gen[0] = per_sm(k_fuse<false, TW, TH>, kGen);
+      k_fuse<false, TW, TH><<<persistent_grid(gen, res_gen[0]), kFuseThreads, kGen, s>>>(p);
+    }
+  }
+  if (p.n_band > 0) {
+    if (half) {
+      if (!res_band[1]) res_band[1] = per_sm(k_fuse_band<true, TW, TH>, kBand);
+      k_fuse_band<true, TW, TH><<<persistent_grid(p.n_band, res_band[1]), kFuseThreads, kBand, s>>>(p);
+    } else {
+      if (!res_band[0]) res_band[0] = per_sm(k_fuse_band<false, TW, TH>, kBand);
+      k_fuse_band<false, TW, TH><<<persistent_grid(p.n_band, res_band[0]), kFuseThreads, kBand, s>>>(p);
+    }
+  }
+  if (p.n_full > 0) {
+    if (!res_own) res_own = per_sm(k_fuse_own<TW, TH>, kOwn);
+    k_fuse_own<TW, TH><<<persistent_grid(p.n_full, res_own), kFuseThreads, kOwn, s>>>(p);
+  }
+}
 
+template <int TW, int TH>
+void fuse_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t s) {
+  if (half)
+    k_fuse_multi<true, TW, TH><<<grid, kFuseThreads, smem_bytes<TW, TH, 2>(), s>>>(m);
+  else
+    k_fuse_multi<false, TW, TH><<<grid, kFuseThreads, smem_bytes<TW, TH, 2>(), s>>>(m);
+}
 
 }  // namespace
 
@@ -935,6 +1423,34 @@ static_assert(kTileShapes[0].w == 64 && kTileShapes[0].h == 32 && kTileShapes[1]
                   kTileShapes[2].w == 32 && kTileShapes[2].h == 32 && kTileShapes[3].w == 128 &&
                   kTileShapes[3].h == 16,
               "the shape table and the kernel instantiations below must agree");
+
+size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
+
+// Once per device, outside any stream capture: every fuse kernel uses more
+// than the default 48 KB of dynamic shared memory.
+cudaError_t fuse_setup_attributes(int) {
+  cudaError_t e = set_smem(k_prewarp_band<false>, kPwSmem);
+  if (e == cudaSuccess) e = set_smem(k_prewarp_band<true>, kPwSmem);
+  if (e == cudaSuccess) e = set_smem(k_prewarp_multi<false>, kPwSmem);
+  if (e == cudaSuccess) e = set_smem(k_prewarp_multi<true>, kPwSmem);
+  if (e == cudaSuccess) e = setup_shape<64, 32>();
+  if (e == cudaSuccess) e = setup_shape<64, 16>();
+  if (e == cudaSuccess) e = setup_shape<32, 32>();
+  if (e == cudaSuccess) e = setup_shape<128, 16>();
+  if (e == cudaSuccess) e = set_smem(k_fuse_multi_mixed<false>, kMixSmem);
+  if (e == cudaSuccess) e = set_smem(k_fuse_multi_mixed<true>, kMixSmem);
+  if (e == cudaSuccess) e = set_smem(k_fuse_own_multi_mixed, kMixOwnSmem);
+  return e;
+}
+
+cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s) {
+  if (p.n_pw_tiles <= 0) return cudaSuccess;
+  if (p.flags & STITCH_FP16_INTERMEDIATE)
+    k_prewarp_band<true><<<p.n_pw_tiles, kFuseThreads, kPwSmem, s>>>(p);
+  else
+    k_prewarp_band<false><<<p.n_pw_tiles, kFuseThreads, kPwSmem, s>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s) {
   if (p.n_tiles <= 0) return cudaSuccess;
@@ -951,9 +1467,9 @@ cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s) {
 cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s) {
   if (m.n_items <= 0) return cudaSuccess;
   if (half)
-    k_prewarp_multi<true><<<m.n_items, kFuseThreads, 0, s>>>(m);
+    k_prewarp_multi<true><<<m.n_items, kFuseThreads, kPwSmem, s>>>(m);
   else
-    k_prewarp_multi<false><<<m.n_items, kFuseThreads, 0, s>>>(m);
+    k_prewarp_multi<false><<<m.n_items, kFuseThreads, kPwSmem, s>>>(m);
   return cudaGetLastError();
 }
 
@@ -962,9 +1478,9 @@ cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int gr
   switch (shape) {
     case -1:
       if (half)
-        k_fuse_multi_mixed<true><<<grid, kFuseThreads, 0, s>>>(m);
+        k_fuse_multi_mixed<true><<<grid, kFuseThreads, kMixSmem, s>>>(m);
       else
-        k_fuse_multi_mixed<false><<<grid, kFuseThreads, 0, s>>>(m);
+        k_fuse_multi_mixed<false><<<grid, kFuseThreads, kMixSmem, s>>>(m);
       break;
     case 0: fuse_multi_by_half<64, 32>(m, half, grid, s); break;
     case 1: fuse_multi_by_half<64, 16>(m, half, grid, s); break;
@@ -978,43 +1494,42 @@ cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int gr
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s) {
   if (m.n_items <= 0) return cudaSuccess;
   switch (shape) {
-    case -1: k_fuse_own_multi_mixed<<<grid, kFuseThreads, 0, s>>>(m); break;
-    case 0: k_fuse_own_multi<64, 32><<<grid, kFuseThreads, 0, s>>>(m); break;
-    case 1: k_fuse_own_multi<64, 16><<<grid, kFuseThreads, 0, s>>>(m); break;
-    case 2: k_fuse_own_multi<32, 32><<<grid, kFuseThreads, 0, s>>>(m); break;
-    case 3: k_fuse_own_multi<128, 16><<<grid, kFuseThreads, 0, s>>>(m); break;
+    case -1: k_fuse_own_multi_mixed<<<grid, kFuseThreads, kMixOwnSmem, s>>>(m); break;
+    case 0: k_fuse_own_multi<64, 32><<<grid, kFuseThreads, smem_bytes<64, 32, 1>(), s>>>(m); break;
+    case 1: k_fuse_own_multi<64, 16><<<grid, kFuseThreads, smem_bytes<64, 16, 1>(), s>>>(m); break;
+    case 2: k_fuse_own_multi<32, 32><<<grid, kFuseThreads, smem_bytes<32, 32, 1>(), s>>>(m); break;
+    case 3: k_fuse_own_multi<128, 16><<<grid, kFuseThreads, smem_bytes<128, 16, 1>(), s>>>(m); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 int fuse_own_multi_blocks_per_sm(int shape) {
-  int n = 0;
   switch (shape) {
-    case -1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi_mixed, kFuseThreads, 0); break;
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<64, 32>, kFuseThreads, 0); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<64, 16>, kFuseThreads, 0); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<32, 32>, kFuseThreads, 0); break;
-    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_own_multi<128, 16>, kFuseThreads, 0); break;
-    default: break;
+    case -1: return per_sm(k_fuse_own_multi_mixed, kMixOwnSmem);
+    case 0: return per_sm(k_fuse_own_multi<64, 32>, smem_bytes<64, 32, 1>());
+    case 1: return per_sm(k_fuse_own_multi<64, 16>, smem_bytes<64, 16, 1>());
+    case 2: return per_sm(k_fuse_own_multi<32, 32>, smem_bytes<32, 32, 1>());
+    case 3: return per_sm(k_fuse_own_multi<128, 16>, smem_bytes<128, 16, 1>());
+    default: return 0;
   }
-  return n;
 }
 
 int fuse_multi_blocks_per_sm(bool half, int shape) {
   switch (shape) {
-    case -1: {
-      int n = 0;
-      if (half)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi_mixed<true>, kFuseThreads, 0);
-      else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fuse_multi_mixed<false>, kFuseThreads, 0);
-      return n;
-    }
-    case 0: return occupancy<64, 32>(half);
-    case 1: return occupancy<64, 16>(half);
-    case 2: return occupancy<32, 32>(half);
-    case 3: return occupancy<128, 16>(half);
+    case -1: return half ? per_sm(k_fuse_multi_mixed<true>, kMixSmem) : per_sm(k_fuse_multi_mixed<false>, kMixSmem);
+    case 0:
+      return half ? per_sm(k_fuse_multi<true, 64, 32>, smem_bytes<64, 32, 2>())
+                  : per_sm(k_fuse_multi<false, 64, 32>, smem_bytes<64, 32, 2>());
+    case 1:
+      return half ? per_sm(k_fuse_multi<true, 64, 16>, smem_bytes<64, 16, 2>())
+                  : per_sm(k_fuse_multi<false, 64, 16>, smem_bytes<64, 16, 2>());
+    case 2:
+      return half ? per_sm(k_fuse_multi<true, 32, 32>, smem_bytes<32, 32, 2>())
+                  : per_sm(k_fuse_multi<false, 32, 32>, smem_bytes<32, 32, 2>());
+    case 3:
+      return half ? per_sm(k_fuse_multi<true, 128, 16>, smem_bytes<128, 16, 2>())
+                  : per_sm(k_fuse_multi<false, 128, 16>, smem_bytes<128, 16, 2>());
     default: return 0;
   }
 }

@@ -36,6 +36,15 @@ constexpr double kCondLimit = 1e12;
 constexpr int kRawSlots = 3;
 constexpr int kColorSlots = 4;
 constexpr int kPwSlots = 2;
+// Output table of the balance curve (Eq. 5) and the final rounding: per
+// channel, entry n holds round_half_even(F(n / 16)) for the fused, clamped
+// value n / 16, n = 0 .. 4080 (a sixteenth of a grey level per step).
+constexpr int kLutEntries = 4096;
+constexpr float kLutTop = 4080.0f;
+constexpr int kLutBytes = 3 * kLutEntries;
+// Internal fuse flag (above the public STITCH_* bits): the band pre-warp of a
+// frame stores v - 128 (the fused path's offset form) instead of v.
+constexpr int kFlagPwOffset = 1 << 20;
 
 // Integer statistics of one frame, written by the stats kernel (K1) and read
 // by the estimate kernel (K2). Frame T uses slot T % kRawSlots.
@@ -79,6 +88,7 @@ struct ColorState {
 // entering the products stay small).
 struct CamDev {
   float h[9];
+  float hm[9];                        // h with rows x and y less half of row w: maps to s - (1/2, 1/2)
   int ox, oy;
   int w, h_px, pitch;
   float wm1, hm1;
@@ -93,13 +103,20 @@ struct BandDev {
   float inv_bw;
 };
 
+// One piece of a fuse tile: columns [16 c0, 16 c1) of the tile (tx, ty); the
+// pieces of one tile write disjoint 16-byte column chunks, so different
+// blocks can stitch them independently.
 struct TileDesc {
   int16_t tx, ty;                     // tile origin / (tile width, tile height)
-  int8_t kind;                        // 0 = own columns of camera idx, fully covered; 1 = touches band
-                                      // idx; 2 = own columns of camera idx, partly covered
-  int8_t idx;
-  int16_t pad;
+  int8_t kind;                        // kTileOwn, kTileBand, kTileOwnPart or kTileBandPart
+  int8_t idx;                         // camera (own kinds) or pair (band kinds)
+  uint8_t c0, c1;                     // column range in 16-pixel units within the tile
 };
+constexpr int kTileOwn = 0;           // own columns of camera idx, every pixel seen by it with a margin
+constexpr int kTileBand = 1;          // inside the blend band rectangle of pair idx
+constexpr int kTileOwnPart = 2;       // own columns of camera idx, partly covered
+constexpr int kTileBandPart = 3;      // band columns of pair idx with other pixels (band edge chunk, rows
+                                      // outside the band rectangle)
 
 // One kTileW x kTileH piece of a band rectangle for the band pre-warp kernel.
 struct PwTile {
@@ -114,13 +131,16 @@ struct alignas(16) FuseParams {
   int halo;
   float max_flow;
   int n_tiles;
-  int n_full;                         // the last n_full tiles are fully covered own tiles (kind 0)
+  int n_band;                         // tiles [n_tiles - n_full - n_band, n_tiles - n_full) are band tiles
+  int n_full;                         // the last n_full tiles are fully covered own tiles
   const TileDesc *tiles;
   int n_pw_tiles;
   const PwTile *pw_tiles;
   void *pw;                           // pre-warped band intermediate (both cameras of every band)
   size_t pw_off[kMaxPairs][2];        // element offsets of band p, left / right camera
   const ColorOut *color;
+  const uint8_t *lut;                 // the colour slot's output table (kLutBytes)
+  unsigned int *win_fallback;         // tiles whose source window did not fit in shared memory (counter)
   CamDev cam[kMaxCams];
   BandDev band[kMaxPairs];
   const uint8_t *src[kMaxCams];
@@ -165,6 +185,8 @@ struct StatsParams {
 
 struct EstimateParams {
   int n_cams, n_pairs, ref, window;
+  int flags;                          // STITCH_BALANCE_OFF selects the identity output table
+  uint8_t *lut;                       // kColorSlots output tables (slot T % kColorSlots), or null
   long long lambda_q;                 // lambda in millionths
   int pair_i[kMaxPairs], pair_j[kMaxPairs];
   int raw_slots;                      // frame T reads slot T % raw_slots and clears slot (T - 1) % raw_slots
@@ -264,6 +286,8 @@ struct CorrParams {
 // Launchers (defined in the kernel files).
 cudaError_t launch_stats(const StatsParams &p, int grid_x, cudaStream_t s);
 cudaError_t launch_estimate(const EstimateParams &p, cudaStream_t s);
+// The output table of one colour slot from its curve (after a state load).
+cudaError_t launch_curve_lut(const ColorOut *slot, int flags, uint8_t *lut, cudaStream_t s);
 cudaError_t estimate_setup();
 cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s);
 cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s);

@@ -126,6 +126,7 @@ def lib():
             "stitch_batch_destroy": (None, [vp]),
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
+            "stitch_window_fallbacks": (ip, [vp, ctypes.POINTER(ctypes.c_ulonglong), ip]),
             "stitch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_destroy": (None, [vp]),
         }
@@ -571,6 +572,13 @@ def stitch_batch_destroy(b) -> None:
 
 def stitch_n_pairs(ctx) -> int:
     return lib().stitch_n_pairs(ctx)
+
+
+def stitch_window_fallbacks(ctx, reset: bool = False) -> int:
+    """Fuse / pre-warp tiles whose source window did not fit in shared memory."""
+    n = ctypes.c_ulonglong(0)
+    _check(lib().stitch_window_fallbacks(ctx, ctypes.byref(n), 1 if reset else 0), ctx)
+    return int(n.value)
 
 
 def stitch_last_error(ctx=None) -> str:
