@@ -440,6 +440,10 @@ struct HostStage {
   cudaEvent_t out_done = nullptr;     // panorama copied out: panorama buffer free
 };
 
+// Streams of a recorded sequence: statistics, estimate, band pre-warp, and
+// two fuse streams taking alternate frames.
+constexpr int kPipeStreams = 5;
+
 struct stitch_ctx {
   Geo g;
   int flags = 0;
@@ -464,7 +468,8 @@ struct stitch_ctx {
   EstimateParams ep{};
   FuseParams fp{};
   cudaStream_t cap_stream = nullptr;
-  cudaStream_t pipe[3] = {};          // stats + pre-warp, estimate, fuse streams of a recorded sequence
+  cudaStream_t pipe[kPipeStreams] = {};   // statistics, estimate, band pre-warp and two fuse streams of a
+                                          // recorded sequence
   cudaEvent_t pev[4][8] = {};         // per-stage completion events (stats, pre-warp, estimate, fuse) by t % 8
   std::vector<GraphEntry> graphs;
   bool prof = false;                  // record stage events (stitch_profile)
@@ -922,7 +927,8 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
+  for (int i = 0; i < kPipeStreams && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
   for (int a = 0; a < 4 && e == cudaSuccess; ++a)
     for (int b = 0; b < 8 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&ctx->pev[a][b], cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -1117,9 +1123,11 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
     if (ge.n_frames == n_frames && ge.parity == parity && ge.prof == ctx->prof && ge.key == key) hit = &ge;
   if (!hit) {
     // Record the sequence on the library's own streams, then replay on `s`.
-    // Frame t runs its statistics and band pre-warp on pipe[0], its estimate
-    // on pipe[1] and its fuse on pipe[2]; event edges keep the order the slot
-    // rings need, so frame t+1's statistics overlap frame t's estimate and fuse.
+    // Frame t runs its statistics on pipe[0], its estimate on pipe[1], its
+    // band pre-warp on pipe[4] and its fuse on pipe[2 + t % 2]; event edges
+    // keep the order the slot rings need. So frame t+1's statistics and
+    // pre-warp overlap frame t's estimate and fuse, and the fuse of two
+    // consecutive frames (different colour and pre-warp slots) overlap too.
     const int T0 = ctx->host_T, F0 = ctx->host_F;
     cudaGraph_t graph = nullptr;
     GraphEntry ge;
@@ -1127,14 +1135,13 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture begin");
     ctx->prof_sink = &ge.pairs;
-    cudaStream_t sA = ctx->pipe[0], sB = ctx->pipe[1], sC = ctx->pipe[2];
+    cudaStream_t sA = ctx->pipe[0], sB = ctx->pipe[1], sW = ctx->pipe[4];
+    cudaStream_t sC2[2] = {ctx->pipe[2], ctx->pipe[3]};
     cudaEvent_t (&ev)[4][8] = ctx->pev;
     enum { kS = 0, kW = 1, kE = 2, kF = 3 };
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     chk(cudaEventRecord(ev[kF][7], ctx->cap_stream));            // fork
-    chk(cudaStreamWaitEvent(sA, ev[kF][7], 0));
-    chk(cudaStreamWaitEvent(sB, ev[kF][7], 0));
-    chk(cudaStreamWaitEvent(sC, ev[kF][7], 0));
+    for (int i = 0; i < kPipeStreams; ++i) chk(cudaStreamWaitEvent(ctx->pipe[i], ev[kF][7], 0));
     int rc = STITCH_OK;
     for (int t = 0; t < n_frames && rc == STITCH_OK && e == cudaSuccess; ++t) {
       const uint8_t *const *fr = frames_dev + (size_t)t * n;
@@ -1145,27 +1152,26 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
       rc = launch_stats_for(ctx, fr, T0 + t, sA);
       chk(cudaEventRecord(ev[kS][t % 8], sA));
       // band pre-warp: its slot was last read by the fuse of frame t - kPwSlots
-      if (t >= kPwSlots) chk(cudaStreamWaitEvent(sA, ev[kF][(t - kPwSlots) % 8], 0));
-      if (rc == STITCH_OK) rc = launch_prewarp_for(ctx, fp, sA);
-      chk(cudaEventRecord(ev[kW][t % 8], sA));
+      if (t >= kPwSlots) chk(cudaStreamWaitEvent(sW, ev[kF][(t - kPwSlots) % 8], 0));
+      if (rc == STITCH_OK) rc = launch_prewarp_for(ctx, fp, sW);
+      chk(cudaEventRecord(ev[kW][t % 8], sW));
       // estimate: after this frame's statistics; its colour slot was last read by fuse t-4
       chk(cudaStreamWaitEvent(sB, ev[kS][t % 8], 0));
       if (t >= 4) chk(cudaStreamWaitEvent(sB, ev[kF][(t - 4) % 8], 0));
       if (rc == STITCH_OK) rc = launch_estimate_for(ctx, sB);
       chk(cudaEventRecord(ev[kE][t % 8], sB));
       // fuse: after this frame's estimate and pre-warp
+      cudaStream_t sC = sC2[t % 2];
       chk(cudaStreamWaitEvent(sC, ev[kE][t % 8], 0));
       chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
       if (rc == STITCH_OK) rc = launch_fuse_for(ctx, fp, sC);
       chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
-    // join
-    chk(cudaEventRecord(ev[kS][0], sA));
-    chk(cudaStreamWaitEvent(ctx->cap_stream, ev[kS][0], 0));
-    chk(cudaEventRecord(ev[kE][0], sB));
-    chk(cudaStreamWaitEvent(ctx->cap_stream, ev[kE][0], 0));
-    chk(cudaEventRecord(ev[kF][0], sC));
-    chk(cudaStreamWaitEvent(ctx->cap_stream, ev[kF][0], 0));
+    // join: every pipeline stream back into the capture stream
+    for (int i = 0; i < kPipeStreams; ++i) {
+      chk(cudaEventRecord(ev[i % 4][i], ctx->pipe[i]));
+      chk(cudaStreamWaitEvent(ctx->cap_stream, ev[i % 4][i], 0));
+    }
     if (e != cudaSuccess && rc == STITCH_OK) rc = cuda_err(ctx, e, "graph capture");
     e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     ctx->prof_sink = nullptr;
@@ -2296,7 +2302,7 @@ void stitch_destroy(stitch_ctx *ctx) {
     cudaEventDestroy(pp.b);
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < kPipeStreams; ++i)
     if (ctx->pipe[i]) cudaStreamDestroy(ctx->pipe[i]);
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 8; ++b)
