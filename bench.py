@@ -96,15 +96,25 @@ class Dist:
 # --------------------------------------------------------------------------- #
 # workload
 # --------------------------------------------------------------------------- #
-def make_workload(name, n_frames, seed, device):
-    import torch
+def make_workload(name, n_frames, seed, device, library=True):
+    """Seeded frames and flows of a workload. library=False (the oracle
+    timings) takes the band sizes from the oracle's own geometry and never
+    loads the CUDA library."""
+    import numpy as np
     from synth import Scene, render_camera_frames, rig_for_config, smooth_flow
-    from paper_2308_09209_b300 import stitch as S
     rig, seq = rig_for_config(name, seed=seed)
     ex = rig.extra or {}
-    cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
-                   max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"))
-    bands, _ = S.stitch_geometry(cfg)
+    if library:
+        from paper_2308_09209_b300 import stitch as S
+        cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
+                       max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"))
+        bands, _ = S.stitch_geometry(cfg)
+    else:
+        from oracle.geometry import Geometry
+        cfg = None
+        g = Geometry(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, projection=ex.get("projection", 0),
+                     cyl=ex.get("cyl"))
+        bands = np.asarray(g.bands, dtype=np.int64)
     scene = Scene(rig.pano_w, rig.pano_h, n_objects=seq["objects"], seed=seed)
     frames, fij, fji = [], [], []
     for t in range(n_frames):
@@ -346,6 +356,86 @@ def oracle_error(gpu_panos, oracle_outs, pano_w):
             "frames": len(gpu_panos)}
 
 
+def host_info():
+    """Cores this process may run on, and the CPU model."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": n, "cpu_model": model}
+
+
+_MC = {}
+
+
+def _mc_init(rig_args):
+    # one per worker process: the oracle's geometry of the rig
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle.geometry import Geometry
+    _MC["geom"] = Geometry(*rig_args[0], projection=rig_args[1], cyl=rig_args[2])
+
+
+def _mc_rows(task):
+    # one strip of rows of one frame: the oracle's fused pixels through the balance
+    import numpy as np
+    from oracle.warp import fuse_pixels, finish
+    d, M_cam, curve, max_flow, flags, r0, r1, W = task
+    n_cams = len(_MC["geom"].w)
+    frames = [np.load(os.path.join(d, f"f{k}.npy"), mmap_mode="r") for k in range(n_cams)]
+    fij = [np.load(os.path.join(d, f"a{p}.npy"), mmap_mode="r") for p in range(n_cams - 1)]
+    fji = [np.load(os.path.join(d, f"b{p}.npy"), mmap_mode="r") for p in range(n_cams - 1)]
+    ys, xs = np.meshgrid(np.arange(r0, r1), np.arange(W), indexing="ij")
+    v, c, _ = fuse_pixels(frames, _MC["geom"], fij, fji, M_cam, max_flow, flags, xs.ravel(), ys.ravel())
+    return r0, finish(v, c, curve, flags)
+
+
+def oracle_all_cores(wl, frame_ids, flags=0):
+    """The oracle on every host core: per frame the colour estimate (serial,
+    in this process) and the fused panorama in strips of rows over a pool of
+    spawned worker processes reading the frame from memory-mapped files.
+    Returns (seconds, output pixels, workers); the files are written outside
+    the timed region."""
+    import multiprocessing as mp
+    import tempfile
+    import numpy as np
+    from oracle.pipeline import OracleStitcher
+    rig, seq = wl["rig"], wl["seq"]
+    ex = rig.extra or {}
+    o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
+                       max_flow=seq["max_flow"], projection=ex.get("projection", 0), cyl=ex.get("cyl"), flags=flags)
+    n = host_info()["nproc"]
+    H, W = rig.pano_h, rig.pano_w
+    step = max(1, H // (4 * n))
+    rig_args = ((rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h), ex.get("projection", 0), ex.get("cyl"))
+    dt = 0.0
+    with tempfile.TemporaryDirectory(dir="/dev/shm" if os.path.isdir("/dev/shm") else None) as d, \
+            mp.get_context("spawn").Pool(n, initializer=_mc_init, initargs=(rig_args,)) as pool:
+        pool.map(_mc_init, [rig_args] * n)          # every worker started and warm
+        for t in frame_ids:
+            fr = [f.cpu().numpy() for f in wl["frames"][t]]
+            for k, f in enumerate(fr):
+                np.save(os.path.join(d, f"f{k}.npy"), f)
+            for p, (a, b) in enumerate(zip(wl["fij"][t], wl["fji"][t])):
+                np.save(os.path.join(d, f"a{p}.npy"), a.cpu().numpy())
+                np.save(os.path.join(d, f"b{p}.npy"), b.cpu().numpy())
+            t0 = time.perf_counter()
+            with one_thread():
+                o.estimate_color(fr)
+            tasks = [(d, o.M_cam, o.curve, o.max_flow, flags, r, min(H, r + step), W) for r in range(0, H, step)]
+            pool.map(_mc_rows, tasks)
+            dt += time.perf_counter() - t0
+    return dt, len(frame_ids) * wl["pano_px"], n
+
+
 def run_reference(args, dist):
     """The oracle as it stands, one bounded sample of the workload per step.
 
@@ -360,7 +450,7 @@ def run_reference(args, dist):
     if dist.rank != 0:
         return
     n_gen = max(1, min(args.frames, args.steps + args.warmup, 4))
-    wl = make_workload(args.workload, n_gen, args.seed, "cpu")
+    wl = make_workload(args.workload, n_gen, args.seed, "cpu", library=False)
     rig, seq = wl["rig"], wl["seq"]
     ex = rig.extra or {}
     o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
@@ -764,10 +854,29 @@ def _run_ours(args, dist, ctxs):
     err = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         dt, px, outs, cpu_s = oracle_frames(wl, [0, 1], keep=True)
-        cpu_baseline = {"value": px / dt / 1e6, "unit": UNIT, "cores": max(1, round(cpu_s / dt)), "kind": "oracle",
-                        "sample": f"frames 0-1 of the workload: estimate + full {wl['rig'].pano_w}x"
-                                  f"{wl['rig'].pano_h} panorama each, numpy float64, one thread (process CPU time / "
-                                  f"wall time {cpu_s / dt:.2f})"}
+        single = {"value": px / dt / 1e6, "unit": UNIT, "cores": max(1, round(cpu_s / dt)),
+                  "sample": f"frames 0-1 of the workload: estimate + full {wl['rig'].pano_w}x"
+                            f"{wl['rig'].pano_h} panorama each, numpy float64, one thread (process CPU time / "
+                            f"wall time {cpu_s / dt:.2f})"}
+        hi = host_info()
+        dta, pxa, na = oracle_all_cores(wl, [0, 1])
+        # the other workloads of the CPU-baseline plan: the whole small rig, and one
+        # frame of the 8 x 4K cylinder (its inputs rendered on the GPU, then copied)
+        wl1 = make_workload("2x640x360", 8, args.seed, "cpu", library=False)
+        d1, p1, _, c1 = oracle_frames(wl1, list(range(8)))
+        d1a, p1a, _ = oracle_all_cores(wl1, list(range(8)))
+        wl5 = make_workload("8x3840x2160cyl", 1, args.seed, dev, library=False)
+        d5a, p5a, _ = oracle_all_cores(wl5, [0])
+        del wl5
+        cpu_baseline = {"value": pxa / dta / 1e6, "unit": UNIT, "cores": na, "kind": "oracle",
+                        "sample": f"frames 0-1 of the workload: the colour estimate (serial) and the full "
+                                  f"{wl['rig'].pano_w}x{wl['rig'].pano_h} panorama in strips of rows over {na} "
+                                  f"spawned worker processes, numpy float64",
+                        "host": hi, "single_thread": single,
+                        "2x640x360_all_8_frames": {"single_thread_mpix_s": p1 / d1 / 1e6,
+                                                   "all_cores_mpix_s": p1a / d1a / 1e6,
+                                                   "single_thread_fps": 8 / d1, "all_cores_fps": 8 / d1a},
+                        "8x3840x2160cyl_frame0": {"all_cores_mpix_s": p5a / d5a / 1e6, "all_cores_fps": 1 / d5a}}
         # the same two frames from a fresh context, compared with the oracle's panoramas
         st3 = S.Stitcher(cfg)
         ctxs.append(st3)

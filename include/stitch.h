@@ -330,6 +330,10 @@ int stitch_profile_read(stitch_ctx *ctx, double *stage_ms, int *stage_count);
  * other; serialise them. Each call clears the part that must start at zero.
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
+ * Later calls on a stream that is not being captured look the address up
+ * again (a cudaDeviceReset reloads the library's device image, possibly at
+ * another address); a call during a capture uses the address found last, so
+ * after a reset make one call outside any capture before capturing again.
  * Launches are asynchronous on `stream`; the call performs no cudaMalloc,
  * cudaFree or other allocation of device memory.
  */
@@ -376,8 +380,22 @@ int stitch_mlp_set_gemm(stitch_mlp *mlp, int engine);
 /* Synchronise and report the network's device error word: STITCH_ETIMEOUT
  * if a bounded tensor-core wait ran out since the last report (the affected
  * outputs are not valid), else STITCH_OK. stitch_mlp_gradients and
- * stitch_mlp_get_params report it too. */
+ * stitch_mlp_get_params report it too. When the final drain of a GEMM's
+ * MMAs ran out, the kernel keeps those MMAs' TMEM columns (freeing them could
+ * hand a later block columns that are still being written): from then on
+ * the condition is sticky -- every later call of this function returns
+ * STITCH_ETIMEOUT, the tcgen05 GEMM kernel returns without work, and
+ * stitch_mlp_forward / train_step / gradients refuse the tcgen05 engine
+ * with STITCH_ETIMEOUT until the network is destroyed; the mma.sync engine
+ * (stitch_mlp_set_gemm) stays usable. */
 int stitch_mlp_status(stitch_mlp *mlp);
+
+/* Failure detection without a device fault: writes `word` (0..3) into the
+ * network's device error word as a timed-out kernel would (bit 0: a wait ran
+ * out; bit 2 with bit 0 = 3: a drain ran out). The next stitch_mlp_status
+ * reports it. For tests of the status handling; the paper has no counterpart.
+ * Returns STITCH_OK, STITCH_EINVAL or STITCH_ECUDA. */
+int stitch_mlp_inject_error(stitch_mlp *mlp, int word);
 
 /* Diagnostic of the library's bounded device waits (failure detection
  * without a fault): one thread polls an mbarrier with the same bounded loop

@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nk = (K + BK - 1) / BK;
+  // An earlier launch gave up on draining its MMAs (error bit 2) and kept its
+  // TMEM columns: no tensor-core work on this device from then on.
+  if (*reinterpret_cast<volatile int *>(err) & 2) return;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
@@ -192,12 +195,16 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
 
   // The last commit covers every MMA issued before it (after a timeout this
   // is the drain of the MMAs still in flight).
+  bool drained = true;
   if (last >= 0) {
     const bool done = mbar_wait(su32(&bar[last % kStages]), (uint32_t)((last / kStages) & 1));
-    if (__syncthreads_or(!done)) bad = true;
+    drained = !__syncthreads_or(!done);
+    if (!drained) bad = true;
   }
   if (bad) {
-    if (tid == 0) atomicExch(err, 1);
+    // bit 0: a wait timed out (this launch's outputs are not valid); bit 2:
+    // the MMAs may still be running, so their TMEM columns stay allocated
+    if (tid == 0) atomicOr(err, drained ? 1 : 3);
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int m = m0 + 32 * warp + lane;
@@ -230,7 +237,11 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(const bf16 *__restrict__ A
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  // Free the columns only when no MMA can still write them (a few columns
+  // kept after a failed drain are lost until the process ends, which is what
+  // bit 2 tells the host).
+  if (warp == 0 && drained)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 cudaError_t launch_wait_selftest(int arrive, int limit, int *err, cudaStream_t s) {

@@ -79,6 +79,7 @@ struct stitch_mlp {
   float *loss = nullptr;
   int *err = nullptr;                                            // device error word (tensor-core waits)
   int gemm = STITCH_MLP_GEMM_TCGEN05;                            // GEMM engine of the large-batch layers
+  bool tc_dead = false;                                          // a tensor-core drain timed out: engine refused
 };
 
 namespace {
@@ -183,17 +184,26 @@ cudaError_t backward(stitch_mlp *n, const bf16 *x, int batch, cudaStream_t s) {
 
 }  // namespace
 
-// Device error word of the network's tensor-core kernels (read and cleared).
+// Device error word of the network's tensor-core kernels: bit 0, a bounded
+// wait ran out (cleared when reported); bit 2, a drain ran out and MMAs may
+// still write their accumulators. Bit 2 is sticky on the device (the GEMM
+// kernel returns at once) and here: the tcgen05 engine is refused until the
+// network is destroyed (the mma.sync engine stays available).
 static int take_err(stitch_mlp *n) {
   int h = 0;
   if (cudaMemcpy(&h, n->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return STITCH_ECUDA;
+  if (h & 2) n->tc_dead = true;
   if (h) {
-    cudaMemset(n->err, 0, 4);
-    record_last_error("a tensor-core wait timed out");
+    if (!(h & 2)) cudaMemset(n->err, 0, 4);
+    record_last_error(n->tc_dead ? "a tensor-core drain timed out: the tcgen05 engine is refused on this network"
+                                 : "a tensor-core wait timed out");
     return STITCH_ETIMEOUT;
   }
-  return STITCH_OK;
+  return n->tc_dead ? STITCH_ETIMEOUT : STITCH_OK;
 }
+
+// The engine refuses tcgen05 work after a failed drain.
+static bool engine_refused(const stitch_mlp *n) { return n->tc_dead && n->gemm == STITCH_MLP_GEMM_TCGEN05; }
 
 extern "C" {
 
@@ -204,6 +214,12 @@ int stitch_mlp_set_gemm(stitch_mlp *n, int engine) {
     return fail(STITCH_EINVAL, "mlp is NULL or unknown GEMM engine");
   n->gemm = engine;
   return STITCH_OK;
+}
+
+int stitch_mlp_inject_error(stitch_mlp *n, int word) {
+  if (!n || word < 0 || word > 3) return fail(STITCH_EINVAL, "mlp is NULL or the word is not 0..3");
+  const cudaError_t e = cudaMemcpy(n->err, &word, sizeof(int), cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? STITCH_OK : fail(STITCH_ECUDA, cudaGetErrorString(e));
 }
 
 int stitch_mlp_status(stitch_mlp *n) {
@@ -330,6 +346,7 @@ int stitch_mlp_forward(stitch_mlp *n, const uint16_t *x_dev, int batch, float *y
   if (!n || !x_dev || !y_dev) return fail(STITCH_EINVAL, "mlp, x and y are required");
   if (batch < 1 || batch > n->max_batch) return fail(STITCH_EINVAL, "batch out of range");
   if (reinterpret_cast<uintptr_t>(x_dev) & 15u) return fail(STITCH_EINVAL, "x must be 16-byte aligned");
+  if (engine_refused(n)) return fail(STITCH_ETIMEOUT, "the tcgen05 engine is refused after a drain timed out");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   bool denormed = false;
   cudaError_t e = forward(n, reinterpret_cast<const bf16 *>(x_dev), batch, false, s, y_dev, &denormed);
@@ -353,6 +370,7 @@ int stitch_mlp_train_step(stitch_mlp *n, const uint16_t *x_dev, const float *t_d
   if (!n || !x_dev || !t_dev) return fail(STITCH_EINVAL, "mlp, x and targets are required");
   if (batch < 32 || batch % 32 != 0 || batch > n->max_batch)
     return fail(STITCH_EINVAL, "batch must be a multiple of 32 up to max_batch");
+  if (engine_refused(n)) return fail(STITCH_ETIMEOUT, "the tcgen05 engine is refused after a drain timed out");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = grads(n, reinterpret_cast<const bf16 *>(x_dev), t_dev, batch, s);
   n->step += 1;
@@ -369,6 +387,7 @@ int stitch_mlp_gradients(stitch_mlp *n, const uint16_t *x_dev, const float *t_de
   if (!n || !x_dev || !t_dev || !grads_host) return fail(STITCH_EINVAL, "mlp, x, targets and output are required");
   if (batch < 32 || batch % 32 != 0 || batch > n->max_batch)
     return fail(STITCH_EINVAL, "batch must be a multiple of 32 up to max_batch");
+  if (engine_refused(n)) return fail(STITCH_ETIMEOUT, "the tcgen05 engine is refused after a drain timed out");
   cudaError_t e = grads(n, reinterpret_cast<const bf16 *>(x_dev), t_dev, batch, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(grads_host, n->g, total_params() * 4, cudaMemcpyDeviceToHost);

@@ -82,14 +82,23 @@ extern "C" int stitch_estimate_color_noalloc(const stitch_config *cfg, const uin
   if (dev < 0 || dev >= kMaxDevices) return fail(STITCH_EINVAL, "device ordinal out of range");
   unsigned char *scratch = nullptr;
   {
+    // The address is looked up on the device's first call, and again on any
+    // call whose stream is not being captured: a cudaDeviceReset reloads the
+    // library's device image, possibly at another address (the set-up is
+    // then redone too). A capturing call uses the cached address.
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs) != cudaSuccess ||
+                           cs != cudaStreamCaptureStatusNone;
+    if (!g_scratch_addr[dev] || !capturing) {
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) return fail(STITCH_ECUDA, "cudaGetSymbolAddress of the scratch failed");
-      e = estimate_setup();
-      if (e != cudaSuccess) return fail(STITCH_ECUDA, "estimate kernel set-up failed");
-      g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+      if (p != g_scratch_addr[dev]) {
+        e = estimate_setup();
+        if (e != cudaSuccess) return fail(STITCH_ECUDA, "estimate kernel set-up failed");
+        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+      }
     }
     scratch = g_scratch_addr[dev];
   }

@@ -102,6 +102,7 @@ def lib():
             "stitch_mlp_destroy": (None, [vp]),
             "stitch_mlp_set_gemm": (ip, [vp, ip]),
             "stitch_mlp_status": (ip, [vp]),
+            "stitch_mlp_inject_error": (ip, [vp, ip]),
             "stitch_mlp_set_norm": (ip, [vp, vp, vp]),
             "stitch_mlp_get_params": (ip, [vp, vp]),
             "stitch_mlp_set_params": (ip, [vp, vp]),
@@ -338,6 +339,17 @@ def stitch_estimate_color_noalloc(cfg: Config, frames, M_out, curve_out, flags_o
     device allocation inside the library (for callers that cannot allocate).
     M_out: float64 CUDA tensor of n_cams * 9; curve_out: float32 CUDA tensor of
     3 * STITCH_CURVE_FLOATS; flags_out: optional int32 CUDA tensor of 1."""
+    import torch
+
+    def _need(t, name, dtype, n):
+        if (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous()
+                or t.numel() < n):
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of at least {n} elements")
+
+    _need(M_out, "M_out", torch.float64, cfg.n_cams * 9)
+    _need(curve_out, "curve_out", torch.float32, 3 * STITCH_CURVE_FLOATS)
+    if flags_out is not None:
+        _need(flags_out, "flags_out", torch.int32, 1)
     c = cfg.c_struct()
     fl = ctypes.c_void_p(flags_out.data_ptr()) if flags_out is not None else None
     return _check(lib().stitch_estimate_color_noalloc(ctypes.byref(c), _ptrs(frames),
@@ -382,6 +394,11 @@ def stitch_mlp_set_gemm(mlp, engine: int) -> int:
 
 def stitch_mlp_status(mlp) -> int:
     return _check(lib().stitch_mlp_status(mlp))
+
+
+def stitch_mlp_inject_error(mlp, word: int) -> int:
+    """Write a timed-out kernel's error word (tests of the status handling)."""
+    return _check(lib().stitch_mlp_inject_error(mlp, word))
 
 
 def stitch_mlp_set_norm(mlp, mu, sd) -> int:

@@ -44,8 +44,14 @@ def test_noalloc_matches_context_estimate_on_two_calls(name):
         M_dev = torch.full((n * 9,), float("nan"), dtype=torch.float64, device="cuda")
         curve_dev = torch.full((3 * S.STITCH_CURVE_FLOATS,), float("nan"), dtype=torch.float32, device="cuda")
         flags_dev = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         assert S.stitch_estimate_color_noalloc(cfg, frames, M_dev, curve_dev, flags_dev) == S.STITCH_OK
         torch.cuda.synchronize()
+        if t == 5:
+            # the second call takes no device memory: free bytes unchanged around it
+            # (the first call in a fresh process may still load kernel code)
+            assert torch.cuda.mem_get_info()[0] == free0
         M_ref, curve_ref, rc = _reference(cfg, frames)
         M = M_dev.cpu().numpy().reshape(n, 3, 3)
         for k in range(n):
@@ -71,3 +77,17 @@ def test_noalloc_rejects_rigs_beyond_the_scratch():
     with pytest.raises(S.StitchError) as ei:
         S.stitch_estimate_color_noalloc(cfg, frames, M_dev, curve_dev)
     assert ei.value.code == S.STITCH_EINVAL and "at most 8 cameras" in str(ei.value)
+
+
+@pytest.mark.gpu
+def test_noalloc_checks_its_output_tensors():
+    ensure_built()
+    rig, seq = rig_for_config("2x640x360", seed=2)
+    cfg = S.Config(rig.cam_w, rig.cam_h, rig.H, rig.pano_w, rig.pano_h, window=seq["window"],
+                   max_flow=seq["max_flow"])
+    frames = [torch.zeros((h, w, 3), dtype=torch.uint8, device="cuda") for w, h in zip(rig.cam_w, rig.cam_h)]
+    curve = torch.zeros((3 * S.STITCH_CURVE_FLOATS,), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):          # float32 instead of float64
+        S.stitch_estimate_color_noalloc(cfg, frames, torch.zeros(18, dtype=torch.float32, device="cuda"), curve)
+    with pytest.raises(ValueError):          # too short
+        S.stitch_estimate_color_noalloc(cfg, frames, torch.zeros(17, dtype=torch.float64, device="cuda"), curve)
