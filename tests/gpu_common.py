@@ -108,3 +108,62 @@ def compare_stats(st_gpu, stats_or, n_pairs):
 
 def rel_err(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# --------------------------------------------------------------------------- #
+# The oracle's whole panorama on every host core (large frames): the colour
+# state comes from the caller's oracle; strips of rows are rendered by spawned
+# worker processes reading the frame from memory-mapped files.
+# --------------------------------------------------------------------------- #
+_PW = {}
+
+
+def _pw_init(rig_args):
+    import os
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    from oracle.geometry import Geometry
+    _PW["geom"] = Geometry(*rig_args[0], projection=rig_args[1], cyl=rig_args[2])
+
+
+def _pw_rows(task):
+    import os
+    from oracle.warp import fuse_pixels, finish
+    d, n_cams, M_cam, curve, max_flow, flags, r0, r1, W = task
+    frames = [np.load(os.path.join(d, f"f{k}.npy"), mmap_mode="r") for k in range(n_cams)]
+    fij = [np.load(os.path.join(d, f"a{p}.npy"), mmap_mode="r") for p in range(n_cams - 1)]
+    fji = [np.load(os.path.join(d, f"b{p}.npy"), mmap_mode="r") for p in range(n_cams - 1)]
+    ys, xs = np.meshgrid(np.arange(r0, r1), np.arange(W), indexing="ij")
+    v, c, e = fuse_pixels(frames, _PW["geom"], fij, fji, M_cam, max_flow, flags, xs.ravel(), ys.ravel())
+    return r0, finish(v, c, curve, flags), e
+
+
+def oracle_frame_parallel(pr, fr_np, fij_np, fji_np):
+    """(planes (3, H, W) uint8, near-edge mask (H, W)) of the oracle's whole
+    panorama for the frame whose colour pr.oracle estimated last."""
+    import multiprocessing as mp
+    import os
+    import tempfile
+    rig, o = pr.rig, pr.oracle
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    H, W = rig.pano_h, rig.pano_w
+    step = max(1, H // (4 * n))
+    rig_args = ((rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h), pr.proj["projection"], pr.proj["cyl"])
+    planes = np.zeros((3, H, W), dtype=np.uint8)
+    near = np.zeros((H, W), dtype=bool)
+    with tempfile.TemporaryDirectory(dir="/dev/shm" if os.path.isdir("/dev/shm") else None) as d:
+        for k, f in enumerate(fr_np):
+            np.save(os.path.join(d, f"f{k}.npy"), f)
+        for p, (a, b) in enumerate(zip(fij_np, fji_np)):
+            np.save(os.path.join(d, f"a{p}.npy"), a)
+            np.save(os.path.join(d, f"b{p}.npy"), b)
+        tasks = [(d, rig.n_cams, o.M_cam, o.curve, o.max_flow, o.flags, r, min(H, r + step), W)
+                 for r in range(0, H, step)]
+        with mp.get_context("spawn").Pool(n, initializer=_pw_init, initargs=(rig_args,)) as pool:
+            for r0, out, e in pool.imap_unordered(_pw_rows, tasks):
+                r1 = r0 + out.shape[0] // W
+                planes[:, r0:r1] = out.T.reshape(3, r1 - r0, W)
+                near[r0:r1] = e.reshape(r1 - r0, W)
+    return planes, near

@@ -77,3 +77,64 @@ def test_flow_argument_errors():
     with pytest.raises(S.StitchError):
         S.stitch_estimate_flow(pr.st.ctx, frames[:1] + [0], fij, fji)
     pr.st.close()
+
+
+def test_flow_identical_where_both_prewarps_are_exact():
+    """Two cameras cropped from one rendered scene at integer offsets, the
+    right one's content moved by (3, -2) against its homography: both
+    pre-warps are exact copies of frame pixels, so both luminance pyramids,
+    every integer cost and every float32 sub-pixel step agree, and the flows
+    must be bit-identical everywhere."""
+    from oracle.pipeline import OracleStitcher
+    from synth import Scene
+    ensure_built()
+    h, w, off, (dx, dy), m = 300, 640, 440, (3, -2), 8
+    scene = Scene(off + w + 2 * m, h + 2 * m, n_objects=4, seed=11)
+    ys, xs = torch.meshgrid(torch.arange(h + 2 * m, dtype=torch.float32), torch.arange(off + w + 2 * m,
+                            dtype=torch.float32), indexing="ij")
+    img = torch.round(scene.render(xs, ys, 0).clamp(0, 255)).to(torch.uint8)
+    fa = img[m:m + h, m:m + w].contiguous()
+    fb = img[m + dy:m + dy + h, m + off + dx:m + off + dx + w].contiguous()
+    T = lambda tx: np.array([[1.0, 0, tx], [0, 1.0, 0], [0, 0, 1.0]])
+    cfg = S.Config([w, w], [h, h], np.stack([T(0), T(off)]), off + w, h, max_flow=8.0)
+    st = S.Stitcher(cfg)
+    frames = [fa.cuda(), fb.cuda()]
+    x0, x1, y0, y1 = st.bands[0].tolist()
+    gij = torch.full((y1 - y0, x1 - x0, 2), float("nan"), dtype=torch.float32, device="cuda")
+    gji = torch.full_like(gij, float("nan"))
+    S.stitch_estimate_flow(st.ctx, frames, [gij], [gji])
+    torch.cuda.synchronize()
+    o = OracleStitcher(cfg.H, cfg.cam_w, cfg.cam_h, cfg.pano_w, cfg.pano_h, max_flow=8.0)
+    oij, oji = pair_flows([fa.numpy(), fb.numpy()], o.geom, 8.0)
+    g1, g2 = gij.cpu().numpy(), gji.cpu().numpy()
+    assert np.array_equal(g1, oij[0]) and np.array_equal(g2, oji[0])
+    # away from the band's border the match is the known shift within the
+    # sub-pixel step (the parabola through asymmetric costs moves it off the
+    # integer by up to half a pixel), in one direction or the other
+    core = (slice(m, -m), slice(m, -m))
+    s = np.array([dx, dy], np.float32)
+    near = lambda f, v: np.all(np.abs(f[core] - v) <= 0.5, axis=-1)
+    assert max(np.mean(near(g1, s)), np.mean(near(g1, -s))) > 0.9
+    assert max(np.mean(near(g2, s)), np.mean(near(g2, -s))) > 0.9
+    st.close()
+
+
+def test_flow_matches_the_oracle_at_full_size():
+    """The benchmark's rig (bands about 400 x 1066): band 0, both directions,
+    with the same bar as the small rigs."""
+    from oracle.flow import band_prewarp, flow
+    pr = Pair("4x1920x1080", seed=0)
+    frames, _, _ = pr.inputs(2)
+    gij, gji = _gpu_flows(pr, frames)
+    fr = [f.cpu().numpy() for f in frames]
+    band = pr.oracle.geom.bands[0]
+    Pi = band_prewarp(fr[0], pr.oracle.geom, 0, band)
+    Pj = band_prewarp(fr[1], pr.oracle.geom, 1, band)
+    oij, oji = flow(Pi, Pj, pr.seq["max_flow"]), flow(Pj, Pi, pr.seq["max_flow"])
+    reach = 4 * max(1, int(np.ceil(pr.seq["max_flow"] / 4))) + 2 + 1 + 0.5
+    for g, o in ((gij[0], oij), (gji[0], oji)):
+        assert g.shape == o.shape and np.all(np.isfinite(g))
+        same = np.all(g == o, axis=2)
+        assert same.mean() >= FRAC_IDENTICAL, same.mean()
+        assert np.all(np.abs(g) <= reach)
+    pr.st.close()
