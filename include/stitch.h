@@ -59,6 +59,7 @@ typedef enum {
 #define STITCH_FP16_INTERMEDIATE 2    /* warped band tiles held in FP16; coordinates stay FP32 */
 #define STITCH_FLOW_WEIGHTS_PRINTED 4 /* Eq. 17 exactly as printed (theta_i on flow_ij) */
 #define STITCH_LEARNED 8              /* learned estimator for M (falls back to the plain fit) */
+#define STITCH_BALANCE_OUTPUT 16      /* balance knots from the stitched image of the previous frame */
 
 #define STITCH_MAX_CAMS 8
 #define STITCH_MAX_PAIRS (STITCH_MAX_CAMS - 1)
@@ -557,6 +558,29 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
 int stitch_batch_tile_shapes(const stitch_batch *b, int *shapes_out);
 void stitch_batch_destroy(stitch_batch *b);
 const char *stitch_batch_last_error(const stitch_batch *b);
+
+/*
+ * Balance on the stitched image (STITCH_BALANCE_OUTPUT; section 2.2 balances
+ * "the whole stitched image", Eq. 5-7): with this flag the knots m1, m2 of
+ * frame T come from the histogram of the panorama stitched for frame T - 1,
+ * before its balance, instead of the pooled histogram of frame T's camera
+ * frames (a one-frame lag; frame 0 is not balanced). A pixel counts when a
+ * camera covers it; its channel's bin is its fused, clamped value v on the
+ * output table's grid of sixteenths, q = round_half_even(16 v), binned at
+ * floor((q + 8) / 16). Eq. 6-7 average the knots of the frames that have a
+ * stitched predecessor (at most the last three). stitch_estimate_color and
+ * stitch_frame calls must alternate (estimate of T, frame of T, estimate of
+ * T + 1, ...); recorded sequences add the edge from each frame's fuse to the
+ * next frame's estimate. Not available in a batch (stitch_batch_create
+ * rejects such contexts).
+ *
+ * stitch_get_output_hist -- that histogram of the latest stitched frame
+ * (before the next stitch_estimate_color consumes it): hist_out (host,
+ * required) receives 3 x 256 uint32 counts, channel-major. Synchronises.
+ * Returns STITCH_OK, STITCH_EINVAL (no such flag, NULL argument) or
+ * STITCH_ECUDA.
+ */
+int stitch_get_output_hist(stitch_ctx *ctx, uint32_t *hist_out);
 
 /* Number of adjacent pairs (n_cams - 1), or -1 for a NULL context. */
 int stitch_n_pairs(const stitch_ctx *ctx);

@@ -46,3 +46,4 @@ BALANCE_OFF = 1
 FP16_INTERMEDIATE = 2
 FLOW_WEIGHTS_PRINTED = 4
 LEARNED = 8
+BALANCE_OUTPUT = 16

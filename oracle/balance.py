@@ -23,7 +23,20 @@ Readings (the paper gives no formula for the curve's targets or exponents):
   slope at both knots.
 * If m2 - m1 < 1 the curve is the identity. With m1 = 0 the dark tail is
   empty, with m2 = 255 the bright tail is empty.
+
+Balance on the stitched image (flag BALANCE_OUTPUT, the other reading of
+"the whole stitched image"): the knots of frame T come from the histogram of
+the stitched panorama of frame T - 1 before its balance (a one-frame lag),
+over its covered pixels. Readings:
+* The histogram is of the fused, clamped value v before Eq. 5 (the balanced
+  output's quantiles sit at the targets, so feeding it back would make every
+  other frame's curve the identity).
+* A pixel's bin is its value on the output table's grid of sixteenths,
+  rounded: q = round_half_even(16 v), bin = floor((q + 8) / 16).
+* Frame 0 has no stitched predecessor: its curve is the identity; Eq. 6-7
+  average the knots of the frames that have one (at most the last three).
 """
+
 from __future__ import annotations
 
 import numpy as np
@@ -92,4 +105,20 @@ def apply(x, params, c: int):
         if m2 < 255:
             bright = x > m2
             out = np.where(bright, 255.0 - (255.0 - d2) * np.power(np.maximum(255.0 - x, 0.0) / (255.0 - m2), g2), out)
+    return out
+
+
+def output_histogram(vals, covered):
+    """(3, 256) int64 histogram of a stitched panorama before its balance:
+    per covered pixel and channel, the fused value v clamped to [0, 255], put
+    on the grid of sixteenths q = round_half_even(16 v) and binned at
+    floor((q + 8) / 16)."""
+    v = np.clip(np.asarray(vals, dtype=np.float64).reshape(-1, 3), 0.0, 255.0)
+    cov = np.asarray(covered, dtype=bool).reshape(-1)
+    q = np.rint(16.0 * v[cov]).astype(np.int64)
+    b = (q + 8) // 16
+    out = np.zeros((3, 256), dtype=np.int64)
+    for c in range(3):
+        for x in b[:, c]:
+            out[c, x] += 1
     return out

@@ -17,6 +17,11 @@ If the window's A is ill-conditioned (1-norm condition > 1e12) or a side of
 the overlap is empty, the pair keeps its previous M (identity before the
 first success) and the frame is flagged singular.
 
+Balance on the stitched image (flag BALANCE_OUTPUT): frame(T) keeps the
+histogram of its panorama before the balance (``balance.output_histogram``)
+and estimate_color(T + 1) takes the knots from it instead of the pooled raw
+histogram; the first frame, with no stitched predecessor, is not balanced.
+
 Learned mode (flag LEARNED with a network given): after the plain estimate,
 each pair's features are its window-pooled overlap histograms (side i then
 side j, each scaled by 256 / count, bfloat16), the network predicts M_hat - I
@@ -57,6 +62,7 @@ class OracleStitcher:
         self.learned = None                    # latest (M_hat, r, used) per pair
         self.n_learned = 0
         self.n_fallback = 0
+        self.out_hist = None                   # balance on the stitched image: last frame's histogram
 
     # -- statistics of one frame (section 2.1 steps 2-3, Eq. 3 terms) --------
     def frame_stats(self, frames):
@@ -99,10 +105,21 @@ class OracleStitcher:
         if (self.flags & 8) and self.mlp is not None and g.n > 1:
             self._learned_select(ok_p, AB)
         self.M_cam = col.chain_to_reference(self.M_pair, g.pairs, g.ref, g.n)
-        m1, m2 = bal.knots(st["pooled"], self.lam)
-        self.knot_hist.append((m1, m2))
-        sm1, sm2 = bal.smooth(self.knot_hist)
-        self.curve = bal.curve_params(sm1, sm2, self.lam)
+        if self.flags & 16:
+            # balance on the stitched image of the previous frame (one-frame lag)
+            if self.out_hist is not None and int(self.out_hist[0].sum()) > 0:
+                m1, m2 = bal.knots(self.out_hist, self.lam)
+                self.knot_hist.append((m1, m2))
+                sm1, sm2 = bal.smooth(self.knot_hist)
+                self.curve = bal.curve_params(sm1, sm2, self.lam)
+            else:
+                self.curve = bal.curve_params(np.zeros(3), np.zeros(3), self.lam)
+            self.out_hist = None
+        else:
+            m1, m2 = bal.knots(st["pooled"], self.lam)
+            self.knot_hist.append((m1, m2))
+            sm1, sm2 = bal.smooth(self.knot_hist)
+            self.curve = bal.curve_params(sm1, sm2, self.lam)
         self.T += 1
         return not self.singular
 
@@ -140,8 +157,14 @@ class OracleStitcher:
 
     def frame(self, frames, flows_ij, flows_ji):
         frames = [np.asarray(f) for f in frames]
-        return _stitch(frames, self.geom, flows_ij, flows_ji, self.M_cam, self.curve,
-                       self.max_flow, self.flags)
+        if not (self.flags & 16):
+            return _stitch(frames, self.geom, flows_ij, flows_ji, self.M_cam, self.curve,
+                           self.max_flow, self.flags)
+        cov = np.zeros((self.geom.pano_h, self.geom.pano_w), dtype=bool)
+        planes, near, vals = _stitch(frames, self.geom, flows_ij, flows_ji, self.M_cam, self.curve,
+                                     self.max_flow, self.flags, cov_out=cov)
+        self.out_hist = bal.output_histogram(vals, cov)
+        return planes, near, vals
 
     def pixels(self, frames, flows_ij, flows_ji, xs, ys):
         """Output of selected pixels only: (uint8 (N, 3), near_edge (N,))."""

@@ -186,8 +186,9 @@ def finish(val, covered, curve, flags):
     return out.astype(np.uint8)
 
 
-def stitch(frames, geom, flows_ij, flows_ji, M_cam, curve, max_flow, flags, rows_per_chunk=64):
-    """Whole panorama: (planes (3, H, W) uint8, near_edge (H, W) bool, val (H, W, 3))."""
+def stitch(frames, geom, flows_ij, flows_ji, M_cam, curve, max_flow, flags, rows_per_chunk=64, cov_out=None):
+    """Whole panorama: (planes (3, H, W) uint8, near_edge (H, W) bool, val (H, W, 3)).
+    cov_out (optional (H, W) bool array) receives the covered pixels."""
     W, H = geom.pano_w, geom.pano_h
     planes = np.zeros((3, H, W), dtype=np.uint8)
     near = np.zeros((H, W), dtype=bool)
@@ -202,4 +203,6 @@ def stitch(frames, geom, flows_ij, flows_ji, M_cam, curve, max_flow, flags, rows
         planes[:, r0:r1, :] = o.T.reshape(3, r1 - r0, W)
         near[r0:r1] = e.reshape(r1 - r0, W)
         vals[r0:r1] = v.reshape(r1 - r0, W, 3)
+        if cov_out is not None:
+            cov_out[r0:r1] = c.reshape(r1 - r0, W)
     return planes, near, vals

@@ -177,7 +177,8 @@ int build_geometry(const stitch_config *cfg, Geo &g, std::string &err) {
   if (!(cfg->lambda > 0.0 && cfg->lambda < 0.5)) FAIL("lambda must be in (0, 0.5)");
   if (!(cfg->max_flow >= 0.0f && cfg->max_flow <= STITCH_MAX_FLOW)) FAIL("max_flow must be in [0, 16]");
   if (cfg->ref_cam < -1 || cfg->ref_cam >= cfg->n_cams) FAIL("ref_cam out of range");
-  if (cfg->flags & ~(STITCH_BALANCE_OFF | STITCH_FP16_INTERMEDIATE | STITCH_FLOW_WEIGHTS_PRINTED | STITCH_LEARNED))
+  if (cfg->flags & ~(STITCH_BALANCE_OFF | STITCH_FP16_INTERMEDIATE | STITCH_FLOW_WEIGHTS_PRINTED | STITCH_LEARNED |
+                     STITCH_BALANCE_OUTPUT))
     FAIL("unknown flag");
   g.n = cfg->n_cams;
   g.pano_w = cfg->pano_w;
@@ -462,6 +463,7 @@ struct stitch_ctx {
   PwTile *pw_tiles = nullptr;
   void *pw = nullptr;                 // band pre-warp intermediate
   uint8_t *lut = nullptr;             // output tables of the colour slots (kColorSlots x kLutBytes)
+  uint32_t *out_hist = nullptr;       // STITCH_BALANCE_OUTPUT: pre-balance histograms, frame F in slot F % 2
   unsigned int *win_fallback = nullptr;   // fuse tiles whose source window did not fit (counter)
   int stats_grid_x = 1;
   StatsParams sp{};
@@ -597,6 +599,7 @@ FuseParams frame_params(stitch_ctx *ctx, const uint8_t *const *frames, const flo
   fp.color = &ctx->state->out[slot];
   fp.lut = ctx->lut + (size_t)slot * kLutBytes;
   fp.win_fallback = ctx->win_fallback;
+  fp.out_hist = ctx->out_hist ? ctx->out_hist + (size_t)(F % 2) * 768 : nullptr;
   fp.flags |= kFlagPwOffset;
   fp.pw = static_cast<char *>(ctx->pw) + (size_t)(F % kPwSlots) * ctx->pw_slot_bytes;
   return fp;
@@ -878,6 +881,10 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->raw, kRawSlots * sizeof(RawStats));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->lut, (size_t)kColorSlots * kLutBytes);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->win_fallback, sizeof(unsigned int));
+  if (e == cudaSuccess && (cfg->flags & STITCH_BALANCE_OUTPUT)) {
+    e = cudaMalloc(&ctx->out_hist, 2 * 768 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->out_hist, 0, 2 * 768 * sizeof(uint32_t));
+  }
   if (e == cudaSuccess) e = cudaMemset(ctx->win_fallback, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->state, sizeof(ColorState));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->tiles, max_tiles(g) * sizeof(TileDesc) + 16);
@@ -989,6 +996,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   ep.state = ctx->state;
   ep.flags = ctx->flags;
   ep.lut = ctx->lut;
+  ep.out_hist = ctx->out_hist;
 
   FuseParams &fp = ctx->fp;
   fp = FuseParams{};
@@ -1158,6 +1166,8 @@ int stitch_sequence(stitch_ctx *ctx, int n_frames, const uint8_t *const *frames_
       // estimate: after this frame's statistics; its colour slot was last read by fuse t-4
       chk(cudaStreamWaitEvent(sB, ev[kS][t % 8], 0));
       if (t >= 4) chk(cudaStreamWaitEvent(sB, ev[kF][(t - 4) % 8], 0));
+      // balance on the stitched image: the previous frame's panorama histogram
+      if (ctx->out_hist && t >= 1) chk(cudaStreamWaitEvent(sB, ev[kF][(t - 1) % 8], 0));
       if (rc == STITCH_OK) rc = launch_estimate_for(ctx, sB);
       chk(cudaEventRecord(ev[kE][t % 8], sB));
       // fuse: after this frame's estimate and pre-warp
@@ -1667,6 +1677,8 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
     else
       e = cudaMemset(ctx->ls, 0, sizeof(LearnedState));
   }
+  // no stitched image precedes the restored state
+  if (e == cudaSuccess && ctx->out_hist) e = cudaMemset(ctx->out_hist, 0, 2 * 768 * sizeof(uint32_t));
   // the output tables follow the restored curves
   for (int sl = 0; sl < kColorSlots && e == cudaSuccess; ++sl)
     e = launch_curve_lut(&ctx->state->out[sl], ctx->flags, ctx->lut + (size_t)sl * kLutBytes, nullptr);
@@ -1755,6 +1767,18 @@ int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used)
 }
 
 int stitch_n_pairs(const stitch_ctx *ctx) { return ctx ? ctx->g.n - 1 : -1; }
+
+int stitch_get_output_hist(stitch_ctx *ctx, uint32_t *hist_out) {
+  if (!ctx || !hist_out) return set_err(ctx, STITCH_EINVAL, "ctx and hist_out are required");
+  if (!ctx->out_hist) return set_err(ctx, STITCH_EINVAL, "the context was not created with STITCH_BALANCE_OUTPUT");
+  const int F = ctx->host_F - 1;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hist_out, ctx->out_hist + (size_t)(((F % 2) + 2) % 2) * 768, 768 * sizeof(uint32_t),
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "output histogram read");
+  return STITCH_OK;
+}
 
 int stitch_window_fallbacks(stitch_ctx *ctx, unsigned long long *count, int reset) {
   if (!ctx || !count) return set_err(ctx, STITCH_EINVAL, "ctx and count are required");
@@ -2011,6 +2035,9 @@ bool batch_ptrs_ok(stitch_batch *b, int n_frames, const uint8_t *const *frames_d
 extern "C" {
 
 int stitch_batch_create(stitch_ctx *const *ctxs, int n_ctx, stitch_batch **out) {
+  for (int i = 0; ctxs && i < n_ctx; ++i)
+    if (ctxs[i] && (ctxs[i]->flags & STITCH_BALANCE_OUTPUT))
+      return batch_err(nullptr, STITCH_EINVAL, "a batch cannot hold a context with STITCH_BALANCE_OUTPUT");
   if (!out) return batch_err(nullptr, STITCH_EINVAL, "out is NULL");
   *out = nullptr;
   if (!ctxs || n_ctx < 1 || n_ctx > STITCH_BATCH_MAX_RIGS)
@@ -2315,6 +2342,7 @@ void stitch_destroy(stitch_ctx *ctx) {
   cudaFree(ctx->pw);
   cudaFree(ctx->lut);
   cudaFree(ctx->win_fallback);
+  cudaFree(ctx->out_hist);
   for (HostStage &hs : ctx->stage) {
     for (int k = 0; k < kMaxCams; ++k) cudaFree(hs.frames[k]);
     for (int p = 0; p < kMaxPairs; ++p) {

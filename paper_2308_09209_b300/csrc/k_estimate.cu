@@ -85,6 +85,10 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
 
   if (tid == 0) sm.sing = 0;
   if (tid < np * 9) sm.M_pair[tid / 9][tid % 9] = S->M_pair[tid / 9][tid % 9];
+  // Balance on the stitched image: the knots come from the pre-balance
+  // histogram of frame T - 1's panorama (none for frame 0).
+  const bool out_mode = (P.flags & STITCH_BALANCE_OUTPUT) && P.out_hist;
+  const uint32_t *ohist = (out_mode && T > 0) ? P.out_hist + ((T - 1) & 1) * 768 : nullptr;
 
   // 1. All prefix sums at once, one warp per histogram.
   for (int q = warp; q < n_scan; q += kWarps) {
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
       const int p = q / 6, side = (q % 6) / 3, c = q % 3;
       src = side == 0 ? raw->Hi[p][c] : raw->Hj[p][c];
     } else {
-      src = raw->pooled[q - np * 6];
+      src = ohist ? ohist + (q - np * 6) * 256 : raw->pooled[q - np * 6];
     }
     warp_scan256(src, sm.cdf[q]);
   }
@@ -201,11 +205,16 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
   } else if (warp == 1 && lane < 3) {
     const int c = lane;
     const int slot = T % kSmoothFrames;
-    S->knots[slot][c][0] = sm.knot[c][0];
-    S->knots[slot][c][1] = sm.knot[c][1];
-    const int cnt = min(T + 1, kSmoothFrames);
+    // with the stitched image's histogram, frame 0 (no predecessor) and an
+    // empty histogram leave the frame unbalanced
+    const bool no_hist = out_mode && (!ohist || sm.cdf[np * 6][255] == 0u);
+    if (!no_hist) {
+      S->knots[slot][c][0] = sm.knot[c][0];
+      S->knots[slot][c][1] = sm.knot[c][1];
+    }
+    const int cnt = no_hist ? 1 : min(out_mode ? T : T + 1, kSmoothFrames);
     long long s1 = 0, s2 = 0;
-    for (int i = cnt - 1; i >= 0; --i) {
+    for (int i = no_hist ? -1 : cnt - 1; i >= 0; --i) {   // unbalanced: both knot means 0, as the oracle's
       const int sl = (T - i) % kSmoothFrames;
       s1 += (sl == slot) ? sm.knot[c][0] : S->knots[sl][c][0];
       s2 += (sl == slot) ? sm.knot[c][1] : S->knots[sl][c][1];
@@ -220,7 +229,7 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
     const float d1 = (float)(255.0 * ((double)P.lambda_q / 1e6));
     const float d2 = (float)(255.0 * (1.0 - (double)P.lambda_q / 1e6));
     (void)lam;
-    const bool ident = (m2 - m1) < 1.0f;
+    const bool ident = no_hist || (m2 - m1) < 1.0f;
     const float span = ident ? 1.0f : (m2 - m1);
     const float sl = (d2 - d1) / span;
     Curve cv;
@@ -243,6 +252,11 @@ __global__ void __launch_bounds__(kT) k_estimate(const EstimateParams P) {
     uint4 *z = reinterpret_cast<uint4 *>(P.raw + ((T + P.raw_slots - 1) % P.raw_slots));
     const int n16 = (int)(sizeof(RawStats) / 16);
     for (int i = tid - 64; i < n16; i += kT - 64) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    // the stitched image's histogram just consumed: frame T + 1's fuse
+    // accumulates into this slot
+    if (ohist)
+      for (int i = tid - 64; i < 768 / 4; i += kT - 64) reinterpret_cast<uint4 *>(const_cast<uint32_t *>(ohist))[i] =
+          make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
   // 8. The output table of this frame's curve (read by the fuse kernels).

@@ -317,6 +317,7 @@ struct __align__(16) SmemHead {
   int item;
   int rig;
   __align__(16) uint8_t lut[kLutBytes];
+  uint32_t ohist[3 * 256];   // STITCH_BALANCE_OUTPUT: the block's share of the pre-balance histogram
 };
 
 template <int TW, int TH, int NW>
@@ -361,15 +362,28 @@ __device__ __forceinline__ uint32_t lut_index(float u) {
   return __float_as_uint(fmaf(u, kLutTop, kMagicRound)) - kMagicRoundBits;
 }
 
+// Pre-balance histogram bin of a table index q (the grid of sixteenths):
+// floor((q + 8) / 16).
+__device__ __forceinline__ uint32_t hist_bin(uint32_t q) { return (q + 8u) >> 4; }
+
 // One pixel's bytes from its fused value v (already scaled by 1/255): the
 // saturation is the clamp to [0, 255], the table applies Eq. 5 and rounds.
+// hist (or null): the block's pre-balance histogram of covered pixels.
 template <int TW, int TH>
-__device__ __forceinline__ void put_px(uint8_t (*out)[TH][TW], const uint8_t *lut, int lx, int ly, bool cov, float3 v) {
+__device__ __forceinline__ void put_px(uint8_t (*out)[TH][TW], const uint8_t *lut, int lx, int ly, bool cov, float3 v,
+                                       uint32_t *hist = nullptr) {
   uint32_t o0 = 0u, o1 = 0u, o2 = 0u;
   if (cov) {
-    o0 = lut[lut_index(__saturatef(v.x))];
-    o1 = lut[kLutEntries + lut_index(__saturatef(v.y))];
-    o2 = lut[2 * kLutEntries + lut_index(__saturatef(v.z))];
+    const uint32_t q0 = lut_index(__saturatef(v.x)), q1 = lut_index(__saturatef(v.y));
+    const uint32_t q2 = lut_index(__saturatef(v.z));
+    o0 = lut[q0];
+    o1 = lut[kLutEntries + q1];
+    o2 = lut[2 * kLutEntries + q2];
+    if (hist) {
+      atomicAdd(&hist[hist_bin(q0)], 1u);
+      atomicAdd(&hist[256 + hist_bin(q1)], 1u);
+      atomicAdd(&hist[512 + hist_bin(q2)], 1u);
+    }
   }
   out[0][ly][lx] = (uint8_t)o0;
   out[1][ly][lx] = (uint8_t)o1;
@@ -535,7 +549,7 @@ __device__ __forceinline__ void taps(const uint32_t *w, uint32_t i, uint32_t (&t
 template <int TW, int TH>
 __device__ __forceinline__ void finish_pair(const float2 (&v)[3], const float4 (*pr)[2], const uint8_t *lut,
                                             uint8_t (*out)[TH][TW], int lx0, int ly0, int lx1, int ly1, bool in0,
-                                            bool in1) {
+                                            bool in1, uint32_t *hist) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float4 a = pr[k][0], b = pr[k][1];
@@ -544,8 +558,13 @@ __device__ __forceinline__ void finish_pair(const float2 (&v)[3], const float4 (
     const float u0 = __saturatef(fmaf(v[0].x, b.z, acc.x));
     const float u1 = __saturatef(fmaf(v[0].y, b.w, acc.y));
     const float2 q = __ffma2_rn(f2(u0, u1), f2(kLutTop), f2(kMagicRound));
-    if (in0) out[k][ly0][lx0] = lut[k * kLutEntries + (__float_as_uint(q.x) - kMagicRoundBits)];
-    if (in1) out[k][ly1][lx1] = lut[k * kLutEntries + (__float_as_uint(q.y) - kMagicRoundBits)];
+    const uint32_t q0 = __float_as_uint(q.x) - kMagicRoundBits, q1 = __float_as_uint(q.y) - kMagicRoundBits;
+    if (in0) out[k][ly0][lx0] = lut[k * kLutEntries + q0];
+    if (in1) out[k][ly1][lx1] = lut[k * kLutEntries + q1];
+    if (hist) {
+      if (in0) atomicAdd(&hist[256 * k + hist_bin(q0)], 1u);
+      if (in1) atomicAdd(&hist[256 * k + hist_bin(q1)], 1u);
+    }
   }
 }
 
@@ -555,7 +574,7 @@ __device__ __forceinline__ void finish_pair(const float2 (&v)[3], const float4 (
 template <int TW, int TH>
 __device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, const uint32_t *win, const BlockColor &bc,
                                           int k, const uint8_t *lut, uint8_t (*out)[TH][TW], int tx0, int ty0,
-                                          int cx0, int cx1) {
+                                          int cx0, int cx1, uint32_t *hist) {
   using PM = PairMap<TW, TH>;
   constexpr int S = WinGeom<TW, TH>::kStride;
   constexpr int kMax = WinGeom<TW, TH>::kAlloc - S - 2;
@@ -584,7 +603,7 @@ __device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, cons
       bilerp_pair(t0, t1, fx, fy, v);
       const int lx0 = PM::lx0(lane, cp), lx1 = PM::lx1(lane, cp);
       finish_pair<TW, TH>(v, bc.pr[k], lut, out, lx0, PM::ly0(warp, s), lx1, PM::ly1(warp, s),
-                          lx0 >= cx0 && lx0 < cx1, lx1 >= cx0 && lx1 < cx1);
+                          lx0 >= cx0 && lx0 < cx1, lx1 >= cx0 && lx1 < cx1, hist);
     }
     y = __fadd2_rn(y, f2(PM::kDy));
   }
@@ -832,7 +851,7 @@ __device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDes
   if (W0.ok) {
     stage_window<G::kStride>(P.src[k], c, W0, st.win[0]);
     __syncthreads();
-    own_pairs<TW, TH>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1);
+    own_pairs<TW, TH>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1, P.out_hist ? h.ohist : nullptr);
   } else {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < (TW / 32) * (TH / 8); ++j) {
@@ -840,7 +859,7 @@ __device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDes
       if (lx < cx0 || lx >= cx1) continue;
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       const bool cov = cam_value<G::kStride>(P, h.bc, k, W0, st.win[0], tx0 + lx, ty0 + ly, v);
-      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v);
+      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v, P.out_hist ? h.ohist : nullptr);
     }
   }
   __syncthreads();
@@ -864,7 +883,7 @@ __device__ __forceinline__ float3 band_tap(const typename PwT<kHalf>::T *pw, int
 // (max_flow + 1 pixels around it) stays inside the band.
 template <bool kHalf, bool kClamp, int TW, int TH>
 __device__ __forceinline__ void band_rows(const FuseParams &P, const BlockColor &bc, int p, int tx0, int ty0, int cx0,
-                                          int cx1, const uint8_t *lut, uint8_t (*out)[TH][TW]) {
+                                          int cx1, const uint8_t *lut, uint8_t (*out)[TH][TW], uint32_t *hist) {
   using PT = typename PwT<kHalf>::T;
   constexpr int kGroups = TW / 32, kRPW = TH / 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -908,7 +927,7 @@ __device__ __forceinline__ void band_rows(const FuseParams &P, const BlockColor 
         o[k] = fmaf(tb, fmaf(Pb.x, Bq.x, fmaf(Pb.y, Bq.y, fmaf(Pb.z, Bq.z, Bq.w))),
                     ta * fmaf(Pa.x, A.x, fmaf(Pa.y, A.y, fmaf(Pa.z, A.z, A.w))));
       }
-      put_px<TW, TH>(out, lut, lx, ly0 + r, true, make_float3(o[0], o[1], o[2]));
+      put_px<TW, TH>(out, lut, lx, ly0 + r, true, make_float3(o[0], o[1], o[2]), hist);
       base.y += 1.0f;
       if (r + 1 < kRPW) {
         fa = na;
@@ -928,10 +947,11 @@ __device__ __forceinline__ void fuse_band_piece(const FuseParams &P, const TileD
   const int reach = (int)ceilf(P.max_flow) + 1;
   const bool interior = tx0 + cx0 - reach >= B.x0 && tx0 + cx1 - 1 + reach + 1 < B.x1 && ty0 - reach >= B.y0 &&
                         ty0 + TH - 1 + reach + 1 < B.y1;
+  uint32_t *hist = P.out_hist ? h.ohist : nullptr;
   if (interior)
-    band_rows<kHalf, false, TW, TH>(P, h.bc, p, tx0, ty0, cx0, cx1, h.lut, out);
+    band_rows<kHalf, false, TW, TH>(P, h.bc, p, tx0, ty0, cx0, cx1, h.lut, out, hist);
   else
-    band_rows<kHalf, true, TW, TH>(P, h.bc, p, tx0, ty0, cx0, cx1, h.lut, out);
+    band_rows<kHalf, true, TW, TH>(P, h.bc, p, tx0, ty0, cx0, cx1, h.lut, out, hist);
   __syncthreads();
   store_tile<TW, TH>(P, tx0, ty0, out, t.c0, t.c1);
 }
@@ -990,7 +1010,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       bool cov = false;
       if (x < P.pano_w && y < P.pano_h) cov = own_value<S>(P, bc, k, k - 1, k + 1, W0, st.win[0], x, y, v);
-      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v);
+      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v, P.out_hist ? h.ohist : nullptr);
     }
   } else {
     const int p = t.idx;
@@ -1026,7 +1046,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
           cov = true;
         }
       }
-      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v);
+      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v, P.out_hist ? h.ohist : nullptr);
     }
   }
   __syncthreads();
@@ -1163,6 +1183,21 @@ __device__ __forceinline__ void copy_params(FuseParams &dst, const FuseParams *s
   for (int i = threadIdx.x; i < (int)(sizeof(FuseParams) / 16); i += blockDim.x) d[i] = __ldg(s + i);
 }
 
+// STITCH_BALANCE_OUTPUT: the block's histogram starts at zero and is added
+// to the frame's histogram once, when the persistent block is done.
+__device__ __forceinline__ void ohist_zero(const FuseParams &P, SmemHead &h) {
+  if (P.out_hist)
+    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) h.ohist[i] = 0u;
+}
+__device__ __forceinline__ void ohist_flush(const FuseParams &P, SmemHead &h) {
+  if (!P.out_hist) return;
+  __syncthreads();
+  for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
+    const uint32_t c = h.ohist[i];
+    if (c) atomicAdd(P.out_hist + i, c);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1183,11 +1218,13 @@ __global__ void __launch_bounds__(kFuseThreads, 3) k_fuse(const FuseParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
   load_color(P, h);
+  ohist_zero(P, h);
   const int n = P.n_tiles - P.n_band - P.n_full;
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     __syncthreads();
     fuse_tile<kHalf, TW, TH>(P, P.tiles[i], h, tile_smem<TW, TH, 2>(smem));
   }
+  ohist_flush(P, h);
 }
 
 // Band pieces (the n_band before the fully covered ones), persistent.
@@ -1197,11 +1234,13 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_band(const FuseParams 
   SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
   SmemBand<TW, TH> &sb = *reinterpret_cast<SmemBand<TW, TH> *>(smem + (sizeof(SmemHead) + 15) / 16 * 16);
   load_color(P, h);
+  ohist_zero(P, h);
   const int base = P.n_tiles - P.n_full - P.n_band;
   for (int i = blockIdx.x; i < P.n_band; i += gridDim.x) {
     __syncthreads();
     fuse_band_piece<kHalf, TW, TH>(P, P.tiles[base + i], h, sb.out);
   }
+  ohist_flush(P, h);
 }
 
 // The fully covered own pieces, which close the list (P.n_full of them).
@@ -1210,11 +1249,13 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own(const FuseParams P
   extern __shared__ __align__(16) unsigned char smem[];
   SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
   load_color(P, h);
+  ohist_zero(P, h);
   const int base = P.n_tiles - P.n_full;
   for (int i = blockIdx.x; i < P.n_full; i += gridDim.x) {
     __syncthreads();
     fuse_own_tile<TW, TH>(P, P.tiles[base + i], h, tile_smem<TW, TH, 1>(smem));
   }
+  ohist_flush(P, h);
 }
 
 // Band pre-warp of several rigs in one launch: block b takes item b.

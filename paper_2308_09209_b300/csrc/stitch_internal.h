@@ -141,6 +141,7 @@ struct alignas(16) FuseParams {
   const ColorOut *color;
   const uint8_t *lut;                 // the colour slot's output table (kLutBytes)
   unsigned int *win_fallback;         // tiles whose source window did not fit in shared memory (counter)
+  uint32_t *out_hist;                 // STITCH_BALANCE_OUTPUT: this frame's pre-balance histogram [3][256], or null
   CamDev cam[kMaxCams];
   BandDev band[kMaxPairs];
   const uint8_t *src[kMaxCams];
@@ -187,6 +188,7 @@ struct EstimateParams {
   int n_cams, n_pairs, ref, window;
   int flags;                          // STITCH_BALANCE_OFF selects the identity output table
   uint8_t *lut;                       // kColorSlots output tables (slot T % kColorSlots), or null
+  uint32_t *out_hist;                 // STITCH_BALANCE_OUTPUT: 2 x [3][256], frame F in slot F % 2, or null
   long long lambda_q;                 // lambda in millionths
   int pair_i[kMaxPairs], pair_j[kMaxPairs];
   int raw_slots;                      // frame T reads slot T % raw_slots and clears slot (T - 1) % raw_slots

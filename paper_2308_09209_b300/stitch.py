@@ -32,6 +32,7 @@ STITCH_BALANCE_OFF = 1
 STITCH_FP16_INTERMEDIATE = 2
 STITCH_FLOW_WEIGHTS_PRINTED = 4
 STITCH_LEARNED = 8
+STITCH_BALANCE_OUTPUT = 16
 STITCH_PROJ_PLANAR = 0
 STITCH_PROJ_CYLINDRICAL = 1
 
@@ -128,6 +129,7 @@ def lib():
             "stitch_batch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_n_pairs": (ip, [vp]),
             "stitch_window_fallbacks": (ip, [vp, ctypes.POINTER(ctypes.c_ulonglong), ip]),
+            "stitch_get_output_hist": (ip, [vp, vp]),
             "stitch_last_error": (ctypes.c_char_p, [vp]),
             "stitch_destroy": (None, [vp]),
         }
@@ -589,6 +591,14 @@ def stitch_batch_destroy(b) -> None:
 
 def stitch_n_pairs(ctx) -> int:
     return lib().stitch_n_pairs(ctx)
+
+
+def stitch_get_output_hist(ctx) -> np.ndarray:
+    """(3, 256) uint32 pre-balance histogram of the latest stitched frame
+    (contexts with STITCH_BALANCE_OUTPUT)."""
+    h = np.zeros((3, 256), dtype=np.uint32)
+    _check(lib().stitch_get_output_hist(ctx, h.ctypes.data), ctx)
+    return h
 
 
 def stitch_window_fallbacks(ctx, reset: bool = False) -> int:

@@ -92,3 +92,52 @@ def test_gamma_tails_closed_form():
     assert np.isclose(bal.apply(np.array([25.5]), p, 0)[0], 12.75 / 64)
     assert np.isclose(bal.apply(np.array([229.5]), p, 0)[0], 255 - 12.75 / 64)
     assert np.isclose(bal.apply(np.array([127.5]), p, 0)[0], 12.75 + 1.5 * 76.5)
+
+
+# --- balance on the stitched image (one-frame lag) ---------------------------
+
+def test_output_histogram_hand_worked():
+    """Three pixels worked by hand: v clamped to [0, 255], q = rint(16 v),
+    bin = (q + 8) // 16; the uncovered pixel does not count."""
+    from oracle.balance import output_histogram
+    v = np.array([[0.0, 255.0, 127.5],       # q = 0, 4080, 2040 -> bins 0, 255, 128
+                  [127.53, 0.03, 300.0],     # q = 2040, 0, 4080 -> bins 128, 0, 255
+                  [-5.0, 64.49, 64.5]])      # not covered
+    h = output_histogram(v, np.array([True, True, False]))
+    want = np.zeros((3, 256), dtype=np.int64)
+    want[0, 0] = want[0, 128] = 1
+    want[1, 255] = want[1, 0] = 1
+    want[2, 128] = want[2, 255] = 1
+    assert np.array_equal(h, want)
+    # on the grid of sixteenths: 64.5 -> q 1032 -> bin 65; 64.4375 -> q 1031 -> bin 64;
+    # 64.40625 -> 16 v = 1030.5, to even q 1030 -> bin 64
+    assert output_histogram(np.array([[64.5, 64.4375, 64.40625]]), np.array([True]))[:, 64:66].tolist() == \
+        [[0, 1], [1, 0], [1, 0]]
+
+
+def test_balance_on_stitched_image_lags_one_frame():
+    """Two cameras at integer offsets seeing one mosaic (M = I, zero flow):
+    frame 0 is not balanced and its panorama is the mosaic; frame 1's knots
+    are the lambda quantiles of that mosaic's histogram, and with a constant
+    mosaic the smoothing of Eq. 6-7 keeps them."""
+    from oracle.pipeline import OracleStitcher
+    from oracle import BALANCE_OUTPUT
+    rng = np.random.RandomState(4)
+    h, w, off = 40, 60, 40
+    mosaic = np.clip(rng.normal(120, 40, (h, off + w, 3)), 0, 255).astype(np.uint8)
+    T = lambda tx: np.array([[1.0, 0, tx], [0, 1.0, 0], [0, 0, 1.0]])
+    frames = [mosaic[:, :w].copy(), mosaic[:, off:off + w].copy()]
+    o = OracleStitcher([T(0), T(off)], [w, w], [h, h], off + w, h, window=3, max_flow=2.0, flags=BALANCE_OUTPUT)
+    fl = [np.zeros((h, w - off, 2), np.float32)]
+    o.estimate_color(frames)
+    assert bool(np.all(o.curve["identity"]))
+    planes, near, vals = o.frame(frames, fl, fl)
+    assert np.array_equal(planes.transpose(1, 2, 0), mosaic)
+    hist = np.stack([np.bincount(mosaic[:, :, c].ravel(), minlength=256) for c in range(3)])
+    assert np.array_equal(o.out_hist, hist)
+    o.estimate_color(frames)
+    m1, m2 = bal.knots(hist, 0.05)
+    assert np.array_equal(o.curve["m1"], m1) and np.array_equal(o.curve["m2"], m2)
+    o.frame(frames, fl, fl)
+    o.estimate_color(frames)
+    assert np.array_equal(o.curve["m1"], m1) and np.array_equal(o.curve["m2"], m2)
