@@ -463,9 +463,12 @@ int stitch_pairs_label(const uint8_t *pairs_dev, int n_pairs, int patch_w, int p
  * network it predicts M with; NULL detaches. The context does not own the
  * network: keep it alive while the context may use it. With a network
  * attached, each colour estimate also forms the window-pooled features of
- * every pair, runs the network and forms the residual
- * r = ||A M_hat - B||_F / ||B||_F from the window's exact A and B; a pair with
- * r <= 1e-3 takes M_hat, any other pair keeps the plain fit. The balance
+ * every pair, runs the network and forms its residual: the relative excess of
+ * Eq. 2's least-squares error over the window's plain fit M* = A^-1 B,
+ * r = ||X (M_hat - M*)||^2 / ||X M*||^2 = tr(D^T A D) / tr(M*^T A M*) with
+ * D = M_hat - M* and the window's exact A = X^T X; a pair whose plain fit
+ * succeeded and whose r <= 1e-3 (transferred colours within about 3 % RMS of
+ * the plain fit's) takes M_hat, any other pair keeps the plain fit. The balance
  * curve always comes from the plain estimate (its knots are exact integer
  * quantiles). Without a network a STITCH_LEARNED context behaves as a plain
  * one.

@@ -111,11 +111,16 @@ def adam_step(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def residual(A, B, M_hat) -> float:
-    """r = ||A M_hat - B||_F / ||B||_F (the fallback test of the learned
-    estimator), float64."""
+    """The fallback test of the learned estimator, float64: how much M_hat
+    raises the least-squares error of Eq. 2 over the plain fit M* = A^-1 B,
+    relative to the energy of the fitted colours,
+    r = ||X (M_hat - M*)||^2 / ||X M*||^2 = tr(D^T A D) / tr(M*^T A M*),
+    D = M_hat - M*, A = X^T X, B = X^T Y (the cross term vanishes at M*)."""
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
-    nb = np.linalg.norm(B)
-    if nb == 0.0:
+    Ms = np.linalg.solve(A, B)
+    D = np.asarray(M_hat, dtype=np.float64) - Ms
+    den = float(np.trace(Ms.T @ A @ Ms))
+    if den <= 0.0:
         return np.inf
-    return float(np.linalg.norm(A @ np.asarray(M_hat, dtype=np.float64) - B) / nb)
+    return float(np.trace(D.T @ A @ D) / den)

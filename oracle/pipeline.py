@@ -26,7 +26,8 @@ Learned mode (flag LEARNED with a network given): after the plain estimate,
 each pair's features are its window-pooled overlap histograms (side i then
 side j, each scaled by 256 / count, bfloat16), the network predicts M_hat - I
 (``oracle.mlp``), and the pair takes M_hat when its plain fit succeeded and
-r = ||A M_hat - B||_F / ||B||_F <= 1e-3 over the window's A and B; otherwise
+r = tr(D^T A D) / tr(M*^T A M*) <= 1e-3 over the window's A, with D = M_hat - M* and
+M* the window's plain fit (the relative excess of Eq. 2's least-squares error); otherwise
 it keeps the plain result. The chosen matrices are chained as usual.
 """
 from __future__ import annotations

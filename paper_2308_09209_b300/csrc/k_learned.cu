@@ -7,10 +7,15 @@
 // (each side's histograms scaled by 256 / count, bfloat16).
 // The network then runs on these features (k_mlp.cu).
 // k_learned_select: per pair, M_hat = I + the network's first nine outputs and
-// the residual r = ||A M_hat - B||_F / ||B||_F over the window's summed A and
-// B (float64). A pair whose plain fit succeeded and whose r <= 1e-3 takes
-// M_hat; any other pair keeps the plain result. The chosen matrices are
-// chained to the reference camera again and replace frame T's colour output.
+// its residual: how much M_hat raises Eq. 2's least-squares error over the
+// plain fit M* = A^-1 B of the window, relative to the energy of the fitted
+// colours, r = ||X (M_hat - M*)||^2 / ||X M*||^2 = tr(D^T A D) / tr(M*^T A M*)
+// with D = M_hat - M* and A = X^T X the window's summed Gram matrix (float64;
+// the cross term vanishes at the optimum). A pair whose plain fit succeeded
+// and whose r <= 1e-3 takes M_hat (its transferred colours within about 3 %
+// RMS of the plain fit's); any other pair keeps the plain result. The chosen
+// matrices are chained to the reference camera again and replace frame T's
+// colour output.
 #include "estimate_common.cuh"
 #include "stitch_internal.h"
 
@@ -75,20 +80,25 @@ __global__ void __launch_bounds__(256) k_learned_select(const LearnedParams P) {
     const int r = e / 3, c = e % 3;
     static const int sym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
     const int nw = min(frame + 1, P.window);
-    unsigned long long As = 0ull, Bs = 0ull;
+    unsigned long long As = 0ull;
     for (int i = 0; i < nw; ++i) {
       const int sl = (frame - i) % kMaxWindow;
       As += S->A_ring[sl][p][sym[e]];
-      Bs += S->B_ring[sl][p][e];
     }
-    const double a = (double)As, b = (double)Bs;
+    const double a = (double)As;
     const double mh = (double)L->y[p][e] + (r == c ? 1.0 : 0.0);
-    // (A M_hat)(r, c) = sum_k A(r, k) M_hat(k, c)
-    double am = 0.0;
+    const double ms = S->M_pair[p][e];              // the plain fit of this window
+    const double d = mh - ms;
+    // (A D)(r, c) and (A M*)(r, c) = sum_k A(r, k) (.)(k, c)
+    double ad = 0.0, am = 0.0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) am += __shfl_sync(0xffffffffu, a, r * 3 + k) * __shfl_sync(0xffffffffu, mh, k * 3 + c);
-    double num = lane < 9 ? (am - b) * (am - b) : 0.0;
-    double den = lane < 9 ? b * b : 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double ark = __shfl_sync(0xffffffffu, a, r * 3 + k);
+      ad += ark * __shfl_sync(0xffffffffu, d, k * 3 + c);
+      am += ark * __shfl_sync(0xffffffffu, ms, k * 3 + c);
+    }
+    double num = lane < 9 ? d * ad : 0.0;           // tr(D^T A D)
+    double den = lane < 9 ? ms * am : 0.0;          // tr(M*^T A M*)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       num += __shfl_down_sync(0xffffffffu, num, o);
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(256) k_learned_select(const LearnedParams P) {
     }
     num = __shfl_sync(0xffffffffu, num, 0);
     den = __shfl_sync(0xffffffffu, den, 0);
-    const double res = den > 0.0 ? sqrt(num / den) : INFINITY;
+    const double res = den > 0.0 ? num / den : INFINITY;
     const bool plain_ok = ((S->singular_last >> p) & 1) == 0;
     const bool use = plain_ok && isfinite(mh) && res <= kResidLimit;   // NaN fails both tests
     const bool all_finite = __all_sync(0xffffffffu, lane >= 9 || isfinite(mh));

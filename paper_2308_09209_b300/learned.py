@@ -8,7 +8,8 @@ and picks batches.
     python -m paper_2308_09209_b300.learned --pairs 200000 --epochs 40 --out weights.npz --evaluate
 
 draws the seeded training pairs (synthetic scenes under random gain, gamma,
-offset and colour cast), labels them on the GPU, trains, and writes the
+offset and colour cast, each side three frames of a moving scene like a rig's
+window-pooled overlap), labels them on the GPU, trains, and writes the
 float32 parameters and the target normalisation to ``--out``.
 """
 from __future__ import annotations
@@ -192,7 +193,7 @@ def evaluate_gain(net, config="2x640x360", seeds=(101, 102, 103, 104), n_frames=
 
 
 def main():
-    from synth import make_pairs
+    from synth import make_window_pairs
     ap = argparse.ArgumentParser()
     ap.add_argument("--pairs", type=int, default=200000)
     ap.add_argument("--held-out", type=int, default=8192)
@@ -205,7 +206,7 @@ def main():
     a = ap.parse_args()
     S.stitch_mlp_n_params()
     t0 = time.perf_counter()
-    pairs, _ = make_pairs(a.pairs + a.held_out, seed=a.seed, device="cuda")
+    pairs, _ = make_window_pairs(a.pairs + a.held_out, seed=a.seed, device="cuda")
     t1 = time.perf_counter()
     feat, targ, M, flags = label_pairs(pairs)
     t2 = time.perf_counter()

@@ -25,7 +25,7 @@ two independent photometric responses.
 from .rig import Rig, make_rig, rig_for_config, CONFIGS, BATCH_RIGS
 from .scene import Scene, render_camera_frames
 from .flow import smooth_flow
-from .pairs import make_pairs, apply_response
+from .pairs import make_pairs, make_window_pairs, apply_response
 
 __all__ = ["Rig", "make_rig", "rig_for_config", "CONFIGS", "BATCH_RIGS", "Scene",
-           "render_camera_frames", "smooth_flow", "make_pairs", "apply_response"]
+           "render_camera_frames", "smooth_flow", "make_pairs", "make_window_pairs", "apply_response"]

@@ -85,3 +85,50 @@ def make_pairs(n, patch_w=96, patch_h=64, seed=0, device="cpu", n_scenes=16, sce
     params = dict(gain_i=resp_i[0], gamma_i=resp_i[1], offset_i=resp_i[2], cast_i=resp_i[3],
                   gain_j=resp_j[0], gamma_j=resp_j[1], offset_j=resp_j[2], cast_j=resp_j[3])
     return out, params
+
+
+def make_window_pairs(n, patch_w=128, patch_h=96, n_frames=3, seed=0, device="cpu", n_scenes=16, scene_w=1152,
+                      scene_h=360, n_times=24, n_objects=6, max_shift=3, cast=0.05, chunk=2048):
+    """n seeded pairs shaped like a rig's window-pooled overlap: each side of
+    a pair is the same crop of one scene at n_frames consecutive times (moving
+    objects), the sub-patches stacked in rows, so that its histograms and
+    sums pool the window as the estimator pools a rig's overlap over W
+    frames. Side j is the crop moved by an integer shift of up to max_shift
+    pixels; each side has its own photometric response (see the module
+    docstring). The scenes are rendered once per time step and the pairs cut
+    from those renders. Returns (pairs uint8 [n, 2, n_frames * patch_h,
+    patch_w, 3], dict of the response parameters)."""
+    rng = np.random.RandomState(seed)
+    scenes = [Scene(scene_w, scene_h, n_objects=n_objects, seed=seed * 1000 + 500 + s) for s in range(n_scenes)]
+    u = torch.arange(scene_w, dtype=torch.float32, device=device)
+    v = torch.arange(scene_h, dtype=torch.float32, device=device)
+    V, U = torch.meshgrid(v, u, indexing="ij")
+    renders = torch.empty((n_scenes, n_times, scene_h, scene_w, 3), dtype=torch.float32, device=device)
+    for s in range(n_scenes):
+        for t in range(n_times):
+            renders[s, t] = scenes[s].render(U, V, t)
+    sid = rng.randint(0, n_scenes, n)
+    t0 = rng.randint(0, n_times - n_frames + 1, n)
+    x0 = rng.randint(max_shift, scene_w - patch_w - max_shift, n)
+    y0 = rng.randint(max_shift, scene_h - patch_h - max_shift, n)
+    sh = rng.randint(-max_shift, max_shift + 1, (n, 2))
+    resp_i = _responses(rng, n, cast)
+    resp_j = _responses(rng, n, cast)
+    out = torch.empty((n, 2, n_frames * patch_h, patch_w, 3), dtype=torch.uint8, device=device)
+    ky = torch.arange(patch_h, device=device).view(1, 1, -1, 1)
+    kx = torch.arange(patch_w, device=device).view(1, 1, 1, -1)
+    kt = torch.arange(n_frames, device=device).view(1, -1, 1, 1)
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        m = c1 - c0
+        S_ = torch.as_tensor(sid[c0:c1], device=device).view(-1, 1, 1, 1)
+        T_ = torch.as_tensor(t0[c0:c1], device=device).view(-1, 1, 1, 1) + kt
+        for side, (dx, dy) in enumerate(((np.zeros(m, np.int64), np.zeros(m, np.int64)), (sh[c0:c1, 0], sh[c0:c1, 1]))):
+            Y_ = torch.as_tensor(y0[c0:c1] + dy, device=device).view(-1, 1, 1, 1) + ky
+            X_ = torch.as_tensor(x0[c0:c1] + dx, device=device).view(-1, 1, 1, 1) + kx
+            rgb = renders[S_, T_, Y_, X_].reshape(m, n_frames * patch_h, patch_w, 3)
+            r = resp_i if side == 0 else resp_j
+            out[c0:c1, side] = apply_response(rgb, *(a[c0:c1] for a in r))
+    params = dict(gain_i=resp_i[0], gamma_i=resp_i[1], offset_i=resp_i[2], cast_i=resp_i[3],
+                  gain_j=resp_j[0], gamma_j=resp_j[1], offset_j=resp_j[2], cast_j=resp_j[3])
+    return out, params

@@ -85,11 +85,24 @@ def test_residual_closed_forms():
     A = np.array([[4.0, 1.0, 0.0], [1.0, 3.0, 1.0], [0.0, 1.0, 2.0]])
     M = np.array([[1.1, 0.0, 0.1], [0.0, 0.9, 0.0], [0.2, 0.0, 1.0]])
     B = A @ M
-    assert om.residual(A, B, M) == 0.0
-    # diagonal A: r = ||A E|| / ||A M|| for M_hat = M + E
+    assert abs(om.residual(A, B, M)) < 1e-28
+    # A = 2 I, M* = I, M_hat = 1.01 I: tr(D^T A D) / tr(M*^T A M*) = 3 * 2e-4 / 6
     A = np.diag([2.0, 2.0, 2.0])
     B = A @ np.eye(3)
-    assert np.isclose(om.residual(A, B, np.eye(3) * 1.01), 0.01, rtol=1e-12)
+    assert np.isclose(om.residual(A, B, np.eye(3) * 1.01), 1e-4, rtol=1e-10)
+
+
+def test_residual_is_the_excess_least_squares_error():
+    """Against the literal Eq. 2 objective on a stacked system: the extra
+    error of M_hat over the least-squares M*, relative to ||X M*||^2."""
+    rng = np.random.default_rng(8)
+    X = rng.uniform(0, 255, (500, 3))
+    Y = X @ np.array([[1.05, 0.02, 0.0], [0.01, 0.97, 0.03], [0.0, 0.02, 1.1]]) + rng.normal(0, 3, (500, 3))
+    Ms = np.linalg.lstsq(X, Y, rcond=None)[0]
+    M_hat = Ms + rng.normal(0, 0.01, (3, 3))
+    f = lambda M: np.sum((X @ M - Y) ** 2)
+    want = (f(M_hat) - f(Ms)) / np.sum((X @ Ms) ** 2)
+    assert np.isclose(om.residual(X.T @ X, X.T @ Y, M_hat), want, rtol=1e-8)
 
 
 def _patch(rng, n=900):
