@@ -655,12 +655,17 @@ bool check_ptrs(const void *const *p, int n) {
 // and own columns of one camera, kTileOwn when that camera covers every
 // pixel of the piece with a margin (coverage is convex on the plane, so the
 // corners decide; on the cylinder every border pixel is tested), else
-// kTileOwnPart. The list holds the general pieces (kinds 2 and 3) first, then
-// the band pieces, then the fully covered own pieces. Returns false (with a
-// message) when a tile would touch two bands.
+// kTileOwnPart. The list holds the general pieces first (the partly covered
+// own pieces, then the band-edge pieces), then the band pieces and the fully
+// covered own pieces. Returns false (with a message) when a tile would touch two bands.
 struct TileCounts {
   int n_band = 0, n_full = 0;
 };
+
+void set_counts(FuseParams &fp, const TileCounts &c) {
+  fp.n_band = c.n_band;
+  fp.n_full = c.n_full;
+}
 
 bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &tiles, TileCounts &cnt, std::string &err) {
   const int TW = kTileShapes[shape].w, TH = kTileShapes[shape].h;
@@ -669,7 +674,7 @@ bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &tiles, TileCoun
     err = "panorama too large for the tile index";
     return false;
   }
-  std::vector<TileDesc> gen, band, full;
+  std::vector<TileDesc> gen, bpart, band, full;
   auto own_piece = [&](int k, int tx, int ty, int x0, int x1) {
     // columns [x0, x1) of tile (tx, ty), owned by camera k
     if (x0 >= x1) return;
@@ -704,7 +709,7 @@ bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &tiles, TileCoun
     t.idx = (int8_t)p;
     t.c0 = (uint8_t)((x0 - tx * TW) / 16);
     t.c1 = (uint8_t)((x1 - tx * TW + 15) / 16);
-    (kind == kTileBand ? band : gen).push_back(t);
+    (kind == kTileBand ? band : bpart).push_back(t);
   };
   for (int ty = 0; ty < nty; ++ty) {
     for (int tx = 0; tx < ntx; ++tx) {
@@ -747,6 +752,7 @@ bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &tiles, TileCoun
   cnt.n_band = (int)band.size();
   cnt.n_full = (int)full.size();
   tiles = gen;
+  tiles.insert(tiles.end(), bpart.begin(), bpart.end());
   tiles.insert(tiles.end(), band.begin(), band.end());
   tiles.insert(tiles.end(), full.begin(), full.end());
   return true;
@@ -1008,8 +1014,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
   fp.halo = ctx->halo;
   fp.max_flow = ctx->max_flow;
   fp.n_tiles = (int)tiles.size();
-  fp.n_band = tcnt.n_band;
-  fp.n_full = tcnt.n_full;
+  set_counts(fp, tcnt);
   fp.tiles = ctx->tiles;
   fp.n_pw_tiles = (int)pw_tiles.size();
   fp.pw_tiles = ctx->pw_tiles;
@@ -1826,8 +1831,7 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
     e = cudaMemcpyAsync(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s);
     fp.tiles = ctx->tiles;
     fp.n_tiles = (int)bt.size();
-    fp.n_band = tc.n_band;
-    fp.n_full = tc.n_full;
+    set_counts(fp, tc);
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_fuse(fp, sh, s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_fuse(fp, sh, s);
@@ -1849,8 +1853,7 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
     build_tiles(ctx->g, best, bt, tc, err);
     e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
     ctx->fp.n_tiles = (int)bt.size();
-    ctx->fp.n_band = tc.n_band;
-    ctx->fp.n_full = tc.n_full;
+    set_counts(ctx->fp, tc);
     ctx->shape = best;
   }
   if (e != cudaSuccess) return cuda_err(ctx, e, "autotune");
@@ -1880,8 +1883,7 @@ int stitch_set_tile_shape(stitch_ctx *ctx, int shape) {
   if (e == cudaSuccess) e = cudaMemcpy(ctx->tiles, bt.data(), bt.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_err(ctx, e, "tile list upload");
   ctx->fp.n_tiles = (int)bt.size();
-  ctx->fp.n_band = tc.n_band;
-  ctx->fp.n_full = tc.n_full;
+  set_counts(ctx->fp, tc);
   ctx->shape = shape;
   for (auto &ge : ctx->graphs) {
     if (ge.exec) cudaGraphExecDestroy(ge.exec);

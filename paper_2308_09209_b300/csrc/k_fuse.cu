@@ -116,8 +116,8 @@ __device__ __forceinline__ void cam_map_f(const CamDev &c, float dx, float dy, f
     nw = fmaf(c.h[6], dx, fmaf(c.h[7], dy, c.h[8]));
   }
   const float r = rcp_approx(nw);
-  sx = nx * r;
-  sy = ny * r;
+  sx = __fmul_rn(nx, r);
+  sy = __fmul_rn(ny, r);
 }
 
 // Integer part and fraction of s with fraction in [0, 1]; for integer s the
@@ -233,9 +233,12 @@ __device__ void stage_window(const uint8_t *__restrict__ src, const CamDev &c, c
   const int G = min((W.w + 4) >> 2, kStride >> 2);
   for (int i = threadIdx.x; i < kStride + 4; i += blockDim.x) s[W.h * kStride + i] = kXByte << 24;
   // G <= kStride / 4 <= blockDim.x: thread i takes group i % G of rows i / G,
-  // i / G + rows_per_pass, ... (one division per window)
-  const int rpp = blockDim.x / G;
-  const int r_first = threadIdx.x / G;
+  // i / G + rows_per_pass, ... The quotients come from an approximate
+  // reciprocal: floor((i + 1/2) / G) = floor(i / G), and (i + 1/2) / G lies at
+  // least 1 / (2 G) >= 1/128 from an integer, far beyond the reciprocal's error.
+  const float inv_g = rcp_approx((float)G);
+  const int rpp = (int)(((float)kFuseThreads + 0.5f) * inv_g);
+  const int r_first = (int)(((float)threadIdx.x + 0.5f) * inv_g);
   const int g = threadIdx.x - r_first * G;
   if (r_first >= rpp || r_first >= W.h) return;
   const int px = W.x0 + 4 * g;
@@ -570,8 +573,10 @@ __device__ __forceinline__ void finish_pair(const float2 (&v)[3], const float4 (
 
 // Every pixel of a fully covered own tile from its staged window (W.ok): the
 // tile lies inside camera k with a margin, so every tap is a frame pixel of
-// the window and the result equals cam_value's for each pixel.
-template <int TW, int TH>
+// the window and the result equals cam_value's for each pixel. kAll: the
+// piece holds every column of the tile (no column tests); kHist: the block's
+// pre-balance histogram is kept.
+template <int TW, int TH, bool kAll, bool kHist>
 __device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, const uint32_t *win, const BlockColor &bc,
                                           int k, const uint8_t *lut, uint8_t (*out)[TH][TW], int tx0, int ty0,
                                           int cx0, int cx1, uint32_t *hist) {
@@ -603,7 +608,8 @@ __device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, cons
       bilerp_pair(t0, t1, fx, fy, v);
       const int lx0 = PM::lx0(lane, cp), lx1 = PM::lx1(lane, cp);
       finish_pair<TW, TH>(v, bc.pr[k], lut, out, lx0, PM::ly0(warp, s), lx1, PM::ly1(warp, s),
-                          lx0 >= cx0 && lx0 < cx1, lx1 >= cx0 && lx1 < cx1, hist);
+                          kAll || (lx0 >= cx0 && lx0 < cx1), kAll || (lx1 >= cx0 && lx1 < cx1),
+                          kHist ? hist : nullptr);
     }
     y = __fadd2_rn(y, f2(PM::kDy));
   }
@@ -638,8 +644,8 @@ __device__ __forceinline__ void cam_point(const CamDev &c, int x, int y, float &
     sy = ny;
   } else {
     const float r = rcp_approx(nw);
-    sx = nx * r;
-    sy = ny * r;
+    sx = __fmul_rn(nx, r);
+    sy = __fmul_rn(ny, r);
   }
 }
 
@@ -702,6 +708,72 @@ __device__ __forceinline__ bool own_value(const FuseParams &P, const BlockColor 
   return second >= 0 && second < P.n_cams && cam_value<S>(P, bc, second, none, win, x, y, o);
 }
 
+template <int TW, int TH>
+__device__ __forceinline__ void ownpart_pairs(const FuseParams &P, const BlockColor &bc, int k, const Window &W,
+                                              const uint32_t *win, const uint8_t *lut, uint8_t (*out)[TH][TW],
+                                              int tx0, int ty0, int cx0, int cx1, uint32_t *hist) {
+  using PM = PairMap<TW, TH>;
+  constexpr int S = WinGeom<TW, TH>::kStride;
+  constexpr int kMax = WinGeom<TW, TH>::kAlloc - S - 2;
+  const CamDev &c = P.cam[k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t off = kMagicRoundBits * (uint32_t)(S + 1) + (uint32_t)W.y0 * (uint32_t)S + (uint32_t)W.x0;
+  const uint32_t wx = (uint32_t)W.w - 1u, wy = (uint32_t)W.h - 1u;   // last window column / row with a right tap
+  const float hx = c.wm1 - 0.5f, hy = c.hm1 - 0.5f;
+  const PairCoords pc = pair_coords<TW, TH>(c, tx0, ty0, lane, warp);
+  float2 y = pc.y0;
+#pragma unroll 1
+  for (int s = 0; s < PM::kSteps; ++s) {
+    const float2 row = pair_row(c, y);
+#pragma unroll
+    for (int cp = 0; cp < PM::kCP; ++cp) {
+      const int lx0 = PM::lx0(lane, cp), lx1 = PM::lx1(lane, cp);
+      const int ly0 = PM::ly0(warp, s), ly1 = PM::ly1(warp, s);
+      const bool col0 = lx0 >= cx0 && lx0 < cx1, col1 = lx1 >= cx0 && lx1 < cx1;
+      const bool in0 = col0 && tx0 + lx0 < P.pano_w && ty0 + ly0 < P.pano_h;
+      const bool in1 = col1 && tx0 + lx1 < P.pano_w && ty0 + ly1 < P.pano_h;
+      // the piece's pixels past the panorama's last column (row padding) are 0
+      if (col0 && !in0) put_px<TW, TH>(out, lut, lx0, ly0, false, make_float3(0.0f, 0.0f, 0.0f));
+      if (col1 && !in1) put_px<TW, TH>(out, lut, lx1, ly1, false, make_float3(0.0f, 0.0f, 0.0f));
+      float2 ux, uy;
+      pair_point(c, pc, cp, row, ux, uy);
+      const float2 nw = __ffma2_rn(row, f2(c.hm[7]), pc.cw[cp]);
+      float2 rx, ry;
+      __half2 fx, fy;
+      split_pair(ux, rx, fx);
+      split_pair(uy, ry, fy);
+      // window-relative taps (unsigned: a tap left of / above the window wraps)
+      const uint32_t wx0 = __float_as_uint(rx.x) - kMagicRoundBits - (uint32_t)W.x0;
+      const uint32_t wx1 = __float_as_uint(rx.y) - kMagicRoundBits - (uint32_t)W.x0;
+      const uint32_t wy0 = __float_as_uint(ry.x) - kMagicRoundBits - (uint32_t)W.y0;
+      const uint32_t wy1 = __float_as_uint(ry.y) - kMagicRoundBits - (uint32_t)W.y0;
+      const bool ok0 = nw.x > 0.0f && ux.x >= -0.5f && ux.x <= hx && uy.x >= -0.5f && uy.x <= hy && wx0 < wx && wy0 < wy;
+      const bool ok1 = nw.y > 0.0f && ux.y >= -0.5f && ux.y <= hx && uy.y >= -0.5f && uy.y <= hy && wx1 < wx && wy1 < wy;
+      if (W.ok && (ok0 || !in0) && (ok1 || !in1)) {
+        const uint32_t i0 = __float_as_uint(ry.x) * (uint32_t)S + __float_as_uint(rx.x) - off;
+        const uint32_t i1 = __float_as_uint(ry.y) * (uint32_t)S + __float_as_uint(rx.y) - off;
+        uint32_t t0[4], t1[4];
+        taps<S, kMax>(win, i0, t0);
+        taps<S, kMax>(win, i1, t1);
+        float2 v[3];
+        bilerp_pair(t0, t1, fx, fy, v);
+        finish_pair<TW, TH>(v, bc.pr[k], lut, out, lx0, ly0, lx1, ly1, in0, in1, hist);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const bool in = q ? in1 : in0;
+          if (!in) continue;
+          const int lx = q ? lx1 : lx0, ly = q ? ly1 : ly0;
+          float3 v = make_float3(0.0f, 0.0f, 0.0f);
+          const bool cov = own_value<S>(P, bc, k, k - 1, k + 1, W, win, tx0 + lx, ty0 + ly, v);
+          put_px<TW, TH>(out, lut, lx, ly, cov, v, hist);
+        }
+      }
+    }
+    y = __fadd2_rn(y, f2(PM::kDy));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Band intermediate: float32 RGB_ or half RGB_ per band pixel and side.
 // ---------------------------------------------------------------------------
@@ -717,12 +789,9 @@ struct PwT<true> {
   using T = uint2;   // four halves
 };
 
-// Bilinear of the intermediate at band-relative tap (lx, ly) with fractions
-// (gx, gy); the neighbours are (lx1, ly1). Returns the three channels.
-__device__ __forceinline__ float3 pw_lerp(const float4 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
-                                          float gy) {
-  const float4 a = __ldg(pw + (size_t)ly * bw + lx), b = __ldg(pw + (size_t)ly * bw + lx1);
-  const float4 d = __ldg(pw + (size_t)ly1 * bw + lx), e = __ldg(pw + (size_t)ly1 * bw + lx1);
+// Bilinear of four intermediate taps (a, b: row ly; d, e: row ly + 1) with
+// fractions (gx, gy), float32: the three channels.
+__device__ __forceinline__ float3 lerp4(float4 a, float4 b, float4 d, float4 e, float gx, float gy) {
   const float2 A = f2(a.x, a.y), B = f2(b.x, b.y), D = f2(d.x, d.y), E = f2(e.x, e.y);
   const float2 dx = __ffma2_rn(A, f2(-1.0f), B);
   const float2 dy = __ffma2_rn(A, f2(-1.0f), D);
@@ -733,10 +802,8 @@ __device__ __forceinline__ float3 pw_lerp(const float4 *pw, int bw, int lx, int 
   return make_float3(o.x, o.y, oz);
 }
 
-__device__ __forceinline__ float3 pw_lerp(const uint2 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
-                                          float gy) {
-  const uint2 a = __ldg(pw + (size_t)ly * bw + lx), b = __ldg(pw + (size_t)ly * bw + lx1);
-  const uint2 d = __ldg(pw + (size_t)ly1 * bw + lx), e = __ldg(pw + (size_t)ly1 * bw + lx1);
+// The same for half taps (four halves R, G, B, 0 per tap), in half2.
+__device__ __forceinline__ float3 lerp_h(uint2 a, uint2 b, uint2 d, uint2 e, float gx, float gy) {
   const __half2 hx = __float2half2_rn(gx), hy = __float2half2_rn(gy);
   float2 o[2];
 #pragma unroll
@@ -750,30 +817,67 @@ __device__ __forceinline__ float3 pw_lerp(const uint2 *pw, int bw, int lx, int l
   return make_float3(o[0].x, o[0].y, o[1].x);
 }
 
-// Remap sample P_k(X) (Eq. 18) of a band's intermediate at the band-relative,
-// half-shifted point qm = X - (x0, y0) - 1/2. kClamp: X may lie outside the
-// band (clamped into it first) and taps may fall on its last row / column.
-template <bool kHalf, bool kClamp>
-__device__ __forceinline__ float3 band_sample(const typename PwT<kHalf>::T *pw, int bw, int bh, float2 qm) {
+// A half tap as the float32 intermediate holds it (exact).
+__device__ __forceinline__ float4 h4f(uint2 u) {
+  const float2 rg = __half22float2(as_h2(u.x));
+  return make_float4(rg.x, rg.y, __low2float(as_h2(u.y)), 0.0f);
+}
+
+// Bilinear of the intermediate at band-relative tap (lx, ly) with fractions
+// (gx, gy); the neighbours are (lx1, ly1). Returns the three channels.
+__device__ __forceinline__ float3 pw_lerp(const float4 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
+                                          float gy) {
+  return lerp4(__ldg(pw + (size_t)ly * bw + lx), __ldg(pw + (size_t)ly * bw + lx1), __ldg(pw + (size_t)ly1 * bw + lx),
+               __ldg(pw + (size_t)ly1 * bw + lx1), gx, gy);
+}
+
+__device__ __forceinline__ float3 pw_lerp(const uint2 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
+                                          float gy) {
+  return lerp_h(__ldg(pw + (size_t)ly * bw + lx), __ldg(pw + (size_t)ly * bw + lx1), __ldg(pw + (size_t)ly1 * bw + lx),
+                __ldg(pw + (size_t)ly1 * bw + lx1), gx, gy);
+}
+
+// Tap of a remap sample: the band-relative tap (lx, ly), the step to its
+// right / lower neighbour (0 where clamped at the band's last column / row)
+// and the fractions; band_sample's arithmetic.
+struct BandTap {
+  int lx, ly, dx, dy;
+  float gx, gy;
+};
+
+template <bool kClamp>
+__device__ __forceinline__ BandTap band_tap_of(float2 qm, int bw, int bh) {
   if (kClamp) {
     qm.x = fminf(fmaxf(qm.x, -0.5f), (float)bw - 1.5f);
     qm.y = fminf(fmaxf(qm.y, -0.5f), (float)bh - 1.5f);
   }
   const float2 r = __fadd2_rn(qm, f2(kMagicRound));
   const float2 d = __ffma2_rn(__fadd2_rn(r, f2(-kMagicRound)), f2(-1.0f), qm);
-  int lx = (int)(__float_as_uint(r.x) - kMagicRoundBits), ly = (int)(__float_as_uint(r.y) - kMagicRoundBits);
-  float gx = d.x + 0.5f, gy = d.y + 0.5f;
-  int lx1 = lx + 1, ly1 = ly + 1;
+  BandTap t;
+  t.lx = (int)(__float_as_uint(r.x) - kMagicRoundBits);
+  t.ly = (int)(__float_as_uint(r.y) - kMagicRoundBits);
+  t.gx = d.x + 0.5f;
+  t.gy = d.y + 0.5f;
+  t.dx = 1;
+  t.dy = 1;
   if (kClamp) {
-    // X == x0 may come back as (x0 - 1, 1): take the tap at x0 instead.
-    if (lx < 0) { lx = 0; gx = 0.0f; }
-    if (ly < 0) { ly = 0; gy = 0.0f; }
-    lx = min(lx, bw - 1);
-    ly = min(ly, bh - 1);
-    lx1 = min(lx + 1, bw - 1);
-    ly1 = min(ly + 1, bh - 1);
+    if (t.lx < 0) { t.lx = 0; t.gx = 0.0f; }
+    if (t.ly < 0) { t.ly = 0; t.gy = 0.0f; }
+    t.lx = min(t.lx, bw - 1);
+    t.ly = min(t.ly, bh - 1);
+    t.dx = min(t.lx + 1, bw - 1) - t.lx;
+    t.dy = min(t.ly + 1, bh - 1) - t.ly;
   }
-  return pw_lerp(pw, bw, lx, ly, lx1, ly1, gx, gy);
+  return t;
+}
+
+// Remap sample P_k(X) (Eq. 18) of a band's intermediate at the band-relative,
+// half-shifted point qm = X - (x0, y0) - 1/2. kClamp: X may lie outside the
+// band (clamped into it first) and taps may fall on its last row / column.
+template <bool kHalf, bool kClamp>
+__device__ __forceinline__ float3 band_sample(const typename PwT<kHalf>::T *pw, int bw, int bh, float2 qm) {
+  const BandTap t = band_tap_of<kClamp>(qm, bw, bh);
+  return pw_lerp(pw, bw, t.lx, t.ly, t.lx + t.dx, t.ly + t.dy, t.gx, t.gy);
 }
 
 // A band pixel (x, y) inside the band rectangle of pair p (Eq. 16-18 and the
@@ -790,7 +894,7 @@ __device__ __forceinline__ float3 band_pixel(const FuseParams &P, const BlockCol
   float2 fb = __ldg(P.flow_ji[p] + fi);
   fa.x = fmaxf(fminf(fa.x, mf), -mf); fa.y = fmaxf(fminf(fa.y, mf), -mf);
   fb.x = fmaxf(fminf(fb.x, mf), -mf); fb.y = fmaxf(fminf(fb.y, mf), -mf);
-  const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
+  const float tb = __fmul_rn((float)(x - B.x0) + 0.5f, B.inv_bw);
   const float ta = 1.0f - tb;
   const float wa = printed ? ta : tb;
   const float wb = printed ? tb : ta;
@@ -851,7 +955,18 @@ __device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDes
   if (W0.ok) {
     stage_window<G::kStride>(P.src[k], c, W0, st.win[0]);
     __syncthreads();
-    own_pairs<TW, TH>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1, P.out_hist ? h.ohist : nullptr);
+    const bool all = t.c0 == 0 && t.c1 == TW / 16;
+    if (P.out_hist) {
+      if (all)
+        own_pairs<TW, TH, true, true>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1, h.ohist);
+      else
+        own_pairs<TW, TH, false, true>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1, h.ohist);
+    } else {
+      if (all)
+        own_pairs<TW, TH, true, false>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1, nullptr);
+      else
+        own_pairs<TW, TH, false, false>(c, W0, st.win[0], h.bc, k, h.lut, st.out, tx0, ty0, cx0, cx1, nullptr);
+    }
   } else {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < (TW / 32) * (TH / 8); ++j) {
@@ -901,7 +1016,7 @@ __device__ __forceinline__ void band_rows(const FuseParams &P, const BlockColor 
     const int lx = lane + 32 * gi;
     if (lx < cx0 || lx >= cx1) continue;
     const int col = tx0 + lx - B.x0;       // band-relative column
-    const float tb = ((float)col + 0.5f) * B.inv_bw;
+    const float tb = __fmul_rn((float)col + 0.5f, B.inv_bw);
     const float ta = 1.0f - tb;
     const float wa = printed ? ta : tb;
     const float wb = printed ? tb : ta;
@@ -1002,16 +1117,8 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
 
   constexpr int kGroups = TW / 32, kRPW = TH / 8;
   if (t.kind == kTileOwnPart) {
-    const int k = t.idx;
-    for (int j = 0; j < kGroups * kRPW; ++j) {
-      const int lx = lane + 32 * (j % kGroups), ly = kRPW * warp + j / kGroups;
-      if (lx < cx0 || lx >= cx1) continue;
-      const int x = tx0 + lx, y = ty0 + ly;
-      float3 v = make_float3(0.0f, 0.0f, 0.0f);
-      bool cov = false;
-      if (x < P.pano_w && y < P.pano_h) cov = own_value<S>(P, bc, k, k - 1, k + 1, W0, st.win[0], x, y, v);
-      put_px<TW, TH>(st.out, h.lut, lx, ly, cov, v, P.out_hist ? h.ohist : nullptr);
-    }
+    ownpart_pairs<TW, TH>(P, bc, t.idx, W0, st.win[0], h.lut, st.out, tx0, ty0, cx0, cx1,
+                          P.out_hist ? h.ohist : nullptr);
   } else {
     const int p = t.idx;
     const BandDev B = P.band[p];
@@ -1028,7 +1135,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
         } else if (x >= B.x1) {
           cov = own_value<S>(P, bc, p + 1, p, p + 2, W1, st.win[1], x, y, v);
         } else if (y < B.y0 || y >= B.y1) {
-          const float tb = ((float)(x - B.x0) + 0.5f) * B.inv_bw;
+          const float tb = __fmul_rn((float)(x - B.x0) + 0.5f, B.inv_bw);
           const float ta = 1.0f - tb;
           float3 va, vb;
           const bool ca = cam_value<S>(P, bc, p, W0, st.win[0], x, y, va);

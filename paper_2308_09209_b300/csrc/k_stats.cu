@@ -1,17 +1,20 @@
 // K1 -- integer colour statistics of one frame (paper section 2.1 steps 2-4,
 // Eq. 1-3 terms; section 2.2 histogram for the balance knots).
 //
-// One streaming pass over every camera frame. Each thread takes groups of 16
+// Each block takes a band of rows of one camera frame, in groups of 16
 // consecutive pixels (48 bytes, three 16-byte loads when the row is 16-byte
-// aligned) and, per pixel:
-//   * adds the three channel values to the pooled full-frame histogram
-//     (section 2.2: the lambda-quantile knots);
-//   * inside a pair's source rectangle, adds to that side's overlap histogram
-//     (section 2.1 step 2); on the colour-source side i it also adds to the
-//     value-weighted histograms W_cd[x_d] += x_c (c != d) and to the Gram sums
+// aligned):
+//   * first every pixel: its three channel values go to the pooled
+//     full-frame histogram (section 2.2: the lambda-quantile knots);
+//   * then the block's part of each of the camera's pair rectangles, read
+//     again (from cache): the pixels go to that side's overlap histogram
+//     (section 2.1 step 2); on the colour-source side i also to the value-
+//     weighted histograms W_cd[x_d] += x_c (c != d) and to the Gram sums
 //     x_c x_d. With these, the estimate kernel forms B = I_i^T L(I_i) without
 //     a second pass over the pixels once the specification L is known:
 //     B_cd = sum_v L_d(v) W_cd(v), B_dd = sum_v L_d(v) v H_i,d(v).
+// Walking each rectangle separately keeps a warp's lanes on one kind of
+// update (only a rectangle's edge groups test their pixels one by one).
 // Counts are accumulated in shared memory and flushed with one global atomic
 // per non-zero bin. All arithmetic is integer, so results are bit-exact.
 #include "stitch_internal.h"
@@ -31,6 +34,46 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
+}
+
+// The group's 48 bytes as 12 little-endian words (bytes past the row's
+// npx pixels are 0).
+__device__ __forceinline__ void load_group(const uint8_t *__restrict__ p, int npx, bool vec, uint32_t (&wd)[12]) {
+  if (vec && npx == 16) {
+    const uint4 q0 = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint4 q1 = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+    const uint4 q2 = __ldg(reinterpret_cast<const uint4 *>(p) + 2);
+    wd[0] = q0.x; wd[1] = q0.y; wd[2] = q0.z; wd[3] = q0.w;
+    wd[4] = q1.x; wd[5] = q1.y; wd[6] = q1.z; wd[7] = q1.w;
+    wd[8] = q2.x; wd[9] = q2.y; wd[10] = q2.z; wd[11] = q2.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) wd[k] = 0u;
+#pragma unroll
+    for (int j = 0; j < 48; ++j)
+      if (j < 3 * npx) wd[j >> 2] |= (uint32_t)__ldg(p + j) << ((j & 3) * 8);
+  }
+}
+
+// Calls f(y, g) for every row y in [ya, yb) and group g in [ga, gb), the
+// block's threads taking (row, group) pairs with a fixed stride; one integer
+// division per call when a row has at most blockDim groups.
+template <typename F>
+__device__ __forceinline__ void span_walk(int ya, int yb, int ga, int gb, F &&f) {
+  const int ng = gb - ga, nt = blockDim.x;
+  if (ya >= yb || ng <= 0) return;
+  if (ng <= nt) {
+    const int rpi = nt / ng;
+    int rr = (int)threadIdx.x / ng;
+    const int g = ga + (int)threadIdx.x - rr * ng;
+    if (rr >= rpi) return;
+    for (int y = ya + rr; y < yb; y += rpi) f(y, g);
+  } else {
+    for (int i = threadIdx.x; i < (yb - ya) * ng; i += nt) {
+      const int rr = i / ng;
+      f(ya + rr, ga + i - rr * ng);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsParams P) {
@@ -73,89 +116,76 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsParams P) {
   const int iq = (act[0] && R[0].is_i) ? 0 : ((act[1] && R[1].is_i) ? 1 : -1);
   unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
 
-  // Rows are walked by a fixed thread -> (row, group) assignment: no division
-  // inside the loop when a row has at most blockDim groups.
-  const int nt = blockDim.x;
-  const bool rowwise = groups <= nt;
-  const int rpi = rowwise ? nt / groups : 1;
-  int rr = rowwise ? (int)threadIdx.x / groups : 0;
-  int g = rowwise ? (int)threadIdx.x - rr * groups : 0;
-  int idx = threadIdx.x;
-  const bool idle = rowwise && (int)threadIdx.x >= rpi * groups;
-  while (!idle) {
-    if (!rowwise) {
-      if (idx >= (r1 - r0) * groups) break;
-      rr = idx / groups;
-      g = idx - rr * groups;
-    } else if (r0 + rr >= r1) {
-      break;
-    }
-    const int y = r0 + rr;
+  // Pass 1, every pixel of rows [r0, r1): the pooled histogram.
+  span_walk(r0, r1, 0, groups, [&](int y, int g) {
     const int x0 = g << 4;
     const int npx = min(16, w - x0);
-    const uint8_t *p = src + (size_t)y * pitch + 3 * x0;
     uint32_t wd[12];
-    if (vec && npx == 16) {
-      const uint4 q0 = __ldg(reinterpret_cast<const uint4 *>(p));
-      const uint4 q1 = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
-      const uint4 q2 = __ldg(reinterpret_cast<const uint4 *>(p) + 2);
-      wd[0] = q0.x; wd[1] = q0.y; wd[2] = q0.z; wd[3] = q0.w;
-      wd[4] = q1.x; wd[5] = q1.y; wd[6] = q1.z; wd[7] = q1.w;
-      wd[8] = q2.x; wd[9] = q2.y; wd[10] = q2.z; wd[11] = q2.w;
+    load_group(src + (size_t)y * pitch + 3 * x0, npx, vec, wd);
+    if (npx == 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        atomicAdd(&s_pool[byte_of(wd, 3 * i)], 1u);
+        atomicAdd(&s_pool[256 + byte_of(wd, 3 * i + 1)], 1u);
+        atomicAdd(&s_pool[512 + byte_of(wd, 3 * i + 2)], 1u);
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) wd[k] = 0u;
-#pragma unroll
-      for (int j = 0; j < 48; ++j)
-        if (j < 3 * npx) wd[j >> 2] |= (uint32_t)__ldg(p + j) << ((j & 3) * 8);
-    }
-    // Overlap rectangles: the group's pixel range [i0, i1) inside each.
-    int i0q[2], i1q[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const bool in = act[q] && y >= R[q].ry0 && y < R[q].ry1;
-      i0q[q] = in ? max(0, R[q].rx0 - x0) : 16;
-      i1q[q] = in ? min(npx, R[q].rx1 - x0) : 0;
-    }
-    uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u, a4 = 0u, a5 = 0u;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (i < npx) {
-        const uint32_t r = byte_of(wd, 3 * i);
-        const uint32_t gg = byte_of(wd, 3 * i + 1);
-        const uint32_t b = byte_of(wd, 3 * i + 2);
-        atomicAdd(&s_pool[r], 1u);
-        atomicAdd(&s_pool[256 + gg], 1u);
-        atomicAdd(&s_pool[512 + b], 1u);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          if (i >= i0q[q] && i < i1q[q]) {
-            uint32_t *Hs = s_role + q * kRoleWords;
-            atomicAdd(&Hs[r], 1u);
-            atomicAdd(&Hs[256 + gg], 1u);
-            atomicAdd(&Hs[512 + b], 1u);
-            if (q == iq) {
-              uint32_t *W = Hs + 768;
-              atomicAdd(&W[0 * 256 + gg], r);   // (c,d) = (0,1): indexed by x_1, adds x_0
-              atomicAdd(&W[1 * 256 + b], r);    // (0,2)
-              atomicAdd(&W[2 * 256 + r], gg);   // (1,0)
-              atomicAdd(&W[3 * 256 + b], gg);   // (1,2)
-              atomicAdd(&W[4 * 256 + r], b);    // (2,0)
-              atomicAdd(&W[5 * 256 + gg], b);   // (2,1)
-              a0 += r * r;
-              a1 += r * gg;
-              a2 += r * b;
-              a3 += gg * gg;
-              a4 += gg * b;
-              a5 += b * b;
-            }
-          }
+      for (int i = 0; i < 16; ++i) {
+        if (i < npx) {
+          atomicAdd(&s_pool[byte_of(wd, 3 * i)], 1u);
+          atomicAdd(&s_pool[256 + byte_of(wd, 3 * i + 1)], 1u);
+          atomicAdd(&s_pool[512 + byte_of(wd, 3 * i + 2)], 1u);
         }
       }
     }
-    // 16 pixels x 255^2 fits in 32 bits; the running total needs 64.
-    acc[0] += a0; acc[1] += a1; acc[2] += a2; acc[3] += a3; acc[4] += a4; acc[5] += a5;
-    if (rowwise) rr += rpi; else idx += nt;
+  });
+
+  // Pass 2, each rectangle's part of the block: overlap histograms, and on
+  // side i the value-weighted histograms and the Gram sums.
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    if (!act[q]) continue;
+    const int ya = max(r0, R[q].ry0), yb = min(r1, R[q].ry1);
+    const int rx0 = R[q].rx0, rx1 = R[q].rx1;
+    uint32_t *Hs = s_role + q * kRoleWords;
+    uint32_t *W = Hs + 768;
+    const bool side_i = q == iq;
+    span_walk(ya, yb, rx0 >> 4, (rx1 + 15) >> 4, [&](int y, int g) {
+      const int x0 = g << 4;
+      const int npx = min(16, w - x0);
+      uint32_t wd[12];
+      load_group(src + (size_t)y * pitch + 3 * x0, npx, vec, wd);
+      const int i0 = max(0, rx0 - x0), i1 = min(npx, rx1 - x0);
+      uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u, a4 = 0u, a5 = 0u;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (i >= i0 && i < i1) {
+          const uint32_t r = byte_of(wd, 3 * i);
+          const uint32_t gg = byte_of(wd, 3 * i + 1);
+          const uint32_t b = byte_of(wd, 3 * i + 2);
+          atomicAdd(&Hs[r], 1u);
+          atomicAdd(&Hs[256 + gg], 1u);
+          atomicAdd(&Hs[512 + b], 1u);
+          if (side_i) {
+            atomicAdd(&W[0 * 256 + gg], r);   // (c,d) = (0,1): indexed by x_1, adds x_0
+            atomicAdd(&W[1 * 256 + b], r);    // (0,2)
+            atomicAdd(&W[2 * 256 + r], gg);   // (1,0)
+            atomicAdd(&W[3 * 256 + b], gg);   // (1,2)
+            atomicAdd(&W[4 * 256 + r], b);    // (2,0)
+            atomicAdd(&W[5 * 256 + gg], b);   // (2,1)
+            a0 += r * r;
+            a1 += r * gg;
+            a2 += r * b;
+            a3 += gg * gg;
+            a4 += gg * b;
+            a5 += b * b;
+          }
+        }
+      }
+      // 16 pixels x 255^2 fits in 32 bits; the running total needs 64.
+      acc[0] += a0; acc[1] += a1; acc[2] += a2; acc[3] += a3; acc[4] += a4; acc[5] += a5;
+    });
   }
   // Gram sums: warp reduction, then one shared 64-bit add per warp.
   if (iq >= 0) {

