@@ -912,7 +912,7 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     pw_off[p][1] = pw_elems + area;
     pw_elems += 2 * area;
   }
-  const size_t pw_bytes = pw_elems * prewarp_elem_bytes((cfg->flags & STITCH_FP16_INTERMEDIATE) != 0);
+  const size_t pw_bytes = pw_elems * prewarp_elem_bytes(true);   // the frame path keeps halves
   if (e == cudaSuccess) e = cudaMalloc(&ctx->pw_tiles, pw_tiles.size() * sizeof(PwTile) + 16);
   ctx->pw_slot_bytes = (pw_bytes + 255) / 256 * 256;
   if (e == cudaSuccess) e = cudaMalloc(&ctx->pw, kPwSlots * ctx->pw_slot_bytes + 16);

@@ -5,9 +5,12 @@
 //
 // k_prewarp_band: the pre-warped image of section 3.1 over each pair's blend
 //   band, for BOTH cameras of the pair, computed once per band pixel and kept
-//   in a small intermediate (float32 RGB, or float16 with
-//   STITCH_FP16_INTERMEDIATE). It does not depend on the colour estimate. In
-//   the frame path the intermediate holds v - 128 (the offset form below).
+//   in a small intermediate. It does not depend on the colour estimate. In
+//   the frame path the intermediate holds v - 128 (the offset form below) as
+//   halves, which hold the half2 bilinear's results exactly;
+//   STITCH_FP16_INTERMEDIATE selects half2 instead of float32 arithmetic for
+//   the remap that reads them. (The flow and the correspondence fit use a
+//   float32 intermediate of the plain pre-warped image.)
 //
 // k_fuse_own: the fully covered own tiles (columns of one camera k, every
 //   pixel seen by k with a margin), about three quarters of a rig's tiles.
@@ -775,19 +778,10 @@ __device__ __forceinline__ void ownpart_pairs(const FuseParams &P, const BlockCo
 }
 
 // ---------------------------------------------------------------------------
-// Band intermediate: float32 RGB_ or half RGB_ per band pixel and side.
+// Band intermediate of the frame path: v - 128 per band pixel and side as
+// four halves (R, G, B, 0). The values are exact halves (the half2 bilinear's
+// results), so the float32 remap reads them without loss.
 // ---------------------------------------------------------------------------
-
-template <bool kHalf>
-struct PwT;
-template <>
-struct PwT<false> {
-  using T = float4;
-};
-template <>
-struct PwT<true> {
-  using T = uint2;   // four halves
-};
 
 // Bilinear of four intermediate taps (a, b: row ly; d, e: row ly + 1) with
 // fractions (gx, gy), float32: the three channels.
@@ -824,17 +818,15 @@ __device__ __forceinline__ float4 h4f(uint2 u) {
 }
 
 // Bilinear of the intermediate at band-relative tap (lx, ly) with fractions
-// (gx, gy); the neighbours are (lx1, ly1). Returns the three channels.
-__device__ __forceinline__ float3 pw_lerp(const float4 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
-                                          float gy) {
-  return lerp4(__ldg(pw + (size_t)ly * bw + lx), __ldg(pw + (size_t)ly * bw + lx1), __ldg(pw + (size_t)ly1 * bw + lx),
-               __ldg(pw + (size_t)ly1 * bw + lx1), gx, gy);
-}
-
+// (gx, gy); the neighbours are (lx1, ly1). kHalf: half2 arithmetic
+// (STITCH_FP16_INTERMEDIATE), else float32. Returns the three channels.
+template <bool kHalf>
 __device__ __forceinline__ float3 pw_lerp(const uint2 *pw, int bw, int lx, int ly, int lx1, int ly1, float gx,
                                           float gy) {
-  return lerp_h(__ldg(pw + (size_t)ly * bw + lx), __ldg(pw + (size_t)ly * bw + lx1), __ldg(pw + (size_t)ly1 * bw + lx),
-                __ldg(pw + (size_t)ly1 * bw + lx1), gx, gy);
+  const uint2 a = __ldg(pw + (size_t)ly * bw + lx), b = __ldg(pw + (size_t)ly * bw + lx1);
+  const uint2 d = __ldg(pw + (size_t)ly1 * bw + lx), e = __ldg(pw + (size_t)ly1 * bw + lx1);
+  if (kHalf) return lerp_h(a, b, d, e, gx, gy);
+  return lerp4(h4f(a), h4f(b), h4f(d), h4f(e), gx, gy);
 }
 
 // Tap of a remap sample: the band-relative tap (lx, ly), the step to its
@@ -875,9 +867,9 @@ __device__ __forceinline__ BandTap band_tap_of(float2 qm, int bw, int bh) {
 // half-shifted point qm = X - (x0, y0) - 1/2. kClamp: X may lie outside the
 // band (clamped into it first) and taps may fall on its last row / column.
 template <bool kHalf, bool kClamp>
-__device__ __forceinline__ float3 band_sample(const typename PwT<kHalf>::T *pw, int bw, int bh, float2 qm) {
+__device__ __forceinline__ float3 band_sample(const uint2 *pw, int bw, int bh, float2 qm) {
   const BandTap t = band_tap_of<kClamp>(qm, bw, bh);
-  return pw_lerp(pw, bw, t.lx, t.ly, t.lx + t.dx, t.ly + t.dy, t.gx, t.gy);
+  return pw_lerp<kHalf>(pw, bw, t.lx, t.ly, t.lx + t.dx, t.ly + t.dy, t.gx, t.gy);
 }
 
 // A band pixel (x, y) inside the band rectangle of pair p (Eq. 16-18 and the
@@ -885,7 +877,7 @@ __device__ __forceinline__ float3 band_sample(const typename PwT<kHalf>::T *pw, 
 template <bool kHalf, bool kClamp>
 __device__ __forceinline__ float3 band_pixel(const FuseParams &P, const BlockColor &bc, int p, int x, int y,
                                              bool printed) {
-  using PT = typename PwT<kHalf>::T;
+  using PT = uint2;
   const BandDev B = P.band[p];
   const int bw = B.x1 - B.x0, bh = B.y1 - B.y0;
   const float mf = P.max_flow;
@@ -985,7 +977,7 @@ __device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDes
 // half-shifted point qm (inside the band when !kClamp), returned in the
 // intermediate's units; the same arithmetic as band_sample.
 template <bool kHalf, bool kClamp>
-__device__ __forceinline__ float3 band_tap(const typename PwT<kHalf>::T *pw, int bw, int bh, float2 qm) {
+__device__ __forceinline__ float3 band_tap(const uint2 *pw, int bw, int bh, float2 qm) {
   return band_sample<kHalf, kClamp>(pw, bw, bh, qm);
 }
 
@@ -999,7 +991,7 @@ __device__ __forceinline__ float3 band_tap(const typename PwT<kHalf>::T *pw, int
 template <bool kHalf, bool kClamp, int TW, int TH>
 __device__ __forceinline__ void band_rows(const FuseParams &P, const BlockColor &bc, int p, int tx0, int ty0, int cx0,
                                           int cx1, const uint8_t *lut, uint8_t (*out)[TH][TW], uint32_t *hist) {
-  using PT = typename PwT<kHalf>::T;
+  using PT = uint2;
   constexpr int kGroups = TW / 32, kRPW = TH / 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const BandDev B = P.band[p];
@@ -1173,7 +1165,6 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
   using PM = PairMap<kTileW, kTileH>;
   constexpr int S = G::kStride;
   constexpr int kMax = G::kAlloc - S - 2;
-  using PT = typename PwT<kHalf>::T;
   const BandDev B = P.band[pt.pair];
   const int bw = B.x1 - B.x0;
   const int rx0 = pt.x0, ry0 = pt.y0;
@@ -1195,7 +1186,11 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
     const CamDev &c = P.cam[k];
     if (W.ok) stage_window<S>(P.src[k], c, W, st.win[side]);
     __syncthreads();
-    PT *dst = reinterpret_cast<PT *>(P.pw) + P.pw_off[pt.pair][side];
+    // the frame path (offset form) and STITCH_FP16_INTERMEDIATE store halves,
+    // the flow and the correspondence fit float32 values
+    const bool hstore = kHalf || offset;
+    uint2 *dst2 = reinterpret_cast<uint2 *>(P.pw) + P.pw_off[pt.pair][side];
+    float4 *dst4 = reinterpret_cast<float4 *>(P.pw) + P.pw_off[pt.pair][side];
     if (offset && W.ok) {
       // Every clamped point of the piece lies in the window (clipped to the
       // frame); a far tap past the frame reads the staged 0x64 column / row
@@ -1225,19 +1220,12 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
         const int x0 = rx0 + PM::lx0(lane, 0), x1 = rx0 + PM::lx1(lane, 0);
         if (y <= ry1) {
           const size_t o = (size_t)(y - B.y0) * bw;
-          if (kHalf) {
-            uint2 *d2 = reinterpret_cast<uint2 *>(dst);
-            if (x0 <= rx1)
-              d2[o + (x0 - B.x0)] = make_uint2(h2_bits(__floats2half2_rn(v[0].x, v[1].x)),
-                                              h2_bits(__floats2half2_rn(v[2].x, 0.0f)));
-            if (x1 <= rx1)
-              d2[o + (x1 - B.x0)] = make_uint2(h2_bits(__floats2half2_rn(v[0].y, v[1].y)),
-                                              h2_bits(__floats2half2_rn(v[2].y, 0.0f)));
-          } else {
-            float4 *d4 = reinterpret_cast<float4 *>(dst);
-            if (x0 <= rx1) d4[o + (x0 - B.x0)] = make_float4(v[0].x, v[1].x, v[2].x, 0.0f);
-            if (x1 <= rx1) d4[o + (x1 - B.x0)] = make_float4(v[0].y, v[1].y, v[2].y, 0.0f);
-          }
+          if (x0 <= rx1)
+            dst2[o + (x0 - B.x0)] = make_uint2(h2_bits(__floats2half2_rn(v[0].x, v[1].x)),
+                                               h2_bits(__floats2half2_rn(v[2].x, 0.0f)));
+          if (x1 <= rx1)
+            dst2[o + (x1 - B.x0)] = make_uint2(h2_bits(__floats2half2_rn(v[0].y, v[1].y)),
+                                               h2_bits(__floats2half2_rn(v[2].y, 0.0f)));
         }
         yy = __fadd2_rn(yy, f2(PM::kDy));
       }
@@ -1271,12 +1259,10 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
           sy = fminf(fmaxf(sy, 0.0f), c.hm1);
           v = W.ok ? win_bilinear<S>(st.win[side], W, sx, sy) : src_bilinear(P.src[k], c, sx, sy);
         }
-        if (kHalf) {
-          reinterpret_cast<uint2 *>(dst)[o] =
-              make_uint2(h2_bits(__floats2half2_rn(v.x, v.y)), h2_bits(__floats2half2_rn(v.z, 0.0f)));
-        } else {
-          reinterpret_cast<float4 *>(dst)[o] = make_float4(v.x, v.y, v.z, 0.0f);
-        }
+        if (hstore)
+          dst2[o] = make_uint2(h2_bits(__floats2half2_rn(v.x, v.y)), h2_bits(__floats2half2_rn(v.z, 0.0f)));
+        else
+          dst4[o] = make_float4(v.x, v.y, v.z, 0.0f);
       }
     }
   }
