@@ -551,9 +551,10 @@ __device__ __forceinline__ void taps(const uint32_t *w, uint32_t i, uint32_t (&t
 }
 
 // v . M + bias through the table for a pixel pair (v held as v - 128), the
-// products in cam_value's order; pr holds the camera's colour pairs.
-template <int TW, int TH>
-__device__ __forceinline__ void finish_pair(const float2 (&v)[3], const float4 (*pr)[2], const uint8_t *lut,
+// products in cam_value's order; pr holds the camera's colour pairs (in
+// shared memory or registers).
+template <int TW, int TH, typename PR>
+__device__ __forceinline__ void finish_pair(const float2 (&v)[3], const PR &pr, const uint8_t *lut,
                                             uint8_t (*out)[TH][TW], int lx0, int ly0, int lx1, int ly1, bool in0,
                                             bool in1, uint32_t *hist) {
 #pragma unroll
@@ -590,6 +591,12 @@ __device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, cons
   // word index of tap (ix, iy) = bits(ry) S + bits(rx) - off
   const uint32_t off = kMagicRoundBits * (uint32_t)(S + 1) + (uint32_t)W.y0 * (uint32_t)S + (uint32_t)W.x0;
   const PairCoords pc = pair_coords<TW, TH>(c, tx0, ty0, lane, warp);
+  float4 prc[3][2];   // the camera's colour pairs, held in registers for the tile
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    prc[q][0] = bc.pr[k][q][0];
+    prc[q][1] = bc.pr[k][q][1];
+  }
   float2 y = pc.y0;
 #pragma unroll 2
   for (int s = 0; s < PM::kSteps; ++s) {
@@ -610,7 +617,7 @@ __device__ __forceinline__ void own_pairs(const CamDev &c, const Window &W, cons
       float2 v[3];
       bilerp_pair(t0, t1, fx, fy, v);
       const int lx0 = PM::lx0(lane, cp), lx1 = PM::lx1(lane, cp);
-      finish_pair<TW, TH>(v, bc.pr[k], lut, out, lx0, PM::ly0(warp, s), lx1, PM::ly1(warp, s),
+      finish_pair<TW, TH>(v, prc, lut, out, lx0, PM::ly0(warp, s), lx1, PM::ly1(warp, s),
                           kAll || (lx0 >= cx0 && lx0 < cx1), kAll || (lx1 >= cx0 && lx1 < cx1),
                           kHist ? hist : nullptr);
     }
