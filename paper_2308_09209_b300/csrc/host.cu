@@ -1933,7 +1933,7 @@ struct stitch_batch {
   int n_pw_items = 0;
   int grid = 0;                       // persistent fuse blocks
   cudaStream_t cap = nullptr;
-  cudaStream_t pipe[3] = {};
+  cudaStream_t pipe[kPipeStreams] = {};   // statistics, estimate, band pre-warp, two fuse streams
   cudaEvent_t ev[4][8] = {};
   std::vector<BatchGraph> graphs;
   std::string err;
@@ -2063,7 +2063,8 @@ int stitch_batch_create(stitch_ctx *const *ctxs, int n_ctx, stitch_batch **out) 
     b->pairs += c->g.n - 1;
   }
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&b->pipe[i], cudaStreamNonBlocking);
+  for (int i = 0; i < kPipeStreams && e == cudaSuccess; ++i)
+    e = cudaStreamCreateWithFlags(&b->pipe[i], cudaStreamNonBlocking);
   for (int a = 0; a < 4 && e == cudaSuccess; ++a)
     for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev[a][k], cudaEventDisableTiming);
   // Each rig starts from its batched-launch shape in the tune cache, else the
@@ -2126,9 +2127,11 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       free_batch_graph(bg);
       return batch_err(b, STITCH_ECUDA, std::string("batch parameters: ") + cudaGetErrorString(e));
     }
-    // Same three-stream structure and slot-ring edges as stitch_sequence, with
+    // Same five-stream structure and slot-ring edges as stitch_sequence, with
     // every rig's statistics and estimate launched per rig and the band
-    // pre-warp and fuse of all rigs in one launch each.
+    // pre-warp and fuse of all rigs in one launch each: frame t's statistics
+    // on pipe[0], its estimate on pipe[1], its band pre-warp on pipe[4] and its
+    // fuse on pipe[2 + t % 2], so consecutive frames' fuses overlap.
     std::vector<char> prof(R);
     for (int r = 0; r < R; ++r) {
       prof[r] = b->ctx[r]->prof;
@@ -2136,28 +2139,32 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-    cudaStream_t sA = b->pipe[0], sB = b->pipe[1], sC = b->pipe[2];
+    cudaStream_t sA = b->pipe[0], sB = b->pipe[1], sW = b->pipe[4];
+    cudaStream_t sC2[2] = {b->pipe[2], b->pipe[3]};
     auto &ev = b->ev;
     enum { kS = 0, kW = 1, kE = 2, kF = 3 };
     auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
     chk(cudaEventRecord(ev[kF][7], b->cap));
-    chk(cudaStreamWaitEvent(sA, ev[kF][7], 0));
-    chk(cudaStreamWaitEvent(sB, ev[kF][7], 0));
-    chk(cudaStreamWaitEvent(sC, ev[kF][7], 0));
+    for (int i = 0; i < kPipeStreams; ++i) chk(cudaStreamWaitEvent(b->pipe[i], ev[kF][7], 0));
     int rc = STITCH_OK;
     for (int t = 0; t < n_frames && rc == STITCH_OK && e == cudaSuccess; ++t) {
+      // statistics: slot (T0+t) % 3 was cleared by the estimate of frame t-2
       if (t >= 2) chk(cudaStreamWaitEvent(sA, ev[kE][(t - 2) % 8], 0));
       for (int r = 0; r < R && rc == STITCH_OK; ++r)
         rc = launch_stats_for(b->ctx[r], frames_dev + (size_t)t * b->cams + b->cam_off[r], b->ctx[r]->host_T + t, sA);
       chk(cudaEventRecord(ev[kS][t % 8], sA));
-      if (t >= kPwSlots) chk(cudaStreamWaitEvent(sA, ev[kF][(t - kPwSlots) % 8], 0));
+      // band pre-warp: its slot was last read by the fuse of frame t - kPwSlots
+      if (t >= kPwSlots) chk(cudaStreamWaitEvent(sW, ev[kF][(t - kPwSlots) % 8], 0));
       MultiParams mp{bg.params, t * R, b->n_pw_items, b->pw_items, nullptr};
-      chk(launch_prewarp_multi(mp, b->half, sA));
-      chk(cudaEventRecord(ev[kW][t % 8], sA));
+      chk(launch_prewarp_multi(mp, b->half, sW));
+      chk(cudaEventRecord(ev[kW][t % 8], sW));
+      // estimate: after this frame's statistics; its colour slot was last read by fuse t-4
       chk(cudaStreamWaitEvent(sB, ev[kS][t % 8], 0));
       if (t >= 4) chk(cudaStreamWaitEvent(sB, ev[kF][(t - 4) % 8], 0));
       for (int r = 0; r < R && rc == STITCH_OK; ++r) rc = launch_estimate_for(b->ctx[r], sB);
       chk(cudaEventRecord(ev[kE][t % 8], sB));
+      // fuse: after this frame's estimate and pre-warp
+      cudaStream_t sC = sC2[t % 2];
       chk(cudaStreamWaitEvent(sC, ev[kE][t % 8], 0));
       chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
       chk(cudaMemsetAsync(bg.counters + 2 * t, 0, 2 * sizeof(int), sC));
@@ -2167,12 +2174,11 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       chk(launch_fuse_own_multi(mo, b->uniform, b->grid_own, sC));
       chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
-    chk(cudaEventRecord(ev[kS][0], sA));
-    chk(cudaStreamWaitEvent(b->cap, ev[kS][0], 0));
-    chk(cudaEventRecord(ev[kE][0], sB));
-    chk(cudaStreamWaitEvent(b->cap, ev[kE][0], 0));
-    chk(cudaEventRecord(ev[kF][0], sC));
-    chk(cudaStreamWaitEvent(b->cap, ev[kF][0], 0));
+    // join: every pipeline stream back into the capture stream
+    for (int i = 0; i < kPipeStreams; ++i) {
+      chk(cudaEventRecord(ev[i % 4][i], b->pipe[i]));
+      chk(cudaStreamWaitEvent(b->cap, ev[i % 4][i], 0));
+    }
     const cudaError_t e_end = cudaStreamEndCapture(b->cap, &graph);
     for (int r = 0; r < R; ++r) b->ctx[r]->prof = prof[r] != 0;
     if (e == cudaSuccess) e = e_end;
@@ -2302,7 +2308,7 @@ void stitch_batch_destroy(stitch_batch *b) {
   cudaFree(b->own_items);
   cudaFree(b->pw_items);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < kPipeStreams; ++i)
     if (b->pipe[i]) cudaStreamDestroy(b->pipe[i]);
   for (int a = 0; a < 4; ++a)
     for (int k = 0; k < 8; ++k)

@@ -19,8 +19,13 @@
 //               the denominator is positive, clamped to [-0.5, 0.5]); the
 //               flow is float(d) + off.
 //
-// One thread per pixel (the matcher: 32 x 8 pixel tiles with both images
-// staged in shared memory); blockIdx.y is (pair, camera) or (pair, direction):
+// The matcher stages both images of a 64 x 16 pixel tile in shared memory and
+// gives each thread a 2 x 2 block of pixels: the four share their parent at
+// the level above, so they test the same candidates, and the eight window
+// rows of the block serve both of its pixel rows (row differences four bytes
+// at a time, summed per pixel column with byte-masked dot products). The
+// sub-pixel step takes one pixel per thread on 32 x 8 tiles. blockIdx.y is
+// (pair, camera) or (pair, direction):
 // direction 0 moves the left camera onto the right one (flow_ij), 1 the
 // right onto the left (flow_ji). All costs are integers, so the chosen
 // displacements follow from the luminance images alone.
@@ -81,18 +86,46 @@ struct MatchTile {
   __align__(16) uint8_t b[kBH][kBWP];
 };
 
-// Load the tiles of block (bx0, by0) with halo `ha` for the moving image.
-__device__ __forceinline__ void load_tiles(MatchTile &T, const uint8_t *__restrict__ A, const uint8_t *__restrict__ B,
-                                           int w, int h, int bx0, int by0, int ha) {
-  const int aw = kTX + 2 * ha, ah = kTY + 2 * ha;
-  for (int i = threadIdx.x; i < aw * ah; i += blockDim.x) {
-    const int ry = i / aw, rx = i - ry * aw;
-    T.a[ry][rx] = __ldg(A + (size_t)clampi(by0 + ry - ha, 0, h - 1) * w + clampi(bx0 + rx - ha, 0, w - 1));
+// Matcher tiles: 64 x 16 pixels, 2 x 2 per thread.
+constexpr int kMX = 64, kMY = 16;
+constexpr int kMAW = kMX + 2 * kHaloA, kMAH = kMY + 2 * kHaloA;
+constexpr int kMBW = kMX + 2 * kWin, kMBH = kMY + 2 * kWin;
+constexpr int kMAWP = (kMAW + 8) & ~3, kMBWP = (kMBW + 8) & ~3;
+
+struct MatchTile2 {
+  __align__(16) uint8_t a[kMAH][kMAWP];
+  __align__(16) uint8_t b[kMBH][kMBWP];
+};
+
+// Rows [0, rows) x columns [0, cols) of a tile from the image, origin (x0, y0)
+// in image coordinates, clamped into the image: thread i takes column i % cols
+// of rows i / cols, i / cols + rows per pass, ... (one division per call).
+template <int kPitch>
+__device__ __forceinline__ void load_rect(uint8_t (*t)[kPitch], const uint8_t *__restrict__ img, int w, int h, int x0,
+                                          int y0, int cols, int rows) {
+  const int nt = blockDim.x;
+  if (cols <= nt) {
+    const int rpp = nt / cols;
+    const int r = (int)threadIdx.x / cols;
+    const int c = (int)threadIdx.x - r * cols;
+    if (r >= rpp) return;
+    const int x = clampi(x0 + c, 0, w - 1);
+    for (int rr = r; rr < rows; rr += rpp) t[rr][c] = __ldg(img + (size_t)clampi(y0 + rr, 0, h - 1) * w + x);
+  } else {
+    for (int i = threadIdx.x; i < cols * rows; i += nt) {
+      const int rr = i / cols, c = i - rr * cols;
+      t[rr][c] = __ldg(img + (size_t)clampi(y0 + rr, 0, h - 1) * w + clampi(x0 + c, 0, w - 1));
+    }
   }
-  for (int i = threadIdx.x; i < kBW * kBH; i += blockDim.x) {
-    const int ry = i / kBW, rx = i - ry * kBW;
-    T.b[ry][rx] = __ldg(B + (size_t)clampi(by0 + ry - kWin, 0, h - 1) * w + clampi(bx0 + rx - kWin, 0, w - 1));
-  }
+}
+
+// The eight bytes [o, o + 8) of a tile row as two words, from three aligned
+// 32-bit loads and two funnel shifts.
+__device__ __forceinline__ uint2 row8(const uint8_t *row, int o) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(row) + (o >> 2);
+  const uint32_t sh = (uint32_t)(o & 3) * 8u;
+  const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+  return make_uint2(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh));
 }
 
 // The seven bytes [o, o + 7) of a tile row as two words (the eighth byte
@@ -139,18 +172,20 @@ __device__ __forceinline__ int level_reach(int lev, int radius) {
 __global__ void __launch_bounds__(kFlowThreads, 3) k_flow_match(const FlowParams P, int lev, int radius) {
   const int pair = blockIdx.y >> 1, dir = blockIdx.y & 1;
   const int w = P.lev[lev].w[pair], h = P.lev[lev].h[pair];
-  const int ntx = (w + kTX - 1) / kTX;
-  if ((int)blockIdx.x >= ntx * ((h + kTY - 1) / kTY)) return;     // block-uniform
-  const int bx0 = (blockIdx.x % ntx) * kTX, by0 = (blockIdx.x / ntx) * kTY;
+  const int ntx = (w + kMX - 1) / kMX;
+  if ((int)blockIdx.x >= ntx * ((h + kMY - 1) / kMY)) return;     // block-uniform
+  const int bx0 = (blockIdx.x % ntx) * kMX, by0 = (blockIdx.x / ntx) * kMY;
   const uint8_t *A = P.Y + P.lev[lev].y_off[pair][dir];        // the image that moves
   const uint8_t *B = P.Y + P.lev[lev].y_off[pair][dir ^ 1];    // the target
   const bool top = lev == kFlowLevels - 1;
   const int reach = level_reach(lev, radius);
   const int ha = kWin + reach;
-  __shared__ MatchTile T;
-  load_tiles(T, A, B, w, h, bx0, by0, ha);
+  __shared__ MatchTile2 T;
+  load_rect<kMAWP>(T.a, A, w, h, bx0 - ha, by0 - ha, kMX + 2 * ha, kMY + 2 * ha);
+  load_rect<kMBWP>(T.b, B, w, h, bx0 - kWin, by0 - kWin, kMBW, kMBH);
   __syncthreads();
-  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  // the thread's 2 x 2 block: columns lx, lx + 1 and rows ly, ly + 1 of the tile
+  const int lx = 2 * (threadIdx.x % (kMX / 2)), ly = 2 * (threadIdx.x / (kMX / 2));
   const int x = bx0 + lx, y = by0 + ly;
   if (x >= w || y >= h) return;
   int sx = 0, sy = 0;
@@ -163,21 +198,48 @@ __global__ void __launch_bounds__(kFlowThreads, 3) k_flow_match(const FlowParams
   const int n_cand = top ? P.n_cand_top : 9;
   const int8_t *cand = top ? P.cand_top : P.cand_fine;
   const int lim = reach;
-  const BWin bw = target_window(T, lx, ly);
-  int best = INT_MAX, bx = sx, by = sy;
+  // the target's eight rows over both pixel rows, eight bytes over both columns
+  uint2 tb[2 * kWin + 2];
+#pragma unroll
+  for (int k = 0; k < 2 * kWin + 2; ++k) tb[k] = row8(T.b[ly + k], lx);
+  int best[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+  int bxs[4] = {sx, sx, sx, sx}, bys[4] = {sy, sy, sy, sy};
   for (int c = 0; c < n_cand; ++c) {
     // the search never leaves the reach; the clamp only guards the tile
     const int dx = clampi(sx + cand[2 * c], -lim, lim), dy = clampi(sy + cand[2 * c + 1], -lim, lim);
-    const int cost = tile_cost(T, bw, ha, lx, ly, dx, dy);
-    if (cost < best) {
-      best = cost;
-      bx = dx;
-      by = dy;
+    const int o = lx + ha - kWin + dx;
+    const uint8_t(*ra)[kMAWP] = T.a + (ly + ha - kWin + dy);
+    // costs of (left, right) x (upper, lower): window rows 0-6 and 1-7
+    unsigned c00 = 0u, c01 = 0u, c10 = 0u, c11 = 0u;
+#pragma unroll
+    for (int k = 0; k < 2 * kWin + 2; ++k) {
+      const uint2 a = row8(ra[k], o);
+      const unsigned d0 = __vabsdiffu4(a.x, tb[k].x), d1 = __vabsdiffu4(a.y, tb[k].y);
+      // left pixel: bytes 0-6; right pixel: bytes 1-7
+      const unsigned sl = __dp4a(d1, 0x00010101u, __dp4a(d0, 0x01010101u, 0u));
+      const unsigned sr = __dp4a(d1, 0x01010101u, __dp4a(d0, 0x01010100u, 0u));
+      if (k < 2 * kWin + 1) { c00 += sl; c01 += sr; }
+      if (k > 0) { c10 += sl; c11 += sr; }
+    }
+    const unsigned cs[4] = {c00, c01, c10, c11};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if ((int)cs[q] < best[q]) {
+        best[q] = (int)cs[q];
+        bxs[q] = dx;
+        bys[q] = dy;
+      }
     }
   }
-  const size_t i = (size_t)y * w + x;
-  P.dx[P.lev[lev].d_off[pair][dir] + i] = (int16_t)bx;
-  P.dy[P.lev[lev].d_off[pair][dir] + i] = (int16_t)by;
+  const size_t base = P.lev[lev].d_off[pair][dir];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int xq = x + (q & 1), yq = y + (q >> 1);
+    if (xq >= w || yq >= h) continue;
+    const size_t i = (size_t)yq * w + xq;
+    P.dx[base + i] = (int16_t)bxs[q];
+    P.dy[base + i] = (int16_t)bys[q];
+  }
 }
 
 __device__ __forceinline__ float subpixel(int cm, int c0, int cp) {
@@ -198,7 +260,8 @@ __global__ void __launch_bounds__(kFlowThreads, 3) k_flow_final(const FlowParams
   const int reach = level_reach(0, radius) + 1;                 // the chosen d and its neighbours
   const int ha = kWin + reach;
   __shared__ MatchTile T;
-  load_tiles(T, A, B, w, h, bx0, by0, ha);
+  load_rect<kAWP>(T.a, A, w, h, bx0 - ha, by0 - ha, kTX + 2 * ha, kTY + 2 * ha);
+  load_rect<kBWP>(T.b, B, w, h, bx0 - kWin, by0 - kWin, kBW, kBH);
   __syncthreads();
   const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
   const int x = bx0 + lx, y = by0 + ly;
@@ -221,10 +284,10 @@ __global__ void __launch_bounds__(kFlowThreads, 3) k_flow_final(const FlowParams
   out[i] = make_float2(__fadd_rn((float)dx, ox), __fadd_rn((float)dy, oy));
 }
 
-dim3 flow_tiles(const FlowParams &p, int lev) {
+dim3 flow_tiles(const FlowParams &p, int lev, int tx, int ty) {
   int most = 0;
   for (int i = 0; i < p.n_pairs; ++i)
-    most = std::max(most, ((p.lev[lev].w[i] + kTX - 1) / kTX) * ((p.lev[lev].h[i] + kTY - 1) / kTY));
+    most = std::max(most, ((p.lev[lev].w[i] + tx - 1) / tx) * ((p.lev[lev].h[i] + ty - 1) / ty));
   return dim3(std::max(1, most), 2 * p.n_pairs);
 }
 
@@ -239,12 +302,12 @@ dim3 flow_grid(const FlowParams &p, int lev) {
 cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s) {
   if (p.n_pairs <= 0) return cudaSuccess;
   if (radius < 1 || radius > kFlowMaxRadius) return cudaErrorInvalidValue;
-  static_assert(kTX * kTY == kFlowThreads, "one pixel per thread");
+  static_assert(kTX * kTY == kFlowThreads && kMX * kMY == 4 * kFlowThreads, "thread layouts of the flow kernels");
   k_flow_luma<<<flow_grid(p, 0), kFlowThreads, 0, s>>>(p);
   for (int lev = 1; lev < kFlowLevels; ++lev) k_flow_down<<<flow_grid(p, lev), kFlowThreads, 0, s>>>(p, lev);
   for (int lev = kFlowLevels - 1; lev >= 0; --lev)
-    k_flow_match<<<flow_tiles(p, lev), kFlowThreads, 0, s>>>(p, lev, radius);
-  k_flow_final<<<flow_tiles(p, 0), kFlowThreads, 0, s>>>(p, radius);
+    k_flow_match<<<flow_tiles(p, lev, kMX, kMY), kFlowThreads, 0, s>>>(p, lev, radius);
+  k_flow_final<<<flow_tiles(p, 0, kTX, kTY), kFlowThreads, 0, s>>>(p, radius);
   return cudaGetLastError();
 }
 
