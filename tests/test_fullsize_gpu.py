@@ -37,3 +37,50 @@ def test_8x3840x2160_cylinder_every_pixel():
     assert rep["within1"] >= FRAC_WITHIN_1 and rep["max"] <= MAX_ABS, rep
     assert rep["n"] + rep["n_near"] == pr.rig.pano_w * pr.rig.pano_h
     pr.st.close()
+
+
+def test_8x3840x2160_cylinder_learned_batched_every_pixel():
+    """The cylindrical rig's full form: learned estimate with fallback, FP16
+    intermediates and the batched persistent launch (three frames in one
+    graph-captured batch sequence). The learned features, network output,
+    residual and decision of every pair match the oracle's learned mode, and
+    every pixel of the last frame meets the bar."""
+    import torch
+    from oracle import mlp as om
+    from oracle.pipeline import OracleStitcher
+    flags = S.STITCH_LEARNED | S.STITCH_FP16_INTERMEDIATE
+    pr = Pair("8x3840x2160cyl", seed=1, flags=flags)
+    net = S.Mlp(max_batch=32, seed=5)
+    mu = np.zeros(om.N_OUT, np.float32)
+    sd = np.full(om.N_OUT, 0.05, np.float32)
+    S.stitch_mlp_set_norm(net.h, mu, sd)
+    params = S.stitch_mlp_get_params(net.h).astype(np.float64)
+    rig, seq = pr.rig, pr.seq
+    pr.oracle = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
+                               max_flow=seq["max_flow"], flags=flags, mlp=dict(params=params, mu=mu, sd=sd),
+                               **pr.proj)
+    S.stitch_attach_mlp(pr.st.ctx, net.h)
+    b = S.stitch_batch_create([pr.st.ctx])
+    n_t = 3
+    ins = [pr.inputs(t) for t in range(n_t)]
+    panos = [pr.st.new_pano() for _ in range(n_t)]
+    S.stitch_batch_sequence(b, n_t, [f for fr, _, _ in ins for f in fr], [f for _, a, _ in ins for f in a],
+                            [f for _, _, c in ins for f in c], panos)
+    torch.cuda.synchronize()
+    for fr, _, _ in ins:
+        pr.oracle.estimate_color([f.cpu().numpy() for f in fr])
+    n_pairs = rig.n_cams - 1
+    M_hat, r, used = S.stitch_get_learned(pr.st.ctx, n_pairs)
+    for p, (Mo, ro, uo) in enumerate(pr.oracle.learned):
+        assert np.linalg.norm(M_hat[p] - Mo) <= 5e-3 * np.linalg.norm(Mo), p
+        assert abs(r[p] - ro) <= 5e-3 * ro + 1e-9, (p, r[p], ro)
+        if abs(ro - 1e-3) > 0.05e-3:
+            assert used[p] == int(uo), p
+    fr, fij, fji = ins[-1]
+    planes, near = oracle_frame_parallel(pr, [f.cpu().numpy() for f in fr], [f.cpu().numpy() for f in fij],
+                                         [f.cpu().numpy() for f in fji])
+    rep = compare_pano(panos[-1], planes, near, rig.pano_w)
+    assert rep["within1"] >= FRAC_WITHIN_1 and rep["max"] <= MAX_ABS, rep
+    S.stitch_batch_destroy(b)
+    pr.st.close()
+    net.close()
