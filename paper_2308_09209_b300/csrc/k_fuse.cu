@@ -332,6 +332,14 @@ struct __align__(16) SmemTile {
   __align__(16) uint8_t out[3][TH][TW];
 };
 
+// Shared memory of the single-rig band pre-warp: the two cameras' window
+// descriptors and staged windows only (no colour constants or tables), so
+// that a one-wave grid fits.
+struct __align__(16) SmemPw {
+  Window sW[2];
+  __align__(16) uint32_t win[2][WinGeom<kTileW, kTileH>::kAlloc];
+};
+
 template <int TW, int TH, int NW>
 constexpr size_t smem_bytes() {
   return (sizeof(SmemHead) + 15) / 16 * 16 + sizeof(SmemTile<TW, TH, NW>);
@@ -1114,7 +1122,6 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
   if (W1.ok) stage_window<S>(P.src[t.idx + 1], P.cam[t.idx + 1], W1, st.win[1]);
   __syncthreads();
 
-  constexpr int kGroups = TW / 32, kRPW = TH / 8;
   if (t.kind == kTileOwnPart) {
     ownpart_pairs<TW, TH>(P, bc, t.idx, W0, st.win[0], h.lut, st.out, tx0, ty0, cx0, cx1,
                           P.out_hist ? h.ohist : nullptr);
@@ -1122,9 +1129,16 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
     const int p = t.idx;
     const BandDev B = P.band[p];
     const bool printed = (P.flags & STITCH_FLOW_WEIGHTS_PRINTED) != 0;
-    for (int j = 0; j < kGroups * kRPW; ++j) {
-      const int lx = lane + 32 * (j % kGroups), ly = kRPW * warp + j / kGroups;
-      if (lx < cx0 || lx >= cx1) continue;
+    // The block's threads take the piece's own pixels (a band-edge chunk is
+    // 16 columns wide): pixel i of the piece is column cx0 + i % pw of row
+    // i / pw; the row comes from an approximate reciprocal of pw / 16
+    // (floor((i / 16 + 1/2) / n) = floor(i / (16 n)), far from rounding).
+    const int n16 = t.c1 - t.c0, pw = 16 * n16;
+    const float inv_n = rcp_approx((float)n16);
+#pragma unroll 1
+    for (int i = threadIdx.x; i < pw * TH; i += kFuseThreads) {
+      const int ly = (int)(((float)(i >> 4) + 0.5f) * inv_n);
+      const int lx = cx0 + (i - ly * pw);
       const int x = tx0 + lx, y = ty0 + ly;
       float3 v = make_float3(0.0f, 0.0f, 0.0f);
       bool cov = false;
@@ -1166,8 +1180,8 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
 // intermediate holds v - 128; otherwise (the flow and the correspondence fit,
 // which want the plain pre-warped image) a float32 bilinear of v.
 template <bool kHalf>
-__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, SmemHead &h,
-                                              SmemTile<kTileW, kTileH, 2> &st) {
+__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, Window *sW,
+                                              uint32_t (*win)[WinGeom<kTileW, kTileH>::kAlloc]) {
   using G = WinGeom<kTileW, kTileH>;
   using PM = PairMap<kTileW, kTileH>;
   constexpr int S = G::kStride;
@@ -1180,7 +1194,7 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
   if (warp < 2) {
     const Window W = warp_window<S, G::kRows>(P.cam[pt.pair + warp], rx0, ry0, rx1, ry1);
     if (lane == 0) {
-      h.sW[warp] = W;
+      sW[warp] = W;
       if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
     }
   }
@@ -1188,10 +1202,10 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
   const bool offset = (P.flags & kFlagPwOffset) != 0;
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
-    const Window W = h.sW[side];
+    const Window W = sW[side];
     const int k = pt.pair + side;
     const CamDev &c = P.cam[k];
-    if (W.ok) stage_window<S>(P.src[k], c, W, st.win[side]);
+    if (W.ok) stage_window<S>(P.src[k], c, W, win[side]);
     __syncthreads();
     // the frame path (offset form) and STITCH_FP16_INTERMEDIATE store halves,
     // the flow and the correspondence fit float32 values
@@ -1219,8 +1233,8 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
         const uint32_t i0 = __float_as_uint(ry.x) * (uint32_t)S + __float_as_uint(rx.x) - off;
         const uint32_t i1 = __float_as_uint(ry.y) * (uint32_t)S + __float_as_uint(rx.y) - off;
         uint32_t t0[4], t1[4];
-        taps<S, kMax>(st.win[side], i0, t0);
-        taps<S, kMax>(st.win[side], i1, t1);
+        taps<S, kMax>(win[side], i0, t0);
+        taps<S, kMax>(win[side], i1, t1);
         float2 v[3];
         bilerp_pair(t0, t1, fx, fy, v);
         const int y = ry0 + PM::ly0(warp, s);
@@ -1264,7 +1278,7 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
           cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
           sx = fminf(fmaxf(sx, 0.0f), c.wm1);
           sy = fminf(fmaxf(sy, 0.0f), c.hm1);
-          v = W.ok ? win_bilinear<S>(st.win[side], W, sx, sy) : src_bilinear(P.src[k], c, sx, sy);
+          v = W.ok ? win_bilinear<S>(win[side], W, sx, sy) : src_bilinear(P.src[k], c, sx, sy);
         }
         if (hstore)
           dst2[o] = make_uint2(h2_bits(__floats2half2_rn(v.x, v.y)), h2_bits(__floats2half2_rn(v.z, 0.0f)));
@@ -1307,8 +1321,8 @@ __device__ __forceinline__ void ohist_flush(const FuseParams &P, SmemHead &h) {
 template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
-  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], h, tile_smem<kTileW, kTileH, 2>(smem));
+  SmemPw &sp = *reinterpret_cast<SmemPw *>(smem);
+  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], sp.sW, sp.win);
 }
 
 // General pieces (the first n_tiles - n_band - n_full of the list),
@@ -1366,7 +1380,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParam
   const MultiItem it = M.items[blockIdx.x];
   copy_params(h.sp, M.params + M.base + it.rig);
   __syncthreads();
-  prewarp_piece<kHalf>(h.sp, it.pw, h, tile_smem<kTileW, kTileH, 2>(smem));
+  prewarp_piece<kHalf>(h.sp, it.pw, h.sW, tile_smem<kTileW, kTileH, 2>(smem).win);
 }
 
 // Next item of a persistent multi-rig launch; reloads the rig's parameters
@@ -1469,7 +1483,8 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi_mixed(const 
 namespace {
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kPwSmem = smem_bytes<kTileW, kTileH, 2>();
+constexpr size_t kPwSmem = sizeof(SmemPw);                      // single-rig band pre-warp
+constexpr size_t kPwMultiSmem = smem_bytes<kTileW, kTileH, 2>();    // multi-rig: the rig's parameters too
 constexpr size_t kMixSmem =
     cmax(cmax(smem_bytes<64, 32, 2>(), smem_bytes<64, 16, 2>()), cmax(smem_bytes<32, 32, 2>(), smem_bytes<128, 16, 2>()));
 constexpr size_t kMixOwnSmem =
@@ -1572,8 +1587,8 @@ size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(floa
 cudaError_t fuse_setup_attributes(int) {
   cudaError_t e = set_smem(k_prewarp_band<false>, kPwSmem);
   if (e == cudaSuccess) e = set_smem(k_prewarp_band<true>, kPwSmem);
-  if (e == cudaSuccess) e = set_smem(k_prewarp_multi<false>, kPwSmem);
-  if (e == cudaSuccess) e = set_smem(k_prewarp_multi<true>, kPwSmem);
+  if (e == cudaSuccess) e = set_smem(k_prewarp_multi<false>, kPwMultiSmem);
+  if (e == cudaSuccess) e = set_smem(k_prewarp_multi<true>, kPwMultiSmem);
   if (e == cudaSuccess) e = setup_shape<64, 32>();
   if (e == cudaSuccess) e = setup_shape<64, 16>();
   if (e == cudaSuccess) e = setup_shape<32, 32>();
@@ -1608,9 +1623,9 @@ cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s) {
 cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s) {
   if (m.n_items <= 0) return cudaSuccess;
   if (half)
-    k_prewarp_multi<true><<<m.n_items, kFuseThreads, kPwSmem, s>>>(m);
+    k_prewarp_multi<true><<<m.n_items, kFuseThreads, kPwMultiSmem, s>>>(m);
   else
-    k_prewarp_multi<false><<<m.n_items, kFuseThreads, kPwSmem, s>>>(m);
+    k_prewarp_multi<false><<<m.n_items, kFuseThreads, kPwMultiSmem, s>>>(m);
   return cudaGetLastError();
 }
 
