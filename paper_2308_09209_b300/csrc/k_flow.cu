@@ -14,18 +14,19 @@
 //               candidates are visited in the tie-break order (|d - start|^2,
 //               then d_y, then d_x) and only a strictly smaller cost replaces
 //               the best, so ties resolve the same way in any schedule.
-// k_flow_final: per axis the parabola through the costs of d - 1, d, d + 1,
-//               off = (c- - c+) / (2 (c- - 2 c0 + c+)) in float32 (0 unless
-//               the denominator is positive, clamped to [-0.5, 0.5]); the
-//               flow is float(d) + off.
+// sub-pixel:   at the full level, per axis the parabola through the costs
+//               of d - 1, d, d + 1, off = (c- - c+) / (2 (c- - 2 c0 + c+)) in
+//               float32 (0 unless the denominator is positive, clamped to
+//               [-0.5, 0.5]); the flow is float(d) + off.
 //
 // The matcher stages both images of a 64 x 16 pixel tile in shared memory and
 // gives each thread a 2 x 2 block of pixels: the four share their parent at
 // the level above, so they test the same candidates, and the eight window
 // rows of the block serve both of its pixel rows (row differences four bytes
-// at a time, summed per pixel column with byte-masked dot products). The
-// sub-pixel step takes one pixel per thread on 32 x 8 tiles. blockIdx.y is
-// (pair, camera) or (pair, direction):
+// at a time, summed per pixel column with byte-masked dot products). At the
+// full level the matcher (k_flow_match_final) ends with the sub-pixel step,
+// reusing the costs of the candidates among d's four neighbours.
+// blockIdx.y is (pair, camera) or (pair, direction):
 // direction 0 moves the left camera onto the right one (flow_ij), 1 the
 // right onto the left (flow_ji). All costs are integers, so the chosen
 // displacements follow from the luminance images alone.
@@ -67,26 +68,16 @@ __global__ void __launch_bounds__(kFlowThreads) k_flow_down(const FlowParams P, 
   }
 }
 
-// Shared-memory tiles of the matcher: a 32 x 8 block of pixels, the target
+// Shared-memory tiles of the matcher: a 64 x 16 block of pixels, the target
 // image over the block plus the window's reach, and the moving image over
 // the block plus the window and the largest displacement the level can
 // test. Both are loaded with the same clamped coordinates as the plain
 // definition, so a tile read equals the clamped image read it replaces.
-constexpr int kTX = 32, kTY = 8;
 constexpr int kReach0 = 4 * kFlowMaxRadius + 2 + 1 + 1;   // |d| at the finest level, plus the sub-pixel neighbours
 constexpr int kHaloA = kWin + kReach0;
-constexpr int kAW = kTX + 2 * kHaloA, kAH = kTY + 2 * kHaloA;
-constexpr int kBW = kTX + 2 * kWin, kBH = kTY + 2 * kWin;
-// Rows padded to whole 32-bit words with room for the third word a 7-byte
-// window at any offset reads (the bytes beyond a row's data are never used).
-constexpr int kAWP = (kAW + 8) & ~3, kBWP = (kBW + 8) & ~3;
-
-struct MatchTile {
-  __align__(16) uint8_t a[kAH][kAWP];
-  __align__(16) uint8_t b[kBH][kBWP];
-};
-
-// Matcher tiles: 64 x 16 pixels, 2 x 2 per thread.
+// 2 x 2 pixels per thread. Rows are padded to whole 32-bit words with room
+// for the third word an 8-byte read at any offset takes (the bytes beyond a
+// row's data are never used).
 constexpr int kMX = 64, kMY = 16;
 constexpr int kMAW = kMX + 2 * kHaloA, kMAH = kMY + 2 * kHaloA;
 constexpr int kMBW = kMX + 2 * kWin, kMBH = kMY + 2 * kWin;
@@ -126,41 +117,6 @@ __device__ __forceinline__ uint2 row8(const uint8_t *row, int o) {
   const uint32_t sh = (uint32_t)(o & 3) * 8u;
   const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
   return make_uint2(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh));
-}
-
-// The seven bytes [o, o + 7) of a tile row as two words (the eighth byte
-// zero), from three aligned 32-bit loads and two funnel shifts.
-__device__ __forceinline__ uint2 row7(const uint8_t *row, int o) {
-  const uint32_t *w = reinterpret_cast<const uint32_t *>(row) + (o >> 2);
-  const uint32_t sh = (uint32_t)(o & 3) * 8u;
-  const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
-  return make_uint2(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh) & 0x00FFFFFFu);
-}
-
-// The target's 7 x 7 window of local pixel (lx, ly), kept in registers.
-struct BWin {
-  uint2 r[2 * kWin + 1];
-};
-
-__device__ __forceinline__ BWin target_window(const MatchTile &T, int lx, int ly) {
-  BWin b;
-#pragma unroll
-  for (int oy = 0; oy < 2 * kWin + 1; ++oy) b.r[oy] = row7(T.b[ly + oy], lx);
-  return b;
-}
-
-// Cost of displacement (dx, dy) at local pixel (lx, ly); |dx|, |dy| <= ha - kWin.
-// Byte-wise absolute differences summed four at a time (the same integer).
-__device__ __forceinline__ int tile_cost(const MatchTile &T, const BWin &b, int ha, int lx, int ly, int dx, int dy) {
-  unsigned c = 0u;
-  const int o = lx + ha - kWin + dx;
-#pragma unroll
-  for (int oy = 0; oy < 2 * kWin + 1; ++oy) {
-    const uint2 a = row7(T.a[ly + ha - kWin + dy + oy], o);
-    c = __dp4a(__vabsdiffu4(a.x, b.r[oy].x), 0x01010101u, c);
-    c = __dp4a(__vabsdiffu4(a.y, b.r[oy].y), 0x01010101u, c);
-  }
-  return (int)c;
 }
 
 __device__ __forceinline__ int level_reach(int lev, int radius) {
@@ -249,39 +205,104 @@ __device__ __forceinline__ float subpixel(int cm, int c0, int cp) {
   return fminf(fmaxf(off, -0.5f), 0.5f);
 }
 
-__global__ void __launch_bounds__(kFlowThreads, 3) k_flow_final(const FlowParams P, int radius) {
+// The full level with the sub-pixel step: the 2 x 2 matcher over the nine
+// refinement candidates, then per pixel the parabolas through the costs of
+// its displacement d and of d -/+ (1, 0), d -/+ (0, 1). Neighbours that were
+// candidates reuse their cost (the same window sums); the others are summed
+// from the tile, whose halo covers d +- 1.
+__device__ __forceinline__ int pixel_cost(const MatchTile2 &T, const uint2 (&tb)[2 * kWin + 2], int ha, int lx,
+                                          int ly, int qx, int qy, int dx, int dy) {
+  const int o = lx + ha - kWin + dx;
+  const uint8_t(*ra)[kMAWP] = T.a + (ly + ha - kWin + dy + qy);
+  const unsigned m0 = qx ? 0x01010100u : 0x01010101u, m1 = qx ? 0x01010101u : 0x00010101u;
+  unsigned c = 0u;
+#pragma unroll
+  for (int k = 0; k < 2 * kWin + 1; ++k) {
+    const uint2 a = row8(ra[k], o);
+    const uint2 t = qy ? tb[k + 1] : tb[k];
+    c = __dp4a(__vabsdiffu4(a.x, t.x), m0, c);
+    c = __dp4a(__vabsdiffu4(a.y, t.y), m1, c);
+  }
+  return (int)c;
+}
+
+__global__ void __launch_bounds__(kFlowThreads, 2) k_flow_match_final(const FlowParams P, int radius) {
   const int pair = blockIdx.y >> 1, dir = blockIdx.y & 1;
   const int w = P.lev[0].w[pair], h = P.lev[0].h[pair];
-  const int ntx = (w + kTX - 1) / kTX;
-  if ((int)blockIdx.x >= ntx * ((h + kTY - 1) / kTY)) return;     // block-uniform
-  const int bx0 = (blockIdx.x % ntx) * kTX, by0 = (blockIdx.x / ntx) * kTY;
+  const int ntx = (w + kMX - 1) / kMX;
+  if ((int)blockIdx.x >= ntx * ((h + kMY - 1) / kMY)) return;     // block-uniform
+  const int bx0 = (blockIdx.x % ntx) * kMX, by0 = (blockIdx.x / ntx) * kMY;
   const uint8_t *A = P.Y + P.lev[0].y_off[pair][dir];
   const uint8_t *B = P.Y + P.lev[0].y_off[pair][dir ^ 1];
-  const int reach = level_reach(0, radius) + 1;                 // the chosen d and its neighbours
-  const int ha = kWin + reach;
-  __shared__ MatchTile T;
-  load_rect<kAWP>(T.a, A, w, h, bx0 - ha, by0 - ha, kTX + 2 * ha, kTY + 2 * ha);
-  load_rect<kBWP>(T.b, B, w, h, bx0 - kWin, by0 - kWin, kBW, kBH);
+  const int reach = level_reach(0, radius);
+  const int ha = kWin + reach + 1;                              // the chosen d and its neighbours
+  __shared__ MatchTile2 T;
+  load_rect<kMAWP>(T.a, A, w, h, bx0 - ha, by0 - ha, kMX + 2 * ha, kMY + 2 * ha);
+  load_rect<kMBWP>(T.b, B, w, h, bx0 - kWin, by0 - kWin, kMBW, kMBH);
   __syncthreads();
-  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
+  const int lx = 2 * (threadIdx.x % (kMX / 2)), ly = 2 * (threadIdx.x / (kMX / 2));
   const int x = bx0 + lx, y = by0 + ly;
   if (x >= w || y >= h) return;
-  const size_t i = (size_t)y * w + x;
-  const int lim = reach - 1;
-  const int dx = clampi(P.dx[P.lev[0].d_off[pair][dir] + i], -lim, lim);
-  const int dy = clampi(P.dy[P.lev[0].d_off[pair][dir] + i], -lim, lim);
-  // costs of d, d -/+ (1, 0), d -/+ (0, 1)
-  const BWin bw = target_window(T, lx, ly);
-  int c[5];
+  const int wu = P.lev[1].w[pair];
+  const size_t j = P.lev[1].d_off[pair][dir] + (size_t)(y >> 1) * wu + (x >> 1);
+  const int sx = 2 * P.dx[j], sy = 2 * P.dy[j];
+  const int lim = reach;
+  uint2 tb[2 * kWin + 2];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int ex = k == 1 ? -1 : (k == 2 ? 1 : 0), ey = k == 3 ? -1 : (k == 4 ? 1 : 0);
-    c[k] = tile_cost(T, bw, ha, lx, ly, dx + ex, dy + ey);
+  for (int k = 0; k < 2 * kWin + 2; ++k) tb[k] = row8(T.b[ly + k], lx);
+  int best[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+  int bxs[4] = {sx, sx, sx, sx}, bys[4] = {sy, sy, sy, sy};
+  int cst[4][9], cdx[9], cdy[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const int dx = clampi(sx + P.cand_fine[2 * c], -lim, lim), dy = clampi(sy + P.cand_fine[2 * c + 1], -lim, lim);
+    cdx[c] = dx;
+    cdy[c] = dy;
+    const int o = lx + ha - kWin + dx;
+    const uint8_t(*ra)[kMAWP] = T.a + (ly + ha - kWin + dy);
+    unsigned c00 = 0u, c01 = 0u, c10 = 0u, c11 = 0u;
+#pragma unroll
+    for (int k = 0; k < 2 * kWin + 2; ++k) {
+      const uint2 a = row8(ra[k], o);
+      const unsigned d0 = __vabsdiffu4(a.x, tb[k].x), d1 = __vabsdiffu4(a.y, tb[k].y);
+      const unsigned sl = __dp4a(d1, 0x00010101u, __dp4a(d0, 0x01010101u, 0u));
+      const unsigned sr = __dp4a(d1, 0x01010101u, __dp4a(d0, 0x01010100u, 0u));
+      if (k < 2 * kWin + 1) { c00 += sl; c01 += sr; }
+      if (k > 0) { c10 += sl; c11 += sr; }
+    }
+    const unsigned cs[4] = {c00, c01, c10, c11};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      cst[q][c] = (int)cs[q];
+      if ((int)cs[q] < best[q]) {
+        best[q] = (int)cs[q];
+        bxs[q] = dx;
+        bys[q] = dy;
+      }
+    }
   }
-  const float ox = subpixel(c[1], c[0], c[2]);
-  const float oy = subpixel(c[3], c[0], c[4]);
-  float2 *out = dir == 0 ? P.out_ij[pair] : P.out_ji[pair];
-  out[i] = make_float2(__fadd_rn((float)dx, ox), __fadd_rn((float)dy, oy));
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int xq = x + (q & 1), yq = y + (q >> 1);
+    if (xq >= w || yq >= h) continue;
+    const int dx = bxs[q], dy = bys[q];
+    // costs of d, d -/+ (1, 0), d -/+ (0, 1)
+    int cc[5];
+    cc[0] = best[q];
+#pragma unroll
+    for (int e = 1; e < 5; ++e) {
+      const int nx = dx + (e == 1 ? -1 : (e == 2 ? 1 : 0)), ny = dy + (e == 3 ? -1 : (e == 4 ? 1 : 0));
+      int v = -1;
+#pragma unroll
+      for (int c = 0; c < 9; ++c)
+        if (cdx[c] == nx && cdy[c] == ny) v = cst[q][c];
+      cc[e] = v >= 0 ? v : pixel_cost(T, tb, ha, lx, ly, q & 1, q >> 1, nx, ny);
+    }
+    const float ox = subpixel(cc[1], cc[0], cc[2]);
+    const float oy = subpixel(cc[3], cc[0], cc[4]);
+    float2 *out = dir == 0 ? P.out_ij[pair] : P.out_ji[pair];
+    out[(size_t)yq * w + xq] = make_float2(__fadd_rn((float)dx, ox), __fadd_rn((float)dy, oy));
+  }
 }
 
 dim3 flow_tiles(const FlowParams &p, int lev, int tx, int ty) {
@@ -302,12 +323,12 @@ dim3 flow_grid(const FlowParams &p, int lev) {
 cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s) {
   if (p.n_pairs <= 0) return cudaSuccess;
   if (radius < 1 || radius > kFlowMaxRadius) return cudaErrorInvalidValue;
-  static_assert(kTX * kTY == kFlowThreads && kMX * kMY == 4 * kFlowThreads, "thread layouts of the flow kernels");
+  static_assert(kMX * kMY == 4 * kFlowThreads && kFlowLevels >= 2, "2 x 2 pixels per thread; a level above the finest");
   k_flow_luma<<<flow_grid(p, 0), kFlowThreads, 0, s>>>(p);
   for (int lev = 1; lev < kFlowLevels; ++lev) k_flow_down<<<flow_grid(p, lev), kFlowThreads, 0, s>>>(p, lev);
-  for (int lev = kFlowLevels - 1; lev >= 0; --lev)
+  for (int lev = kFlowLevels - 1; lev >= 1; --lev)
     k_flow_match<<<flow_tiles(p, lev, kMX, kMY), kFlowThreads, 0, s>>>(p, lev, radius);
-  k_flow_final<<<flow_tiles(p, 0, kTX, kTY), kFlowThreads, 0, s>>>(p, radius);
+  k_flow_match_final<<<flow_tiles(p, 0, kMX, kMY), kFlowThreads, 0, s>>>(p, radius);
   return cudaGetLastError();
 }
 
