@@ -495,7 +495,9 @@ int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used)
  *
  * stitch_autotune times the fuse of one frame (after the band pre-warp of
  * that frame) with every shape that fits the rig (a tile may touch at most
- * one blend band), `reps` launches each, keeps the fastest in the context and
+ * one blend band), `reps` launches each, keeps the fastest in the context
+ * (shape 0 unless another is more than 5 % faster: alone the shapes time within
+ * a few per cent, and shape 0 overlaps best with the other stages) and
  * records it: for the rest of the process, and in the file named by the
  * environment variable STITCH_TUNE_CACHE when set, keyed by the GPU model,
  * the rig geometry and STITCH_FP16_INTERMEDIATE. stitch_init picks up a
@@ -547,7 +549,8 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
  * stitch_batch_sequence with n_frames = 1; the panoramas are written),
  * one rig at a time: with the other rigs at their current shapes, both fuse
  * launches of the batch are timed (`reps` times each) with every shape that
- * fits rig r, and the fastest is kept before the next rig. The chosen shapes
+ * fits rig r, and the fastest (with the same 5 % preference for shape 0) is
+ * kept before the next rig. The chosen shapes
  * are recorded per rig like stitch_autotune's (process table and
  * STITCH_TUNE_CACHE), under a key marked as batched. shapes_out (optional):
  * one int per rig. ms_out (optional): n_rigs x STITCH_TILE_SHAPES floats,

@@ -762,6 +762,10 @@ bool build_tiles(const Geo &g, int shape, std::vector<TileDesc> &tiles, TileCoun
 // tile): room for any shape's list.
 size_t max_tiles(const Geo &g) { return 5 * (size_t)((g.pano_w + 31) / 32) * (size_t)((g.pano_h + 15) / 16); }
 
+// A tile shape replaces the default one only when it is faster by more than
+// this factor.
+constexpr float kTuneMargin = 0.95f;
+
 // ---------------------------------------------------------------------------
 // Autotuner results: the fastest fuse tile shape per (GPU, rig geometry,
 // intermediate precision), kept for the process and, when STITCH_TUNE_CACHE
@@ -1329,12 +1333,18 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   // Level sizes and buffer layout.
   FlowParams fl{};
   fl.n_pairs = np;
+  // The full level's luminance comes first, laid out like the band pre-warp
+  // (same offsets, one byte per element), so that the pre-warp writes it.
   size_t pw_elems = 0, y_bytes = 0, d_elems = 0;
   for (int p = 0; p < np; ++p) {
-    int w = g.band[p][1] - g.band[p][0], h = g.band[p][3] - g.band[p][2];
+    const int w = g.band[p][1] - g.band[p][0], h = g.band[p][3] - g.band[p][2];
     fl.pw_off[p][0] = pw_elems;
     fl.pw_off[p][1] = pw_elems + (size_t)w * h;
     pw_elems += 2 * (size_t)w * h;
+  }
+  y_bytes = pw_elems;
+  for (int p = 0; p < np; ++p) {
+    int w = g.band[p][1] - g.band[p][0], h = g.band[p][3] - g.band[p][2];
     for (int l = 0; l < kFlowLevels; ++l) {
       if (l > 0) {
         w = (w + 1) / 2;
@@ -1343,19 +1353,21 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
       fl.lev[l].w[p] = w;
       fl.lev[l].h[p] = h;
       for (int k = 0; k < 2; ++k) {
-        fl.lev[l].y_off[p][k] = y_bytes;
-        y_bytes += (size_t)w * h;
+        if (l == 0) {
+          fl.lev[l].y_off[p][k] = fl.pw_off[p][k];
+        } else {
+          fl.lev[l].y_off[p][k] = y_bytes;
+          y_bytes += (size_t)w * h;
+        }
         fl.lev[l].d_off[p][k] = d_elems;
         d_elems += (size_t)w * h;
       }
     }
   }
   cudaError_t e = cudaSuccess;
-  if (!ctx->flow_pw) e = cudaMalloc(&ctx->flow_pw, pw_elems * sizeof(float4) + 16);
-  if (e == cudaSuccess && !ctx->flow_Y) e = cudaMalloc(&ctx->flow_Y, y_bytes + 16);
+  if (!ctx->flow_Y) e = cudaMalloc(&ctx->flow_Y, y_bytes + 16);
   if (e == cudaSuccess && !ctx->flow_d) e = cudaMalloc(&ctx->flow_d, 2 * d_elems * sizeof(int16_t) + 16);
   if (e != cudaSuccess) return cuda_err(ctx, e, "flow buffers");
-  fl.pw = ctx->flow_pw;
   fl.Y = ctx->flow_Y;
   fl.dx = ctx->flow_d;
   fl.dy = ctx->flow_d + d_elems;
@@ -1382,11 +1394,17 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   };
   fl.n_cand_top = order(radius, fl.cand_top);
   order(1, fl.cand_fine);
-  // The float32 band pre-warp into the flow's own buffer, then the flow.
+  // The float32 band pre-warp, written as the full level's luminance, then
+  // the flow.
   const float *none[kMaxPairs] = {};
   FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
   fp.flags &= ~(STITCH_FP16_INTERMEDIATE | kFlagPwOffset);
-  fp.pw = ctx->flow_pw;
+  fp.flags |= kFlagPwLuma;
+  for (int p = 0; p < np; ++p) {
+    fp.pw_off[p][0] = fl.pw_off[p][0];
+    fp.pw_off[p][1] = fl.pw_off[p][1];
+  }
+  fp.pw = ctx->flow_Y;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   e = launch_prewarp(fp, s);
   if (e == cudaSuccess) e = launch_flow(fl, radius, s);
@@ -1847,6 +1865,10 @@ int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const flo
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e == cudaSuccess && best < 0) e = cudaErrorInvalidValue;
+  // The default shape stays unless another is clearly faster: the shapes time
+  // within a few per cent of each other when the fuse runs alone, and the
+  // default overlaps best with the other stages of the frame pipeline.
+  if (e == cudaSuccess && ms[0] > 0.0f && ms[best] > kTuneMargin * ms[0]) best = 0;
   // Keep the winner: its tile list goes back into the context.
   if (e == cudaSuccess) {
     bt.clear();
@@ -2277,6 +2299,9 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
         best = sh;
       }
     }
+    // as for one rig: the default shape unless another is clearly faster
+    const float t0 = ms[(size_t)r * kNumTileShapes];
+    if (t0 > 0.0f && best_ms > kTuneMargin * t0) best = 0;
     cur[r] = best;
   }
   if (e0) cudaEventDestroy(e0);

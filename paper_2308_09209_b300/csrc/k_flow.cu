@@ -3,8 +3,9 @@
 // 17-18). The paper takes it from a library routine; this is a
 // coarse-to-fine block matcher on integer luminance:
 //
-// k_flow_luma:  Y = round-half-even(clamp((R + 2G + B) / 4, 0, 255)) of both
-//               cameras' float32 pre-warped band images (uint8).
+// luminance:    Y = round-half-even(clamp((R + 2G + B) / 4, 0, 255)) of both
+//               cameras' float32 pre-warped band samples (uint8), written by
+//               the band pre-warp itself (k_prewarp_band, kFlagPwLuma).
 // k_flow_down:  the next pyramid level, (a + b + c + d + 2) >> 2 over 2 x 2
 //               blocks, the last row / column repeated for odd sizes.
 // k_flow_match: per pixel of a level and direction, the displacement d with
@@ -40,19 +41,6 @@ constexpr int kFlowThreads = 256;
 constexpr int kWin = 3;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-__global__ void __launch_bounds__(kFlowThreads) k_flow_luma(const FlowParams P) {
-  const int pair = blockIdx.y >> 1, side = blockIdx.y & 1;
-  const int w = P.lev[0].w[pair], h = P.lev[0].h[pair];
-  const int n = w * h;
-  const float4 *src = P.pw + P.pw_off[pair][side];
-  uint8_t *Y = P.Y + P.lev[0].y_off[pair][side];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float4 v = __ldg(src + i);
-    const float s = __fmul_rn(__fadd_rn(__fadd_rn(v.x, __fmul_rn(2.0f, v.y)), v.z), 0.25f);
-    Y[i] = (uint8_t)__float2int_rn(fminf(fmaxf(s, 0.0f), 255.0f));
-  }
-}
 
 __global__ void __launch_bounds__(kFlowThreads) k_flow_down(const FlowParams P, int lev) {
   const int pair = blockIdx.y >> 1, side = blockIdx.y & 1;
@@ -324,7 +312,6 @@ cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s) {
   if (p.n_pairs <= 0) return cudaSuccess;
   if (radius < 1 || radius > kFlowMaxRadius) return cudaErrorInvalidValue;
   static_assert(kMX * kMY == 4 * kFlowThreads && kFlowLevels >= 2, "2 x 2 pixels per thread; a level above the finest");
-  k_flow_luma<<<flow_grid(p, 0), kFlowThreads, 0, s>>>(p);
   for (int lev = 1; lev < kFlowLevels; ++lev) k_flow_down<<<flow_grid(p, lev), kFlowThreads, 0, s>>>(p, lev);
   for (int lev = kFlowLevels - 1; lev >= 1; --lev)
     k_flow_match<<<flow_tiles(p, lev, kMX, kMY), kFlowThreads, 0, s>>>(p, lev, radius);

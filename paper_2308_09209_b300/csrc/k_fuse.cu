@@ -181,15 +181,25 @@ __device__ __forceinline__ float3 src_bilinear(const uint8_t *__restrict__ src, 
 
 struct Window {
   int x0, y0, w, h, ok;
+  int a16;                           // staged in 16-pixel groups from 16-byte aligned rows (x0 % 16 == 0)
 };
+
+// Rows of the frame start on 16-byte boundaries (base and pitch), so a
+// 16-pixel group starting at a multiple of 16 pixels is three aligned
+// 16-byte words.
+__device__ __forceinline__ bool rows16(const uint8_t *src, const CamDev &c) {
+  return ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)c.pitch) & 15u) == 0;
+}
 
 // Source window of the panorama rectangle [rx0, rx1] x [ry0, ry1] (inclusive)
 // in camera c: the bounding box of the mapped corners plus one pixel of margin
 // and the right / bottom tap, clipped to the frame. Computed by one warp (lane
 // & 3 picks a corner); every lane returns the same window. ok = 0 when a corner
-// maps behind the camera, the box is empty or it exceeds the capacity.
+// maps behind the camera, the box is empty or it exceeds the capacity. With
+// a16 (rows16) the left edge moves down to a multiple of 16 pixels when the
+// wider window still fits, so that staging takes aligned 16-pixel groups.
 template <int kStride, int kRows>
-__device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry1) {
+__device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry1, bool a16) {
   const int k = threadIdx.x & 3;
   const int px = (k & 1) ? rx1 : rx0;
   const int py = (k & 2) ? ry1 : ry0;
@@ -214,6 +224,9 @@ __device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry
   W.y0 = max(0, (int)floorf(lo_y) - 1);
   const int x1 = min(c.w - 1, (int)floorf(hi_x) + 2);
   const int y1 = min(c.h_px - 1, (int)floorf(hi_y) + 2);
+  // aligned: 16 ceil((w + 1) / 16) words per row (the word past the window included)
+  W.a16 = (kStride % 16 == 0 && a16 && x1 - (W.x0 & ~15) + 1 <= kStride - 1) ? 1 : 0;
+  if (W.a16) W.x0 &= ~15;
   W.w = x1 - W.x0 + 1;
   W.h = y1 - W.y0 + 1;
   W.ok = (front && W.w >= 2 && W.h >= 2 && W.w <= kStride && W.h <= kRows) ? 1 : 0;
@@ -222,7 +235,7 @@ __device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry
 
 __device__ __forceinline__ Window no_window() {
   Window W;
-  W.x0 = W.y0 = W.w = W.h = W.ok = 0;
+  W.x0 = W.y0 = W.w = W.h = W.ok = W.a16 = 0;
   return W;
 }
 
@@ -233,8 +246,51 @@ __device__ __forceinline__ Window no_window() {
 // a tap with zero weight there still reads a finite value.
 template <int kStride>
 __device__ void stage_window(const uint8_t *__restrict__ src, const CamDev &c, const Window &W, uint32_t *s) {
-  const int G = min((W.w + 4) >> 2, kStride >> 2);
   for (int i = threadIdx.x; i < kStride + 4; i += blockDim.x) s[W.h * kStride + i] = kXByte << 24;
+  if (W.a16) {
+    // 16 pixels (48 bytes, three aligned 16-byte words) per step; groups that
+    // reach past the frame's right edge are read byte by byte (0x64 words
+    // past the edge).
+    const int G16 = (W.w + 16) >> 4;               // <= kStride / 16 (warp_window checked)
+    const float inv16 = rcp_approx((float)G16);
+    const int rpp16 = (int)(((float)kFuseThreads + 0.5f) * inv16);
+    const int rf = (int)(((float)threadIdx.x + 0.5f) * inv16);
+    const int g16 = threadIdx.x - rf * G16;
+    if (rf >= rpp16 || rf >= W.h) return;
+    const int px = W.x0 + 16 * g16;
+    const int nv = min(16, max(0, c.w - px));      // pixels of the group inside the frame
+    const uint8_t *row = src + (size_t)(W.y0 + rf) * c.pitch + 3 * px;
+    const size_t rstep = (size_t)rpp16 * (size_t)c.pitch;
+    uint32_t *dst = s + rf * kStride + 16 * g16;
+    for (int r = rf; r < W.h; r += rpp16, row += rstep, dst += rpp16 * kStride) {
+      uint32_t q[12];
+      if (nv == 16) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(row));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(row) + 1);
+        const uint4 d = __ldg(reinterpret_cast<const uint4 *>(row) + 2);
+        q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+        q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+        q[8] = d.x; q[9] = d.y; q[10] = d.z; q[11] = d.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) q[k] = 0u;
+#pragma unroll
+        for (int j = 0; j < 48; ++j)
+          if (j < 3 * nv) q[j >> 2] |= (uint32_t)__ldg(row + j) << ((j & 3) * 8);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t q0 = q[3 * k], q1 = q[3 * k + 1], q2 = q[3 * k + 2];
+        const uint32_t p0 = __byte_perm(q0, kXByte, 0x4210u);
+        const uint32_t p1 = (__byte_perm(q0, q1, 0x0543u) & 0x00ffffffu) | (kXByte << 24);
+        const uint32_t p2 = (__byte_perm(q1, q2, 0x0432u) & 0x00ffffffu) | (kXByte << 24);
+        const uint32_t p3 = __byte_perm(q2, kXByte, 0x4321u);
+        *reinterpret_cast<uint4 *>(dst + 4 * k) = make_uint4(p0, p1, p2, p3);
+      }
+    }
+    return;
+  }
+  const int G = min((W.w + 4) >> 2, kStride >> 2);
   // G <= kStride / 4 <= blockDim.x: thread i takes group i % G of rows i / G,
   // i / G + rows_per_pass, ... The quotients come from an approximate
   // reciprocal: floor((i + 1/2) / G) = floor(i / G), and (i + 1/2) / G lies at
@@ -951,7 +1007,7 @@ __device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDes
   const int k = t.idx;
   const CamDev &c = P.cam[k];
   if (warp == 0) {
-    const Window W = warp_window<G::kStride, G::kRows>(c, tx0 + cx0, ty0, tx0 + cx1 - 1, ty1);
+    const Window W = warp_window<G::kStride, G::kRows>(c, tx0 + cx0, ty0, tx0 + cx1 - 1, ty1, rows16(P.src[k], c));
     if ((threadIdx.x & 31) == 0) {
       h.sW[0] = W;
       if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
@@ -1103,12 +1159,14 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
     if (!empty) {
       if (t.kind == kTileOwnPart) {
         need = warp == 0;
-        if (need) W = warp_window<S, G::kRows>(P.cam[t.idx], px0, ty0, px1, ty1);
+        if (need) W = warp_window<S, G::kRows>(P.cam[t.idx], px0, ty0, px1, ty1, rows16(P.src[t.idx], P.cam[t.idx]));
       } else {
         const BandDev B = P.band[t.idx];
         const bool rows_out = ty0 < B.y0 || ty1 >= B.y1;
         need = warp == 0 ? (px0 < B.x0 || (rows_out && px1 >= B.x0)) : (px1 >= B.x1 || (rows_out && px0 < B.x1));
-        if (need) W = warp_window<S, G::kRows>(P.cam[t.idx + warp], px0, ty0, px1, ty1);
+        if (need)
+          W = warp_window<S, G::kRows>(P.cam[t.idx + warp], px0, ty0, px1, ty1,
+                                       rows16(P.src[t.idx + warp], P.cam[t.idx + warp]));
       }
     }
     if (lane == 0) {
@@ -1192,7 +1250,8 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
   const int rx1 = min(rx0 + kTileW, B.x1) - 1, ry1 = min(ry0 + kTileH, B.y1) - 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < 2) {
-    const Window W = warp_window<S, G::kRows>(P.cam[pt.pair + warp], rx0, ry0, rx1, ry1);
+    const Window W = warp_window<S, G::kRows>(P.cam[pt.pair + warp], rx0, ry0, rx1, ry1,
+                                               rows16(P.src[pt.pair + warp], P.cam[pt.pair + warp]));
     if (lane == 0) {
       sW[warp] = W;
       if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
@@ -1210,8 +1269,10 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
     // the frame path (offset form) and STITCH_FP16_INTERMEDIATE store halves,
     // the flow and the correspondence fit float32 values
     const bool hstore = kHalf || offset;
+    const bool luma = !offset && (P.flags & kFlagPwLuma) != 0;
     uint2 *dst2 = reinterpret_cast<uint2 *>(P.pw) + P.pw_off[pt.pair][side];
     float4 *dst4 = reinterpret_cast<float4 *>(P.pw) + P.pw_off[pt.pair][side];
+    uint8_t *dsty = reinterpret_cast<uint8_t *>(P.pw) + P.pw_off[pt.pair][side];
     if (offset && W.ok) {
       // Every clamped point of the piece lies in the window (clipped to the
       // frame); a far tap past the frame reads the staged 0x64 column / row
@@ -1280,10 +1341,15 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
           sy = fminf(fmaxf(sy, 0.0f), c.hm1);
           v = W.ok ? win_bilinear<S>(win[side], W, sx, sy) : src_bilinear(P.src[k], c, sx, sy);
         }
-        if (hstore)
+        if (luma) {
+          // the flow's luminance: round-half-even(clamp((R + 2G + B) / 4, 0, 255))
+          const float y4 = __fmul_rn(__fadd_rn(__fadd_rn(v.x, __fmul_rn(2.0f, v.y)), v.z), 0.25f);
+          dsty[o] = (uint8_t)__float2int_rn(fminf(fmaxf(y4, 0.0f), 255.0f));
+        } else if (hstore) {
           dst2[o] = make_uint2(h2_bits(__floats2half2_rn(v.x, v.y)), h2_bits(__floats2half2_rn(v.z, 0.0f)));
-        else
+        } else {
           dst4[o] = make_float4(v.x, v.y, v.z, 0.0f);
+        }
       }
     }
   }

@@ -45,6 +45,10 @@ constexpr int kLutBytes = 3 * kLutEntries;
 // Internal fuse flag (above the public STITCH_* bits): the band pre-warp of a
 // frame stores v - 128 (the fused path's offset form) instead of v.
 constexpr int kFlagPwOffset = 1 << 20;
+// Band pre-warp for the flow: write the integer luminance of the float32
+// samples (one byte per band pixel and side, element offsets pw_off) instead
+// of the samples themselves.
+constexpr int kFlagPwLuma = 1 << 21;
 
 // Integer statistics of one frame, written by the stats kernel (K1) and read
 // by the estimate kernel (K2). Frame T uses slot T % kRawSlots.
@@ -262,8 +266,7 @@ struct FlowLevelDev {
 struct FlowParams {
   int n_pairs;
   FlowLevelDev lev[kFlowLevels];
-  const float4 *pw;                   // float32 pre-warped bands (layout of FuseParams::pw)
-  size_t pw_off[kMaxPairs][2];
+  size_t pw_off[kMaxPairs][2];        // full-level luminance of band p, left / right camera (offsets into Y)
   uint8_t *Y;
   int16_t *dx, *dy;
   float2 *out_ij[kMaxPairs], *out_ji[kMaxPairs];

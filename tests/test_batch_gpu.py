@@ -34,7 +34,9 @@ def test_every_tile_shape_gives_the_same_panorama():
         assert torch.equal(out, ref), f"shape {S.TILE_SHAPES[shape]}"
     assert fits >= 3
     shape, ms = S.stitch_autotune(pr.st.ctx, frames, fij, fji, pr.st.new_pano(), reps=3)
-    assert ms[shape] > 0 and ms[shape] == ms[ms > 0].min()
+    # the fastest shape, or the default one when none beats it by more than 5 %
+    fastest = ms[ms > 0].min()
+    assert ms[shape] > 0 and (ms[shape] == fastest or (shape == 0 and fastest > 0.95 * ms[0])), ms
     assert S.stitch_tile_shape(pr.st.ctx)[0] == shape
     out = pr.st.frame(frames, fij, fji)
     torch.cuda.synchronize()
@@ -141,8 +143,10 @@ def test_full_batch_against_the_oracle_on_sampled_pixels():
     shapes, ms = S.stitch_batch_autotune(b, fr, fij, fji, pano, reps=2)
     assert S.stitch_batch_tile_shapes(b) == shapes and ms.shape == (len(rigs), S.STITCH_TILE_SHAPES)
     for r, sh in enumerate(shapes):
-        # every rig's chosen shape is its fastest fitting one (the other rigs at their shapes then)
-        assert ms[r, sh] > 0 and ms[r, sh] == ms[r][ms[r] > 0].min()
+        # every rig's chosen shape is its fastest fitting one (the other rigs at their shapes then),
+        # or the default one when none beats it by more than 5 %
+        fastest = ms[r][ms[r] > 0].min()
+        assert ms[r, sh] > 0 and (ms[r, sh] == fastest or (sh == 0 and fastest > 0.95 * ms[r, 0])), ms[r]
     fr, fij, fji, pano = _flat(rigs, n_frames)
     S.stitch_batch_sequence(b, n_frames, fr, fij, fji, pano)
     torch.cuda.synchronize()
