@@ -375,7 +375,9 @@ int prepare_estimate_params(const stitch_config *cfg, StatsParams &sp, int &grid
     rows += g.h[k];
     max_h = std::max(max_h, g.h[k]);
   }
-  const int rpb = (int)std::max(1ll, (rows + 4ll * sms - 1) / (4ll * sms));
+  // about two statistics blocks per SM: the per-block clearing and flushing
+  // of the shared histograms is then a small share of the work
+  const int rpb = (int)std::max(1ll, (rows + 2ll * sms - 1) / (2ll * sms));
   sp = StatsParams{};
   sp.n_cams = g.n;
   sp.rows_per_block = rpb;
@@ -963,7 +965,9 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     rows += g.h[k];
     max_h = std::max(max_h, g.h[k]);
   }
-  const int rpb = (int)std::max(1ll, (rows + 4ll * sms - 1) / (4ll * sms));
+  // about two statistics blocks per SM: the per-block clearing and flushing
+  // of the shared histograms is then a small share of the work
+  const int rpb = (int)std::max(1ll, (rows + 2ll * sms - 1) / (2ll * sms));
   StatsParams &sp = ctx->sp;
   sp = StatsParams{};
   sp.n_cams = g.n;
@@ -1936,7 +1940,7 @@ struct BatchGraph {
   int n_frames = 0;
   cudaGraphExec_t exec = nullptr;
   FuseParams *params = nullptr;       // n_frames x n_rigs parameter blocks
-  int *counters = nullptr;            // two work counters per frame (band / partly covered, fully covered)
+  int *counters = nullptr;            // three work counters per frame (partly covered [+ band], band, fully covered)
 };
 
 struct stitch_batch {
@@ -1946,8 +1950,11 @@ struct stitch_batch {
   bool half = false;
   int cams = 0, pairs = 0;            // totals over the rigs
   std::vector<int> cam_off, pair_off;
-  MultiItem *fuse_items = nullptr;    // band and partly covered tiles of every rig
-  int n_fuse_items = 0;
+  MultiItem *fuse_items = nullptr;    // partly covered pieces of every rig (and the band pieces when the
+  int n_fuse_items = 0;               // rigs' tile shapes differ)
+  MultiItem *band_items = nullptr;    // band pieces of every rig (rigs of one tile shape)
+  int n_band_items = 0;
+  int grid_band = 0;
   MultiItem *own_items = nullptr;     // fully covered own tiles of every rig
   int n_own_items = 0;
   int grid_own = 0;
@@ -1999,36 +2006,49 @@ int batch_items(stitch_batch *b, const std::vector<int> &shapes) {
         for (int x = g.band[p][0]; x < g.band[p][1]; x += kTileW)
           pw.push_back(MultiItem{r, 0, TileDesc{}, PwTile{p, x, y}});
   }
-  // the general pieces (costliest per pixel) first, so that the dynamic schedule ends evenly
-  part.insert(part.end(), band.begin(), band.end());
-  band.swap(part);
+  int uniform = shapes.empty() ? 0 : shapes[0];
+  for (int sh : shapes)
+    if (sh != uniform) uniform = -1;
+  // Rigs of one tile shape: the band pieces in their own persistent kernel
+  // (as for a single rig). Otherwise they follow the partly covered pieces,
+  // which go first (costliest per pixel) so that the dynamic schedule ends
+  // evenly.
+  if (uniform < 0) {
+    part.insert(part.end(), band.begin(), band.end());
+    band.clear();
+  }
   cudaFree(b->fuse_items);
+  cudaFree(b->band_items);
   cudaFree(b->own_items);
   cudaFree(b->pw_items);
   b->fuse_items = nullptr;
+  b->band_items = nullptr;
   b->own_items = nullptr;
   b->pw_items = nullptr;
-  cudaError_t e = cudaMalloc(&b->fuse_items, band.size() * sizeof(MultiItem) + 16);
+  cudaError_t e = cudaMalloc(&b->fuse_items, part.size() * sizeof(MultiItem) + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&b->band_items, band.size() * sizeof(MultiItem) + 16);
   if (e == cudaSuccess) e = cudaMalloc(&b->own_items, full.size() * sizeof(MultiItem) + 16);
   if (e == cudaSuccess) e = cudaMalloc(&b->pw_items, pw.size() * sizeof(MultiItem) + 16);
+  if (e == cudaSuccess && !part.empty())
+    e = cudaMemcpy(b->fuse_items, part.data(), part.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !band.empty())
-    e = cudaMemcpy(b->fuse_items, band.data(), band.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(b->band_items, band.data(), band.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !full.empty())
     e = cudaMemcpy(b->own_items, full.data(), full.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !pw.empty())
     e = cudaMemcpy(b->pw_items, pw.data(), pw.size() * sizeof(MultiItem), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return batch_err(b, STITCH_ECUDA, std::string("batch work lists: ") + cudaGetErrorString(e));
-  b->n_fuse_items = (int)band.size();
+  b->n_fuse_items = (int)part.size();
+  b->n_band_items = (int)band.size();
   b->n_own_items = (int)full.size();
   b->n_pw_items = (int)pw.size();
   int sms = 148, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int uniform = shapes.empty() ? 0 : shapes[0];
-  for (int sh : shapes)
-    if (sh != uniform) uniform = -1;
   const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, uniform));
   b->grid = std::max(1, std::min(b->n_fuse_items, per_sm * sms));
+  const int per_sm_band = uniform < 0 ? 1 : std::max(1, fuse_band_multi_blocks_per_sm(b->half, uniform));
+  b->grid_band = std::max(1, std::min(b->n_band_items, per_sm_band * sms));
   const int per_sm_own = std::max(1, fuse_own_multi_blocks_per_sm(uniform));
   b->grid_own = std::max(1, std::min(b->n_own_items, per_sm_own * sms));
   b->shapes = shapes;
@@ -2132,7 +2152,7 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
     bg.key = key;
     bg.n_frames = n_frames;
     cudaError_t e = cudaMalloc(&bg.params, (size_t)n_frames * R * sizeof(FuseParams));
-    if (e == cudaSuccess) e = cudaMalloc(&bg.counters, (size_t)n_frames * 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&bg.counters, (size_t)n_frames * 3 * sizeof(int));
     std::vector<FuseParams> hp((size_t)n_frames * R);
     for (int t = 0; t < n_frames; ++t)
       for (int r = 0; r < R; ++r) {
@@ -2189,10 +2209,12 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       cudaStream_t sC = sC2[t % 2];
       chk(cudaStreamWaitEvent(sC, ev[kE][t % 8], 0));
       chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
-      chk(cudaMemsetAsync(bg.counters + 2 * t, 0, 2 * sizeof(int), sC));
-      MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + 2 * t};
+      chk(cudaMemsetAsync(bg.counters + 3 * t, 0, 3 * sizeof(int), sC));
+      MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + 3 * t};
       chk(launch_fuse_multi(mf, b->half, b->uniform, b->grid, sC));
-      MultiParams mo{bg.params, t * R, b->n_own_items, b->own_items, bg.counters + 2 * t + 1};
+      MultiParams mb{bg.params, t * R, b->n_band_items, b->band_items, bg.counters + 3 * t + 1};
+      chk(launch_fuse_band_multi(mb, b->half, b->uniform, b->grid_band, sC));
+      MultiParams mo{bg.params, t * R, b->n_own_items, b->own_items, bg.counters + 3 * t + 2};
       chk(launch_fuse_own_multi(mo, b->uniform, b->grid_own, sC));
       chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
@@ -2241,7 +2263,7 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
   FuseParams *params = nullptr;
   int *counter = nullptr;
   if (e == cudaSuccess) e = cudaMalloc(&params, R * sizeof(FuseParams));
-  if (e == cudaSuccess) e = cudaMalloc(&counter, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&counter, 3 * sizeof(int));
   std::vector<FuseParams> hp(R);
   for (int r = 0; r < R; ++r) {
     stitch_ctx *c = b->ctx[r];
@@ -2261,10 +2283,12 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
   // Both fuse launches of the frame with the current work lists, timed.
   auto timed = [&](float &ms) {
     MultiParams mf{params, 0, b->n_fuse_items, b->fuse_items, counter};
-    MultiParams mo{params, 0, b->n_own_items, b->own_items, counter + 1};
+    MultiParams mb{params, 0, b->n_band_items, b->band_items, counter + 1};
+    MultiParams mo{params, 0, b->n_own_items, b->own_items, counter + 2};
     auto both = [&]() {
-      cudaError_t x = cudaMemsetAsync(counter, 0, 2 * sizeof(int), b->cap);
+      cudaError_t x = cudaMemsetAsync(counter, 0, 3 * sizeof(int), b->cap);
       if (x == cudaSuccess) x = launch_fuse_multi(mf, b->half, b->uniform, b->grid, b->cap);
+      if (x == cudaSuccess) x = launch_fuse_band_multi(mb, b->half, b->uniform, b->grid_band, b->cap);
       if (x == cudaSuccess) x = launch_fuse_own_multi(mo, b->uniform, b->grid_own, b->cap);
       return x;
     };
@@ -2330,6 +2354,7 @@ void stitch_batch_destroy(stitch_batch *b) {
   cudaDeviceSynchronize();
   for (auto &g : b->graphs) free_batch_graph(g);
   cudaFree(b->fuse_items);
+  cudaFree(b->band_items);
   cudaFree(b->own_items);
   cudaFree(b->pw_items);
   if (b->cap) cudaStreamDestroy(b->cap);

@@ -396,6 +396,12 @@ struct __align__(16) SmemPw {
   __align__(16) uint32_t win[2][WinGeom<kTileW, kTileH>::kAlloc];
 };
 
+// The same for the multi-rig band pre-warp, with the item's rig parameters.
+struct __align__(16) SmemPwMulti {
+  FuseParams sp;
+  SmemPw pw;
+};
+
 template <int TW, int TH, int NW>
 constexpr size_t smem_bytes() {
   return (sizeof(SmemHead) + 15) / 16 * 16 + sizeof(SmemTile<TW, TH, NW>);
@@ -1442,11 +1448,11 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own(const FuseParams P
 template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParams M) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  SmemPwMulti &sm = *reinterpret_cast<SmemPwMulti *>(smem);
   const MultiItem it = M.items[blockIdx.x];
-  copy_params(h.sp, M.params + M.base + it.rig);
+  copy_params(sm.sp, M.params + M.base + it.rig);
   __syncthreads();
-  prewarp_piece<kHalf>(h.sp, it.pw, h.sW, tile_smem<kTileW, kTileH, 2>(smem).win);
+  prewarp_piece<kHalf>(sm.sp, it.pw, sm.pw.sW, sm.pw.win);
 }
 
 // Next item of a persistent multi-rig launch; reloads the rig's parameters
@@ -1516,6 +1522,18 @@ __global__ void __launch_bounds__(kFuseThreads, 3) k_fuse_multi_mixed(const Mult
   }
 }
 
+// Persistent fuse over the band pieces of several rigs that share one tile
+// shape (the single-rig band kernel's register budget and shared memory).
+template <bool kHalf, int TW, int TH>
+__global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_band_multi(const MultiParams M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemHead &h = *reinterpret_cast<SmemHead *>(smem);
+  SmemBand<TW, TH> &sb = *reinterpret_cast<SmemBand<TW, TH> *>(smem + (sizeof(SmemHead) + 15) / 16 * 16);
+  if (threadIdx.x == 0) h.rig = -1;
+  MultiItem it;
+  while (next_item(M, h, it)) fuse_band_piece<kHalf, TW, TH>(h.sp, it.tile, h, sb.out);
+}
+
 // Persistent fuse over the fully covered own tiles of several rigs (one shape
 // for all rigs, or each rig's own).
 template <int TW, int TH>
@@ -1550,7 +1568,7 @@ namespace {
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kPwSmem = sizeof(SmemPw);                      // single-rig band pre-warp
-constexpr size_t kPwMultiSmem = smem_bytes<kTileW, kTileH, 2>();    // multi-rig: the rig's parameters too
+constexpr size_t kPwMultiSmem = sizeof(SmemPwMulti);                // multi-rig: the rig's parameters too
 constexpr size_t kMixSmem =
     cmax(cmax(smem_bytes<64, 32, 2>(), smem_bytes<64, 16, 2>()), cmax(smem_bytes<32, 32, 2>(), smem_bytes<128, 16, 2>()));
 constexpr size_t kMixOwnSmem =
@@ -1571,6 +1589,8 @@ cudaError_t setup_shape() {
   if (e == cudaSuccess) e = set_smem(k_fuse_multi<false, TW, TH>, smem_bytes<TW, TH, 2>());
   if (e == cudaSuccess) e = set_smem(k_fuse_multi<true, TW, TH>, smem_bytes<TW, TH, 2>());
   if (e == cudaSuccess) e = set_smem(k_fuse_own_multi<TW, TH>, smem_bytes<TW, TH, 1>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_band_multi<false, TW, TH>, band_smem_bytes<TW, TH>());
+  if (e == cudaSuccess) e = set_smem(k_fuse_band_multi<true, TW, TH>, band_smem_bytes<TW, TH>());
   return e;
 }
 
@@ -1629,6 +1649,20 @@ void fuse_by_half(const FuseParams &p, cudaStream_t s) {
     if (!res_own) res_own = per_sm(k_fuse_own<TW, TH>, kOwn);
     k_fuse_own<TW, TH><<<persistent_grid(p.n_full, res_own), kFuseThreads, kOwn, s>>>(p);
   }
+}
+
+template <int TW, int TH>
+void band_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t s) {
+  if (half)
+    k_fuse_band_multi<true, TW, TH><<<grid, kFuseThreads, band_smem_bytes<TW, TH>(), s>>>(m);
+  else
+    k_fuse_band_multi<false, TW, TH><<<grid, kFuseThreads, band_smem_bytes<TW, TH>(), s>>>(m);
+}
+
+template <int TW, int TH>
+int band_multi_per_sm(bool half) {
+  return half ? per_sm(k_fuse_band_multi<true, TW, TH>, band_smem_bytes<TW, TH>())
+              : per_sm(k_fuse_band_multi<false, TW, TH>, band_smem_bytes<TW, TH>());
 }
 
 template <int TW, int TH>
@@ -1724,6 +1758,28 @@ cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cud
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_fuse_band_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s) {
+  if (m.n_items <= 0) return cudaSuccess;
+  switch (shape) {
+    case 0: band_multi_by_half<64, 32>(m, half, grid, s); break;
+    case 1: band_multi_by_half<64, 16>(m, half, grid, s); break;
+    case 2: band_multi_by_half<32, 32>(m, half, grid, s); break;
+    case 3: band_multi_by_half<128, 16>(m, half, grid, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int fuse_band_multi_blocks_per_sm(bool half, int shape) {
+  switch (shape) {
+    case 0: return band_multi_per_sm<64, 32>(half);
+    case 1: return band_multi_per_sm<64, 16>(half);
+    case 2: return band_multi_per_sm<32, 32>(half);
+    case 3: return band_multi_per_sm<128, 16>(half);
+    default: return 0;
+  }
 }
 
 int fuse_own_multi_blocks_per_sm(int shape) {

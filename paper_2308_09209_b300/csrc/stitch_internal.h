@@ -303,6 +303,8 @@ cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int gr
 int fuse_multi_blocks_per_sm(bool half, int shape);
 cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);
 int fuse_own_multi_blocks_per_sm(int shape);
+cudaError_t launch_fuse_band_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s);
+int fuse_band_multi_blocks_per_sm(bool half, int shape);
 cudaError_t fuse_setup_attributes(int max_halo);
 // The correspondence sums of every pair (blocks per pair, fixed-order totals).
 cudaError_t launch_corr(const CorrParams &p, int blocks, cudaStream_t s);
