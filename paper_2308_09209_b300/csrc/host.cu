@@ -472,6 +472,8 @@ struct stitch_ctx {
   EstimateParams ep{};
   FuseParams fp{};
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t net_stream = nullptr;  // learned contexts: the network beside the plain estimate
+  cudaEvent_t net_ev[2] = {};         // fork (statistics done) and join (network done)
   cudaStream_t pipe[kPipeStreams] = {};   // statistics, estimate, band pre-warp and two fuse streams of a
                                           // recorded sequence
   cudaEvent_t pev[4][8] = {};         // per-stage completion events (stats, pre-warp, estimate, fuse) by t % 8
@@ -562,10 +564,11 @@ int launch_stats_for(stitch_ctx *ctx, const uint8_t *const *frames, int T, cudaS
 
 int launch_estimate_for(stitch_ctx *ctx, cudaStream_t s) {
   cudaEvent_t e0 = prof_mark(ctx, s);
-  cudaError_t e = launch_estimate(ctx->ep, s);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+  cudaError_t e = cudaSuccess;
   if (ctx->mlp && ctx->ls && ctx->g.n > 1) {
-    // Learned estimate of frame T (after the plain one): features, network, residual test.
+    // Learned estimate of frame T: the features and the network read only
+    // the statistics, so they run on their own stream beside the plain
+    // estimate; the residual test and re-chain join both.
     LearnedParams lp{};
     lp.n_cams = ctx->g.n;
     lp.n_pairs = ctx->g.n - 1;
@@ -575,13 +578,23 @@ int launch_estimate_for(stitch_ctx *ctx, cudaStream_t s) {
     lp.raw = ctx->raw;
     lp.state = ctx->state;
     lp.ls = ctx->ls;
-    e = launch_learned_features(lp, s);
+    cudaStream_t n = ctx->net_stream;
+    e = cudaEventRecord(ctx->net_ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(n, ctx->net_ev[0], 0);
+    if (e == cudaSuccess) e = launch_learned_features(lp, n);
     if (e != cudaSuccess) return cuda_err(ctx, e, "learned features launch");
     const int rc = stitch_mlp_forward(ctx->mlp, reinterpret_cast<const uint16_t *>(&ctx->ls->feat[0][0]), lp.n_pairs,
-                                      &ctx->ls->y[0][0], reinterpret_cast<stitch_stream_t>(s));
+                                      &ctx->ls->y[0][0], reinterpret_cast<stitch_stream_t>(n));
     if (rc != STITCH_OK) return set_err(ctx, rc, std::string("network forward: ") + g_last_error);
-    e = launch_learned_select(lp, s);
+    e = cudaEventRecord(ctx->net_ev[1], n);
+    if (e == cudaSuccess) e = launch_estimate(ctx->ep, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
+    e = cudaStreamWaitEvent(s, ctx->net_ev[1], 0);
+    if (e == cudaSuccess) e = launch_learned_select(lp, s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "learned select launch");
+  } else {
+    e = launch_estimate(ctx->ep, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "estimate launch");
   }
   cudaEvent_t e1 = prof_mark(ctx, s);
   prof_pair(ctx, e0, e1, 1);
@@ -950,6 +963,8 @@ int stitch_init(const stitch_config *cfg, stitch_ctx **out) {
     e = cudaStreamCreateWithFlags(&ctx->pipe[i], cudaStreamNonBlocking);
   for (int a = 0; a < 4 && e == cudaSuccess; ++a)
     for (int b = 0; b < 8 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&ctx->pev[a][b], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->net_stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ctx->net_ev[k], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     const int code = cuda_err(nullptr, e, "stitch_init");
     stitch_destroy(ctx);
@@ -1703,6 +1718,8 @@ int stitch_load_state(stitch_ctx *ctx, const void *buf, size_t size) {
                      cudaMemcpyHostToDevice);
     else
       e = cudaMemset(ctx->ls, 0, sizeof(LearnedState));
+    // the learned features follow the restored frame index
+    if (e == cudaSuccess) e = cudaMemcpy(&ctx->ls->frame, &ctx->state->T, sizeof(int), cudaMemcpyDeviceToDevice);
   }
   // no stitched image precedes the restored state
   if (e == cudaSuccess && ctx->out_hist) e = cudaMemset(ctx->out_hist, 0, 2 * 768 * sizeof(uint32_t));
@@ -1753,6 +1770,9 @@ int stitch_attach_mlp(stitch_ctx *ctx, stitch_mlp *mlp) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, e, "device synchronize");
   ctx->mlp = mlp;
+  // the learned features start at the next frame to be estimated
+  if (mlp) e = cudaMemcpy(&ctx->ls->frame, &ctx->state->T, sizeof(int), cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "learned frame index");
   // Recorded sequences embed the launches of the estimate stage: record again.
   for (auto &ge : ctx->graphs) {
     if (ge.exec) cudaGraphExecDestroy(ge.exec);
@@ -2387,6 +2407,9 @@ void stitch_destroy(stitch_ctx *ctx) {
     cudaEventDestroy(pp.b);
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->net_stream) cudaStreamDestroy(ctx->net_stream);
+  for (int k = 0; k < 2; ++k)
+    if (ctx->net_ev[k]) cudaEventDestroy(ctx->net_ev[k]);
   for (int i = 0; i < kPipeStreams; ++i)
     if (ctx->pipe[i]) cudaStreamDestroy(ctx->pipe[i]);
   for (int a = 0; a < 4; ++a)

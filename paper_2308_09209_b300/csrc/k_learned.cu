@@ -1,6 +1,8 @@
-// Learned estimate of the pair matrices inside the per-frame pipeline. Runs
-// after the plain estimate (K2) of frame T, which has stored the window's
-// exact Eq. 3 terms, the plain M of every pair and advanced the frame index.
+// Learned estimate of the pair matrices inside the per-frame pipeline.
+// k_learned_features and the network run beside the plain estimate (K2) of
+// frame T, on the statistics alone; k_learned_select runs after both, when K2
+// has stored the window's exact Eq. 3 terms and the plain M of every pair and
+// advanced the frame index.
 //
 // k_learned_features: per pair, keep frame T's overlap histograms in a ring,
 // pool them over the window {T-W+1..T} and write the network's features
@@ -35,10 +37,13 @@ __global__ void __launch_bounds__(256) k_learned_features(const LearnedParams P)
   const int p = blockIdx.x;
   const int side = blockIdx.y / 3, ch = blockIdx.y % 3;
   const int v = threadIdx.x;
-  const int frame = P.state->T - 1;
+  LearnedState *L = P.ls;
+  // the frame being estimated: this kernel runs beside the plain estimate,
+  // which advances the colour state's T, so the index comes from the learned
+  // state (k_learned_select moves it on after both)
+  const int frame = L->frame;
   const int slot = frame % kMaxWindow;
   const RawStats *raw = P.raw + (frame % P.raw_slots);
-  LearnedState *L = P.ls;
   const int nw = min(frame + 1, P.window);
   const uint32_t *cur = side == 0 ? &raw->Hi[p][0][0] : &raw->Hj[p][0][0];
   __shared__ unsigned long long part[8];
@@ -133,6 +138,7 @@ __global__ void __launch_bounds__(256) k_learned_select(const LearnedParams P) {
     if (lane == 0) {
       L->n_learned += (unsigned long long)n_used;
       L->n_fallback += (unsigned long long)(np - n_used);
+      L->frame = S->T;                // the next frame's features
     }
   }
 }

@@ -223,7 +223,7 @@ struct LearnedState {
   double M_hat[kMaxPairs][9];
   double resid[kMaxPairs];
   int used[kMaxPairs];
-  int pad;
+  int frame;                          // the frame whose features are formed next (the colour state's T)
   unsigned long long n_learned, n_fallback;
 };
 
