@@ -1348,7 +1348,7 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
     if ((reinterpret_cast<uintptr_t>(flow_ij_dev[p]) | reinterpret_cast<uintptr_t>(flow_ji_dev[p])) & 7u)
       return set_err(ctx, STITCH_EINVAL, "flows must be 8-byte aligned");
   const int radius = std::max(1, (int)std::ceil((double)ctx->max_flow / (double)(1 << (kFlowLevels - 1))));
-  if (radius > kFlowMaxRadius) return set_err(ctx, STITCH_EINVAL, "max_flow above 32 px is beyond the flow search");
+  if (radius > kFlowMaxRadius) return set_err(ctx, STITCH_EINVAL, "max_flow above 16 px is beyond the flow search");
   // Level sizes and buffer layout.
   FlowParams fl{};
   fl.n_pairs = np;
@@ -1394,25 +1394,6 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
     fl.out_ij[p] = reinterpret_cast<float2 *>(flow_ij_dev[p]);
     fl.out_ji[p] = reinterpret_cast<float2 *>(flow_ji_dev[p]);
   }
-  // Candidates in the tie-break order: |e|^2, then e_y, then e_x.
-  auto order = [](int r, int8_t *out) {
-    std::vector<std::array<int, 2>> c;
-    for (int ey = -r; ey <= r; ++ey)
-      for (int ex = -r; ex <= r; ++ex) c.push_back({ex, ey});
-    std::stable_sort(c.begin(), c.end(), [](const std::array<int, 2> &a, const std::array<int, 2> &b) {
-      const int na = a[0] * a[0] + a[1] * a[1], nb = b[0] * b[0] + b[1] * b[1];
-      if (na != nb) return na < nb;
-      if (a[1] != b[1]) return a[1] < b[1];
-      return a[0] < b[0];
-    });
-    for (size_t i = 0; i < c.size(); ++i) {
-      out[2 * i] = (int8_t)c[i][0];
-      out[2 * i + 1] = (int8_t)c[i][1];
-    }
-    return (int)c.size();
-  };
-  fl.n_cand_top = order(radius, fl.cand_top);
-  order(1, fl.cand_fine);
   // The float32 band pre-warp, written as the full level's luminance, then
   // the flow.
   const float *none[kMaxPairs] = {};

@@ -255,7 +255,8 @@ struct RefineParams {
 // Band optical flow (k_flow.cu): a coarse-to-fine block matcher over the
 // luminance of both cameras' pre-warped band images.
 constexpr int kFlowLevels = 3;
-constexpr int kFlowMaxRadius = 8;     // coarsest search radius: max_flow up to 32 px
+constexpr int kFlowMaxRadius = 4;     // coarsest search radius: max_flow up to STITCH_MAX_FLOW = 16 px
+static_assert(STITCH_MAX_FLOW <= (float)(kFlowMaxRadius << (kFlowLevels - 1)), "the coarsest search covers max_flow");
 
 struct FlowLevelDev {
   int w[kMaxPairs], h[kMaxPairs];     // level size of every band
@@ -270,9 +271,6 @@ struct FlowParams {
   uint8_t *Y;
   int16_t *dx, *dy;
   float2 *out_ij[kMaxPairs], *out_ji[kMaxPairs];
-  int n_cand_top;                     // candidates of the coarsest level, in tie-break order
-  int8_t cand_top[2 * (2 * kFlowMaxRadius + 1) * (2 * kFlowMaxRadius + 1)];
-  int8_t cand_fine[18];               // the 3 x 3 refinement, in tie-break order
 };
 
 // One-frame colour transfer from pixel correspondences (k_corr.cu).

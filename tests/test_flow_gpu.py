@@ -79,12 +79,15 @@ def test_flow_argument_errors():
     pr.st.close()
 
 
-def test_flow_identical_where_both_prewarps_are_exact():
+@pytest.mark.parametrize("max_flow", [8.0, 4.0, 12.0, 16.0])
+def test_flow_identical_where_both_prewarps_are_exact(max_flow):
     """Two cameras cropped from one rendered scene at integer offsets, the
     right one's content moved by (3, -2) against its homography: both
     pre-warps are exact copies of frame pixels, so both luminance pyramids,
     every integer cost and every float32 sub-pixel step agree, and the flows
-    must be bit-identical everywhere."""
+    must be bit-identical everywhere. The search radius at the coarsest level
+    is max_flow / 4: 1, 2, 3 and 4 (STITCH_MAX_FLOW) take one strip of three
+    candidates per column, two overlapping strips, and three."""
     from oracle.pipeline import OracleStitcher
     from synth import Scene
     ensure_built()
@@ -96,7 +99,7 @@ def test_flow_identical_where_both_prewarps_are_exact():
     fa = img[m:m + h, m:m + w].contiguous()
     fb = img[m + dy:m + dy + h, m + off + dx:m + off + dx + w].contiguous()
     T = lambda tx: np.array([[1.0, 0, tx], [0, 1.0, 0], [0, 0, 1.0]])
-    cfg = S.Config([w, w], [h, h], np.stack([T(0), T(off)]), off + w, h, max_flow=8.0)
+    cfg = S.Config([w, w], [h, h], np.stack([T(0), T(off)]), off + w, h, max_flow=max_flow)
     st = S.Stitcher(cfg)
     frames = [fa.cuda(), fb.cuda()]
     x0, x1, y0, y1 = st.bands[0].tolist()
@@ -104,10 +107,13 @@ def test_flow_identical_where_both_prewarps_are_exact():
     gji = torch.full_like(gij, float("nan"))
     S.stitch_estimate_flow(st.ctx, frames, [gij], [gji])
     torch.cuda.synchronize()
-    o = OracleStitcher(cfg.H, cfg.cam_w, cfg.cam_h, cfg.pano_w, cfg.pano_h, max_flow=8.0)
-    oij, oji = pair_flows([fa.numpy(), fb.numpy()], o.geom, 8.0)
+    o = OracleStitcher(cfg.H, cfg.cam_w, cfg.cam_h, cfg.pano_w, cfg.pano_h, max_flow=max_flow)
+    oij, oji = pair_flows([fa.numpy(), fb.numpy()], o.geom, max_flow)
     g1, g2 = gij.cpu().numpy(), gji.cpu().numpy()
     assert np.array_equal(g1, oij[0]) and np.array_equal(g2, oji[0])
+    if max_flow != 8.0:
+        st.close()
+        return
     # away from the band's border the match is the known shift within the
     # sub-pixel step (the parabola through asymmetric costs moves it off the
     # integer by up to half a pixel), in one direction or the other: the
