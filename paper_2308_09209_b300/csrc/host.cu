@@ -1394,8 +1394,8 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
     fl.out_ij[p] = reinterpret_cast<float2 *>(flow_ij_dev[p]);
     fl.out_ji[p] = reinterpret_cast<float2 *>(flow_ji_dev[p]);
   }
-  // The float32 band pre-warp, written as the full level's luminance, then
-  // the flow.
+  // The float32 band pre-warp, written as the luminance pyramid, then the
+  // matcher.
   const float *none[kMaxPairs] = {};
   FuseParams fp = frame_params(ctx, frames_dev, none, none, nullptr, ctx->host_T - 1, ctx->host_F);
   fp.flags &= ~(STITCH_FP16_INTERMEDIATE | kFlagPwOffset);
@@ -1403,6 +1403,11 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   for (int p = 0; p < np; ++p) {
     fp.pw_off[p][0] = fl.pw_off[p][0];
     fp.pw_off[p][1] = fl.pw_off[p][1];
+    for (int l = 1; l < kFlowLevels; ++l) {
+      fp.lum_off[l - 1][p][0] = fl.lev[l].y_off[p][0];
+      fp.lum_off[l - 1][p][1] = fl.lev[l].y_off[p][1];
+      fp.lum_w[l - 1][p] = fl.lev[l].w[p];
+    }
   }
   fp.pw = ctx->flow_Y;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

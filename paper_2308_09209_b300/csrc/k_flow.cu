@@ -4,10 +4,12 @@
 // coarse-to-fine block matcher on integer luminance:
 //
 // luminance:    Y = round-half-even(clamp((R + 2G + B) / 4, 0, 255)) of both
-//               cameras' float32 pre-warped band samples (uint8), written by
-//               the band pre-warp itself (k_prewarp_band, kFlagPwLuma).
-// k_flow_down:  the next pyramid level, (a + b + c + d + 2) >> 2 over 2 x 2
-//               blocks, the last row / column repeated for odd sizes.
+//               cameras' float32 pre-warped band samples (uint8; R + 2G + B of
+//               each tap interpolated once), and the pyramid's next levels,
+//               (a + b + c + d + 2) >> 2 over 2 x 2 blocks, the last row /
+//               column repeated for odd sizes: all written by the band
+//               pre-warp itself (k_prewarp_band, kFlagPwLuma), each 64 x 32
+//               piece building its share of levels 1 and 2 in shared memory.
 // k_flow_match: per pixel of a level and direction, the displacement d with
 //               the smallest sum of |Y_a(q + d + o) - Y_b(q + o)| over the
 //               7 x 7 window o (coordinates clamped into the level), over
@@ -44,20 +46,6 @@ constexpr int kFlowThreads = 256;
 constexpr int kWin = 3;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-__global__ void __launch_bounds__(kFlowThreads) k_flow_down(const FlowParams P, int lev) {
-  const int pair = blockIdx.y >> 1, side = blockIdx.y & 1;
-  const int wi = P.lev[lev - 1].w[pair], hi = P.lev[lev - 1].h[pair];
-  const int w = P.lev[lev].w[pair], h = P.lev[lev].h[pair];
-  const uint8_t *in = P.Y + P.lev[lev - 1].y_off[pair][side];
-  uint8_t *out = P.Y + P.lev[lev].y_off[pair][side];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w * h; i += gridDim.x * blockDim.x) {
-    const int y = i / w, x = i - y * w;
-    const int x0 = 2 * x, y0 = 2 * y, x1 = min(2 * x + 1, wi - 1), y1 = min(2 * y + 1, hi - 1);
-    const int s = in[y0 * wi + x0] + in[y1 * wi + x0] + in[y0 * wi + x1] + in[y1 * wi + x1];
-    out[i] = (uint8_t)((s + 2) >> 2);
-  }
-}
 
 // Shared-memory tiles of the matcher: a 64 x 16 block of pixels, the target
 // image over the block plus the window's reach, and the moving image over
@@ -394,19 +382,12 @@ dim3 flow_tiles(const FlowParams &p, int lev, int tx, int ty) {
   return dim3(std::max(1, most), 2 * p.n_pairs);
 }
 
-dim3 flow_grid(const FlowParams &p, int lev) {
-  int most = 0;
-  for (int i = 0; i < p.n_pairs; ++i) most = std::max(most, p.lev[lev].w[i] * p.lev[lev].h[i]);
-  return dim3(std::max(1, std::min(1024, (most + kFlowThreads - 1) / kFlowThreads)), 2 * p.n_pairs);
-}
-
 }  // namespace
 
 cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s) {
   if (p.n_pairs <= 0) return cudaSuccess;
   if (radius < 1 || radius > kFlowMaxRadius) return cudaErrorInvalidValue;
   static_assert(kMX * kMY == 4 * kFlowThreads && kFlowLevels >= 2, "2 x 2 pixels per thread; a level above the finest");
-  for (int lev = 1; lev < kFlowLevels; ++lev) k_flow_down<<<flow_grid(p, lev), kFlowThreads, 0, s>>>(p, lev);
   for (int lev = kFlowLevels - 1; lev >= 1; --lev)
     k_flow_match<<<flow_tiles(p, lev, kMX, kMY), kFlowThreads, 0, s>>>(p, lev, radius);
   k_flow_match_final<<<flow_tiles(p, 0, kMX, kMY), kFlowThreads, 0, s>>>(p, radius);

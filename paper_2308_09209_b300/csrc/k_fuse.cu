@@ -57,6 +57,7 @@
 // rig changes. When the rigs' tile shapes differ, the *_mixed forms run
 // every tile with its rig's shape.
 #include <algorithm>
+#include <cstddef>
 #include <cuda_fp16.h>
 
 #include "stitch_internal.h"
@@ -357,6 +358,50 @@ __device__ __forceinline__ float3 win_bilinear(const uint32_t *s, const Window &
   return bilerp_words(p[0], p[1], p[kStride], p[kStride + 1], fx, fy);
 }
 
+// Luminance sum L = R + 2G + B of an RGBX word (exact, one dot product).
+__device__ __forceinline__ float luma_word(uint32_t w) {
+  return (float)__dp4a(w, 0x00010201u, 0u);
+}
+
+// The bilinear sample of L at (sx, sy) from a staged window (taps clamped
+// into the window as in win_bilinear): L of each tap, interpolated once,
+// which is the interpolated channels' R + 2G + B with fewer roundings.
+template <int kStride>
+__device__ __forceinline__ float win_luma(const uint32_t *s, const Window &W, float sx, float sy) {
+  int ix, iy;
+  float fx, fy;
+  split(sx, ix, fx);
+  split(sy, iy, fy);
+  int lx = ix - W.x0, ly = iy - W.y0;
+  if (lx > W.w - 2) { lx = W.w - 2; fx = 1.0f; }
+  if (ly > W.h - 2) { ly = W.h - 2; fy = 1.0f; }
+  lx = max(lx, 0);
+  ly = max(ly, 0);
+  const uint32_t *p = s + ly * kStride + lx;
+  const float A = luma_word(p[0]), B = luma_word(p[1]), D = luma_word(p[kStride]), E = luma_word(p[kStride + 1]);
+  const float top = fmaf(fx, B - A, A);
+  const float bot = fmaf(fx, E - D, D);
+  return fmaf(fy, bot - top, top);
+}
+
+// The same from the frame in global memory (windows that did not fit).
+__device__ __forceinline__ float src_luma(const uint8_t *__restrict__ src, const CamDev &c, float sx, float sy) {
+  int ix, iy;
+  float fx, fy;
+  split(sx, ix, fx);
+  split(sy, iy, fy);
+  ix = min(max(ix, 0), c.w - 1);
+  iy = min(max(iy, 0), c.h_px - 1);
+  const int ix1 = min(ix + 1, c.w - 1), iy1 = min(iy + 1, c.h_px - 1);
+  const uint8_t *r0 = src + (size_t)iy * c.pitch;
+  const uint8_t *r1 = src + (size_t)iy1 * c.pitch;
+  auto L = [](const uint8_t *q) { return (float)((int)__ldg(q) + 2 * (int)__ldg(q + 1) + (int)__ldg(q + 2)); };
+  const float A = L(r0 + 3 * ix), B = L(r0 + 3 * ix1), D = L(r1 + 3 * ix), E = L(r1 + 3 * ix1);
+  const float top = fmaf(fx, B - A, A);
+  const float bot = fmaf(fx, E - D, D);
+  return fmaf(fy, bot - top, top);
+}
+
 // ---------------------------------------------------------------------------
 // Shared memory common to every fuse kernel: colour constants, window
 // descriptors, the output table and (multi-rig kernels) the rig's parameters.
@@ -394,6 +439,8 @@ struct __align__(16) SmemTile {
 struct __align__(16) SmemPw {
   Window sW[2];
   __align__(16) uint32_t win[2][WinGeom<kTileW, kTileH>::kAlloc];
+  uint8_t lum[kTileH][kTileW];            // kFlagPwLuma: the piece's luminance, level 0
+  uint8_t lum1[kTileH / 2][kTileW / 2];   // and level 1
 };
 
 // The same for the multi-rig band pre-warp, with the item's rig parameters.
@@ -1244,8 +1291,9 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
 // intermediate holds v - 128; otherwise (the flow and the correspondence fit,
 // which want the plain pre-warped image) a float32 bilinear of v.
 template <bool kHalf>
-__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, Window *sW,
-                                              uint32_t (*win)[WinGeom<kTileW, kTileH>::kAlloc]) {
+__device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile pt, SmemPw &sp) {
+  Window *sW = sp.sW;
+  uint32_t (*win)[WinGeom<kTileW, kTileH>::kAlloc] = sp.win;
   using G = WinGeom<kTileW, kTileH>;
   using PM = PairMap<kTileW, kTileH>;
   constexpr int S = G::kStride;
@@ -1345,18 +1393,53 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
           cam_map_f(c, (float)(x - c.ox), (float)(y - c.oy), sx, sy, nw);
           sx = fminf(fmaxf(sx, 0.0f), c.wm1);
           sy = fminf(fmaxf(sy, 0.0f), c.hm1);
+          if (luma) {
+            // the flow's luminance: round-half-even(clamp((R + 2G + B) / 4, 0, 255))
+            const float L = W.ok ? win_luma<S>(win[side], W, sx, sy) : src_luma(P.src[k], c, sx, sy);
+            const uint8_t yv = (uint8_t)__float2int_rn(fminf(fmaxf(L * 0.25f, 0.0f), 255.0f));
+            dsty[o] = yv;
+            sp.lum[y - ry0][x - rx0] = yv;
+            continue;
+          }
           v = W.ok ? win_bilinear<S>(win[side], W, sx, sy) : src_bilinear(P.src[k], c, sx, sy);
         }
-        if (luma) {
-          // the flow's luminance: round-half-even(clamp((R + 2G + B) / 4, 0, 255))
-          const float y4 = __fmul_rn(__fadd_rn(__fadd_rn(v.x, __fmul_rn(2.0f, v.y)), v.z), 0.25f);
-          dsty[o] = (uint8_t)__float2int_rn(fminf(fmaxf(y4, 0.0f), 255.0f));
-        } else if (hstore) {
+        if (hstore) {
           dst2[o] = make_uint2(h2_bits(__floats2half2_rn(v.x, v.y)), h2_bits(__floats2half2_rn(v.z, 0.0f)));
         } else {
           dst4[o] = make_float4(v.x, v.y, v.z, 0.0f);
         }
       }
+    }
+    if (luma) {
+      // Levels 1 and 2 of the flow's pyramid over this piece: (a + b + c +
+      // d + 2) >> 2 over 2 x 2 blocks, the last row / column repeated for odd
+      // sizes. Pieces start at multiples of 64 x 32 band pixels, so every
+      // block of both levels lies inside one piece, and the piece's clipped
+      // extent is where the band's odd last row / column repeats.
+      __syncthreads();
+      const int bx = rx0 - B.x0, by = ry0 - B.y0;          // band-relative origin (even, a multiple of 4)
+      const int nx0 = rx1 - rx0 + 1, ny0 = ry1 - ry0 + 1;
+      const int nx1 = (nx0 + 1) >> 1, ny1 = (ny0 + 1) >> 1;
+      uint8_t *d1 = reinterpret_cast<uint8_t *>(P.pw) + P.lum_off[0][pt.pair][side];
+      const int w1 = P.lum_w[0][pt.pair];
+      for (int i = threadIdx.x; i < nx1 * ny1; i += blockDim.x) {
+        const int yy = i / nx1, xx = i - yy * nx1;
+        const int xa = 2 * xx, ya = 2 * yy, xb = min(xa + 1, nx0 - 1), yb = min(ya + 1, ny0 - 1);
+        const int v = (sp.lum[ya][xa] + sp.lum[yb][xa] + sp.lum[ya][xb] + sp.lum[yb][xb] + 2) >> 2;
+        sp.lum1[yy][xx] = (uint8_t)v;
+        d1[(size_t)((by >> 1) + yy) * w1 + (bx >> 1) + xx] = (uint8_t)v;
+      }
+      __syncthreads();
+      const int nx2 = (nx1 + 1) >> 1, ny2 = (ny1 + 1) >> 1;
+      uint8_t *d2 = reinterpret_cast<uint8_t *>(P.pw) + P.lum_off[1][pt.pair][side];
+      const int w2 = P.lum_w[1][pt.pair];
+      for (int i = threadIdx.x; i < nx2 * ny2; i += blockDim.x) {
+        const int yy = i / nx2, xx = i - yy * nx2;
+        const int xa = 2 * xx, ya = 2 * yy, xb = min(xa + 1, nx1 - 1), yb = min(ya + 1, ny1 - 1);
+        const int v = (sp.lum1[ya][xa] + sp.lum1[yb][xa] + sp.lum1[ya][xb] + sp.lum1[yb][xb] + 2) >> 2;
+        d2[(size_t)((by >> 2) + yy) * w2 + (bx >> 2) + xx] = (uint8_t)v;
+      }
+      __syncthreads();   // the next side rewrites the tiles
     }
   }
 }
@@ -1394,7 +1477,7 @@ template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_band(const FuseParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   SmemPw &sp = *reinterpret_cast<SmemPw *>(smem);
-  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], sp.sW, sp.win);
+  prewarp_piece<kHalf>(P, P.pw_tiles[blockIdx.x], sp);
 }
 
 // General pieces (the first n_tiles - n_band - n_full of the list),
@@ -1444,7 +1527,8 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own(const FuseParams P
   ohist_flush(P, h);
 }
 
-// Band pre-warp of several rigs in one launch: block b takes item b.
+// Band pre-warp of several rigs in one launch (the frame path: launched
+// without the flow's luminance tiles): block b takes item b.
 template <bool kHalf>
 __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParams M) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1452,7 +1536,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_prewarp_multi(const MultiParam
   const MultiItem it = M.items[blockIdx.x];
   copy_params(sm.sp, M.params + M.base + it.rig);
   __syncthreads();
-  prewarp_piece<kHalf>(sm.sp, it.pw, sm.pw.sW, sm.pw.win);
+  prewarp_piece<kHalf>(sm.sp, it.pw, sm.pw);
 }
 
 // Next item of a persistent multi-rig launch; reloads the rig's parameters
@@ -1567,8 +1651,11 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi_mixed(const 
 namespace {
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kPwSmem = sizeof(SmemPw);                      // single-rig band pre-warp
-constexpr size_t kPwMultiSmem = sizeof(SmemPwMulti);                // multi-rig: the rig's parameters too
+constexpr size_t kPwSmem = sizeof(SmemPw);                      // single-rig band pre-warp (the flow's, with
+                                                                 // its luminance tiles)
+constexpr size_t kPwSmemFrame = (offsetof(SmemPw, lum) + 15) / 16 * 16;   // without them: only kFlagPwLuma uses them
+constexpr size_t kPwMultiSmem = offsetof(SmemPwMulti, pw) + kPwSmemFrame;   // multi-rig (frame path): the rig's
+                                                                              // parameters too
 constexpr size_t kMixSmem =
     cmax(cmax(smem_bytes<64, 32, 2>(), smem_bytes<64, 16, 2>()), cmax(smem_bytes<32, 32, 2>(), smem_bytes<128, 16, 2>()));
 constexpr size_t kMixOwnSmem =
@@ -1701,10 +1788,11 @@ cudaError_t fuse_setup_attributes(int) {
 
 cudaError_t launch_prewarp(const FuseParams &p, cudaStream_t s) {
   if (p.n_pw_tiles <= 0) return cudaSuccess;
+  const size_t smem = (p.flags & kFlagPwLuma) ? kPwSmem : kPwSmemFrame;
   if (p.flags & STITCH_FP16_INTERMEDIATE)
-    k_prewarp_band<true><<<p.n_pw_tiles, kFuseThreads, kPwSmem, s>>>(p);
+    k_prewarp_band<true><<<p.n_pw_tiles, kFuseThreads, smem, s>>>(p);
   else
-    k_prewarp_band<false><<<p.n_pw_tiles, kFuseThreads, kPwSmem, s>>>(p);
+    k_prewarp_band<false><<<p.n_pw_tiles, kFuseThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,8 @@ constexpr int kLutBytes = 3 * kLutEntries;
 constexpr int kFlagPwOffset = 1 << 20;
 // Band pre-warp for the flow: write the integer luminance of the float32
 // samples (one byte per band pixel and side, element offsets pw_off) instead
-// of the samples themselves.
+// of the samples themselves, and the next two levels of its pyramid
+// (FuseParams::lum_off / lum_w).
 constexpr int kFlagPwLuma = 1 << 21;
 
 // Integer statistics of one frame, written by the stats kernel (K1) and read
@@ -146,6 +147,8 @@ struct alignas(16) FuseParams {
   const uint8_t *lut;                 // the colour slot's output table (kLutBytes)
   unsigned int *win_fallback;         // tiles whose source window did not fit in shared memory (counter)
   uint32_t *out_hist;                 // STITCH_BALANCE_OUTPUT: this frame's pre-balance histogram [3][256], or null
+  size_t lum_off[2][kMaxPairs][2];    // kFlagPwLuma: byte offsets (into pw) of pyramid levels 1 and 2, band p, side
+  int lum_w[2][kMaxPairs];            // their widths
   CamDev cam[kMaxCams];
   BandDev band[kMaxPairs];
   const uint8_t *src[kMaxCams];
@@ -257,6 +260,7 @@ struct RefineParams {
 constexpr int kFlowLevels = 3;
 constexpr int kFlowMaxRadius = 4;     // coarsest search radius: max_flow up to STITCH_MAX_FLOW = 16 px
 static_assert(STITCH_MAX_FLOW <= (float)(kFlowMaxRadius << (kFlowLevels - 1)), "the coarsest search covers max_flow");
+static_assert(kFlowLevels == 3, "the band pre-warp writes levels 1 and 2 of the luminance pyramid");
 
 struct FlowLevelDev {
   int w[kMaxPairs], h[kMaxPairs];     // level size of every band
@@ -307,6 +311,8 @@ cudaError_t fuse_setup_attributes(int max_halo);
 // The correspondence sums of every pair (blocks per pair, fixed-order totals).
 cudaError_t launch_corr(const CorrParams &p, int blocks, cudaStream_t s);
 // Every level of the band flow of every pair, both directions.
+// The matcher levels of every pair (the band pre-warp under kFlagPwLuma has
+// written every luminance level).
 cudaError_t launch_flow(const FlowParams &p, int radius, cudaStream_t s);
 // One radix pass (key bits [shift, shift + 8)) of every band-flow median.
 cudaError_t launch_refine_pass(const RefineParams &p, int shift, cudaStream_t s);
