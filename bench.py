@@ -645,6 +645,10 @@ def run_extras(args, dev, stream, ctxs):
     plain = S.Stitcher(wl["cfg"])
     ctxs.append(plain)
     ms_plain = _time(lambda: S.stitch_sequence(plain.ctx, F, fr, a, c, pp, stream), stream, 3)
+    S.stitch_window_fallbacks(plain.ctx, reset=True)
+    S.stitch_sequence(plain.ctx, n_r, fr[:n_r * 8], a[:n_r * 7], c[:n_r * 7], pp[:n_r], stream)
+    stream.synchronize()
+    cyl_fb = S.stitch_window_fallbacks(plain.ctx, reset=True) / n_r
     wl["cfg"].flags = S.STITCH_FP16_INTERMEDIATE | S.STITCH_LEARNED
     full = S.Stitcher(wl["cfg"])
     ctxs.append(full)
@@ -664,6 +668,8 @@ def run_extras(args, dev, stream, ctxs):
                           "full_form": "learned estimate with fallback, fp16 intermediates, batched launch, "
                                        f"tile {S.TILE_SHAPES[shapes_full[0]]}",
                           "learned_fallback_rate": n_f / max(n_l + n_f, 1),
+                          "window_fallbacks_per_frame": cyl_fb,
+                          "tile_shape_plain": list(S.stitch_tile_shape(plain.ctx)[1]),
                           "path_bytes_per_frame": wl["in_bytes"] + wl["flow_bytes"] + wl["out_bytes"]}
     S.stitch_batch_destroy(bf)
     net.close()
@@ -755,6 +761,12 @@ def _run_ours(args, dist, ctxs):
             acc[k] += r[k]
     S.stitch_profile(st.ctx, False)
     stage_timing = "event nodes in the replayed graph"
+    # fuse tiles and pre-warp pieces whose source window did not fit in shared
+    # memory (they take the per-pixel path with taps from global memory), per frame
+    S.stitch_window_fallbacks(st.ctx, reset=True)
+    step()
+    stream.synchronize()
+    win_fb = S.stitch_window_fallbacks(st.ctx, reset=True) / F
 
     # The same stages serialised: direct calls on one stream, one frame after
     # another, with the library's stage events around each launch group, so
@@ -949,6 +961,7 @@ def _run_ours(args, dist, ctxs):
                        "status": rc, "parallelism": f"replicas x{dist.world}",
                        "tile_shape": list(S.stitch_tile_shape(st.ctx)[1]),
                        "autotune_ms": [round(float(m), 4) for m in shape_ms],
+                       "window_fallbacks_per_frame": win_fb,
                        "oracle_error": err, **extras},
             "roofline": {"bound": "hbm", "kernel": "fused warp stage of a frame (k_prewarp_band + k_fuse + k_fuse_band + k_fuse_own)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

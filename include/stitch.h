@@ -598,7 +598,10 @@ int stitch_n_pairs(const stitch_ctx *ctx);
  * since stitch_init or the last reset, whose source window did not fit the
  * kernel's staging capacity (about 1.5 x the tile width by the tile height
  * + 16 rows) and therefore sampled the frame with per-pixel global loads
- * instead. The result is the same either way; only the speed differs.
+ * instead. Tiles whose window the frame's edge clips to under 2 x 2 pixels,
+ * or with a corner behind the camera, take the per-pixel path too but are
+ * not counted: there the window is not too large, only degenerate. The
+ * result is the same either way; only the speed differs.
  * *count (required) receives the counter; reset != 0 clears it afterwards.
  * Synchronises the device. Returns STITCH_OK, STITCH_EINVAL or STITCH_ECUDA.
  */

@@ -74,7 +74,8 @@ constexpr float kHalfOffset = 1152.0f;       // 1024 + 128: half (1024 + v) minu
 
 // Source windows: a fixed row stride per tile shape (tap offsets become
 // immediates); windows wider or taller than the capacity fall back to
-// per-pixel global gathers and are counted.
+// per-pixel global gathers and are counted (windows clipped by the frame to a
+// sliver, or with a corner behind the camera, take the same path uncounted).
 template <int TW, int TH>
 struct WinGeom {
   static constexpr int kStride = TW + TW / 2;          // words per staged row
@@ -183,6 +184,7 @@ __device__ __forceinline__ float3 src_bilinear(const uint8_t *__restrict__ src, 
 struct Window {
   int x0, y0, w, h, ok;
   int a16;                           // staged in 16-pixel groups from 16-byte aligned rows (x0 % 16 == 0)
+  int over;                          // a proper window (in front, at least 2 x 2) beyond the capacity
 };
 
 // Rows of the frame start on 16-byte boundaries (base and pitch), so a
@@ -230,13 +232,15 @@ __device__ Window warp_window(const CamDev &c, int rx0, int ry0, int rx1, int ry
   if (W.a16) W.x0 &= ~15;
   W.w = x1 - W.x0 + 1;
   W.h = y1 - W.y0 + 1;
-  W.ok = (front && W.w >= 2 && W.h >= 2 && W.w <= kStride && W.h <= kRows) ? 1 : 0;
+  const bool proper = front && W.w >= 2 && W.h >= 2;
+  W.ok = (proper && W.w <= kStride && W.h <= kRows) ? 1 : 0;
+  W.over = (proper && !W.ok) ? 1 : 0;
   return W;
 }
 
 __device__ __forceinline__ Window no_window() {
   Window W;
-  W.x0 = W.y0 = W.w = W.h = W.ok = W.a16 = 0;
+  W.x0 = W.y0 = W.w = W.h = W.ok = W.a16 = W.over = 0;
   return W;
 }
 
@@ -1063,7 +1067,7 @@ __device__ __forceinline__ void fuse_own_tile(const FuseParams &P, const TileDes
     const Window W = warp_window<G::kStride, G::kRows>(c, tx0 + cx0, ty0, tx0 + cx1 - 1, ty1, rows16(P.src[k], c));
     if ((threadIdx.x & 31) == 0) {
       h.sW[0] = W;
-      if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
+      if (W.over && P.win_fallback) atomicAdd(P.win_fallback, 1u);
     }
   }
   __syncthreads();
@@ -1224,7 +1228,7 @@ __device__ __forceinline__ void fuse_tile(const FuseParams &P, const TileDesc t,
     }
     if (lane == 0) {
       h.sW[warp] = W;
-      if (need && !W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
+      if (need && W.over && P.win_fallback) atomicAdd(P.win_fallback, 1u);
     }
   }
   __syncthreads();
@@ -1308,7 +1312,7 @@ __device__ __forceinline__ void prewarp_piece(const FuseParams &P, const PwTile 
                                                rows16(P.src[pt.pair + warp], P.cam[pt.pair + warp]));
     if (lane == 0) {
       sW[warp] = W;
-      if (!W.ok && P.win_fallback) atomicAdd(P.win_fallback, 1u);
+      if (W.over && P.win_fallback) atomicAdd(P.win_fallback, 1u);
     }
   }
   __syncthreads();

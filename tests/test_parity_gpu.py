@@ -83,6 +83,24 @@ def test_full_size_4x1080p_stats_and_sampled_pixels():
         assert d.max() <= 2 and (d <= 1).mean() >= 0.9999, (d.max(), (d <= 1).mean())
 
 
+def test_benchmark_rig_windows_all_fit():
+    """No fuse tile or band pre-warp piece of the 4 x 1080p rig has a source
+    window beyond the shared-memory staging capacity, at any tile shape: the
+    counter of tiles that fell back to per-pixel taps from global memory for
+    that reason stays 0 (the largest window this rig needs is 132 x 22
+    source pixels at 128 x 16 tiles, against a capacity of 192 x 40)."""
+    pr = Pair("4x1920x1080", seed=0)
+    frames, fij, fji = pr.inputs(0)
+    pr.st.estimate_color(frames)
+    for shape in range(S.STITCH_TILE_SHAPES):
+        S.stitch_set_tile_shape(pr.st.ctx, shape)
+        S.stitch_window_fallbacks(pr.st.ctx, reset=True)
+        pr.st.frame(frames, fij, fji)
+        S.stitch_sync(pr.st.ctx)
+        assert S.stitch_window_fallbacks(pr.st.ctx) == 0, S.TILE_SHAPES[shape]
+    pr.st.close()
+
+
 def test_full_size_4x1080p_graph_sequence_as_benchmarked():
     """The benchmark's launch form: a recorded multi-stream sequence of frames
     of the 4 x 1080p workload (window 5, flow 8 px, moving objects); every
