@@ -721,6 +721,21 @@ def _run_ours(args, dist, ctxs):
     def step():
         S.stitch_sequence(st.ctx, F, frames, fij, fji, panos, stream)
 
+    # The autotuner times the fuse kernels alone; a shape it prefers over the
+    # default is confirmed on the whole overlapped sequence (both shapes, a few
+    # steps each, outside the timed region) and kept only if it is faster there.
+    shape_check = None
+    tuned = S.stitch_tile_shape(st.ctx)[0]
+    if args.tile_shape < 0 and tuned != 0:
+        ms_tuned = _time(step, stream, 3)
+        S.stitch_set_tile_shape(st.ctx, 0)
+        ms_default = _time(step, stream, 3)
+        if ms_tuned < ms_default:
+            S.stitch_set_tile_shape(st.ctx, tuned)
+        shape_check = {"autotuner": list(S.TILE_SHAPES[tuned]),
+                       "sequence_ms": {"x".join(map(str, S.TILE_SHAPES[tuned])): ms_tuned,
+                                       "x".join(map(str, S.TILE_SHAPES[0])): ms_default}}
+
     for _ in range(args.warmup):
         step()
     stream.synchronize()
@@ -961,6 +976,7 @@ def _run_ours(args, dist, ctxs):
                        "status": rc, "parallelism": f"replicas x{dist.world}",
                        "tile_shape": list(S.stitch_tile_shape(st.ctx)[1]),
                        "autotune_ms": [round(float(m), 4) for m in shape_ms],
+                       "tile_shape_check": shape_check,
                        "window_fallbacks_per_frame": win_fb,
                        "oracle_error": err, **extras},
             "roofline": {"bound": "hbm", "kernel": "fused warp stage of a frame (k_prewarp_band + k_fuse + k_fuse_band + k_fuse_own)",

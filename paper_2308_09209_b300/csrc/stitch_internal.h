@@ -261,6 +261,8 @@ constexpr int kFlowLevels = 3;
 constexpr int kFlowMaxRadius = 4;     // coarsest search radius: max_flow up to STITCH_MAX_FLOW = 16 px
 static_assert(STITCH_MAX_FLOW <= (float)(kFlowMaxRadius << (kFlowLevels - 1)), "the coarsest search covers max_flow");
 static_assert(kFlowLevels == 3, "the band pre-warp writes levels 1 and 2 of the luminance pyramid");
+static_assert(kTileW % 4 == 0 && kTileH % 4 == 0,
+              "pre-warp pieces start at multiples of 4 band pixels, so each builds whole 2 x 2 blocks of both levels");
 
 struct FlowLevelDev {
   int w[kMaxPairs], h[kMaxPairs];     // level size of every band
