@@ -193,6 +193,22 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
                          float *const *flow_ji_dev, stitch_stream_t stream);
 
 /*
+ * stitch_get_flow_luma -- one level of the integer luminance pyramid that the
+ * latest stitch_estimate_flow on this context matched (paper section 3.2; the
+ * pyramid is this library's flow, not printed in the paper): level `level`
+ * (0 = full band resolution, then each level the 2 x 2 average of the one
+ * below, 3 levels) of camera `pair + side` (side 0 = the left camera of the
+ * pair, 1 = the right one) over the blend band of pair `pair`. *w and *h
+ * (each optional) receive the level's size; out_host (caller-owned host
+ * memory of w * h bytes, rows of w bytes; NULL to query the size only)
+ * receives the image. A diagnostic: it lets a test separate the float32
+ * pre-warp's rounding of the luminance from the integer matching that
+ * follows. Synchronises the device. Returns STITCH_OK, STITCH_EINVAL (no flow
+ * estimated yet, or an index out of range) or STITCH_ECUDA.
+ */
+int stitch_get_flow_luma(stitch_ctx *ctx, int pair, int side, int level, uint8_t *out_host, int *w, int *h);
+
+/*
  * stitch_pair_M_correspondence -- the one-frame colour transfer from pixel
  * correspondences that the paper compares its 3D-M against (Tables 2-3, the
  * 2D-M method): for every pair, with colour source i and target j oriented

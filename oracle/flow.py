@@ -104,12 +104,22 @@ def _subpixel(cm, c0, cp):
     return np.clip(off, np.float32(-0.5), np.float32(0.5)).astype(np.float32)
 
 
+def pyramid(P):
+    """Steps 1-2: the integer luminance pyramid of a float RGB image, finest
+    level first."""
+    pyr = [luminance(P)]
+    for _ in range(LEVELS - 1):
+        pyr.append(downsample(pyr[-1]))
+    return pyr
+
+
 def flow(Pa, Pb, max_flow):
     """Flow (float32 (bh, bw, 2)) moving image a onto image b (steps 1-5)."""
-    pyr_a, pyr_b = [luminance(Pa)], [luminance(Pb)]
-    for _ in range(LEVELS - 1):
-        pyr_a.append(downsample(pyr_a[-1]))
-        pyr_b.append(downsample(pyr_b[-1]))
+    return flow_from_pyramids(pyramid(Pa), pyramid(Pb), max_flow)
+
+
+def flow_from_pyramids(pyr_a, pyr_b, max_flow):
+    """Steps 3-5 on given luminance pyramids (integer images, finest first)."""
     radius = max(1, int(math.ceil(max_flow / 2 ** (LEVELS - 1))))
     h, w = pyr_a[-1].shape
     dx = np.zeros((h, w), np.int64)

@@ -486,6 +486,8 @@ struct stitch_ctx {
   float4 *flow_pw = nullptr;          // stitch_estimate_flow: float32 pre-warped bands
   uint8_t *flow_Y = nullptr;          // its luminance pyramids
   int16_t *flow_d = nullptr;          // its chosen displacements (dx then dy)
+  FlowParams flow_fl{};               // the latest stitch_estimate_flow's level sizes and offsets
+  bool flow_ready = false;            // (for stitch_get_flow_luma)
   RefineState *refine_state = nullptr;  // stitch_refine_homographies: radix-selection state
   uint32_t *refine_hist = nullptr;      // and histograms (8 medians per pair)
   double *corr_buf = nullptr;         // stitch_pair_M_correspondence: block partials, then the totals
@@ -1414,6 +1416,25 @@ int stitch_estimate_flow(stitch_ctx *ctx, const uint8_t *const *frames_dev, floa
   e = launch_prewarp(fp, s);
   if (e == cudaSuccess) e = launch_flow(fl, radius, s);
   if (e != cudaSuccess) return cuda_err(ctx, e, "flow launch");
+  ctx->flow_fl = fl;
+  ctx->flow_ready = true;
+  return STITCH_OK;
+}
+
+int stitch_get_flow_luma(stitch_ctx *ctx, int pair, int side, int level, uint8_t *out_host, int *w, int *h) {
+  if (!ctx) return set_err(nullptr, STITCH_EINVAL, "ctx is NULL");
+  if (!ctx->flow_ready) return set_err(ctx, STITCH_EINVAL, "no flow has been estimated on this context");
+  if (pair < 0 || pair >= ctx->flow_fl.n_pairs || side < 0 || side > 1 || level < 0 || level >= kFlowLevels)
+    return set_err(ctx, STITCH_EINVAL, "pair, side or level out of range");
+  const int lw = ctx->flow_fl.lev[level].w[pair], lh = ctx->flow_fl.lev[level].h[pair];
+  if (w) *w = lw;
+  if (h) *h = lh;
+  if (!out_host) return STITCH_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(out_host, ctx->flow_Y + ctx->flow_fl.lev[level].y_off[pair][side], (size_t)lw * (size_t)lh,
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "flow luminance read");
   return STITCH_OK;
 }
 

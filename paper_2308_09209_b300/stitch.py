@@ -123,6 +123,8 @@ def lib():
             "stitch_batch_tile_shapes": (ip, [vp, vp]),
             "stitch_refine_homographies": (ip, [vp, pp, pp, vp, vp]),
             "stitch_estimate_flow": (ip, [vp, pp, pp, pp, vp]),
+            "stitch_get_flow_luma": (ip, [vp, ip, ip, ip, vp, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
             "stitch_pair_M_correspondence": (ip, [vp, pp, vp]),
             "stitch_selftest_wait": (ip, [ip, ip]),
             "stitch_batch_destroy": (None, [vp]),
@@ -571,6 +573,16 @@ def stitch_estimate_flow(ctx, frames, flows_ij, flows_ji, stream=None) -> None:
     """Band optical flow of one frame into the caller's float32 [bh, bw, 2]
     device tensors flows_ij / flows_ji (one per pair)."""
     _check(lib().stitch_estimate_flow(ctx, _ptrs(frames), _ptrs(flows_ij), _ptrs(flows_ji), _stream(stream)), ctx)
+
+
+def stitch_get_flow_luma(ctx, pair: int, side: int, level: int) -> np.ndarray:
+    """Level `level` of the luminance pyramid (uint8 [h, w]) of camera
+    pair + side over pair `pair`'s band, from the latest stitch_estimate_flow."""
+    w, h = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().stitch_get_flow_luma(ctx, pair, side, level, None, ctypes.byref(w), ctypes.byref(h)), ctx)
+    out = np.empty((h.value, w.value), dtype=np.uint8)
+    _check(lib().stitch_get_flow_luma(ctx, pair, side, level, out.ctypes.data, None, None), ctx)
+    return out
 
 
 def stitch_refine_homographies(ctx, flows_ij, flows_ji, n_cams: int):

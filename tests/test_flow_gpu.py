@@ -8,7 +8,12 @@ opposite sides of a rounding midpoint (up to about 2 pixels in 10^4 on the
 cylinder, whose float32 ray arithmetic strays furthest), each such pixel
 enters the 7 x 7 windows of 49 pixels, and the coarse levels spread a
 changed choice to its children: at least 98 % of the band pixels must carry
-bit-identical flows, and the others must stay within the search reach."""
+bit-identical flows, and the others must stay within the search reach.
+
+The two sources are also separated exactly: the library's luminance pyramid
+(stitch_get_flow_luma) differs from the oracle's by one grey level at no more
+than 0.1 % of the pixels, and the oracle's matcher run on the library's own
+pyramid reproduces the library's flows bit for bit everywhere."""
 import numpy as np
 import pytest
 import torch
@@ -149,4 +154,36 @@ def test_flow_matches_the_oracle_at_full_size():
         same = np.all(g == o, axis=2)
         assert same.mean() >= FRAC_IDENTICAL, same.mean()
         assert np.all(np.abs(g) <= reach)
+    pr.st.close()
+
+
+@pytest.mark.parametrize("config,seed,t", [("4x1920x1080", 0, 2), ("4x640x360cyl", 1, 0)])
+def test_matcher_exact_on_the_librarys_luminance(config, seed, t):
+    """The two sources of difference, separated. (1) Luminance: the library's
+    float32 pre-warp rounds to the oracle's integer luminance except at a few
+    pixels, by one grey level at most, and its pyramid levels 1 and 2 are the
+    exact integer reductions of its own level 0. (2) Matching: every cost is an
+    integer and the sub-pixel step is float32 on both sides, so the oracle's
+    matcher (section 3.2 steps 3-5) run on the library's own pyramids must give
+    the library's flows bit for bit, everywhere, in both directions (band 0;
+    the benchmark rig at full size and the small cylindrical rig)."""
+    from oracle.flow import band_prewarp, downsample, flow_from_pyramids, luminance
+    pr = Pair(config, seed=seed)
+    frames, _, _ = pr.inputs(t)
+    gij, gji = _gpu_flows(pr, frames)
+    fr = [f.cpu().numpy() for f in frames]
+    geom = pr.oracle.geom
+    band = geom.bands[0]
+    pyr = {}
+    for side in (0, 1):
+        levels = [S.stitch_get_flow_luma(pr.st.ctx, 0, side, lev).astype(np.int64) for lev in range(3)]
+        Yo = luminance(band_prewarp(fr[side], geom, side, band))
+        d = np.abs(levels[0] - Yo)
+        assert levels[0].shape == Yo.shape and d.max() <= 1 and (d > 0).mean() <= 1e-3, (d.max(), (d > 0).mean())
+        assert np.array_equal(levels[1], downsample(levels[0]))
+        assert np.array_equal(levels[2], downsample(levels[1]))
+        pyr[side] = levels
+    mf = pr.seq["max_flow"]
+    assert np.array_equal(gij[0], flow_from_pyramids(pyr[0], pyr[1], mf))
+    assert np.array_equal(gji[0], flow_from_pyramids(pyr[1], pyr[0], mf))
     pr.st.close()
