@@ -2,6 +2,8 @@
 several rigs: every shape and the batch must give exactly what one rig
 stitched alone gives, and the batch's outputs are checked against the FP64
 oracle on sampled pixels."""
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 import torch
@@ -10,7 +12,8 @@ from oracle.pipeline import OracleStitcher
 from paper_2308_09209_b300 import stitch as S
 from synth import BATCH_RIGS, Scene, render_camera_frames, rig_for_config
 
-from gpu_common import FRAC_WITHIN_1, MAX_ABS, M_REL_TOL, Pair, compare_pano, ensure_built, flows_for
+from gpu_common import (FRAC_WITHIN_1, MAX_ABS, M_REL_TOL, Pair, compare_pano, ensure_built, flows_for,
+                        oracle_frame_parallel)
 
 pytestmark = pytest.mark.gpu
 
@@ -125,11 +128,11 @@ def test_batch_equals_each_rig_alone(fp16):
         r["st"].close()
 
 
-def test_full_batch_against_the_oracle_on_sampled_pixels():
+def test_full_batch_against_the_oracle_every_pixel():
     """The four rigs of the batched workload (a mixed 6x1080p + 2x720p rig,
     3x1080p, 4x2160p, 2x720p), FP16 intermediates, tile shape autotuned: every
-    rig's panorama against the FP64 oracle on sampled pixels, and its pair
-    matrices against the oracle's."""
+    pixel of every rig's panorama against the FP64 oracle's whole panorama,
+    and its pair matrices against the oracle's."""
     ensure_built()
     n_frames = 2
     rigs = _rig_inputs(BATCH_RIGS, [10, 11, 12, 13], n_frames)
@@ -150,7 +153,6 @@ def test_full_batch_against_the_oracle_on_sampled_pixels():
     fr, fij, fji, pano = _flat(rigs, n_frames)
     S.stitch_batch_sequence(b, n_frames, fr, fij, fji, pano)
     torch.cuda.synchronize()
-    rng = np.random.default_rng(0)
     for r in rigs:
         rig, seq = r["rig"], r["seq"]
         o = OracleStitcher(rig.H, rig.cam_w, rig.cam_h, rig.pano_w, rig.pano_h, window=seq["window"],
@@ -159,14 +161,13 @@ def test_full_batch_against_the_oracle_on_sampled_pixels():
             fr_np = [f.cpu().numpy() for f in r["frames"][t]]
             o.estimate_color(fr_np)
         t = n_frames - 1
-        xs = rng.integers(0, rig.pano_w, 40000)
-        ys = rng.integers(0, rig.pano_h, 40000)
-        vals, near = o.pixels([f.cpu().numpy() for f in r["frames"][t]],
-                              [f.cpu().numpy() for f in r["flows"][t][0]],
-                              [f.cpu().numpy() for f in r["flows"][t][1]], xs, ys)
-        g = r["panos"][t].cpu().numpy()[:, ys, xs].T.astype(np.int16)
-        d = np.abs(g - vals.astype(np.int16)).max(1)[~near]
-        assert (d <= 1).mean() >= FRAC_WITHIN_1 and d.max() <= MAX_ABS, (rig.cam_w, d.max())
+        view = SimpleNamespace(rig=rig, oracle=o, proj=dict(projection=0, cyl=None))
+        planes, near = oracle_frame_parallel(view, [f.cpu().numpy() for f in r["frames"][t]],
+                                             [f.cpu().numpy() for f in r["flows"][t][0]],
+                                             [f.cpu().numpy() for f in r["flows"][t][1]])
+        rep = compare_pano(r["panos"][t], planes, near, rig.pano_w)
+        assert rep["within1"] >= FRAC_WITHIN_1 and rep["max"] <= MAX_ABS, (rig.cam_w, rep)
+        assert rep["n"] + rep["n_near"] == rig.pano_w * rig.pano_h
         Mp = S.stitch_get_pair_M(r["st"].ctx, len(rig.cam_w) - 1)
         for p in range(len(rig.cam_w) - 1):
             assert np.linalg.norm(Mp[p] - o.M_pair[p]) <= M_REL_TOL * np.linalg.norm(o.M_pair[p])
