@@ -546,7 +546,10 @@ int stitch_tile_shape(const stitch_ctx *ctx, int *tile_w, int *tile_h);
  * stitches one rig; this is the serving form. The contexts keep their own
  * state and may still be used alone between batch calls. All contexts must
  * share the device and the STITCH_FP16_INTERMEDIATE flag. The batch does not
- * own the contexts: destroy the batch first.
+ * own the contexts: destroy the batch first. A batch of one rig has no
+ * cross-rig work to merge: its calls run that rig's own persistent kernels
+ * (stitch_sequence at the batch's tile shape; stitch_autotune for
+ * stitch_batch_autotune).
  */
 #define STITCH_BATCH_MAX_RIGS 16
 typedef struct stitch_batch stitch_batch;

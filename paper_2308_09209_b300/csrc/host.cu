@@ -2161,6 +2161,16 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
     return batch_err(b, STITCH_EINVAL,
                      "pointer arrays must be complete and non-NULL, panoramas 16-byte and flows 8-byte aligned");
   const int R = (int)b->ctx.size();
+  if (R == 1) {
+    // One rig: there is no cross-rig work to merge, so the frames run the
+    // rig's own persistent kernels in its recorded sequence graph (the same
+    // streams and slot rings), at the batch's tile shape.
+    stitch_ctx *c = b->ctx[0];
+    int rc = STITCH_OK;
+    if (c->shape != b->shapes[0]) rc = stitch_set_tile_shape(c, b->shapes[0]);
+    if (rc == STITCH_OK) rc = stitch_sequence(c, n_frames, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev, stream);
+    return rc == STITCH_OK ? STITCH_OK : batch_err(b, rc, "batch sequence: " + c->err);
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::vector<const void *> key;
   for (int i = 0; i < n_frames * b->cams; ++i) key.push_back(frames_dev[i]);
@@ -2286,6 +2296,19 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
   if (!batch_ptrs_ok(b, 1, frames_dev, flow_ij_dev, flow_ji_dev, pano_dev))
     return batch_err(b, STITCH_EINVAL, "pointer arrays must be complete, non-NULL and aligned");
   const int R = (int)b->ctx.size();
+  if (R == 1) {
+    // One rig runs its own kernels (stitch_batch_sequence): tune those.
+    int shape = 0;
+    float ms1[kNumTileShapes];
+    int rc = stitch_autotune(b->ctx[0], frames_dev, flow_ij_dev, flow_ji_dev, pano_dev[0], reps, &shape, ms1);
+    if (rc != STITCH_OK) return batch_err(b, rc, "batch autotune: " + b->ctx[0]->err);
+    rc = batch_items(b, std::vector<int>{shape});
+    if (rc != STITCH_OK) return rc;
+    if (shapes_out) shapes_out[0] = shape;
+    if (ms_out)
+      for (int sh = 0; sh < kNumTileShapes; ++sh) ms_out[sh] = ms1[sh];
+    return STITCH_OK;
+  }
   cudaError_t e = cudaDeviceSynchronize();
   FuseParams *params = nullptr;
   int *counter = nullptr;
