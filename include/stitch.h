@@ -522,7 +522,10 @@ int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used)
  * STITCH_TILE_SHAPES floats, the mean ms per fuse launch of each shape, -1
  * for a shape that does not fit. Synchronous.
  */
-#define STITCH_TILE_SHAPES 4
+/* The shapes, by index (width x height in panorama pixels; 2 to 16 pixels
+ * per thread of a 256-thread block): 64 x 32 (the default), 64 x 16, 32 x 32,
+ * 128 x 16, 32 x 16, 128 x 32. */
+#define STITCH_TILE_SHAPES 6
 int stitch_autotune(stitch_ctx *ctx, const uint8_t *const *frames_dev, const float *const *flow_ij_dev,
                     const float *const *flow_ji_dev, uint8_t *pano_dev, int reps, int *shape_out, float *ms_out);
 

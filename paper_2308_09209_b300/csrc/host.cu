@@ -1988,6 +1988,7 @@ struct stitch_batch {
   MultiItem *pw_items = nullptr;
   int n_pw_items = 0;
   int grid = 0;                       // persistent fuse blocks
+  size_t mix_smem = 0, mix_own_smem = 0;   // mixed-shape kernels: shared memory for the rigs' shapes
   cudaStream_t cap = nullptr;
   cudaStream_t pipe[kPipeStreams] = {};   // statistics, estimate, band pre-warp, two fuse streams
   cudaEvent_t ev[4][8] = {};
@@ -2072,11 +2073,13 @@ int batch_items(stitch_batch *b, const std::vector<int> &shapes) {
   int sms = 148, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, uniform));
+  b->mix_smem = uniform < 0 ? fuse_mixed_smem(shapes.data(), (int)shapes.size(), 2) : 0;
+  b->mix_own_smem = uniform < 0 ? fuse_mixed_smem(shapes.data(), (int)shapes.size(), 1) : 0;
+  const int per_sm = std::max(1, fuse_multi_blocks_per_sm(b->half, uniform, b->mix_smem));
   b->grid = std::max(1, std::min(b->n_fuse_items, per_sm * sms));
   const int per_sm_band = uniform < 0 ? 1 : std::max(1, fuse_band_multi_blocks_per_sm(b->half, uniform));
   b->grid_band = std::max(1, std::min(b->n_band_items, per_sm_band * sms));
-  const int per_sm_own = std::max(1, fuse_own_multi_blocks_per_sm(uniform));
+  const int per_sm_own = std::max(1, fuse_own_multi_blocks_per_sm(uniform, b->mix_own_smem));
   b->grid_own = std::max(1, std::min(b->n_own_items, per_sm_own * sms));
   b->shapes = shapes;
   b->uniform = uniform;
@@ -2248,11 +2251,11 @@ int stitch_batch_sequence(stitch_batch *b, int n_frames, const uint8_t *const *f
       chk(cudaStreamWaitEvent(sC, ev[kW][t % 8], 0));
       chk(cudaMemsetAsync(bg.counters + 3 * t, 0, 3 * sizeof(int), sC));
       MultiParams mf{bg.params, t * R, b->n_fuse_items, b->fuse_items, bg.counters + 3 * t};
-      chk(launch_fuse_multi(mf, b->half, b->uniform, b->grid, sC));
+      chk(launch_fuse_multi(mf, b->half, b->uniform, b->grid, sC, b->mix_smem));
       MultiParams mb{bg.params, t * R, b->n_band_items, b->band_items, bg.counters + 3 * t + 1};
       chk(launch_fuse_band_multi(mb, b->half, b->uniform, b->grid_band, sC));
       MultiParams mo{bg.params, t * R, b->n_own_items, b->own_items, bg.counters + 3 * t + 2};
-      chk(launch_fuse_own_multi(mo, b->uniform, b->grid_own, sC));
+      chk(launch_fuse_own_multi(mo, b->uniform, b->grid_own, sC, b->mix_own_smem));
       chk(cudaEventRecord(ev[kF][t % 8], sC));
     }
     // join: every pipeline stream back into the capture stream
@@ -2337,9 +2340,9 @@ int stitch_batch_autotune(stitch_batch *b, const uint8_t *const *frames_dev, con
     MultiParams mo{params, 0, b->n_own_items, b->own_items, counter + 2};
     auto both = [&]() {
       cudaError_t x = cudaMemsetAsync(counter, 0, 3 * sizeof(int), b->cap);
-      if (x == cudaSuccess) x = launch_fuse_multi(mf, b->half, b->uniform, b->grid, b->cap);
+      if (x == cudaSuccess) x = launch_fuse_multi(mf, b->half, b->uniform, b->grid, b->cap, b->mix_smem);
       if (x == cudaSuccess) x = launch_fuse_band_multi(mb, b->half, b->uniform, b->grid_band, b->cap);
-      if (x == cudaSuccess) x = launch_fuse_own_multi(mo, b->uniform, b->grid_own, b->cap);
+      if (x == cudaSuccess) x = launch_fuse_own_multi(mo, b->uniform, b->grid_own, b->cap, b->mix_own_smem);
       return x;
     };
     cudaError_t x = cudaSuccess;

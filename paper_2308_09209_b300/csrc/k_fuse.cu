@@ -1605,7 +1605,9 @@ __global__ void __launch_bounds__(kFuseThreads, 3) k_fuse_multi_mixed(const Mult
       case 0: multi_tile<kHalf, 64, 32>(h, it.tile, smem); break;
       case 1: multi_tile<kHalf, 64, 16>(h, it.tile, smem); break;
       case 2: multi_tile<kHalf, 32, 32>(h, it.tile, smem); break;
-      default: multi_tile<kHalf, 128, 16>(h, it.tile, smem); break;
+      case 3: multi_tile<kHalf, 128, 16>(h, it.tile, smem); break;
+      case 4: multi_tile<kHalf, 32, 16>(h, it.tile, smem); break;
+      default: multi_tile<kHalf, 128, 32>(h, it.tile, smem); break;
     }
   }
 }
@@ -1643,7 +1645,9 @@ __global__ void __launch_bounds__(kFuseThreads, 4) k_fuse_own_multi_mixed(const 
       case 0: multi_own_tile<64, 32>(h, it.tile, smem); break;
       case 1: multi_own_tile<64, 16>(h, it.tile, smem); break;
       case 2: multi_own_tile<32, 32>(h, it.tile, smem); break;
-      default: multi_own_tile<128, 16>(h, it.tile, smem); break;
+      case 3: multi_own_tile<128, 16>(h, it.tile, smem); break;
+      case 4: multi_own_tile<32, 16>(h, it.tile, smem); break;
+      default: multi_own_tile<128, 32>(h, it.tile, smem); break;
     }
   }
 }
@@ -1661,9 +1665,11 @@ constexpr size_t kPwSmemFrame = (offsetof(SmemPw, lum) + 15) / 16 * 16;   // wit
 constexpr size_t kPwMultiSmem = offsetof(SmemPwMulti, pw) + kPwSmemFrame;   // multi-rig (frame path): the rig's
                                                                               // parameters too
 constexpr size_t kMixSmem =
-    cmax(cmax(smem_bytes<64, 32, 2>(), smem_bytes<64, 16, 2>()), cmax(smem_bytes<32, 32, 2>(), smem_bytes<128, 16, 2>()));
+    cmax(cmax(cmax(smem_bytes<64, 32, 2>(), smem_bytes<64, 16, 2>()), cmax(smem_bytes<32, 32, 2>(), smem_bytes<128, 16, 2>())),
+         cmax(smem_bytes<32, 16, 2>(), smem_bytes<128, 32, 2>()));
 constexpr size_t kMixOwnSmem =
-    cmax(cmax(smem_bytes<64, 32, 1>(), smem_bytes<64, 16, 1>()), cmax(smem_bytes<32, 32, 1>(), smem_bytes<128, 16, 1>()));
+    cmax(cmax(cmax(smem_bytes<64, 32, 1>(), smem_bytes<64, 16, 1>()), cmax(smem_bytes<32, 32, 1>(), smem_bytes<128, 16, 1>())),
+         cmax(smem_bytes<32, 16, 1>(), smem_bytes<128, 32, 1>()));
 
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
@@ -1766,9 +1772,10 @@ void fuse_multi_by_half(const MultiParams &m, bool half, int grid, cudaStream_t 
 
 }  // namespace
 
-static_assert(kTileShapes[0].w == 64 && kTileShapes[0].h == 32 && kTileShapes[1].w == 64 && kTileShapes[1].h == 16 &&
-                  kTileShapes[2].w == 32 && kTileShapes[2].h == 32 && kTileShapes[3].w == 128 &&
-                  kTileShapes[3].h == 16,
+static_assert(kNumTileShapes == 6 && kTileShapes[0].w == 64 && kTileShapes[0].h == 32 && kTileShapes[1].w == 64 &&
+                  kTileShapes[1].h == 16 && kTileShapes[2].w == 32 && kTileShapes[2].h == 32 &&
+                  kTileShapes[3].w == 128 && kTileShapes[3].h == 16 && kTileShapes[4].w == 32 &&
+                  kTileShapes[4].h == 16 && kTileShapes[5].w == 128 && kTileShapes[5].h == 32,
               "the shape table and the kernel instantiations below must agree");
 
 size_t prewarp_elem_bytes(bool fp16) { return fp16 ? sizeof(uint2) : sizeof(float4); }
@@ -1784,6 +1791,8 @@ cudaError_t fuse_setup_attributes(int) {
   if (e == cudaSuccess) e = setup_shape<64, 16>();
   if (e == cudaSuccess) e = setup_shape<32, 32>();
   if (e == cudaSuccess) e = setup_shape<128, 16>();
+  if (e == cudaSuccess) e = setup_shape<32, 16>();
+  if (e == cudaSuccess) e = setup_shape<128, 32>();
   if (e == cudaSuccess) e = set_smem(k_fuse_multi_mixed<false>, kMixSmem);
   if (e == cudaSuccess) e = set_smem(k_fuse_multi_mixed<true>, kMixSmem);
   if (e == cudaSuccess) e = set_smem(k_fuse_own_multi_mixed, kMixOwnSmem);
@@ -1807,6 +1816,8 @@ cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s) {
     case 1: fuse_by_half<64, 16>(p, s); break;
     case 2: fuse_by_half<32, 32>(p, s); break;
     case 3: fuse_by_half<128, 16>(p, s); break;
+    case 4: fuse_by_half<32, 16>(p, s); break;
+    case 5: fuse_by_half<128, 32>(p, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1821,32 +1832,56 @@ cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s) {
+size_t fuse_mixed_smem(const int *shapes, int n, int windows) {
+  size_t most = 0;
+  for (int i = 0; i < n; ++i) {
+    size_t b = windows == 2 ? kMixSmem : kMixOwnSmem;
+    switch (shapes[i]) {
+      case 0: b = windows == 2 ? smem_bytes<64, 32, 2>() : smem_bytes<64, 32, 1>(); break;
+      case 1: b = windows == 2 ? smem_bytes<64, 16, 2>() : smem_bytes<64, 16, 1>(); break;
+      case 2: b = windows == 2 ? smem_bytes<32, 32, 2>() : smem_bytes<32, 32, 1>(); break;
+      case 3: b = windows == 2 ? smem_bytes<128, 16, 2>() : smem_bytes<128, 16, 1>(); break;
+      case 4: b = windows == 2 ? smem_bytes<32, 16, 2>() : smem_bytes<32, 16, 1>(); break;
+      case 5: b = windows == 2 ? smem_bytes<128, 32, 2>() : smem_bytes<128, 32, 1>(); break;
+      default: break;
+    }
+    most = std::max(most, b);
+  }
+  return most;
+}
+
+cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s,
+                              size_t mixed_smem) {
   if (m.n_items <= 0) return cudaSuccess;
+  const size_t mix = mixed_smem ? mixed_smem : kMixSmem;
   switch (shape) {
     case -1:
       if (half)
-        k_fuse_multi_mixed<true><<<grid, kFuseThreads, kMixSmem, s>>>(m);
+        k_fuse_multi_mixed<true><<<grid, kFuseThreads, mix, s>>>(m);
       else
-        k_fuse_multi_mixed<false><<<grid, kFuseThreads, kMixSmem, s>>>(m);
+        k_fuse_multi_mixed<false><<<grid, kFuseThreads, mix, s>>>(m);
       break;
     case 0: fuse_multi_by_half<64, 32>(m, half, grid, s); break;
     case 1: fuse_multi_by_half<64, 16>(m, half, grid, s); break;
     case 2: fuse_multi_by_half<32, 32>(m, half, grid, s); break;
     case 3: fuse_multi_by_half<128, 16>(m, half, grid, s); break;
+    case 4: fuse_multi_by_half<32, 16>(m, half, grid, s); break;
+    case 5: fuse_multi_by_half<128, 32>(m, half, grid, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s) {
+cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s, size_t mixed_smem) {
   if (m.n_items <= 0) return cudaSuccess;
   switch (shape) {
-    case -1: k_fuse_own_multi_mixed<<<grid, kFuseThreads, kMixOwnSmem, s>>>(m); break;
+    case -1: k_fuse_own_multi_mixed<<<grid, kFuseThreads, mixed_smem ? mixed_smem : kMixOwnSmem, s>>>(m); break;
     case 0: k_fuse_own_multi<64, 32><<<grid, kFuseThreads, smem_bytes<64, 32, 1>(), s>>>(m); break;
     case 1: k_fuse_own_multi<64, 16><<<grid, kFuseThreads, smem_bytes<64, 16, 1>(), s>>>(m); break;
     case 2: k_fuse_own_multi<32, 32><<<grid, kFuseThreads, smem_bytes<32, 32, 1>(), s>>>(m); break;
     case 3: k_fuse_own_multi<128, 16><<<grid, kFuseThreads, smem_bytes<128, 16, 1>(), s>>>(m); break;
+    case 4: k_fuse_own_multi<32, 16><<<grid, kFuseThreads, smem_bytes<32, 16, 1>(), s>>>(m); break;
+    case 5: k_fuse_own_multi<128, 32><<<grid, kFuseThreads, smem_bytes<128, 32, 1>(), s>>>(m); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1859,6 +1894,8 @@ cudaError_t launch_fuse_band_multi(const MultiParams &m, bool half, int shape, i
     case 1: band_multi_by_half<64, 16>(m, half, grid, s); break;
     case 2: band_multi_by_half<32, 32>(m, half, grid, s); break;
     case 3: band_multi_by_half<128, 16>(m, half, grid, s); break;
+    case 4: band_multi_by_half<32, 16>(m, half, grid, s); break;
+    case 5: band_multi_by_half<128, 32>(m, half, grid, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -1870,24 +1907,29 @@ int fuse_band_multi_blocks_per_sm(bool half, int shape) {
     case 1: return band_multi_per_sm<64, 16>(half);
     case 2: return band_multi_per_sm<32, 32>(half);
     case 3: return band_multi_per_sm<128, 16>(half);
+    case 4: return band_multi_per_sm<32, 16>(half);
+    case 5: return band_multi_per_sm<128, 32>(half);
     default: return 0;
   }
 }
 
-int fuse_own_multi_blocks_per_sm(int shape) {
+int fuse_own_multi_blocks_per_sm(int shape, size_t mixed_smem) {
   switch (shape) {
-    case -1: return per_sm(k_fuse_own_multi_mixed, kMixOwnSmem);
+    case -1: return per_sm(k_fuse_own_multi_mixed, mixed_smem ? mixed_smem : kMixOwnSmem);
     case 0: return per_sm(k_fuse_own_multi<64, 32>, smem_bytes<64, 32, 1>());
     case 1: return per_sm(k_fuse_own_multi<64, 16>, smem_bytes<64, 16, 1>());
     case 2: return per_sm(k_fuse_own_multi<32, 32>, smem_bytes<32, 32, 1>());
     case 3: return per_sm(k_fuse_own_multi<128, 16>, smem_bytes<128, 16, 1>());
+    case 4: return per_sm(k_fuse_own_multi<32, 16>, smem_bytes<32, 16, 1>());
+    case 5: return per_sm(k_fuse_own_multi<128, 32>, smem_bytes<128, 32, 1>());
     default: return 0;
   }
 }
 
-int fuse_multi_blocks_per_sm(bool half, int shape) {
+int fuse_multi_blocks_per_sm(bool half, int shape, size_t mixed_smem) {
+  const size_t mix = mixed_smem ? mixed_smem : kMixSmem;
   switch (shape) {
-    case -1: return half ? per_sm(k_fuse_multi_mixed<true>, kMixSmem) : per_sm(k_fuse_multi_mixed<false>, kMixSmem);
+    case -1: return half ? per_sm(k_fuse_multi_mixed<true>, mix) : per_sm(k_fuse_multi_mixed<false>, mix);
     case 0:
       return half ? per_sm(k_fuse_multi<true, 64, 32>, smem_bytes<64, 32, 2>())
                   : per_sm(k_fuse_multi<false, 64, 32>, smem_bytes<64, 32, 2>());
@@ -1900,6 +1942,12 @@ int fuse_multi_blocks_per_sm(bool half, int shape) {
     case 3:
       return half ? per_sm(k_fuse_multi<true, 128, 16>, smem_bytes<128, 16, 2>())
                   : per_sm(k_fuse_multi<false, 128, 16>, smem_bytes<128, 16, 2>());
+    case 4:
+      return half ? per_sm(k_fuse_multi<true, 32, 16>, smem_bytes<32, 16, 2>())
+                  : per_sm(k_fuse_multi<false, 32, 16>, smem_bytes<32, 16, 2>());
+    case 5:
+      return half ? per_sm(k_fuse_multi<true, 128, 32>, smem_bytes<128, 32, 2>())
+                  : per_sm(k_fuse_multi<false, 128, 32>, smem_bytes<128, 32, 2>());
     default: return 0;
   }
 }

@@ -19,13 +19,14 @@ constexpr int kTileW = 64;            // band pre-warp piece: 64 x 32 panorama p
 constexpr int kTileH = 32;
 constexpr int kFuseThreads = 256;
 // Fuse tile shapes (panorama pixels) the autotuner chooses from; shape 0 is
-// the default. Width is a multiple of 32 (a warp spans 32 columns), and
-// width x height is a multiple of the 256 threads of a block.
+// the default. Width is a multiple of 32 (a warp spans 32 columns), height a
+// multiple of 16, and width x height a multiple of the 256 threads of a
+// block: 2 (32 x 16) to 16 (128 x 32) pixels per thread.
 struct TileShape {
   int w, h;
 };
-constexpr int kNumTileShapes = 4;
-constexpr TileShape kTileShapes[kNumTileShapes] = {{64, 32}, {64, 16}, {32, 32}, {128, 16}};
+constexpr int kNumTileShapes = 6;
+constexpr TileShape kTileShapes[kNumTileShapes] = {{64, 32}, {64, 16}, {32, 32}, {128, 16}, {32, 16}, {128, 32}};
 constexpr int kStatsThreads = 256;
 constexpr int kEstimateThreads = 256;
 constexpr double kCondLimit = 1e12;
@@ -303,10 +304,16 @@ cudaError_t launch_fuse(const FuseParams &p, int shape, cudaStream_t s);
 cudaError_t launch_prewarp_multi(const MultiParams &m, bool half, cudaStream_t s);
 // The persistent multi-rig fuse kernels: shape >= 0 when every rig uses that
 // tile shape, -1 to run every item with its MultiItem::shape.
-cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s);
-int fuse_multi_blocks_per_sm(bool half, int shape);
-cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s);
-int fuse_own_multi_blocks_per_sm(int shape);
+// mixed_smem: for shape -1, the dynamic shared memory of the mixed-shape
+// kernels (fuse_mixed_smem over the batch's shapes; 0 = enough for any shape).
+cudaError_t launch_fuse_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s,
+                              size_t mixed_smem = 0);
+int fuse_multi_blocks_per_sm(bool half, int shape, size_t mixed_smem = 0);
+cudaError_t launch_fuse_own_multi(const MultiParams &m, int shape, int grid, cudaStream_t s, size_t mixed_smem = 0);
+int fuse_own_multi_blocks_per_sm(int shape, size_t mixed_smem = 0);
+// Shared memory a mixed-shape fuse kernel needs for tiles of the given shapes
+// (windows = 2: band and partly covered pieces; 1: fully covered own tiles).
+size_t fuse_mixed_smem(const int *shapes, int n, int windows);
 cudaError_t launch_fuse_band_multi(const MultiParams &m, bool half, int shape, int grid, cudaStream_t s);
 int fuse_band_multi_blocks_per_sm(bool half, int shape);
 cudaError_t fuse_setup_attributes(int max_halo);

@@ -493,9 +493,9 @@ class Mlp:
 # --------------------------------------------------------------------------- #
 # Tile shapes, autotuner, batched rigs
 # --------------------------------------------------------------------------- #
-STITCH_TILE_SHAPES = 4
+STITCH_TILE_SHAPES = 6
 STITCH_BATCH_MAX_RIGS = 16
-TILE_SHAPES = ((64, 32), (64, 16), (32, 32), (128, 16))
+TILE_SHAPES = ((64, 32), (64, 16), (32, 32), (128, 16), (32, 16), (128, 32))
 
 
 def stitch_autotune(ctx, frames, flows_ij, flows_ji, pano, reps: int = 5):
