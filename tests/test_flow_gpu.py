@@ -74,6 +74,16 @@ def test_flow_argument_errors():
     ensure_built()
     pr = Pair("2x640x360", seed=0)
     frames, fij, fji = pr.inputs(0)
+    with pytest.raises(S.StitchError) as ei:          # no flow estimated yet
+        S.stitch_get_flow_luma(pr.st.ctx, 0, 0, 0)
+    assert ei.value.code == S.STITCH_EINVAL
+    S.stitch_estimate_flow(pr.st.ctx, frames, fij, fji)
+    for pair, side, level in ((1, 0, 0), (0, 2, 0), (0, 0, 3), (-1, 0, 0)):
+        with pytest.raises(S.StitchError):
+            S.stitch_get_flow_luma(pr.st.ctx, pair, side, level)
+    y2 = S.stitch_get_flow_luma(pr.st.ctx, 0, 1, 2)
+    x0, x1, y0, y1 = pr.st.bands[0].tolist()
+    assert y2.shape == ((y1 - y0 + 3) // 4, (x1 - x0 + 3) // 4)
     with pytest.raises(S.StitchError):
         S.stitch_estimate_flow(pr.st.ctx, frames, [0], fji)
     bad = torch.empty(fij[0].numel() * 4 + 16, dtype=torch.uint8, device="cuda")
