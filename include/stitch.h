@@ -512,8 +512,9 @@ int stitch_get_learned(stitch_ctx *ctx, double *M_hat, double *resid, int *used)
  * stitch_autotune times the fuse of one frame (after the band pre-warp of
  * that frame) with every shape that fits the rig (a tile may touch at most
  * one blend band), `reps` launches each, keeps the fastest in the context
- * (shape 0 unless another is more than 5 % faster: alone the shapes time within
- * a few per cent, and shape 0 overlaps best with the other stages) and
+ * (shape 0 unless another is more than 5 % faster: the fuse timed alone is
+ * only a proxy for the overlapped sequence of frames, so small differences
+ * are not trusted) and
  * records it: for the rest of the process, and in the file named by the
  * environment variable STITCH_TUNE_CACHE when set, keyed by the GPU model,
  * the rig geometry and STITCH_FP16_INTERMEDIATE. stitch_init picks up a
